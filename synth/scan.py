@@ -1,0 +1,225 @@
+"""Seeded synthetic scans, noise bands, skies and timelines.
+
+Shapes and statistics follow the paper's ground-based simulations (Sect. 5):
+a constant-elevation back-and-forth raster over a flat patch, a half-wave
+plate angle per sample, a Gaussian I/Q/U sky, and noise with a 1/f spectrum
+P(f) = sigma^2 (1 + (f_knee/f)^alpha) that is stationary within each
+(detector, interval) block.  The inverse-noise weight handed to the solver is
+a symmetric banded Toeplitz matrix per block; its band is built here and
+passed to both sides as data, so the oracle and the CUDA path consume the
+identical coefficients.
+
+Nothing here applies the pointing transpose, the band to a timeline, or any
+preconditioner: those are the method and live on each side separately.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FS_HZ = 100.0          # sampling rate of every configured workload
+SCAN_SPEED_PX = 0.14   # raster speed in pixels per sample (0.4 deg/s, ~1.7' pixels, 100 Hz)
+
+
+@dataclass
+class Scan:
+    """Pointing and noise model of one scan (one map-making problem).
+
+    Samples are stored detector-major: detector ``d`` owns samples
+    ``[d*n_t, (d+1)*n_t)``.  Each detector timeline is cut into ``n_int`` equal
+    stationary intervals; a block is one (detector, interval) pair and
+    ``block_off`` holds the block boundaries.  ``band[block_band[b]]`` holds
+    the Toeplitz coefficients c_0..c_lambda of block ``b``.
+    """
+    nx: int
+    ny: int
+    n_det: int
+    n_t: int
+    n_int: int
+    half_bw: int
+    pix: np.ndarray          # int32 [N]; -1 marks a flagged sample
+    psi: np.ndarray          # float32 [N]; HWP angle in radians, [0, pi)
+    block_off: np.ndarray    # int64 [n_blocks + 1]
+    block_band: np.ndarray   # int32 [n_blocks]
+    band: np.ndarray         # float64 [n_bands, half_bw + 1]
+    f_knee: np.ndarray       # float64 [n_det]
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_pix(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.pix.shape[0])
+
+    @property
+    def n_blocks(self) -> int:
+        return int(self.block_off.shape[0] - 1)
+
+    @property
+    def n_bands(self) -> int:
+        return int(self.band.shape[0])
+
+
+def _next_pow2(n: int) -> int:
+    p = 1
+    while p < n:
+        p *= 2
+    return p
+
+
+def toeplitz_band(half_bw: int, f_knee: float, alpha: float = 1.0,
+                  sigma: float = 1.0, fs: float = FS_HZ) -> np.ndarray:
+    """Coefficients c_0..c_lambda of a banded inverse-noise Toeplitz matrix.
+
+    c_k is the inverse DFT of 1/P(f) on an L-point grid (L the power of two
+    at least 8*lambda, at least 16), with the f = 0 bin set to 1/P(f_1), cut
+    to |k| <= lambda.  The symbol S(w) = c_0 + 2 sum_k c_k cos(k w) of the cut
+    band is then checked on a grid of 64*lambda points; if it is not positive
+    c_0 is raised until it is, so every finite section of the matrix is SPD.
+    """
+    L = max(16, _next_pow2(8 * max(half_bw, 1)))
+    f = np.fft.rfftfreq(L, 1.0 / fs)
+    fpos = np.where(f > 0, f, f[1])
+    P = sigma ** 2 * (1.0 + (f_knee / fpos) ** alpha) if f_knee > 0 else np.full_like(f, sigma ** 2)
+    c = np.fft.irfft(1.0 / P, n=L)
+    band = np.array(c[:half_bw + 1], dtype=np.float64)
+    if half_bw > 0:
+        M = _next_pow2(64 * half_bw)
+        h = np.zeros(M)
+        h[:half_bw + 1] = band
+        h[M - half_bw:] = band[1:][::-1]
+        S = np.fft.rfft(h).real
+        smin = float(S.min())
+        if smin <= 0.0:
+            band[0] += -smin + 1e-6 * band[0]
+    return band
+
+
+def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
+              f_knee=1.0, alpha: float = 1.0, sigma: float = 1.0, seed: int = 0,
+              speed: float = SCAN_SPEED_PX, flag_frac: float = 0.0,
+              fs: float = FS_HZ) -> Scan:
+    """Back-and-forth raster scan of an nx x ny patch by ``n_det`` detectors.
+
+    Azimuth: a triangle wave over [0, nx) at ``speed`` pixels per sample with
+    a random phase per detector.  Elevation: a slow drift that crosses the
+    patch once per detector timeline, with detector offsets spread over a
+    quarter of the patch height.  HWP angle psi ~ U[0, pi) i.i.d. per sample.
+    ``f_knee`` is a scalar or a (lo, hi) range drawn uniformly per detector.
+    A fraction ``flag_frac`` of samples is flagged (pixel -1).
+    """
+    if n_t % n_int != 0:
+        raise ValueError("n_t must be a multiple of n_int")
+    rng = np.random.default_rng(seed)
+    N = n_det * n_t
+    pix = np.empty(N, dtype=np.int32)
+    t = np.arange(n_t, dtype=np.float64)
+    x0 = rng.uniform(0.0, 2.0 * nx, size=n_det)
+    y0 = rng.uniform(0.0, ny)
+    for d in range(n_det):
+        pos = np.mod(x0[d] + speed * t, 2.0 * nx)
+        x = np.where(pos < nx, pos, 2.0 * nx - pos)
+        ix = np.clip(np.floor(x).astype(np.int64), 0, nx - 1)
+        oy = d * (ny / 4.0) / n_det
+        y = np.mod(y0 + oy + t * (ny / n_t), ny)
+        iy = np.clip(np.floor(y).astype(np.int64), 0, ny - 1)
+        pix[d * n_t:(d + 1) * n_t] = (iy * nx + ix).astype(np.int32)
+    psi = (rng.random(N) * np.pi).astype(np.float32)
+    psi = np.minimum(psi, np.float32(np.nextafter(np.float32(np.pi), np.float32(0))))
+    if flag_frac > 0:
+        pix[rng.random(N) < flag_frac] = -1
+    if np.ndim(f_knee) == 0:
+        fk = np.full(n_det, float(f_knee))
+    else:
+        lo, hi = f_knee
+        fk = rng.uniform(lo, hi, size=n_det)
+    blen = n_t // n_int
+    block_off = np.arange(n_det * n_int + 1, dtype=np.int64) * blen
+    block_band = np.repeat(np.arange(n_det, dtype=np.int32), n_int)
+    band = np.stack([toeplitz_band(half_bw, float(fk[d]), alpha, sigma, fs) for d in range(n_det)])
+    return Scan(nx=nx, ny=ny, n_det=n_det, n_t=n_t, n_int=n_int, half_bw=half_bw,
+                pix=pix, psi=psi, block_off=block_off, block_band=block_band,
+                band=band, f_knee=fk, seed=seed,
+                meta=dict(alpha=alpha, sigma=sigma, fs=fs, speed=speed, flag_frac=flag_frac))
+
+
+def make_sky(n_pix: int, seed: int = 0, sigma_i: float = 1.0, sigma_qu: float = 0.1) -> np.ndarray:
+    """Gaussian sky [n_pix, 3]: I ~ N(0, sigma_i^2), Q, U ~ N(0, sigma_qu^2)."""
+    rng = np.random.default_rng(seed + 7919)
+    s = rng.standard_normal((n_pix, 3))
+    s[:, 0] *= sigma_i
+    s[:, 1:] *= sigma_qu
+    return s
+
+
+def make_noise(scan: Scan, seed: int = 0) -> np.ndarray:
+    """1/f noise per stationary block, shaped in Fourier space (float64 [N]).
+
+    For each block, white N(0, 1) samples are multiplied in the rFFT domain
+    by sqrt(1 + (f_knee/f)^alpha) (the f = 0 bin takes the f_1 value) and
+    scaled by sigma.  Blocks are independent.
+    """
+    rng = np.random.default_rng(seed + 104729)
+    alpha = scan.meta.get("alpha", 1.0)
+    sigma = scan.meta.get("sigma", 1.0)
+    fs = scan.meta.get("fs", FS_HZ)
+    n = np.empty(scan.n_samples, dtype=np.float64)
+    blen = scan.n_t // scan.n_int
+    f = np.fft.rfftfreq(blen, 1.0 / fs)
+    fpos = np.where(f > 0, f, f[1] if f.shape[0] > 1 else 1.0)
+    for d in range(scan.n_det):
+        fk = float(scan.f_knee[d])
+        shape = np.sqrt(1.0 + (fk / fpos) ** alpha) if fk > 0 else np.ones_like(f)
+        w = rng.standard_normal((scan.n_int, blen))
+        seg = np.fft.irfft(np.fft.rfft(w, axis=1) * shape, n=blen, axis=1) * sigma
+        n[d * scan.n_t:(d + 1) * scan.n_t] = seg.reshape(-1)
+    return n
+
+
+def make_tod(scan: Scan, sky: np.ndarray | None, noise: np.ndarray | None) -> np.ndarray:
+    """Timeline d_t = I_p + Q_p cos 2psi_t + U_p sin 2psi_t + n_t (float64 [N]).
+
+    This is the data model the paper simulates (Sect. 2, Eq. datamodel); it
+    only synthesises an input.  Flagged samples carry noise only.
+    """
+    d = np.zeros(scan.n_samples, dtype=np.float64)
+    if sky is not None:
+        ok = scan.pix >= 0
+        p = scan.pix[ok]
+        ang = 2.0 * scan.psi[ok].astype(np.float64)
+        d[ok] = sky[p, 0] + sky[p, 1] * np.cos(ang) + sky[p, 2] * np.sin(ang)
+    if noise is not None:
+        d += noise
+    return d
+
+
+def mc_lengths(n_rhs: int, lo: int, hi: int, seed: int = 0) -> np.ndarray:
+    """Per right-hand-side timeline lengths (samples per detector), U[lo, hi]."""
+    rng = np.random.default_rng(seed + 3)
+    return rng.integers(lo, hi + 1, size=n_rhs).astype(np.int64)
+
+
+# Workload shapes.  "c1".."c5" follow the configured map-making problems;
+# "tiny"/"small" are the sizes the oracle runs in well under a second.
+CONFIGS = {
+    "tiny":  dict(nx=4, ny=4, n_det=2, n_t=512, n_int=2, half_bw=8, f_knee=1.0),
+    "small": dict(nx=8, ny=8, n_det=4, n_t=4096, n_int=4, half_bw=64, f_knee=1.0),
+    # Plain M_BD PCG: 32x32 patch, 8 det x 32768 samples, lambda 512, 8 intervals.
+    "c1":    dict(nx=32, ny=32, n_det=8, n_t=32768, n_int=8, half_bw=512, f_knee=1.0),
+    # Two-level vs M_BD: 256x256 patch, 128 det x 2^20, f_knee U[0.1, 2], lambda 2048, 64 intervals.
+    "c2":    dict(nx=256, ny=256, n_det=128, n_t=1 << 20, n_int=64, half_bw=2048, f_knee=(0.1, 2.0)),
+    # Batched Monte Carlo master scan: c1 geometry, 2^20 samples per detector, 4096-sample intervals.
+    "c3":    dict(nx=32, ny=32, n_det=8, n_t=1 << 20, n_int=256, half_bw=512, f_knee=1.0),
+    # Mixed precision at scale: 512x512 patch, 1024 det x 2^20 (lambda and intervals as c2).
+    "c4":    dict(nx=512, ny=512, n_det=1024, n_t=1 << 20, n_int=64, half_bw=2048, f_knee=(0.1, 2.0)),
+}
+
+
+def scan_from_config(name: str, seed: int = 0, **overrides) -> Scan:
+    cfg = dict(CONFIGS[name])
+    cfg.update(overrides)
+    return make_scan(seed=seed, **cfg)

@@ -1,0 +1,224 @@
+/*
+ * mapmaker.h -- C ABI of the GB300 map-making library (libmapmaker.so).
+ *
+ * The library solves the map-making system of Puglisi et al., "Iterative
+ * map-making with two-level preconditioning for polarized CMB data sets":
+ *
+ *   A x = b,   A = P^T W P,   b = P^T W d                 (Sect. 3, Eq. linearsystem)
+ *
+ * where P is the pointing matrix with rows (1, cos 2psi_t, sin 2psi_t) on the
+ * pixel seen by sample t (Sect. 2, Eq. datamodel) and W = N^-1 is the
+ * inverse-noise weight, here a symmetric banded Toeplitz matrix for each
+ * stationary (detector, interval) block (any SPD weight gives an unbiased
+ * estimate, Sect. 2, Eq. estimator).  PCG (Sect. 3, Eq. pcg) runs with the
+ * block-diagonal preconditioner M_BD (Sect. 3.1, Eq. mbd) or the two-level
+ * preconditioner M_2l = M_BD (1 - A Z E^-1 Z^T) + Z E^-1 Z^T, E = Z^T A Z
+ * (Sect. 3.2, Eq. m2l), whose deflation basis Z holds Ritz vectors of
+ * M_BD A from the Arnoldi process (Sect. 6; Appendix A, Algorithm arnoldi).
+ *
+ * Conventions shared by every call
+ *  - Status codes only; no C++ exception crosses this boundary.  After a
+ *    failure mm_last_error() returns a message owned by the context.
+ *  - Maps at the boundary are float64 arrays [nrhs][n_pix][3] holding
+ *    (I, Q, U) per pixel, whatever the precision of the context.
+ *  - Timelines (TOD) at the boundary are [nrhs][n_samples] of float64 for an
+ *    MM_FP64 context and of float32 for an MM_FP32_MIXED context.
+ *  - Arguments tagged "mem" take MM_HOST (pageable or pinned host memory) or
+ *    MM_DEVICE (device memory on the context's device).  The caller keeps
+ *    ownership of every pointer it passes; the library copies what it keeps.
+ *  - Work is ordered on the context's CUDA stream.  Calls return after the
+ *    results they write to host memory (maps, info, counts) are complete;
+ *    device outputs are complete once the stream reaches the call's end.
+ *  - A context is not thread safe: one host thread at a time per context.
+ */
+#ifndef MAPMAKER_H
+#define MAPMAKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_ARG = 1,            /* invalid argument (message says which)          */
+    MM_ERR_OOM = 2,            /* device allocation failed or budget exceeded     */
+    MM_ERR_CUDA = 3,           /* a CUDA runtime call failed                      */
+    MM_ERR_STATE = 4,          /* call out of order (e.g. solve before setup)     */
+    MM_ERR_NOT_CONVERGED = 5,  /* PCG hit max_iter; the map is still written     */
+    MM_ERR_BREAKDOWN = 6,      /* p^T A p <= 0 or a NaN appeared                  */
+    MM_ERR_SINGULAR = 7,       /* coarse operator E is not SPD                    */
+    MM_ERR_TIMEOUT = 8         /* a bounded device wait gave up                   */
+} mm_status;
+
+typedef enum {
+    MM_FP64 = 0,        /* gather, filter and scatter in float64                 */
+    MM_FP32_MIXED = 1   /* gather/filter/scatter in float32 with float32
+                           accumulation; PCG vectors, inner products, residual
+                           norms, Arnoldi orthogonalisation, E and M_BD in
+                           float64; the solve refines against a float64 A x   */
+} mm_precision;
+
+typedef enum { MM_PRECOND_BD = 0, MM_PRECOND_2L = 1 } mm_precond;
+
+enum { MM_HOST = 0, MM_DEVICE = 1 };
+
+typedef struct {
+    int32_t iters;          /* products with A inside PCG                         */
+    int32_t status;         /* mm_status of this right-hand side                  */
+    double rel_res;         /* final recurrence residual ||r_k|| / ||b||          */
+    double true_rel_res;    /* ||b - A x|| / ||b|| with a float64 product at exit  */
+    double t_solve_ms;      /* device time of the whole solve call                */
+    int32_t refinements;    /* outer float64 residual refinements (mixed mode)    */
+    int32_t pad;
+} mm_solve_info;
+
+/* Create a context on CUDA device `device`, ordered on `cuda_stream`
+ * (a cudaStream_t; NULL means the legacy default stream).  *out receives the
+ * context, which owns all device memory it allocates.  Errors: MM_ERR_ARG,
+ * MM_ERR_CUDA. */
+mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision prec);
+
+/* Release the context and every device buffer it owns.  NULL is accepted. */
+mm_status mm_destroy(mm_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  The pointer
+ * stays valid until the next call on the context. */
+const char* mm_last_error(const mm_ctx* ctx);
+
+/* Pointing P and weight W (Sect. 2, Eq. datamodel and Eq. estimator).
+ *  n_samples        timeline length N_t.
+ *  n_det            the timeline is n_det equal detector timelines laid end to
+ *                   end (n_samples % n_det == 0); per-RHS lengths in mm_solve
+ *                   count samples per detector.  Use 1 for a single timeline.
+ *  n_pix            pixels; unknowns are (I, Q, U) per pixel.
+ *  pix [n_samples]  pixel of each sample, -1 marks a flagged sample (zero row
+ *                   of P); values must lie in [-1, n_pix).
+ *  psi [n_samples]  HWP angle in radians; the row of P is (1, cos 2psi, sin 2psi).
+ *  n_blocks, block_off [n_blocks+1]  stationary blocks [off_b, off_{b+1}),
+ *                   contiguous, increasing, block_off[0] = 0,
+ *                   block_off[n_blocks] = n_samples, none straddling two
+ *                   detector timelines.
+ *  block_band [n_blocks]  band index of each block, in [0, n_bands).
+ *  half_bw          lambda >= 0; band [n_bands][half_bw+1] holds c_0..c_lambda
+ *                   of each symmetric banded Toeplitz W block (host float64).
+ *                   Within a block W_{tt'} = c_|t-t'| for |t-t'| <= lambda and
+ *                   the band is cut at the block edges.  The caller guarantees
+ *                   W is SPD.
+ *  mem              where pix and psi live; block_off, block_band and band are
+ *                   always host arrays.
+ * Replaces any earlier pointing and drops M_BD and the coarse space.
+ * Errors: MM_ERR_ARG (sizes, ranges), MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32_t n_pix,
+                            const int32_t* pix, const float* psi,
+                            int32_t n_blocks, const int64_t* block_off, const int32_t* block_band,
+                            int32_t n_bands, int32_t half_bw, const double* band, int mem);
+
+/* Block-diagonal preconditioner M_BD^-1 = P^T diag(W) P (Sect. 3.1, Eq. mbd):
+ * one 3x3 block per pixel, summed and inverted in float64.  A pixel with fewer
+ * than 3 hits or with lambda_min/lambda_max of its block below rcond_min is
+ * dropped: its samples are flagged (pixel -1) in the context's copy of P, so
+ * A and every later product exclude it, and its map entries solve to 0.
+ * *n_dropped_out (may be NULL) receives the number of dropped pixels.
+ * Errors: MM_ERR_STATE (no pointing), MM_ERR_ARG, MM_ERR_CUDA. */
+mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out);
+
+/* b = P^T W d (Sect. 3, Eq. linearsystem) for nrhs timelines, computed in
+ * float64 whatever the context precision.  tod [nrhs][n_samples] (element
+ * type per context precision), b_out [nrhs][n_pix][3] float64, both in `mem`.
+ * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int mem);
+
+/* y = A x = P^T W P x (Sect. 3, Eq. linearsystem), matrix-free, in the
+ * context precision: gather, banded-Toeplitz filter and scatter-add fused in
+ * one pass per sample segment.  x, y [nrhs][n_pix][3] float64 in `mem`.
+ * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int mem);
+
+/* y = M x for M = M_BD (Sect. 3.1, Eq. mbd) or M_2l (Sect. 3.2, Eq. m2l).
+ * x, y [nrhs][n_pix][3] float64 in `mem`.  Needs mm_build_bd, and for M_2l a
+ * coarse space.  Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_CUDA. */
+mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, double* y,
+                           int32_t nrhs, int mem);
+
+/* Coarse space for M_2l (Sect. 6; Appendix A).  Runs Arnoldi on
+ * B = M_BD A from r_0 = M_BD b (b [n_pix][3] float64 in `mem`; NULL uses the
+ * first right-hand side of the last mm_rhs/mm_solve call), with two classical
+ * Gram-Schmidt passes per step in float64, stopping when h_{j+1,j} <= eps_arn
+ * or after m_max steps.  Ritz pairs of H_m (Eq. ritz) are sorted by real part;
+ * the k smallest (or, if k <= 0, all with real part below eps_lambda) form Z,
+ * a complex pair adding its real and imaginary parts.  Z is orthonormalised,
+ * AZ = A Z and E = Z^T A Z are formed, and E is factored (float64).
+ * *k_out (may be NULL) receives dim Z.  Needs mm_build_bd.
+ * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_SINGULAR, MM_ERR_CUDA. */
+mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, double eps_arn,
+                          int32_t k, double eps_lambda, int32_t* k_out, int mem);
+
+/* Install a deflation basis Z [k][n_pix][3] float64 (`mem`) instead of
+ * building one: the paper's "simplified" reuse of a basis computed on another
+ * data subset (Sect. 7).  AZ and E = Z^T A Z are formed with this context's A.
+ * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_SINGULAR, MM_ERR_CUDA. */
+mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem);
+
+/* Copy out the current basis Z [k][n_pix][3] (host, may be NULL), the Ritz
+ * values kept [k] (host, may be NULL) and k.  Errors: MM_ERR_STATE. */
+mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k_out);
+
+/* Solve A x = b for nrhs timelines with PCG (Sect. 3, Eq. pcg), x_0 = 0,
+ * stopping when ||r_k|| / ||b|| <= tol (recurrence residual) or after max_iter
+ * products with A.  In MM_FP32_MIXED the float32 operator drives PCG and
+ * float64 residuals b - A x refine the solution until the float64 residual
+ * meets tol.
+ *  tod [nrhs][n_samples] in `mem`; map_out [nrhs][n_pix][3] float64 in `mem`.
+ *  rhs_len_or_null [nrhs] (host): samples per detector used by each
+ *      right-hand side (its timelines are the first rhs_len[i] samples of each
+ *      detector, as in a Monte Carlo batch of uneven lengths); each then has
+ *      its own A_i and M_BD,i, while a coarse space, if any, is shared.  NULL
+ *      uses whole timelines.
+ *  info [nrhs] (host, may be NULL) receives per-RHS results.
+ * Returns MM_OK when every right-hand side converged, MM_ERR_NOT_CONVERGED
+ * when one did not (maps are written either way), MM_ERR_BREAKDOWN on a
+ * non-positive p^T A p or a NaN.  Other errors: MM_ERR_STATE, MM_ERR_ARG,
+ * MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
+                   const int64_t* rhs_len_or_null, mm_precond precond, double tol,
+                   int32_t max_iter, mm_solve_info* info, int mem);
+
+/* Tuning knobs, by name.  "filter": 0 auto, 1 direct band, 2 FFT
+ * overlap-save; "fft_log2": FFT length 2^v for the FFT filter (0 = auto);
+ * "direct_tile": outputs per CTA of the direct filter; "check_every": PCG
+ * iterations between host convergence checks; "graphs": 1 to replay captured
+ * CUDA graphs of PCG iterations.  Errors: MM_ERR_ARG for an unknown name or
+ * value. */
+mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
+
+/* Read back a tuning knob or statistic ("filter", "fft_log2", "direct_tile",
+ * "check_every", "graphs", "last_apply_ms", "device_bytes").  Errors: MM_ERR_ARG. */
+mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value);
+
+/* Stepwise solve for schedulers that interleave many solves (continuous
+ * batching).  mm_solve_begin sets up the same solve as mm_solve and runs no
+ * iteration; mm_solve_step runs up to n_iter PCG iterations (enqueued on the
+ * context stream) and sets *done to 1 once every right-hand side has
+ * converged or reached max_iter; mm_solve_end writes maps and info exactly
+ * like mm_solve and returns its status.  Steps of different contexts on
+ * different streams overlap on the device. */
+mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64_t* rhs_len_or_null,
+                         mm_precond precond, double tol, int32_t max_iter, int mem);
+mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done);
+mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem);
+
+/* Device bytes a context needs for a problem of this shape (pointing, maps,
+ * PCG state, Arnoldi basis of m_max vectors and k coarse vectors), for
+ * admission control.  Pure host arithmetic. */
+int64_t mm_estimate_bytes(int64_t n_samples, int32_t n_pix, int32_t n_bands, int32_t half_bw,
+                          int32_t nrhs, int32_t m_max, int32_t k, mm_precision prec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAPMAKER_H */

@@ -1,0 +1,1353 @@
+// C ABI entry points (include/mapmaker.h): context, pointing set-up, M_BD,
+// coarse space, A x, preconditioners and the PCG driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mapmaker.h"
+#include "common.cuh"
+
+namespace mm {
+
+// ---------------- device buffers ----------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct Plan {
+    int variant = 0;   // 1 direct, 2 fft
+    int L = 0, logL = 0, V = 0;
+    int f64 = 0;
+    int nrhs = 0;
+    std::vector<int64_t> lens;
+    DevBuf segs;
+    int n_work = 0;
+};
+
+struct FftTables {
+    int L = 0;
+    DevBuf tw, H;
+};
+
+enum Phase { PH_IDLE = 0, PH_INNER = 1, PH_DONE = 2 };
+
+}  // namespace mm
+
+using namespace mm;
+
+struct mm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mm_precision prec = MM_FP64;
+    std::string err;
+
+    // options
+    int opt_filter = 0, opt_fft_log2 = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
+    double last_apply_ms = 0.0;
+
+    // pointing
+    bool have_pointing = false;
+    int64_t n_samples = 0, n_t = 0;
+    int n_det = 1, n_pix = 0, n_blocks = 0, n_bands = 0, lam = 0;
+    std::vector<int64_t> block_off;
+    std::vector<int32_t> block_band;
+    std::vector<double> band;
+    DevBuf d_pix, d_psi, d_cs64, d_block_off, d_block_band, d_band64, d_band32;
+    FftTables fft32, fft64;
+    std::vector<std::unique_ptr<Plan>> plans;
+
+    // M_BD
+    bool have_bd = false;
+    DevBuf d_good, d_bd, d_sums, d_dropped;
+    DevBuf d_bd_rhs;   // per right-hand side, [nrhs][n_pix][6]
+
+    // coarse space
+    int k = 0;
+    DevBuf d_Z, d_AZ, d_Einv, d_W, d_h;
+    std::vector<double> ritz;
+
+    // workspace
+    DevBuf w_a, w_b, w_src, w_q, w_partial, w_counter, w_norms, d_lastb;
+    bool have_lastb = false;
+    int grid_x = 1;
+
+    // solve state
+    int phase = PH_IDLE;
+    int nrhs = 0;
+    mm_precond precond = MM_PRECOND_BD;
+    double tol = 1e-8;
+    int max_iter = 0;
+    bool use_lens = false;
+    std::vector<int64_t> lens;
+    DevBuf s_tod, s_b, s_x, s_r, s_z, s_p, s_src, s_q, s_st, s_hist, s_u, s_xtot, s_rtrue, s_q64, s_mask;
+    Plan* plan_op = nullptr;
+    Plan* plan_64 = nullptr;
+    std::vector<RhsState> h_st;
+    std::vector<int32_t> tot_iters, refinements, final_status;
+    std::vector<double> true_res, rec_res, bnorm;
+    int outer = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_iters = 0;
+};
+
+namespace {
+
+mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+#define CKL()                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                                      \
+        if (e_ != cudaSuccess) return fail(ctx, MM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        mm_status s_ = (expr);         \
+        if (s_ != MM_OK) return s_;    \
+    } while (0)
+
+bool is_f32(const mm_ctx* c) { return c->prec == MM_FP32_MIXED; }
+
+cudaError_t copy_in(void* dst, const void* src, size_t bytes, int mem, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, src, bytes, mem == MM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+}
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+int64_t max_block_len(const mm_ctx* c) {
+    int64_t m = 0;
+    for (int b = 0; b < c->n_blocks; ++b) m = std::max(m, c->block_off[b + 1] - c->block_off[b]);
+    return m;
+}
+
+// FFT length for the overlap-save filter: minimise segments per block times
+// L log L, within the shared-memory limit of the precision.
+int auto_fft_log2(const mm_ctx* c, bool f64) {
+    const int64_t nb = std::max<int64_t>(1, max_block_len(c));
+    const int maxlog = f64 ? 13 : 14;
+    int best = -1;
+    double best_cost = 1e300;
+    for (int lg = 6; lg <= maxlog; ++lg) {
+        const int L = 1 << lg;
+        const int V = L - 2 * c->lam;
+        if (V < 32) continue;
+        const int64_t segs = (nb + V - 1) / V;
+        const double cost = (double)segs * L * lg;
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = lg;
+        }
+    }
+    return best;
+}
+
+mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, int L, bool f64) {
+    if (ft.L == L) return MM_OK;
+    const int logL = ilog2(L);
+    // twiddles exp(-2 pi i e / L) in float64 on the host
+    std::vector<double> tw64(2 * (size_t)L);
+    for (int e = 0; e < L; ++e) {
+        const double ang = -2.0 * M_PI * (double)e / (double)L;
+        tw64[2 * e] = std::cos(ang);
+        tw64[2 * e + 1] = std::sin(ang);
+    }
+    // circular placement of each band: h[i] = c_i, h[L - i] = c_i
+    std::vector<double> h((size_t)ctx->n_bands * L, 0.0);
+    for (int b = 0; b < ctx->n_bands; ++b) {
+        const double* c = &ctx->band[(size_t)b * (ctx->lam + 1)];
+        double* hb = &h[(size_t)b * L];
+        hb[0] = c[0];
+        for (int i = 1; i <= ctx->lam; ++i) {
+            hb[i] = c[i];
+            hb[L - i] = c[i];
+        }
+    }
+    DevBuf d_tw64, d_h, d_H64, d_work;
+    CK(d_tw64.ensure(tw64.size() * 8));
+    CK(d_h.ensure(h.size() * 8));
+    CK(d_H64.ensure(h.size() * 8));
+    CK(d_work.ensure((size_t)ctx->n_bands * (L + (L >> 4)) * 16));
+    CK(cudaMemcpyAsync(d_tw64.p, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_h.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    launch_fft_spectrum(d_h.as<double>(), d_H64.as<double>(), d_work.as<double2>(), d_tw64.as<double2>(),
+                        ctx->n_bands, L, logL, ctx->stream);
+    CKL();
+    if (f64) {
+        CK(ft.tw.ensure(tw64.size() * 8));
+        CK(ft.H.ensure(h.size() * 8));
+        CK(cudaMemcpyAsync(ft.tw.p, d_tw64.p, tw64.size() * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.H.p, d_H64.p, h.size() * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        std::vector<double> H64(h.size());
+        CK(cudaMemcpyAsync(H64.data(), d_H64.p, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::vector<float> H32(h.size()), tw32(tw64.size());
+        for (size_t i = 0; i < h.size(); ++i) H32[i] = (float)H64[i];
+        for (size_t i = 0; i < tw64.size(); ++i) tw32[i] = (float)tw64[i];
+        CK(ft.tw.ensure(tw32.size() * 4));
+        CK(ft.H.ensure(H32.size() * 4));
+        CK(cudaMemcpyAsync(ft.tw.p, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.H.p, H32.data(), H32.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    ft.L = L;
+    return MM_OK;
+}
+
+// Segment list: for every block, chunk and right-hand side, pairs of segments
+// that share a band.
+mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
+    int variant = ctx->opt_filter;
+    int L = 0, logL = 0, V = 0;
+    if (variant == 0) variant = (ctx->lam <= 32) ? 1 : 2;
+    if (variant == 2) {
+        logL = ctx->opt_fft_log2 > 0 ? ctx->opt_fft_log2 : auto_fft_log2(ctx, f64);
+        if (f64 && logL > 13) logL = 13;
+        if (logL < 6 || (1 << logL) - 2 * ctx->lam < 32) {
+            if (ctx->opt_filter == 2) return fail(ctx, MM_ERR_ARG, "FFT length too short for the band half-width");
+            variant = 1;
+        } else {
+            L = 1 << logL;
+            V = L - 2 * ctx->lam;
+        }
+    }
+    if (variant == 1) {
+        V = std::max(32, ctx->opt_direct_tile);
+        L = 0;
+        logL = 0;
+        const size_t sm = direct_smem_bytes(V, ctx->lam, f64);
+        if (sm > 200 * 1024) return fail(ctx, MM_ERR_ARG, "direct filter tile plus halo exceeds shared memory");
+    }
+    for (auto& p : ctx->plans)
+        if (p->variant == variant && p->L == L && p->V == V && p->f64 == (int)f64 && p->nrhs == nrhs && p->lens == lens) {
+            *out = p.get();
+            return MM_OK;
+        }
+    std::vector<Seg> segs;
+    auto push = [&](const Seg& s) {
+        if (segs.size() % 2 == 1 && segs.back().band != s.band) {
+            Seg e{};
+            e.n_out = 0;
+            e.band = segs.back().band;
+            segs.push_back(e);
+        }
+        segs.push_back(s);
+    };
+    for (int b = 0; b < ctx->n_blocks; ++b) {
+        const int64_t o0 = ctx->block_off[b], o1 = ctx->block_off[b + 1];
+        const int64_t det0 = (o0 / ctx->n_t) * ctx->n_t;
+        for (int64_t c0 = o0; c0 < o1; c0 += V) {
+            for (int r = 0; r < nrhs; ++r) {
+                int64_t hi = o1;
+                if (!lens.empty()) hi = std::min(hi, det0 + lens[r]);
+                if (c0 >= hi) continue;
+                Seg s{};
+                s.out0 = c0;
+                s.lo = o0;
+                s.hi = hi;
+                s.rhs = r;
+                s.n_out = (int32_t)std::min<int64_t>(V, hi - c0);
+                s.band = ctx->block_band[b];
+                push(s);
+            }
+        }
+    }
+    if (segs.size() % 2 == 1) {
+        Seg e{};
+        e.band = segs.back().band;
+        segs.push_back(e);
+    }
+    auto p = std::make_unique<Plan>();
+    p->variant = variant;
+    p->L = L;
+    p->logL = logL;
+    p->V = V;
+    p->f64 = f64;
+    p->nrhs = nrhs;
+    p->lens = lens;
+    p->n_work = (int)(segs.size() / 2);
+    CK(p->segs.ensure(std::max<size_t>(1, segs.size()) * sizeof(Seg)));
+    if (!segs.empty())
+        CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (variant == 2) TRY(build_fft_tables(ctx, f64 ? ctx->fft64 : ctx->fft32, L, f64));
+    ctx->plans.push_back(std::move(p));
+    *out = ctx->plans.back().get();
+    return MM_OK;
+}
+
+// dst (V4<T>[nrhs][n_pix], zeroed by the caller) += P^T W (P src | d).
+mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, void* dst, const RhsState* st,
+                     int tod_is_float) {
+    FilterArgs a{};
+    a.segs = plan->segs.as<Seg>();
+    a.n_work = plan->n_work;
+    a.pix = ctx->d_pix.as<int32_t>();
+    a.psi = ctx->d_psi.as<float>();
+    a.cs64 = ctx->d_cs64.as<double2>();
+    a.src = src;
+    a.n_samples = ctx->n_samples;
+    a.dst = dst;
+    a.n_pix = ctx->n_pix;
+    a.lam = ctx->lam;
+    a.L = plan->L;
+    a.logL = plan->logL;
+    a.V = plan->V;
+    a.state = st;
+    a.tod_is_float = tod_is_float;
+    if (plan->variant == 2) {
+        FftTables& ft = plan->f64 ? ctx->fft64 : ctx->fft32;
+        a.H = ft.H.p;
+        a.tw = ft.tw.p;
+        if (plan->f64) launch_filter_fft_f64(a, from_tod, ctx->stream);
+        else launch_filter_fft_f32(a, from_tod, ctx->stream);
+    } else {
+        a.band = plan->f64 ? ctx->d_band64.p : ctx->d_band32.p;
+        if (plan->f64) launch_filter_direct_f64(a, from_tod, ctx->stream);
+        else launch_filter_direct_f32(a, from_tod, ctx->stream);
+    }
+    CKL();
+    return MM_OK;
+}
+
+mm_status ensure_work(mm_ctx* ctx, int nrhs, int kmax) {
+    const size_t nv = (size_t)ctx->n_pix * std::max(1, nrhs);
+    CK(ctx->w_a.ensure(nv * sizeof(V4<double>)));
+    CK(ctx->w_b.ensure(nv * sizeof(V4<double>)));
+    CK(ctx->w_src.ensure(nv * sizeof(V4<double>)));
+    CK(ctx->w_q.ensure(nv * sizeof(V4<double>)));
+    const size_t per = (size_t)std::max({2, kmax, 1}) * std::max(1, nrhs);
+    CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max<size_t>(per, 512) * sizeof(double)));
+    if (ctx->w_counter.bytes < (size_t)std::max(1, nrhs) * sizeof(unsigned)) {
+        CK(ctx->w_counter.ensure((size_t)std::max(1, nrhs) * sizeof(unsigned) + 64));
+        CK(cudaMemsetAsync(ctx->w_counter.p, 0, ctx->w_counter.bytes, ctx->stream));
+    }
+    CK(ctx->w_norms.ensure((size_t)std::max(1, nrhs) * sizeof(double) + 64));
+    return MM_OK;
+}
+
+// out (V4<double>) = A in (V4<double>) for nrhs vectors, operator precision
+// f64 or the context's.
+mm_status apply_A_dev(mm_ctx* ctx, bool f64, const V4<double>* in, V4<double>* out, int nrhs, const Plan* forced = nullptr) {
+    Plan* plan = nullptr;
+    if (forced) plan = const_cast<Plan*>(forced);
+    else TRY(get_plan(ctx, f64, nrhs, {}, &plan));
+    TRY(ensure_work(ctx, nrhs, ctx->k));
+    const int64_t nv = (int64_t)ctx->n_pix * nrhs;
+    if (f64) {
+        CK(cudaMemsetAsync(out, 0, nv * sizeof(V4<double>), ctx->stream));
+        TRY(run_filter(ctx, plan, false, in, out, nullptr, 0));
+    } else {
+        V4<float>* src = ctx->w_src.as<V4<float>>();
+        V4<float>* q = ctx->w_q.as<V4<float>>();
+        launch_to_f32(in, src, nv, ctx->stream);
+        CK(cudaMemsetAsync(q, 0, nv * sizeof(V4<float>), ctx->stream));
+        TRY(run_filter(ctx, plan, false, src, q, nullptr, 0));
+        launch_from_f32(q, out, nv, ctx->stream);
+        CKL();
+    }
+    return MM_OK;
+}
+
+PcgArgs pcg_args(mm_ctx* ctx) {
+    PcgArgs a{};
+    a.n_pix = ctx->n_pix;
+    a.nrhs = ctx->nrhs;
+    a.st = ctx->s_st.as<RhsState>();
+    a.x = ctx->s_x.as<V4<double>>();
+    a.r = ctx->s_r.as<V4<double>>();
+    a.z = ctx->s_z.as<V4<double>>();
+    a.p = ctx->s_p.as<V4<double>>();
+    if (is_f32(ctx)) {
+        a.q32 = ctx->s_q.as<V4<float>>();
+        a.src_f32 = 1;
+    } else {
+        a.q64 = ctx->s_q.as<V4<double>>();
+        a.src_f32 = 0;
+    }
+    a.src = ctx->s_src.p;
+    a.qacc = ctx->s_q.p;
+    a.bd = ctx->use_lens ? ctx->d_bd_rhs.as<double>() : ctx->d_bd.as<double>();
+    a.bd_per_rhs = ctx->use_lens ? 1 : 0;
+    a.k = ctx->k;
+    a.Z = ctx->d_Z.as<V4<double>>();
+    a.AZ = ctx->d_AZ.as<V4<double>>();
+    a.Einv = ctx->d_Einv.as<double>();
+    a.u = ctx->s_u.as<double>();
+    a.partial = ctx->w_partial.as<double>();
+    a.counter = ctx->w_counter.as<unsigned>();
+    a.hist = ctx->s_hist.as<double>();
+    a.hist_stride = ctx->max_iter + 1;
+    a.grid_x = ctx->grid_x;
+    return a;
+}
+
+// Preconditioner on r -> z with rz (and beta when finalize_beta).
+void precond_step(mm_ctx* ctx, const PcgArgs& a, int finalize_beta) {
+    if (ctx->precond == MM_PRECOND_2L) {
+        launch_m2l_ztr(a, a.r, ctx->stream);
+        launch_m2l_apply(a, a.r, a.z, finalize_beta, ctx->stream);
+    } else {
+        launch_precond_bd_dot(a, finalize_beta, ctx->stream);
+    }
+}
+
+mm_status pcg_iteration(mm_ctx* ctx) {
+    PcgArgs a = pcg_args(ctx);
+    launch_pcg_src(a, 0, ctx->stream);
+    TRY(run_filter(ctx, ctx->plan_op, false, ctx->s_src.p, ctx->s_q.p, a.st, 0));
+    launch_pcg_pq(a, ctx->stream);
+    const int two = ctx->precond == MM_PRECOND_2L;
+    launch_pcg_update(a, two, ctx->stream);
+    if (two) {
+        launch_m2l_ztr(a, a.r, ctx->stream);
+        launch_m2l_apply(a, a.r, a.z, 1, ctx->stream);
+    }
+    CKL();
+    return MM_OK;
+}
+
+// Start PCG on right-hand sides b (V4<double>), per-RHS tolerances and iteration budgets.
+mm_status pcg_start(mm_ctx* ctx, const V4<double>* b, const std::vector<double>& tols, const std::vector<int>& budgets) {
+    std::vector<RhsState> st(ctx->nrhs);
+    for (int i = 0; i < ctx->nrhs; ++i) {
+        st[i] = RhsState{};
+        st[i].tol = tols[i];
+        st[i].max_iter = budgets[i];
+    }
+    CK(cudaMemcpyAsync(ctx->s_st.p, st.data(), st.size() * sizeof(RhsState), cudaMemcpyHostToDevice, ctx->stream));
+    PcgArgs a = pcg_args(ctx);
+    launch_pcg_init(a, b, ctx->stream);
+    precond_step(ctx, a, 0);
+    CKL();
+    return MM_OK;
+}
+
+mm_status read_state(mm_ctx* ctx) {
+    ctx->h_st.resize(ctx->nrhs);
+    CK(cudaMemcpyAsync(ctx->h_st.data(), ctx->s_st.p, ctx->nrhs * sizeof(RhsState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+// float64 residual b - A x per right-hand side (x in s_xtot or s_x), written to
+// s_rtrue; norms to host.
+mm_status true_residual(mm_ctx* ctx, const V4<double>* x, std::vector<double>& rr) {
+    TRY(apply_A_dev(ctx, true, x, ctx->s_q64.as<V4<double>>(), ctx->nrhs, ctx->plan_64));
+    launch_residual(ctx->s_b.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), ctx->s_rtrue.as<V4<double>>(),
+                    ctx->w_norms.as<double>(), ctx->n_pix, ctx->nrhs, ctx->w_partial.as<double>(),
+                    ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+    CKL();
+    rr.resize(ctx->nrhs);
+    CK(cudaMemcpyAsync(rr.data(), ctx->w_norms.p, ctx->nrhs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& v : rr) v = std::sqrt(std::max(0.0, v));
+    return MM_OK;
+}
+
+void destroy_graph(mm_ctx* ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_iters = 0;
+}
+
+mm_status bd_for_lens(mm_ctx* ctx) {
+    // per right-hand side M_BD over its active samples; pixel selection stays the full-scan one
+    const int R = ctx->nrhs;
+    std::vector<int64_t> sorted(ctx->lens);
+    std::vector<int> order(R);
+    for (int i = 0; i < R; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->lens[a] < ctx->lens[b]; });
+    for (int i = 0; i < R; ++i) sorted[i] = ctx->lens[order[i]];
+    DevBuf d_sorted, sums, bdsorted;
+    CK(d_sorted.ensure(R * sizeof(int64_t)));
+    CK(cudaMemcpyAsync(d_sorted.p, sorted.data(), R * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(sums.ensure((size_t)R * ctx->n_pix * 7 * sizeof(double)));
+    CK(cudaMemsetAsync(sums.p, 0, sums.bytes, ctx->stream));
+    launch_bd_accumulate(ctx->d_pix.as<int32_t>(), ctx->d_psi.as<float>(), ctx->d_block_off.as<int64_t>(),
+                         ctx->d_block_band.as<int32_t>(), ctx->d_band64.as<double>(), ctx->lam + 1, ctx->n_blocks, 0,
+                         ctx->n_t, d_sorted.as<int64_t>(), R, sums.as<double>(), ctx->n_pix, ctx->stream);
+    CK(bdsorted.ensure((size_t)R * ctx->n_pix * 6 * sizeof(double)));
+    launch_bd_invert(sums.as<double>(), bdsorted.as<double>(), ctx->d_good.as<uint8_t>(), nullptr, ctx->n_pix, R, 0.0, 0,
+                     ctx->stream);
+    CKL();
+    CK(ctx->d_bd_rhs.ensure((size_t)R * ctx->n_pix * 6 * sizeof(double)));
+    const size_t per = (size_t)ctx->n_pix * 6 * sizeof(double);
+    for (int i = 0; i < R; ++i)
+        CK(cudaMemcpyAsync(ctx->d_bd_rhs.as<char>() + (size_t)order[i] * per, bdsorted.as<char>() + (size_t)i * per, per,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+// Orthonormalise the columns of X [kin][n] (kept columns only) into Y, twice (CholQR2).
+mm_status orthonormalise(mm_ctx* ctx, DevBuf& X, int kin, int* kout) {
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    int kcur = kin;
+    for (int pass = 0; pass < 2; ++pass) {
+        DevBuf dG;
+        CK(dG.ensure((size_t)kcur * kcur * sizeof(double)));
+        TRY(ensure_work(ctx, 1, std::max(kcur, ctx->k)));
+        CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(kcur, 2) * sizeof(double) + 64));
+        launch_gram(X.as<double>(), kcur, X.as<double>(), kcur, n, n, dG.as<double>(), ctx->w_partial.as<double>(),
+                    ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+        CKL();
+        std::vector<double> G((size_t)kcur * kcur);
+        CK(cudaMemcpyAsync(G.data(), dG.p, G.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        // Cholesky with column dropping on near-dependence
+        std::vector<int> keep;
+        std::vector<double> L;
+        for (int j = 0; j < kcur; ++j) {
+            std::vector<int> trial = keep;
+            trial.push_back(j);
+            const int t = (int)trial.size();
+            std::vector<double> S((size_t)t * t);
+            for (int a = 0; a < t; ++a)
+                for (int b = 0; b < t; ++b) S[(size_t)a * t + b] = 0.5 * (G[(size_t)trial[a] * kcur + trial[b]] + G[(size_t)trial[b] * kcur + trial[a]]);
+            std::vector<double> Sc = S;
+            const double dj = G[(size_t)j * kcur + j];
+            if (host_cholesky(Sc, t) && Sc[(size_t)(t - 1) * t + (t - 1)] > 1e-7 * std::sqrt(std::max(dj, 1e-300))) {
+                keep = trial;
+                L = Sc;
+            }
+        }
+        const int kk = (int)keep.size();
+        if (kk == 0) return fail(ctx, MM_ERR_SINGULAR, "deflation basis has no independent column");
+        // C = L^-T (upper) mapped back to the input columns
+        std::vector<double> Lt((size_t)kk * kk), Rinv;
+        for (int a = 0; a < kk; ++a)
+            for (int b = 0; b < kk; ++b) Lt[(size_t)a * kk + b] = L[(size_t)b * kk + a];
+        host_upper_inverse(Lt, kk, Rinv);
+        std::vector<double> C((size_t)kcur * kk, 0.0);
+        for (int a = 0; a < kk; ++a)
+            for (int c = 0; c < kk; ++c) C[(size_t)keep[a] * kk + c] = Rinv[(size_t)a * kk + c];
+        DevBuf dC, Y;
+        CK(dC.ensure(C.size() * 8));
+        CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CK(Y.ensure((size_t)kk * n * 8));
+        launch_combo(X.as<double>(), n, kcur, dC.as<double>(), kk, Y.as<double>(), n, n, ctx->stream);
+        CKL();
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::swap(X.p, Y.p);
+        std::swap(X.bytes, Y.bytes);
+        kcur = kk;
+    }
+    *kout = kcur;
+    return MM_OK;
+}
+
+// Given Z (ctx->d_Z, k columns), form AZ, E = Z^T A Z and E^-1.
+mm_status finish_coarse(mm_ctx* ctx) {
+    const int k = ctx->k;
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    CK(ctx->d_AZ.ensure((size_t)k * n * 8));
+    TRY(apply_A_dev(ctx, !is_f32(ctx), ctx->d_Z.as<V4<double>>(), ctx->d_AZ.as<V4<double>>(), k));
+    DevBuf dG;
+    CK(dG.ensure((size_t)k * k * 8));
+    CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(k, 2) * sizeof(double) + 64));
+    launch_gram(ctx->d_Z.as<double>(), k, ctx->d_AZ.as<double>(), k, n, n, dG.as<double>(), ctx->w_partial.as<double>(),
+                ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+    CKL();
+    std::vector<double> G((size_t)k * k), E((size_t)k * k);
+    CK(cudaMemcpyAsync(G.data(), dG.p, G.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) E[(size_t)i * k + j] = 0.5 * (G[(size_t)j * k + i] + G[(size_t)i * k + j]);
+    std::vector<double> L = E, Einv;
+    if (!host_cholesky(L, k)) {
+        ctx->k = 0;
+        return fail(ctx, MM_ERR_SINGULAR, "coarse operator E = Z^T A Z is not positive definite");
+    }
+    host_spd_inverse_from_chol(L, k, Einv);
+    CK(ctx->d_Einv.ensure(Einv.size() * 8));
+    CK(cudaMemcpyAsync(ctx->d_Einv.p, Einv.data(), Einv.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision prec) {
+    if (!out) return MM_ERR_ARG;
+    *out = nullptr;
+    if (prec != MM_FP64 && prec != MM_FP32_MIXED) return MM_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MM_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return MM_ERR_CUDA;
+    mm_ctx* ctx = new mm_ctx();
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    ctx->prec = prec;
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx;
+    return MM_OK;
+}
+
+mm_status mm_destroy(mm_ctx* ctx) {
+    if (!ctx) return MM_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    destroy_graph(ctx);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return MM_OK;
+}
+
+const char* mm_last_error(const mm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32_t n_pix, const int32_t* pix,
+                            const float* psi, int32_t n_blocks, const int64_t* block_off, const int32_t* block_band,
+                            int32_t n_bands, int32_t half_bw, const double* band, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    if (n_samples <= 0 || n_pix <= 0 || n_blocks <= 0 || n_bands <= 0 || half_bw < 0 || n_det <= 0)
+        return fail(ctx, MM_ERR_ARG, "sizes must be positive (half_bw >= 0)");
+    if (n_samples % n_det != 0) return fail(ctx, MM_ERR_ARG, "n_samples must be a multiple of n_det");
+    if (!pix || !psi || !block_off || !block_band || !band) return fail(ctx, MM_ERR_ARG, "null array");
+    if (mem != MM_HOST && mem != MM_DEVICE) return fail(ctx, MM_ERR_ARG, "mem must be MM_HOST or MM_DEVICE");
+    const int64_t n_t = n_samples / n_det;
+    if (block_off[0] != 0 || block_off[n_blocks] != n_samples)
+        return fail(ctx, MM_ERR_ARG, "block_off must start at 0 and end at n_samples");
+    for (int b = 0; b < n_blocks; ++b) {
+        if (block_off[b + 1] <= block_off[b]) return fail(ctx, MM_ERR_ARG, "block_off must be strictly increasing");
+        if (block_off[b] / n_t != (block_off[b + 1] - 1) / n_t)
+            return fail(ctx, MM_ERR_ARG, "a block straddles two detector timelines");
+        if (block_band[b] < 0 || block_band[b] >= n_bands) return fail(ctx, MM_ERR_ARG, "block_band out of range");
+        if (block_off[b + 1] - block_off[b] > (int64_t)INT32_MAX) return fail(ctx, MM_ERR_ARG, "block too long");
+    }
+    if (n_pix > (1 << 26)) return fail(ctx, MM_ERR_ARG, "n_pix too large");
+    for (size_t i = 0; i < (size_t)n_bands * (half_bw + 1); ++i)
+        if (!std::isfinite(band[i])) return fail(ctx, MM_ERR_ARG, "band holds a non-finite value");
+    if (mem == MM_HOST) {
+        for (int64_t t = 0; t < n_samples; ++t)
+            if (pix[t] < -1 || pix[t] >= n_pix) return fail(ctx, MM_ERR_ARG, "pix out of range [-1, n_pix)");
+    }
+    destroy_graph(ctx);
+    ctx->have_pointing = ctx->have_bd = false;
+    ctx->k = 0;
+    ctx->have_lastb = false;
+    ctx->plans.clear();
+    ctx->fft32.L = ctx->fft64.L = 0;
+    ctx->n_samples = n_samples;
+    ctx->n_det = n_det;
+    ctx->n_t = n_t;
+    ctx->n_pix = n_pix;
+    ctx->n_blocks = n_blocks;
+    ctx->n_bands = n_bands;
+    ctx->lam = half_bw;
+    ctx->block_off.assign(block_off, block_off + n_blocks + 1);
+    ctx->block_band.assign(block_band, block_band + n_blocks);
+    ctx->band.assign(band, band + (size_t)n_bands * (half_bw + 1));
+    const int64_t gb = (n_pix + 255) / 256;
+    ctx->grid_x = (int)std::min<int64_t>(gb, 304);
+    CK(ctx->d_pix.ensure(n_samples * 4));
+    CK(ctx->d_psi.ensure(n_samples * 4));
+    CK(ctx->d_cs64.ensure(n_samples * 16));
+    CK(copy_in(ctx->d_pix.p, pix, n_samples * 4, mem, ctx->stream));
+    CK(copy_in(ctx->d_psi.p, psi, n_samples * 4, mem, ctx->stream));
+    launch_weights64(ctx->d_psi.as<float>(), ctx->d_cs64.as<double2>(), n_samples, ctx->stream);
+    CKL();
+    CK(ctx->d_block_off.ensure((n_blocks + 1) * 8));
+    CK(ctx->d_block_band.ensure(n_blocks * 4));
+    CK(cudaMemcpyAsync(ctx->d_block_off.p, block_off, (n_blocks + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_block_band.p, block_band, n_blocks * 4, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float> b32(ctx->band.size());
+    for (size_t i = 0; i < b32.size(); ++i) b32[i] = (float)ctx->band[i];
+    CK(ctx->d_band64.ensure(ctx->band.size() * 8));
+    CK(ctx->d_band32.ensure(b32.size() * 4));
+    CK(cudaMemcpyAsync(ctx->d_band64.p, ctx->band.data(), ctx->band.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_band32.p, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->have_pointing = true;
+    return MM_OK;
+}
+
+mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
+    if (!(rcond_min >= 0.0) || rcond_min > 1.0) return fail(ctx, MM_ERR_ARG, "rcond_min must lie in [0, 1]");
+    CK(cudaSetDevice(ctx->device));
+    const int n_pix = ctx->n_pix;
+    CK(ctx->d_sums.ensure((size_t)n_pix * 7 * 8));
+    CK(ctx->d_good.ensure(n_pix));
+    CK(ctx->d_bd.ensure((size_t)n_pix * 6 * 8));
+    CK(ctx->d_dropped.ensure(16));
+    CK(cudaMemsetAsync(ctx->d_sums.p, 0, ctx->d_sums.bytes, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_dropped.p, 0, 16, ctx->stream));
+    DevBuf d_len;
+    CK(d_len.ensure(8));
+    const int64_t full = ctx->n_t;
+    CK(cudaMemcpyAsync(d_len.p, &full, 8, cudaMemcpyHostToDevice, ctx->stream));
+    launch_bd_accumulate(ctx->d_pix.as<int32_t>(), ctx->d_psi.as<float>(), ctx->d_block_off.as<int64_t>(),
+                         ctx->d_block_band.as<int32_t>(), ctx->d_band64.as<double>(), ctx->lam + 1, ctx->n_blocks, 0,
+                         ctx->n_t, d_len.as<int64_t>(), 1, ctx->d_sums.as<double>(), n_pix, ctx->stream);
+    launch_bd_invert(ctx->d_sums.as<double>(), ctx->d_bd.as<double>(), ctx->d_good.as<uint8_t>(),
+                     ctx->d_dropped.as<int>(), n_pix, 1, rcond_min, 1, ctx->stream);
+    launch_flag_samples(ctx->d_pix.as<int32_t>(), ctx->d_good.as<uint8_t>(), ctx->n_samples, ctx->stream);
+    CKL();
+    int dropped = 0;
+    CK(cudaMemcpyAsync(&dropped, ctx->d_dropped.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_dropped_out) *n_dropped_out = dropped;
+    ctx->have_bd = true;
+    ctx->k = 0;
+    return MM_OK;
+}
+
+mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
+    if (!tod || !b_out || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
+    CK(cudaSetDevice(ctx->device));
+    const size_t esz = is_f32(ctx) ? 4 : 8;
+    DevBuf d_tod;
+    const void* src = tod;
+    if (mem == MM_HOST) {
+        CK(d_tod.ensure((size_t)nrhs * ctx->n_samples * esz));
+        CK(cudaMemcpyAsync(d_tod.p, tod, d_tod.bytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = d_tod.p;
+    }
+    Plan* plan = nullptr;
+    TRY(get_plan(ctx, true, nrhs, {}, &plan));
+    TRY(ensure_work(ctx, nrhs, ctx->k));
+    DevBuf q;
+    CK(q.ensure((size_t)nrhs * ctx->n_pix * sizeof(V4<double>)));
+    CK(cudaMemsetAsync(q.p, 0, q.bytes, ctx->stream));
+    TRY(run_filter(ctx, plan, true, src, q.p, nullptr, is_f32(ctx) ? 1 : 0));
+    CK(ctx->d_lastb.ensure((size_t)ctx->n_pix * sizeof(V4<double>)));
+    CK(cudaMemcpyAsync(ctx->d_lastb.p, q.p, (size_t)ctx->n_pix * sizeof(V4<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->have_lastb = true;
+    if (mem == MM_HOST) {
+        DevBuf o;
+        CK(o.ensure((size_t)nrhs * ctx->n_pix * 3 * 8));
+        launch_map_out(q.as<V4<double>>(), o.as<double>(), (int64_t)nrhs * ctx->n_pix, ctx->stream);
+        CKL();
+        CK(cudaMemcpyAsync(b_out, o.p, o.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+        launch_map_out(q.as<V4<double>>(), b_out, (int64_t)nrhs * ctx->n_pix, ctx->stream);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
+    if (!x || !y || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
+    CK(cudaSetDevice(ctx->device));
+    TRY(ensure_work(ctx, nrhs, ctx->k));
+    const int64_t nv = (int64_t)nrhs * ctx->n_pix;
+    DevBuf in3, in4, out4;
+    CK(in4.ensure(nv * sizeof(V4<double>)));
+    CK(out4.ensure(nv * sizeof(V4<double>)));
+    const double* xsrc = x;
+    if (mem == MM_HOST) {
+        CK(in3.ensure(nv * 3 * 8));
+        CK(cudaMemcpyAsync(in3.p, x, nv * 24, cudaMemcpyHostToDevice, ctx->stream));
+        xsrc = in3.as<double>();
+    }
+    launch_map_in(xsrc, in4.as<V4<double>>(), nv, ctx->stream);
+    CKL();
+    Plan* plan = nullptr;
+    TRY(get_plan(ctx, !is_f32(ctx), nrhs, {}, &plan));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    TRY(apply_A_dev(ctx, !is_f32(ctx), in4.as<V4<double>>(), out4.as<V4<double>>(), nrhs, plan));
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    if (mem == MM_HOST) {
+        DevBuf o;
+        CK(o.ensure(nv * 24));
+        launch_map_out(out4.as<V4<double>>(), o.as<double>(), nv, ctx->stream);
+        CKL();
+        CK(cudaMemcpyAsync(y, o.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        launch_map_out(out4.as<V4<double>>(), y, nv, ctx->stream);
+        CKL();
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->last_apply_ms = ms;
+    return MM_OK;
+}
+
+mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, double* y, int32_t nrhs, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (which == MM_PRECOND_2L && ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space");
+    if (which != MM_PRECOND_BD && which != MM_PRECOND_2L) return fail(ctx, MM_ERR_ARG, "unknown preconditioner");
+    if (!x || !y || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
+    CK(cudaSetDevice(ctx->device));
+    TRY(ensure_work(ctx, nrhs, ctx->k));
+    const int64_t nv = (int64_t)nrhs * ctx->n_pix;
+    DevBuf in3, in4, out4, u;
+    CK(in4.ensure(nv * sizeof(V4<double>)));
+    CK(out4.ensure(nv * sizeof(V4<double>)));
+    const double* xsrc = x;
+    if (mem == MM_HOST) {
+        CK(in3.ensure(nv * 24));
+        CK(cudaMemcpyAsync(in3.p, x, nv * 24, cudaMemcpyHostToDevice, ctx->stream));
+        xsrc = in3.as<double>();
+    }
+    launch_map_in(xsrc, in4.as<V4<double>>(), nv, ctx->stream);
+    if (which == MM_PRECOND_BD) {
+        launch_bd_apply(ctx->d_bd.as<double>(), 0, in4.as<V4<double>>(), out4.as<V4<double>>(), ctx->n_pix, nrhs,
+                        ctx->stream);
+    } else {
+        CK(u.ensure((size_t)nrhs * ctx->k * 8));
+        CK(ctx->w_partial.ensure((size_t)ctx->grid_x * nrhs * ctx->k * 8 + 64));
+        PcgArgs a{};
+        a.n_pix = ctx->n_pix;
+        a.nrhs = nrhs;
+        a.st = nullptr;
+        a.bd = ctx->d_bd.as<double>();
+        a.bd_per_rhs = 0;
+        a.k = ctx->k;
+        a.Z = ctx->d_Z.as<V4<double>>();
+        a.AZ = ctx->d_AZ.as<V4<double>>();
+        a.Einv = ctx->d_Einv.as<double>();
+        a.u = u.as<double>();
+        a.partial = ctx->w_partial.as<double>();
+        a.counter = ctx->w_counter.as<unsigned>();
+        a.grid_x = ctx->grid_x;
+        launch_m2l_ztr(a, in4.as<V4<double>>(), ctx->stream);
+        launch_m2l_apply(a, in4.as<V4<double>>(), out4.as<V4<double>>(), -1, ctx->stream);
+    }
+    CKL();
+    if (mem == MM_HOST) {
+        DevBuf o;
+        CK(o.ensure(nv * 24));
+        launch_map_out(out4.as<V4<double>>(), o.as<double>(), nv, ctx->stream);
+        CK(cudaMemcpyAsync(y, o.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+        launch_map_out(out4.as<V4<double>>(), y, nv, ctx->stream);
+    }
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, double eps_arn, int32_t k,
+                          double eps_lambda, int32_t* k_out, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (m_max <= 0 || m_max > 1024) return fail(ctx, MM_ERR_ARG, "m_max must lie in [1, 1024]");
+    if (k > 128) return fail(ctx, MM_ERR_ARG, "k must be at most 128");
+    if (!b_or_null && !ctx->have_lastb) return fail(ctx, MM_ERR_STATE, "no right-hand side: pass b or call mm_rhs");
+    CK(cudaSetDevice(ctx->device));
+    const int n_pix = ctx->n_pix;
+    const int64_t n = (int64_t)n_pix * 4;
+    ctx->k = 0;
+    TRY(ensure_work(ctx, 1, 128));
+    CK(ctx->w_partial.ensure((size_t)ctx->grid_x * (m_max + 2) * 8 + 64));
+    CK(ctx->d_W.ensure((size_t)(m_max + 1) * n * 8));
+    CK(ctx->d_h.ensure((size_t)(m_max + 2) * 8 * 2));
+    V4<double>* bvec = ctx->w_a.as<V4<double>>();
+    if (b_or_null) {
+        DevBuf in3;
+        const double* src = b_or_null;
+        if (mem == MM_HOST) {
+            CK(in3.ensure(n_pix * 24));
+            CK(cudaMemcpyAsync(in3.p, b_or_null, n_pix * 24, cudaMemcpyHostToDevice, ctx->stream));
+            src = in3.as<double>();
+        }
+        launch_map_in(src, bvec, n_pix, ctx->stream);
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        CK(cudaMemcpyAsync(bvec, ctx->d_lastb.p, n_pix * sizeof(V4<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    double* W = ctx->d_W.as<double>();
+    // w_1 = M_BD b / ||M_BD b||
+    launch_bd_apply(ctx->d_bd.as<double>(), 0, bvec, reinterpret_cast<V4<double>*>(W), n_pix, 1, ctx->stream);
+    double* h = ctx->d_h.as<double>();
+    launch_multidot(W, n, 1, W, n, h, ctx->w_partial.as<double>(), ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+    double nrm2 = 0.0;
+    CK(cudaMemcpyAsync(&nrm2, h, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!(nrm2 > 0.0)) return fail(ctx, MM_ERR_ARG, "M_BD b is zero: no Krylov space");
+    launch_scale_host(W, n, 1.0 / std::sqrt(nrm2), ctx->stream);
+    std::vector<double> H((size_t)(m_max + 1) * m_max, 0.0);   // row-major (m_max+1) x m_max
+    Plan* plan = nullptr;
+    const bool f64 = !is_f32(ctx);
+    TRY(get_plan(ctx, f64, 1, {}, &plan));
+    V4<double>* q = ctx->w_b.as<V4<double>>();
+    int m = m_max;
+    std::vector<double> hcol(m_max + 2);
+    for (int j = 0; j < m_max; ++j) {
+        double* wj = W + (int64_t)j * n;
+        double* v = W + (int64_t)(j + 1) * n;
+        TRY(apply_A_dev(ctx, f64, reinterpret_cast<V4<double>*>(wj), q, 1, plan));
+        launch_bd_apply(ctx->d_bd.as<double>(), 0, q, reinterpret_cast<V4<double>*>(v), n_pix, 1, ctx->stream);
+        // two classical Gram-Schmidt passes
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_multidot(W, n, j + 1, v, n, h + (size_t)pass * (m_max + 2), ctx->w_partial.as<double>(),
+                            ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+            launch_sub_combo(W, n, j + 1, h + (size_t)pass * (m_max + 2), v, n, ctx->stream);
+        }
+        launch_multidot(v, n, 1, v, n, h + (size_t)(m_max + 1), ctx->w_partial.as<double>(), ctx->w_counter.as<unsigned>(),
+                        ctx->grid_x, ctx->stream);
+        CKL();
+        std::vector<double> h2(2 * (size_t)(m_max + 2));
+        CK(cudaMemcpyAsync(h2.data(), h, h2.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m_max + j] = h2[i] + h2[(size_t)(m_max + 2) + i];
+        const double hn = std::sqrt(std::max(0.0, h2[m_max + 1]));
+        H[(size_t)(j + 1) * m_max + j] = hn;
+        if (!(hn > eps_arn)) {
+            m = j + 1;
+            break;
+        }
+        launch_scale_host(v, n, 1.0 / hn, ctx->stream);
+    }
+    // Ritz pairs of H_m
+    std::vector<double> Hm((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m_max + j];
+    std::vector<double> wr, wi, vr, vi;
+    if (!host_eig(Hm, m, wr, wi, vr, vi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m did not converge");
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
+    std::vector<char> used(m, 0);
+    std::vector<std::vector<double>> cols;
+    std::vector<double> vals;
+    const int kwant = k > 0 ? std::min(k, m) : m;
+    for (int idx : order) {
+        if ((int)cols.size() >= kwant) break;
+        if (used[idx]) continue;
+        if (k <= 0 && !(wr[idx] < eps_lambda)) break;
+        used[idx] = 1;
+        std::vector<double> c(m);
+        for (int i = 0; i < m; ++i) c[i] = vr[(size_t)i * m + idx];
+        cols.push_back(c);
+        vals.push_back(wr[idx]);
+        if (wi[idx] != 0.0) {
+            int partner = -1;
+            double best = 1e300;
+            for (int j2 = 0; j2 < m; ++j2) {
+                if (used[j2]) continue;
+                const double d = std::fabs(wr[j2] - wr[idx]) + std::fabs(wi[j2] + wi[idx]);
+                if (d < best) {
+                    best = d;
+                    partner = j2;
+                }
+            }
+            if (partner >= 0) used[partner] = 1;
+            if ((int)cols.size() < kwant) {
+                std::vector<double> ci(m);
+                for (int i = 0; i < m; ++i) ci[i] = vi[(size_t)i * m + idx];
+                cols.push_back(ci);
+                vals.push_back(wr[idx]);
+            }
+        }
+    }
+    const int ksel = (int)cols.size();
+    if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
+    std::vector<double> C((size_t)m * ksel);
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < ksel; ++c) C[(size_t)r * ksel + c] = cols[c][r];
+    DevBuf dC;
+    CK(dC.ensure(C.size() * 8));
+    CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx->d_Z.ensure((size_t)ksel * n * 8));
+    launch_combo(W, n, m, dC.as<double>(), ksel, ctx->d_Z.as<double>(), n, n, ctx->stream);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    int kk = 0;
+    TRY(orthonormalise(ctx, ctx->d_Z, ksel, &kk));
+    ctx->k = kk;
+    ctx->ritz.assign(vals.begin(), vals.begin() + std::min<size_t>(vals.size(), kk));
+    TRY(finish_coarse(ctx));
+    if (k_out) *k_out = ctx->k;
+    return MM_OK;
+}
+
+mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (k <= 0 || k > 128 || !Z) return fail(ctx, MM_ERR_ARG, "k must lie in [1, 128] and Z non-null");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    ctx->k = 0;
+    DevBuf in3;
+    const double* src = Z;
+    if (mem == MM_HOST) {
+        CK(in3.ensure((size_t)k * ctx->n_pix * 24));
+        CK(cudaMemcpyAsync(in3.p, Z, in3.bytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = in3.as<double>();
+    }
+    CK(ctx->d_Z.ensure((size_t)k * n * 8));
+    launch_map_in(src, ctx->d_Z.as<V4<double>>(), (int64_t)k * ctx->n_pix, ctx->stream);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    int kk = 0;
+    TRY(orthonormalise(ctx, ctx->d_Z, k, &kk));
+    ctx->k = kk;
+    ctx->ritz.assign(kk, 0.0);
+    TRY(finish_coarse(ctx));
+    return MM_OK;
+}
+
+mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k_out) {
+    if (!ctx) return MM_ERR_ARG;
+    if (ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space");
+    CK(cudaSetDevice(ctx->device));
+    if (k_out) *k_out = ctx->k;
+    if (ritz_out)
+        for (int i = 0; i < ctx->k; ++i) ritz_out[i] = i < (int)ctx->ritz.size() ? ctx->ritz[i] : 0.0;
+    if (Z_out) {
+        DevBuf o;
+        const int64_t nv = (int64_t)ctx->k * ctx->n_pix;
+        CK(o.ensure(nv * 24));
+        launch_map_out(ctx->d_Z.as<V4<double>>(), o.as<double>(), nv, ctx->stream);
+        CKL();
+        CK(cudaMemcpyAsync(Z_out, o.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return MM_OK;
+}
+
+mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64_t* rhs_len, mm_precond precond,
+                         double tol, int32_t max_iter, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (!tod || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null TOD or nrhs <= 0");
+    if (precond != MM_PRECOND_BD && precond != MM_PRECOND_2L) return fail(ctx, MM_ERR_ARG, "unknown preconditioner");
+    if (precond == MM_PRECOND_2L && ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space for M_2l");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MM_ERR_ARG, "tol must be >= 0 and max_iter >= 0");
+    if (rhs_len)
+        for (int i = 0; i < nrhs; ++i)
+            if (rhs_len[i] <= 0 || rhs_len[i] > ctx->n_t) return fail(ctx, MM_ERR_ARG, "rhs_len out of (0, n_t]");
+    CK(cudaSetDevice(ctx->device));
+    destroy_graph(ctx);
+    ctx->nrhs = nrhs;
+    ctx->precond = precond;
+    ctx->tol = tol;
+    ctx->max_iter = max_iter;
+    ctx->use_lens = rhs_len != nullptr;
+    ctx->lens.clear();
+    if (rhs_len) ctx->lens.assign(rhs_len, rhs_len + nrhs);
+    const int64_t nv = (int64_t)nrhs * ctx->n_pix;
+    const size_t v4 = nv * sizeof(V4<double>);
+    const bool f32 = is_f32(ctx);
+    TRY(ensure_work(ctx, nrhs, ctx->k));
+    CK(ctx->w_partial.ensure((size_t)ctx->grid_x * nrhs * std::max(2, ctx->k) * 8 + 64));
+    CK(ctx->s_b.ensure(v4));
+    CK(ctx->s_x.ensure(v4));
+    CK(ctx->s_r.ensure(v4));
+    CK(ctx->s_z.ensure(v4));
+    CK(ctx->s_p.ensure(v4));
+    CK(ctx->s_src.ensure(f32 ? nv * sizeof(V4<float>) : v4));
+    CK(ctx->s_q.ensure(f32 ? nv * sizeof(V4<float>) : v4));
+    CK(ctx->s_q64.ensure(v4));
+    CK(ctx->s_xtot.ensure(v4));
+    CK(ctx->s_rtrue.ensure(v4));
+    CK(ctx->s_st.ensure(nrhs * sizeof(RhsState)));
+    CK(ctx->s_hist.ensure((size_t)nrhs * (max_iter + 1) * 8));
+    CK(ctx->s_u.ensure((size_t)nrhs * std::max(1, ctx->k) * 8));
+    CK(ctx->s_mask.ensure((size_t)nrhs * 4 + 16));
+    if (ctx->use_lens) TRY(bd_for_lens(ctx));
+    TRY(get_plan(ctx, !f32, nrhs, ctx->lens, &ctx->plan_op));
+    TRY(get_plan(ctx, true, nrhs, ctx->lens, &ctx->plan_64));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    const size_t esz = f32 ? 4 : 8;
+    const void* src = tod;
+    if (mem == MM_HOST) {
+        CK(ctx->s_tod.ensure((size_t)nrhs * ctx->n_samples * esz));
+        CK(cudaMemcpyAsync(ctx->s_tod.p, tod, (size_t)nrhs * ctx->n_samples * esz, cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->s_tod.p;
+    }
+    // b = P^T W d in float64
+    CK(cudaMemsetAsync(ctx->s_b.p, 0, v4, ctx->stream));
+    TRY(run_filter(ctx, ctx->plan_64, true, src, ctx->s_b.p, nullptr, f32 ? 1 : 0));
+    CK(ctx->d_lastb.ensure((size_t)ctx->n_pix * sizeof(V4<double>)));
+    CK(cudaMemcpyAsync(ctx->d_lastb.p, ctx->s_b.p, (size_t)ctx->n_pix * sizeof(V4<double>), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    ctx->have_lastb = true;
+    CK(cudaMemsetAsync(ctx->s_xtot.p, 0, v4, ctx->stream));
+    ctx->tot_iters.assign(nrhs, 0);
+    ctx->refinements.assign(nrhs, 0);
+    ctx->final_status.assign(nrhs, 0);
+    ctx->true_res.assign(nrhs, 1.0);
+    ctx->rec_res.assign(nrhs, 1.0);
+    ctx->outer = 0;
+    // ||b|| on the host for the refinement tolerances
+    std::vector<double> bb;
+    {
+        CK(cudaMemsetAsync(ctx->s_q64.p, 0, v4, ctx->stream));
+        launch_residual(ctx->s_b.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), nullptr, ctx->w_norms.as<double>(),
+                        ctx->n_pix, nrhs, ctx->w_partial.as<double>(), ctx->w_counter.as<unsigned>(), ctx->grid_x,
+                        ctx->stream);
+        CKL();
+        bb.resize(nrhs);
+        CK(cudaMemcpyAsync(bb.data(), ctx->w_norms.p, nrhs * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->bnorm.resize(nrhs);
+        for (int i = 0; i < nrhs; ++i) ctx->bnorm[i] = std::sqrt(bb[i]);
+    }
+    std::vector<double> tols(nrhs);
+    std::vector<int> budgets(nrhs, max_iter);
+    for (int i = 0; i < nrhs; ++i) tols[i] = f32 ? std::max(tol, 2e-6) : tol;
+    TRY(pcg_start(ctx, ctx->s_b.as<V4<double>>(), tols, budgets));
+    ctx->phase = PH_INNER;
+    return MM_OK;
+}
+
+static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
+    // all inner PCG runs have stopped: accumulate and (mixed) refine
+    const int R = ctx->nrhs;
+    std::vector<int32_t> mask(R, 1);
+    for (int i = 0; i < R; ++i) {
+        ctx->tot_iters[i] += ctx->h_st[i].iters;
+        if (ctx->h_st[i].iters > 0 || ctx->outer == 0) ctx->rec_res[i] = ctx->h_st[i].relres;
+        if (ctx->h_st[i].status == 6) ctx->final_status[i] = MM_ERR_BREAKDOWN;
+    }
+    CK(cudaMemcpyAsync(ctx->s_mask.p, mask.data(), R * 4, cudaMemcpyHostToDevice, ctx->stream));
+    launch_axpy_masked(ctx->s_xtot.as<double>(), ctx->s_x.as<double>(), (int64_t)ctx->n_pix * 4, R,
+                       ctx->s_mask.as<int32_t>(), ctx->stream);
+    CKL();
+    std::vector<double> rr;
+    TRY(true_residual(ctx, ctx->s_xtot.as<V4<double>>(), rr));
+    bool again = false;
+    std::vector<double> tols(R, 0.0);
+    std::vector<int> budgets(R, 0);
+    for (int i = 0; i < R; ++i) {
+        ctx->true_res[i] = ctx->bnorm[i] > 0 ? rr[i] / ctx->bnorm[i] : 0.0;
+        if (!is_f32(ctx)) continue;
+        const int left = ctx->max_iter - ctx->tot_iters[i];
+        if (ctx->final_status[i] == MM_ERR_BREAKDOWN) continue;
+        if (allow_refine && ctx->true_res[i] > ctx->tol && left > 0 && ctx->outer < 8 && rr[i] > 0) {
+            again = true;
+            budgets[i] = left;
+            tols[i] = std::max(0.5 * ctx->tol * ctx->bnorm[i] / rr[i], 2e-6);
+        }
+    }
+    if (again) {
+        ctx->outer += 1;
+        for (int i = 0; i < R; ++i)
+            if (budgets[i] > 0) ctx->refinements[i] += 1;
+        TRY(pcg_start(ctx, ctx->s_rtrue.as<V4<double>>(), tols, budgets));
+        *done = 0;
+        return MM_OK;
+    }
+    for (int i = 0; i < R; ++i) {
+        if (ctx->final_status[i] != 0) continue;
+        const double target = is_f32(ctx) ? ctx->true_res[i] : ctx->rec_res[i];
+        if (!(target <= ctx->tol)) ctx->final_status[i] = MM_ERR_NOT_CONVERGED;
+    }
+    ctx->phase = PH_DONE;
+    *done = 1;
+    return MM_OK;
+}
+
+mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done) {
+    if (!ctx) return MM_ERR_ARG;
+    if (ctx->phase == PH_DONE) {
+        if (done) *done = 1;
+        return MM_OK;
+    }
+    if (ctx->phase != PH_INNER) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
+    CK(cudaSetDevice(ctx->device));
+    int32_t d = 0;
+    if (n_iter > 0) {
+        if (ctx->opt_graphs && n_iter == ctx->opt_check_every) {
+            if (!ctx->graph_exec) {
+                // one eager iteration first so every kernel attribute is configured
+                TRY(pcg_iteration(ctx));
+                cudaGraph_t g;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                mm_status s = MM_OK;
+                for (int i = 0; i < n_iter && s == MM_OK; ++i) s = pcg_iteration(ctx);
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                if (s != MM_OK) return s;
+                CK(e);
+                CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+                cudaGraphDestroy(g);
+                ctx->graph_iters = n_iter;
+            }
+            CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+        } else {
+            for (int i = 0; i < n_iter; ++i) TRY(pcg_iteration(ctx));
+        }
+    }
+    TRY(read_state(ctx));
+    bool any = false;
+    for (int i = 0; i < ctx->nrhs; ++i) any = any || ctx->h_st[i].active;
+    if (!any) TRY(finish_inner(ctx, &d, true));
+    if (done) *done = d;
+    return MM_OK;
+}
+
+mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    if (ctx->phase == PH_IDLE) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->phase == PH_INNER) {
+        // stopped early by the caller: account for what ran, no further refinement
+        TRY(read_state(ctx));
+        int32_t d = 0;
+        TRY(finish_inner(ctx, &d, false));
+        for (int i = 0; i < ctx->nrhs; ++i)
+            if (ctx->final_status[i] == 0 && !(ctx->true_res[i] <= ctx->tol)) ctx->final_status[i] = MM_ERR_NOT_CONVERGED;
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    const int R = ctx->nrhs;
+    const int64_t nv = (int64_t)R * ctx->n_pix;
+    if (map_out) {
+        if (mem == MM_HOST) {
+            DevBuf o;
+            CK(o.ensure(nv * 24));
+            launch_map_out(ctx->s_xtot.as<V4<double>>(), o.as<double>(), nv, ctx->stream);
+            CKL();
+            CK(cudaMemcpyAsync(map_out, o.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            launch_map_out(ctx->s_xtot.as<V4<double>>(), map_out, nv, ctx->stream);
+            CKL();
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    mm_status overall = MM_OK;
+    for (int i = 0; i < R; ++i) {
+        if (ctx->final_status[i] == MM_ERR_BREAKDOWN) overall = MM_ERR_BREAKDOWN;
+        else if (ctx->final_status[i] == MM_ERR_NOT_CONVERGED && overall == MM_OK) overall = MM_ERR_NOT_CONVERGED;
+        if (info) {
+            info[i].iters = ctx->tot_iters[i];
+            info[i].status = ctx->final_status[i];
+            info[i].rel_res = ctx->rec_res[i];
+            info[i].true_rel_res = ctx->true_res[i];
+            info[i].t_solve_ms = ms;
+            info[i].refinements = ctx->refinements[i];
+            info[i].pad = 0;
+        }
+    }
+    ctx->phase = PH_IDLE;
+    destroy_graph(ctx);
+    if (overall == MM_ERR_NOT_CONVERGED) ctx->err = "at least one right-hand side did not converge";
+    if (overall == MM_ERR_BREAKDOWN) ctx->err = "PCG breakdown (p^T A p <= 0 or NaN)";
+    return overall;
+}
+
+mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs, const int64_t* rhs_len,
+                   mm_precond precond, double tol, int32_t max_iter, mm_solve_info* info, int mem) {
+    TRY(mm_solve_begin(ctx, tod, nrhs, rhs_len, precond, tol, max_iter, mem));
+    int32_t done = 0;
+    while (!done) TRY(mm_solve_step(ctx, ctx->opt_check_every, &done));
+    return mm_solve_end(ctx, map_out, info, mem);
+}
+
+mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
+    if (!ctx || !name) return MM_ERR_ARG;
+    const std::string n(name);
+    const int v = (int)value;
+    if (n == "filter") {
+        if (v < 0 || v > 2) return fail(ctx, MM_ERR_ARG, "filter must be 0, 1 or 2");
+        ctx->opt_filter = v;
+    } else if (n == "fft_log2") {
+        if (v != 0 && (v < 6 || v > 14)) return fail(ctx, MM_ERR_ARG, "fft_log2 must be 0 or in [6, 14]");
+        ctx->opt_fft_log2 = v;
+    } else if (n == "direct_tile") {
+        if (v < 32 || v > 65536) return fail(ctx, MM_ERR_ARG, "direct_tile must lie in [32, 65536]");
+        ctx->opt_direct_tile = v;
+    } else if (n == "check_every") {
+        if (v < 1 || v > 100000) return fail(ctx, MM_ERR_ARG, "check_every must be >= 1");
+        ctx->opt_check_every = v;
+    } else if (n == "graphs") {
+        ctx->opt_graphs = v ? 1 : 0;
+    } else {
+        return fail(ctx, MM_ERR_ARG, "unknown option " + n);
+    }
+    return MM_OK;
+}
+
+mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
+    if (!ctx || !name || !value) return MM_ERR_ARG;
+    const std::string n(name);
+    if (n == "filter") *value = ctx->opt_filter;
+    else if (n == "fft_log2") *value = ctx->opt_fft_log2;
+    else if (n == "direct_tile") *value = ctx->opt_direct_tile;
+    else if (n == "check_every") *value = ctx->opt_check_every;
+    else if (n == "graphs") *value = ctx->opt_graphs;
+    else if (n == "last_apply_ms") *value = ctx->last_apply_ms;
+    else if (n == "plan_fft_log2") {
+        Plan* p = nullptr;
+        if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");
+        TRY(get_plan(ctx, !is_f32(ctx), 1, {}, &p));
+        *value = p->variant == 2 ? p->logL : 0;
+    } else if (n == "device_bytes") {
+        size_t f = 0, t = 0;
+        cudaMemGetInfo(&f, &t);
+        *value = (double)(t - f);
+    } else return fail(ctx, MM_ERR_ARG, "unknown option " + n);
+    return MM_OK;
+}
+
+int64_t mm_estimate_bytes(int64_t n_samples, int32_t n_pix, int32_t n_bands, int32_t half_bw, int32_t nrhs,
+                          int32_t m_max, int32_t k, mm_precision prec) {
+    const int64_t esz = prec == MM_FP32_MIXED ? 4 : 8;
+    int64_t b = n_samples * (4 + 4 + 16);              // pix, psi, float64 weights
+    b += (int64_t)nrhs * n_samples * esz;              // timelines
+    b += (int64_t)n_pix * 32 * (12 + 2 * (int64_t)nrhs * 6);  // maps and PCG state
+    b += (int64_t)(m_max + 1) * n_pix * 32;            // Arnoldi basis
+    b += (int64_t)2 * k * n_pix * 32;                  // Z, AZ
+    b += (int64_t)n_bands * (int64_t)16384 * 12;       // spectra
+    b += (int64_t)n_pix * 7 * 8 * std::max(1, nrhs);   // M_BD sums
+    b += n_samples / 64 * 40 * std::max(1, nrhs);      // segment lists
+    (void)half_bw;
+    return b;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Shared types and launcher declarations of the map-making library.
+//
+// Layouts in device memory
+//   pointing   pix int32[N], psi float32[N] (and, for float64 products, the
+//              weights (cos 2psi, sin 2psi) as double2[N] precomputed once)
+//   maps       [nrhs][n_pix] of 4-wide vectors (I, Q, U, 0); float4 for the
+//              float32 operator, V4<double> (32-byte aligned) elsewhere.  The
+//              fourth lane keeps every pixel one aligned vector load.
+//   segments   the timeline is cut into output segments inside stationary
+//              blocks; each CTA of the filter kernels processes one pair of
+//              segments (see Seg).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mm {
+
+template <typename T> struct __align__(sizeof(T) * 4) V4 { T x, y, z, w; };
+template <typename T> struct __align__(sizeof(T) * 2) C2 { T x, y; };
+
+// One output segment of one stationary block for one right-hand side.
+//   outputs  t in [out0, out0 + n_out)
+//   inputs   t in [out0 - lambda, out0 + n_out + lambda) clipped to [lo, hi),
+//            the block's active range for this right-hand side.
+// Segments are stored in pairs; a pair shares one band (one filter) so two
+// real timelines travel as the real and imaginary parts of one complex FFT.
+// n_out == 0 marks an empty slot.
+struct Seg {
+    int64_t out0;
+    int64_t lo, hi;
+    int32_t rhs;
+    int32_t n_out;
+    int32_t band;
+    int32_t pad;
+};
+
+// Per-right-hand-side PCG scalars kept on the device (float64).
+struct RhsState {
+    double rz;       // r^T z of the current iterate
+    double pq;       // p^T A p
+    double alpha, beta;
+    double bnorm;    // ||b||
+    double relres;   // ||r_k|| / ||b||
+    double tol;
+    int32_t active;  // 1 while iterating
+    int32_t iters;
+    int32_t status;  // 0 ok/running, 5 not converged, 6 breakdown
+    int32_t max_iter;
+};
+
+// ---------------- filter (A x, b) ----------------
+struct FilterArgs {
+    const Seg* segs;       // [2 * n_work]
+    int n_work;
+    const int32_t* pix;
+    const float* psi;
+    const double2* cs64;   // float64 weights, may be null for float32
+    const void* src;       // maps [nrhs][n_pix] (V4<T>) or TOD [nrhs][n_samples] (T)
+    int64_t n_samples;
+    void* dst;             // accumulators [nrhs][n_pix] (V4<T>)
+    int n_pix;
+    const void* H;         // FFT: [n_bands][L] real spectrum (digit-reversed, 1/L folded in)
+    const void* tw;        // FFT: [L] twiddles exp(-2 pi i e / L)
+    const void* band;      // direct: [n_bands][lambda+1]
+    int L, logL, lam, V;
+    const RhsState* state; // may be null: all right-hand sides active
+    int tod_is_float;      // src TOD element type when from_tod (1: float, 0: double)
+};
+
+// T = float or double; from_tod selects b = P^T W d (src is a TOD).
+void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s);
+void launch_filter_fft_f64(const FilterArgs& a, bool from_tod, cudaStream_t s);
+void launch_filter_direct_f32(const FilterArgs& a, bool from_tod, cudaStream_t s);
+void launch_filter_direct_f64(const FilterArgs& a, bool from_tod, cudaStream_t s);
+size_t fft_smem_bytes(int L, bool f64);
+size_t direct_smem_bytes(int V, int lam, bool f64);
+// H = DIF(h) for each band in float64 through global scratch; h [n_bands][L].
+void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw,
+                         int n_bands, int L, int logL, cudaStream_t s);
+void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s);
+
+// ---------------- vectors, preconditioners, reductions ----------------
+void launch_map_in(const double* src3, V4<double>* dst4, int64_t n_vec, cudaStream_t s);
+void launch_map_out(const V4<double>* src4, double* dst3, int64_t n_vec, cudaStream_t s);
+void launch_to_f32(const V4<double>* src, V4<float>* dst, int64_t n, cudaStream_t s);
+void launch_from_f32(const V4<float>* src, V4<double>* dst, int64_t n, cudaStream_t s);
+void launch_zero(void* p, size_t bytes, cudaStream_t s);
+
+// M_BD build: 6 sums + hits per pixel; then flagging and inversion.
+void launch_bd_accumulate(const int32_t* pix, const float* psi, const int64_t* block_off,
+                          const int32_t* block_band, const double* band, int lam1, int n_blocks,
+                          int64_t t_cap_per_det, int64_t n_t, const int64_t* rhs_len, int nrhs,
+                          double* sums /*[nrhs][n_pix][7]*/, int n_pix, cudaStream_t s);
+void launch_bd_invert(const double* sums, double* bd /*[nrhs][n_pix][6]*/, uint8_t* good,
+                      int* n_dropped, int n_pix, int nrhs, double rcond_min, int set_good,
+                      cudaStream_t s);
+void launch_flag_samples(int32_t* pix, const uint8_t* good, int64_t n, cudaStream_t s);
+void launch_bd_apply(const double* bd, int bd_per_rhs, const V4<double>* x, V4<double>* y,
+                     int n_pix, int nrhs, cudaStream_t s);
+
+// PCG building blocks (all nrhs at once; grid.y = rhs).
+struct PcgArgs {
+    int n_pix, nrhs;
+    RhsState* st;
+    V4<double>* x; V4<double>* r; V4<double>* z; V4<double>* p;
+    const V4<double>* q64;   // A p in float64 (FP64 operator)
+    const V4<float>* q32;    // A p in float32 (FP32 operator)
+    void* src;               // gather source for the next product (V4<T>)
+    int src_f32;
+    void* qacc;              // accumulator to clear (V4<T>)
+    const double* bd; int bd_per_rhs;
+    // two-level
+    int k;
+    const V4<double>* Z; const V4<double>* AZ; const double* Einv;
+    double* u;               // [nrhs][k]
+    double* partial;         // reduction scratch
+    unsigned* counter;       // [nrhs]
+    double* hist;            // [nrhs][hist_stride]
+    int hist_stride;
+    int grid_x;
+};
+void launch_pcg_init(const PcgArgs& a, const V4<double>* b, cudaStream_t s);
+void launch_pcg_src(const PcgArgs& a, int first, cudaStream_t s);
+void launch_pcg_pq(const PcgArgs& a, cudaStream_t s);
+void launch_pcg_update(const PcgArgs& a, int two_level, cudaStream_t s);
+void launch_precond_bd_dot(const PcgArgs& a, int finalize_beta, cudaStream_t s);
+void launch_m2l_ztr(const PcgArgs& a, const V4<double>* v, cudaStream_t s);
+void launch_m2l_apply(const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta,
+                      cudaStream_t s);
+
+// Tall-skinny float64 products over vectors of n doubles (n = 4 n_pix).
+// h[i] = sum_n X[i][n] v[n] for i < m  (deterministic two-phase reduction)
+void launch_multidot(const double* X, int64_t ldx, int m, const double* v, int64_t n,
+                     double* h, double* partial, unsigned* counter, int grid_x, cudaStream_t s);
+// v[n] -= sum_i X[i][n] h[i]
+void launch_sub_combo(const double* X, int64_t ldx, int m, const double* h, double* v, int64_t n,
+                      cudaStream_t s);
+// Y[c][n] = sum_i X[i][n] C[i*kc + c] for c < kc
+void launch_combo(const double* X, int64_t ldx, int m, const double* C, int kc, double* Y,
+                  int64_t ldy, int64_t n, cudaStream_t s);
+// G[j*mx + i] = sum_n X[i][n] Y[j][n]
+void launch_gram(const double* X, int mx, const double* Y, int my, int64_t ld, int64_t n, double* G,
+                 double* partial, unsigned* counter, int grid_x, cudaStream_t s);
+void launch_scale_host(double* v, int64_t n, double factor, cudaStream_t s);
+void launch_residual(const V4<double>* b, const V4<double>* q, V4<double>* r_out, double* norms, int n_pix,
+                     int nrhs, double* partial, unsigned* counter, int grid_x, cudaStream_t s);
+void launch_axpy_masked(double* y, const double* x, int64_t n_per, int nrhs, const int32_t* mask,
+                        cudaStream_t s);
+
+// ---------------- host linear algebra ----------------
+// Eigenvalues and right eigenvectors of a real m x m matrix (row-major),
+// via complex shifted QR and inverse iteration.  Returns false on failure.
+bool host_eig(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi,
+              std::vector<double>& vr, std::vector<double>& vi);
+// Lower Cholesky factor in place (row-major n x n); false if not SPD.
+bool host_cholesky(std::vector<double>& A, int n);
+// Inverse of an SPD matrix from its Cholesky factor.
+void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
+// Inverse of an upper-triangular matrix R (row-major).
+void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
+
+}  // namespace mm

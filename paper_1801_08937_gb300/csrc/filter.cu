@@ -1,0 +1,473 @@
+// Fused A x = P^T W P x and b = P^T W d kernels.
+//
+// One CTA handles one pair of output segments (see Seg).  Per pair it
+//   1. gathers y_t = I_p + Q_p cos 2psi_t + U_p sin 2psi_t over the segment
+//      plus a lambda halo on each side, clipped to the block (Sect. 2,
+//      Eq. datamodel), or reads d_t for the right-hand side;
+//   2. applies the block's banded Toeplitz weight W (Sect. 2, Eq. estimator)
+//      -- FFT variant: both segments ride in one complex FFT of length L
+//      (real part / imaginary part), are multiplied by the real spectrum of
+//      the symmetric band and transformed back (overlap-save: the central
+//      L - 2 lambda outputs are exact linear-convolution values);
+//      -- direct variant: the band sum in shared memory;
+//   3. scatters z_t (1, cos 2psi_t, sin 2psi_t) into the map (P^T), first
+//      summing runs of equal consecutive pixels inside each warp so one
+//      atomic carries a whole run.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mm {
+
+constexpr int FFT_NT = 256;
+constexpr int DIRECT_NT = 256;
+
+// Padded shared-memory index: one spare element every 16 keeps the strided
+// butterfly accesses of the late passes spread over the banks.
+__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
+
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+__device__ __forceinline__ C2<float> ldtw(const C2<float>* tw, int e) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(tw) + e);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ C2<double> ldtw(const C2<double>* tw, int e) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(tw) + e);
+    return {v.x, v.y};
+}
+
+// ---- small forward DFTs in registers, natural order in and out, W_R = e^{-2 pi i / R} ----
+template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
+    const C2<T> s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = {d02.x + d13.y, d02.y - d13.x};   // d02 - i d13
+    a3 = {d02.x - d13.y, d02.y + d13.x};   // d02 + i d13
+}
+
+template <typename T, int R> struct Dft;
+template <typename T> struct Dft<T, 2> {
+    static __device__ __forceinline__ void run(C2<T>* a) {
+        const C2<T> t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    }
+};
+template <typename T> struct Dft<T, 4> {
+    static __device__ __forceinline__ void run(C2<T>* a) { dft4(a[0], a[1], a[2], a[3]); }
+};
+template <typename T> struct Dft<T, 8> {
+    static __device__ __forceinline__ void run(C2<T>* a) {
+        const T r2 = T(0.70710678118654752440);
+        // n = 2 n1 + n2, k = k1 + 4 k2
+        dft4(a[0], a[2], a[4], a[6]);
+        dft4(a[1], a[3], a[5], a[7]);
+        a[3] = cmul(a[3], C2<T>{r2, -r2});
+        a[5] = C2<T>{a[5].y, -a[5].x};
+        a[7] = cmul(a[7], C2<T>{-r2, -r2});
+        C2<T> o[8];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            o[k1] = cadd(a[2 * k1], a[2 * k1 + 1]);
+            o[k1 + 4] = csub(a[2 * k1], a[2 * k1 + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = o[i];
+    }
+};
+template <typename T> struct Dft<T, 16> {
+    static __device__ __forceinline__ void run(C2<T>* a) {
+        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
+        const T r2 = T(0.70710678118654752440);
+        // n = 4 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+        // a[n2 + 4 k1] *= W16^(n2 k1)
+        a[5] = cmul(a[5], C2<T>{c1, -s1});
+        a[9] = cmul(a[9], C2<T>{r2, -r2});
+        a[13] = cmul(a[13], C2<T>{s1, -c1});
+        a[6] = cmul(a[6], C2<T>{r2, -r2});
+        a[10] = C2<T>{a[10].y, -a[10].x};
+        a[14] = cmul(a[14], C2<T>{-r2, -r2});
+        a[7] = cmul(a[7], C2<T>{s1, -c1});
+        a[11] = cmul(a[11], C2<T>{-r2, -r2});
+        a[15] = cmul(a[15], C2<T>{-c1, s1});
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+        C2<T> o[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = a[4 * k1 + k2];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[i] = o[i];
+    }
+};
+
+// Decimation-in-frequency pass of radix R over spans of 2^logS (in place):
+// for each butterfly j < S/R of each span, DFT_R over elements j + r S/R,
+// then output q times W_S^(j q).  Natural order in, digit-reversed out.
+template <typename T, int R, int LOGR>
+__device__ __forceinline__ void dif_pass(C2<T>* s, const C2<T>* __restrict__ tw, int logL, int logS) {
+    const int logSr = logS - LOGR;
+    const int nbf = 1 << (logL - LOGR);
+    const int tsh = logL - logS;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        const int g = bf >> logSr;
+        const int j = bf & ((1 << logSr) - 1);
+        const int base = (g << logS) + j;
+        C2<T> a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + (r << logSr))];
+        Dft<T, R>::run(a);
+        if (logSr > 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], ldtw(tw, (j * q) << tsh));
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) s[sidx(base + (q << logSr))] = a[q];
+    }
+}
+
+// The matching decimation-in-time pass in the conjugate domain: element q
+// times W_S^(j q), then DFT_R.  Run on conj(X) in the reverse pass order it
+// yields L * conj(x): the exact inverse of the DIF passes.
+template <typename T, int R, int LOGR>
+__device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw, int logL, int logS) {
+    const int logSr = logS - LOGR;
+    const int nbf = 1 << (logL - LOGR);
+    const int tsh = logL - logS;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        const int g = bf >> logSr;
+        const int j = bf & ((1 << logSr) - 1);
+        const int base = (g << logS) + j;
+        C2<T> a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = s[sidx(base + (q << logSr))];
+        if (logSr > 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], ldtw(tw, (j * q) << tsh));
+        }
+        Dft<T, R>::run(a);
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[sidx(base + (r << logSr))] = a[r];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void tail_dif(C2<T>* s, const C2<T>* tw, int logL, int rem) {
+    if (rem == 1) dif_pass<T, 2, 1>(s, tw, logL, 1);
+    else if (rem == 2) dif_pass<T, 4, 2>(s, tw, logL, 2);
+    else if (rem == 3) dif_pass<T, 8, 3>(s, tw, logL, 3);
+}
+template <typename T>
+__device__ __forceinline__ void tail_dit(C2<T>* s, const C2<T>* tw, int logL, int rem) {
+    if (rem == 1) dit_pass<T, 2, 1>(s, tw, logL, 1);
+    else if (rem == 2) dit_pass<T, 4, 2>(s, tw, logL, 2);
+    else if (rem == 3) dit_pass<T, 8, 3>(s, tw, logL, 3);
+}
+
+// Forward transform: radix-16 passes from span L down, then one radix-2^rem pass.
+template <typename T>
+__device__ void fft_dif(C2<T>* s, const C2<T>* tw, int logL) {
+    const int n16 = logL >> 2, rem = logL & 3;
+    int logS = logL;
+    for (int p = 0; p < n16; ++p) {
+        dif_pass<T, 16, 4>(s, tw, logL, logS);
+        logS -= 4;
+        __syncthreads();
+    }
+    if (rem) {
+        tail_dif<T>(s, tw, logL, rem);
+        __syncthreads();
+    }
+}
+template <typename T>
+__device__ void fft_dit_conj(C2<T>* s, const C2<T>* tw, int logL) {
+    const int n16 = logL >> 2, rem = logL & 3;
+    if (rem) {
+        tail_dit<T>(s, tw, logL, rem);
+        __syncthreads();
+    }
+    int logS = rem + 4;
+    for (int p = 0; p < n16; ++p) {
+        dit_pass<T, 16, 4>(s, tw, logL, logS);
+        logS += 4;
+        __syncthreads();
+    }
+}
+
+// ---- pointing weights ----
+// float32: __sincosf on 2 psi - pi in [-pi, pi), where its error stays near
+// 4e-7; cos 2psi = -cos(2psi - pi), sin 2psi = -sin(2psi - pi).
+__device__ __forceinline__ void weights(const FilterArgs& a, int64_t t, float& c, float& s) {
+    const float x = fmaf(2.0f, __ldg(a.psi + t), -3.14159265358979323846f);
+    float sn, cs;
+    __sincosf(x, &sn, &cs);
+    c = -cs;
+    s = -sn;
+}
+__device__ __forceinline__ void weights(const FilterArgs& a, int64_t t, double& c, double& s) {
+    const double2 v = __ldg(a.cs64 + t);
+    c = v.x;
+    s = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ V4<T> ldmap(const V4<T>* m);
+template <>
+__device__ __forceinline__ V4<float> ldmap(const V4<float>* m) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(m));
+    return {v.x, v.y, v.z, v.w};
+}
+template <>
+__device__ __forceinline__ V4<double> ldmap(const V4<double>* m) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(m));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(m) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// y_t of right-hand side `rhs`: (P x)_t, or d_t when FROM_TOD.
+template <typename T, bool FROM_TOD>
+__device__ __forceinline__ T sample_value(const FilterArgs& a, int64_t t, int rhs) {
+    if (FROM_TOD) {
+        if (a.tod_is_float) return T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t));
+        return T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t));
+    } else {
+        const int p = __ldg(a.pix + t);
+        if (p < 0) return T(0);
+        T c, s;
+        weights(a, t, c, s);
+        const V4<T> m = ldmap<T>(reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix + p);
+        return m.x + c * m.y + s * m.z;
+    }
+}
+
+__device__ __forceinline__ void atomic_add3(V4<float>* q, float a, float b, float c) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    atomicAdd(reinterpret_cast<float4*>(q), make_float4(a, b, c, 0.0f));
+#else
+    atomicAdd(&q->x, a);
+    atomicAdd(&q->y, b);
+    atomicAdd(&q->z, c);
+#endif
+}
+__device__ __forceinline__ void atomic_add3(V4<double>* q, double a, double b, double c) {
+    atomicAdd(&q->x, a);
+    atomicAdd(&q->y, b);
+    atomicAdd(&q->z, c);
+}
+
+// Warp-cooperative P^T: every lane holds one sample (p < 0: nothing).
+// Consecutive lanes with equal p form a run; a suffix sum inside each run
+// leaves the run total on its first lane, which issues one atomic.
+template <typename T>
+__device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<T>* q) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const int pprev = __shfl_up_sync(FULL, p, 1);
+    const bool head = (lane == 0) || (p != pprev);
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const int end = above ? (__ffs(above) - 1) : 32;
+    T v0 = z, v1 = z * c, v2 = z * s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T o0 = __shfl_down_sync(FULL, v0, d);
+        const T o1 = __shfl_down_sync(FULL, v1, d);
+        const T o2 = __shfl_down_sync(FULL, v2, d);
+        if ((int)lane + d < end) {
+            v0 += o0;
+            v1 += o1;
+            v2 += o2;
+        }
+    }
+    if (head && p >= 0) atomic_add3(q + p, v0, v1, v2);
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_one(const FilterArgs& a, const Seg& S, bool act, int i, T zval) {
+    int p = -1;
+    T c = T(0), s = T(0), z = T(0);
+    if (act && i < S.n_out) {
+        const int64_t t = S.out0 + i;
+        p = __ldg(a.pix + t);
+        if (p >= 0) {
+            weights(a, t, c, s);
+            z = zval;
+        }
+    }
+    scatter_warp<T>(p, c, s, z, reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(act ? S.rhs : 0) * a.n_pix);
+}
+
+template <typename T>
+__device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
+    return S.n_out > 0 && (a.state == nullptr || a.state[S.rhs].active);
+}
+
+// ---------------- FFT overlap-save variant ----------------
+template <typename T, bool FROM_TOD>
+__global__ void __launch_bounds__(FFT_NT) k_filter_fft(const FilterArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
+    const Seg A = a.segs[2 * blockIdx.x];
+    const Seg B = a.segs[2 * blockIdx.x + 1];
+    const bool actA = seg_active<T>(a, A);
+    const bool actB = seg_active<T>(a, B);
+    if (!actA && !actB) return;
+    const int L = a.L, lam = a.lam, logL = a.logL;
+    const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
+
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        T ya = T(0), yb = T(0);
+        if (actA) {
+            const int64_t t = A.out0 - lam + i;
+            if (t >= A.lo && t < A.hi) ya = sample_value<T, FROM_TOD>(a, t, A.rhs);
+        }
+        if (actB) {
+            const int64_t t = B.out0 - lam + i;
+            if (t >= B.lo && t < B.hi) yb = sample_value<T, FROM_TOD>(a, t, B.rhs);
+        }
+        s[sidx(i)] = C2<T>{ya, yb};
+    }
+    __syncthreads();
+    fft_dif<T>(s, tw, logL);
+    const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const C2<T> v = s[sidx(i)];
+        const T h = __ldg(H + i);
+        s[sidx(i)] = C2<T>{v.x * h, -v.y * h};
+    }
+    __syncthreads();
+    fft_dit_conj<T>(s, tw, logL);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int vmax = max(actA ? A.n_out : 0, actB ? B.n_out : 0);
+    for (int base = warp * 32; base < vmax; base += nwarp * 32) {
+        const int i = base + lane;
+        const int ii = min(lam + i, L - 1);
+        const C2<T> v = s[sidx(ii)];
+        scatter_one<T>(a, A, actA, i, v.x);
+        scatter_one<T>(a, B, actB, i, -v.y);
+    }
+}
+
+// ---------------- direct band variant ----------------
+template <typename T, bool FROM_TOD>
+__global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lam = a.lam;
+    T* c = reinterpret_cast<T*>(smraw);
+    T* y = c + ((lam + 1 + 1) & ~1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const Seg S = a.segs[2 * blockIdx.x + half];
+        if (!seg_active<T>(a, S)) continue;   // uniform across the CTA
+        const T* band = reinterpret_cast<const T*>(a.band) + (int64_t)S.band * (lam + 1);
+        for (int k = threadIdx.x; k <= lam; k += blockDim.x) c[k] = band[k];
+        const int nin = S.n_out + 2 * lam;
+        for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+            const int64_t t = S.out0 - lam + i;
+            y[i] = (t >= S.lo && t < S.hi) ? sample_value<T, FROM_TOD>(a, t, S.rhs) : T(0);
+        }
+        __syncthreads();
+        for (int base = warp * 32; base < S.n_out; base += nwarp * 32) {
+            const int i = base + lane;
+            T z = T(0);
+            if (i < S.n_out) {
+                const T* yc = y + lam + i;
+                z = c[0] * yc[0];
+                for (int k = 1; k <= lam; ++k) z += c[k] * (yc[-k] + yc[k]);
+            }
+            scatter_one<T>(a, S, true, i, z);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------- setup kernels ----------------
+__global__ void k_fft_spectrum(const double* h, double* H, C2<double>* work, const C2<double>* tw, int L,
+                               int logL) {
+    C2<double>* s = work + (int64_t)blockIdx.x * (L + (L >> 4));
+    const double* hb = h + (int64_t)blockIdx.x * L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) s[sidx(i)] = C2<double>{hb[i], 0.0};
+    __syncthreads();
+    fft_dif<double>(s, tw, logL);
+    const double inv = 1.0 / (double)L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) H[(int64_t)blockIdx.x * L + i] = s[sidx(i)].x * inv;
+}
+
+__global__ void k_weights64(const float* psi, double2* cs, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double sn, c;
+        sincos(2.0 * (double)psi[t], &sn, &c);
+        cs[t] = make_double2(c, sn);
+    }
+}
+
+// ---------------- launchers ----------------
+size_t fft_smem_bytes(int L, bool f64) { return (size_t)(L + (L >> 4)) * (f64 ? 16 : 8); }
+size_t direct_smem_bytes(int V, int lam, bool f64) {
+    return (size_t)(((lam + 2) & ~1) + V + 2 * lam) * (f64 ? 8 : 4);
+}
+
+template <typename T, bool FROM_TOD>
+static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
+    if (a.n_work <= 0) return;
+    const size_t sm = fft_smem_bytes(a.L, sizeof(T) == 8);
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        configured = sm;
+    }
+    k_filter_fft<T, FROM_TOD><<<a.n_work, FFT_NT, sm, s>>>(a);
+}
+template <typename T, bool FROM_TOD>
+static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
+    if (a.n_work <= 0) return;
+    const size_t sm = direct_smem_bytes(a.V, a.lam, sizeof(T) == 8);
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaFuncSetAttribute(k_filter_direct<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        configured = sm;
+    }
+    k_filter_direct<T, FROM_TOD><<<a.n_work, DIRECT_NT, sm, s>>>(a);
+}
+
+void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s) {
+    if (from_tod) launch_fft_t<float, true>(a, s);
+    else launch_fft_t<float, false>(a, s);
+}
+void launch_filter_fft_f64(const FilterArgs& a, bool from_tod, cudaStream_t s) {
+    if (from_tod) launch_fft_t<double, true>(a, s);
+    else launch_fft_t<double, false>(a, s);
+}
+void launch_filter_direct_f32(const FilterArgs& a, bool from_tod, cudaStream_t s) {
+    if (from_tod) launch_direct_t<float, true>(a, s);
+    else launch_direct_t<float, false>(a, s);
+}
+void launch_filter_direct_f64(const FilterArgs& a, bool from_tod, cudaStream_t s) {
+    if (from_tod) launch_direct_t<double, true>(a, s);
+    else launch_direct_t<double, false>(a, s);
+}
+
+void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw, int n_bands, int L,
+                         int logL, cudaStream_t s) {
+    if (n_bands <= 0) return;
+    k_fft_spectrum<<<n_bands, 256, 0, s>>>(h, H_out, reinterpret_cast<C2<double>*>(work),
+                                           reinterpret_cast<const C2<double>*>(tw), L, logL);
+}
+
+void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    k_weights64<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(psi, cs, n);
+}
+
+}  // namespace mm

@@ -120,18 +120,22 @@ def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
     t = np.arange(n_t, dtype=np.float64)
     x0 = rng.uniform(0.0, 2.0 * nx, size=n_det)
     y0 = rng.uniform(0.0, ny)
+    st = speed * t
+    ty = t * (ny / n_t)
     for d in range(n_det):
-        pos = np.mod(x0[d] + speed * t, 2.0 * nx)
-        x = np.where(pos < nx, pos, 2.0 * nx - pos)
-        ix = np.clip(np.floor(x).astype(np.int64), 0, nx - 1)
+        pos = np.mod(x0[d] + st, 2.0 * nx)
+        np.subtract(2.0 * nx, pos, out=pos, where=pos >= nx)
+        ix = np.minimum(pos.astype(np.int32), nx - 1)
         oy = d * (ny / 4.0) / n_det
-        y = np.mod(y0 + oy + t * (ny / n_t), ny)
-        iy = np.clip(np.floor(y).astype(np.int64), 0, ny - 1)
-        pix[d * n_t:(d + 1) * n_t] = (iy * nx + ix).astype(np.int32)
-    psi = (rng.random(N) * np.pi).astype(np.float32)
-    psi = np.minimum(psi, np.float32(np.nextafter(np.float32(np.pi), np.float32(0))))
+        y = np.mod(y0 + oy + ty, ny)
+        iy = np.minimum(y.astype(np.int32), ny - 1)
+        np.multiply(iy, nx, out=iy)
+        np.add(iy, ix, out=pix[d * n_t:(d + 1) * n_t])
+    psi = rng.random(N, dtype=np.float32)
+    psi *= np.float32(np.pi)
+    np.minimum(psi, np.nextafter(np.float32(np.pi), np.float32(0)), out=psi)
     if flag_frac > 0:
-        pix[rng.random(N) < flag_frac] = -1
+        pix[rng.random(N, dtype=np.float32) < flag_frac] = -1
     if np.ndim(f_knee) == 0:
         fk = np.full(n_det, float(f_knee))
     else:
@@ -186,12 +190,18 @@ def make_tod(scan: Scan, sky: np.ndarray | None, noise: np.ndarray | None) -> np
     This is the data model the paper simulates (Sect. 2, Eq. datamodel); it
     only synthesises an input.  Flagged samples carry noise only.
     """
-    d = np.zeros(scan.n_samples, dtype=np.float64)
+    N = scan.n_samples
+    d = np.zeros(N, dtype=np.float64)
     if sky is not None:
-        ok = scan.pix >= 0
-        p = scan.pix[ok]
-        ang = 2.0 * scan.psi[ok].astype(np.float64)
-        d[ok] = sky[p, 0] + sky[p, 1] * np.cos(ang) + sky[p, 2] * np.sin(ang)
+        chunk = 1 << 20
+        for a in range(0, N, chunk):
+            b = min(N, a + chunk)
+            pix = scan.pix[a:b]
+            ok = pix >= 0
+            p = pix[ok]
+            ang = 2.0 * scan.psi[a:b][ok].astype(np.float64)
+            seg = d[a:b]
+            seg[ok] = sky[p, 0] + sky[p, 1] * np.cos(ang) + sky[p, 2] * np.sin(ang)
     if noise is not None:
         d += noise
     return d

@@ -1,0 +1,68 @@
+"""Shared set-up for the parity tests: oracle problems and seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+import synth
+
+
+def oracle_problem(scan, rcond_min=1e-3):
+    """Oracle view of a scan after the pixel selection (samples of dropped pixels flagged)."""
+    prob = O.Problem.from_scan(scan)
+    blocks, hits = O.bd_blocks(prob)
+    good = O.select_pixels(blocks, hits, rcond_min)
+    prob = prob.with_pix(O.flag_samples(prob.pix, good))
+    blocks, _ = O.bd_blocks(prob)
+    mbd = O.bd_inverse(blocks, good)
+    return prob, mbd, good
+
+
+def truncated_problem(scan, length, rcond_min=1e-3, good=None):
+    """Oracle problem of the first `length` samples of every detector timeline.
+
+    Pixel selection comes from the full scan (``good``), as in the library.
+    """
+    keep = (np.arange(scan.n_samples) % scan.n_t) < length
+    pix = scan.pix.astype(np.int64).copy()
+    if good is not None:
+        ok = pix >= 0
+        bad = np.zeros_like(ok)
+        bad[ok] = ~good[pix[ok]]
+        pix[bad] = -1
+    offs = []
+    bands = []
+    for b in range(scan.n_blocks):
+        o0, o1 = int(scan.block_off[b]), int(scan.block_off[b + 1])
+        d0 = (o0 // scan.n_t) * scan.n_t
+        hi = min(o1, d0 + length)
+        if hi > o0:
+            offs.append((o0, hi))
+            bands.append(scan.block_band[b])
+    idx = np.concatenate([np.arange(a, b) for a, b in offs])
+    new_off = np.concatenate([[0], np.cumsum([b - a for a, b in offs])])
+    prob = O.Problem(pix[idx], scan.psi[idx], new_off, scan.band, np.array(bands), scan.n_pix)
+    blocks, hits = O.bd_blocks(prob)
+    g = good if good is not None else O.select_pixels(blocks, hits, rcond_min)
+    mbd = O.bd_inverse(blocks, g & (hits > 0))
+    return prob, mbd, idx
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def scan_and_tod(name_or_cfg, seed=0, sky=True, noise=True, **over):
+    if isinstance(name_or_cfg, str):
+        scan = synth.scan_from_config(name_or_cfg, seed=seed, **over)
+    else:
+        cfg = dict(name_or_cfg)
+        cfg.update(over)
+        scan = synth.make_scan(seed=seed, **cfg)
+    s = synth.make_sky(scan.n_pix, seed) if sky else None
+    n = synth.make_noise(scan, seed) if noise else None
+    d = synth.make_tod(scan, s, n)
+    return scan, d, s

@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: float64 operator 1e-11 relative (FFT rounding of a few ulp per
+pass); float32 operator 1e-5 relative on A x; solved maps 1e-6 relative to
+an oracle solution converged far below the PCG tolerance.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from helpers import oracle_problem, rel, scan_and_tod, truncated_problem
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1801_08937_gb300")
+MM = P.mapmaker
+
+TOL64 = 1e-11
+TOL32 = 1e-5
+
+
+def ctx_for(scan, prec=MM.MM_FP64, filt=0, fft_log2=0):
+    c = MM.Context(0, None, prec)
+    c.set_option("filter", filt)
+    if fft_log2:
+        c.set_option("fft_log2", fft_log2)
+    c.setup_scan(scan)
+    return c
+
+
+def ragged(scan, seed=0, min_len=40):
+    """Re-cut every detector timeline into blocks of uneven length."""
+    rng = np.random.default_rng(seed)
+    offs = [0]
+    bands = []
+    for d in range(scan.n_det):
+        t0, t1 = d * scan.n_t, (d + 1) * scan.n_t
+        cuts = np.sort(rng.choice(np.arange(t0 + min_len, t1 - min_len), size=3, replace=False))
+        pts = [p for p in cuts if p - offs[-1] >= min_len] + [t1]
+        for p in pts:
+            offs.append(int(p))
+            bands.append(d % scan.n_bands)
+    s = copy.copy(scan)
+    s.block_off = np.array(offs, dtype=np.int64)
+    s.block_band = np.array(bands, dtype=np.int32)
+    return s
+
+
+SMALL = dict(nx=8, ny=8, n_det=4, n_t=4096, n_int=4, half_bw=64, f_knee=1.0)
+
+
+@pytest.mark.parametrize("filt,fft_log2", [(1, 0), (2, 0), (2, 8), (2, 10)])
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_apply_A_matches_oracle(filt, fft_log2, prec):
+    scan = ragged(synth.make_scan(seed=1, flag_frac=0.01, **SMALL), seed=1)
+    prob = O.Problem.from_scan(scan)
+    c = ctx_for(scan, prec, filt, fft_log2)
+    x = np.random.default_rng(2).standard_normal((2, scan.n_pix, 3))
+    y = c.apply_A(x)
+    for r in range(2):
+        ref = O.apply_A(prob, x[r])
+        assert rel(y[r], ref) < (TOL64 if prec == MM.MM_FP64 else TOL32)
+
+
+@pytest.mark.parametrize("lam,blen", [(0, 512), (3, 512), (150, 100), (64, 65), (200, 4096)])
+def test_apply_A_band_edges(lam, blen):
+    """Bands wider than blocks, zero bands, one-tap bands: truncation at block edges."""
+    scan = synth.make_scan(nx=4, ny=4, n_det=2, n_t=blen * 4, n_int=4, half_bw=lam, f_knee=1.0, seed=3)
+    prob = O.Problem.from_scan(scan)
+    x = np.random.default_rng(3).standard_normal((scan.n_pix, 3))
+    ref = O.apply_A(prob, x)
+    for filt in (1, 2):
+        if filt == 2 and 2 * lam + 32 > (1 << 13):
+            continue
+        c = ctx_for(scan, MM.MM_FP64, filt)
+        assert rel(c.apply_A(x)[0], ref) < TOL64
+
+
+def test_apply_A_c1_full_size():
+    scan = synth.scan_from_config("c1", seed=0)
+    prob = O.Problem.from_scan(scan)
+    x = np.random.default_rng(4).standard_normal((scan.n_pix, 3))
+    ref = O.apply_A(prob, x)
+    for prec, tol in ((MM.MM_FP64, TOL64), (MM.MM_FP32_MIXED, TOL32)):
+        c = ctx_for(scan, prec)
+        assert rel(c.apply_A(x)[0], ref) < tol
+
+
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_rhs_matches_oracle(prec):
+    scan, d, _ = scan_and_tod(SMALL, seed=5, flag_frac=0.01)
+    prob = O.Problem.from_scan(scan)
+    c = ctx_for(scan, prec)
+    tod = d.astype(c.tod_dtype)
+    b = c.rhs(tod)
+    ref = O.rhs(prob, tod.astype(np.float64))
+    assert rel(b[0], ref) < TOL64
+
+
+def test_bd_build_and_apply_match_oracle():
+    scan = synth.make_scan(seed=6, flag_frac=0.02, **SMALL)
+    # make two pixels degenerate: a single angle and a single hit
+    scan.psi[scan.pix == 5] = 0.3
+    scan.pix[(scan.pix == 9)] = -1
+    scan.pix[100] = 9
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan)
+    dropped = c.build_bd(1e-3)
+    assert dropped == int((~good).sum())
+    r = np.random.default_rng(6).standard_normal((scan.n_pix, 3))
+    z = c.apply_precond(MM.MM_PRECOND_BD, r)
+    assert rel(z[0], O.bd_apply(mbd, r)) < 1e-12
+    # A after flagging equals the oracle's A on the flagged pointing
+    x = np.random.default_rng(7).standard_normal((scan.n_pix, 3))
+    assert rel(c.apply_A(x)[0], O.apply_A(prob, x)) < TOL64
+
+
+def _oracle_solution(prob, mbd, b):
+    return O.pcg(lambda v: O.apply_A(prob, v).reshape(-1), lambda v: O.bd_apply(mbd, v).reshape(-1),
+                 b.reshape(-1), tol=1e-13, max_iter=5000)[0]
+
+
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_solve_bd_matches_oracle(prec):
+    scan, d, _ = scan_and_tod(SMALL, seed=8)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan, prec)
+    c.build_bd()
+    tod = d.astype(c.tod_dtype)
+    x, info = c.solve(tod, MM.MM_PRECOND_BD, tol=1e-10, max_iter=2000)
+    assert info[0]["status"] == "MM_OK"
+    assert info[0]["true_rel_res"] < 1e-9
+    b = O.rhs(prob, tod.astype(np.float64))
+    xo = _oracle_solution(prob, mbd, b)
+    assert rel(x[0], xo) < 1e-6
+
+
+def test_signal_only_recovers_sky():
+    scan, d, s = scan_and_tod(SMALL, seed=9, noise=False)
+    prob, mbd, good = oracle_problem(scan)
+    s[~good] = 0
+    d = synth.make_tod(scan, s, None)
+    c = ctx_for(scan)
+    c.build_bd()
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-12, max_iter=3000)
+    assert rel(x[0], s) < 1e-8
+
+
+def test_white_noise_converges_in_one_iteration():
+    scan, d, _ = scan_and_tod(dict(SMALL, half_bw=0, f_knee=0.0), seed=10)
+    c = ctx_for(scan)
+    c.build_bd()
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=50)
+    assert info[0]["iters"] == 1
+
+
+def test_coarse_space_identities_and_ritz_values():
+    scan, d, _ = scan_and_tod(SMALL, seed=11)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan)
+    c.build_bd()
+    b = c.rhs(d)
+    k = c.build_coarse(b[0], m_max=12, eps_arn=1e-14, k=6)
+    assert k == 6
+    Z, ritz = c.get_coarse()
+    # oracle Arnoldi from the same start
+    A_fn = lambda v: O.apply_A(prob, v).reshape(-1)  # noqa: E731
+    M_fn = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+    bo = O.rhs(prob, d).reshape(-1)
+    W, H, m = O.arnoldi(lambda v: M_fn(A_fn(v)), M_fn(bo), 12, 1e-14)
+    Zo, vals = O.ritz_basis(W, H, m, 6)
+    np.testing.assert_allclose(np.sort(ritz), np.sort(vals), rtol=1e-7, atol=1e-9)
+    # same subspace: projector difference
+    Zg = Z.reshape(k, -1).T
+    Pg = Zg @ Zg.T
+    Po = Zo @ Zo.T
+    assert np.linalg.norm(Pg - Po) < 1e-6
+    # Eq. ident: M_2l A Z = Z, through the library's own operators
+    AZ = c.apply_A(Z)
+    MAZ = c.apply_precond(MM.MM_PRECOND_2L, AZ)
+    assert rel(MAZ, Z) < 1e-10
+    # M_2l A y = M_BD A y for y with Z^T A y = 0
+    y = np.random.default_rng(11).standard_normal((scan.n_pix, 3))
+    y[~good] = 0
+    Ay = c.apply_A(y)[0].reshape(-1)
+    AZf = AZ.reshape(k, -1).T
+    E = Zg.T @ AZf
+    y = y.reshape(-1) - Zg @ np.linalg.solve(E, AZf.T @ y.reshape(-1))
+    y = y.reshape(scan.n_pix, 3)
+    Ay = c.apply_A(y)
+    np.testing.assert_allclose(c.apply_precond(MM.MM_PRECOND_2L, Ay), c.apply_precond(MM.MM_PRECOND_BD, Ay),
+                               atol=1e-9 * np.abs(Ay).max())
+
+
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_solve_2l_beats_bd_and_matches_oracle(prec):
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=2048, n_int=2, half_bw=64, f_knee=2.0)
+    scan, d, _ = scan_and_tod(cfg, seed=12)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan, prec)
+    c.build_bd()
+    tod = d.astype(c.tod_dtype)
+    xbd, ibd = c.solve(tod, MM.MM_PRECOND_BD, tol=1e-8, max_iter=2000)
+    k = c.build_coarse(None, m_max=60, eps_arn=1e-10, k=8)
+    assert k == 8
+    x2l, i2l = c.solve(tod, MM.MM_PRECOND_2L, tol=1e-8, max_iter=2000)
+    assert i2l[0]["status"] == "MM_OK" and ibd[0]["status"] == "MM_OK"
+    assert i2l[0]["iters"] < ibd[0]["iters"]
+    xo = _oracle_solution(prob, mbd, O.rhs(prob, tod.astype(np.float64)))
+    assert rel(x2l[0], xo) < 1e-6
+    assert rel(xbd[0], xo) < 1e-6
+
+
+def test_batched_uneven_lengths_match_standalone_and_oracle():
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=8192, n_int=8, half_bw=32, f_knee=1.0)
+    scan = synth.make_scan(seed=13, **cfg)
+    lens = np.array([8192, 5000, 6143, 4097, 7777], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 100 + i), synth.make_noise(scan, 100 + i))
+                     for i in range(len(lens))])
+    c = ctx_for(scan)
+    c.build_bd()
+    xb, ib = c.solve(tods, MM.MM_PRECOND_BD, tol=1e-10, max_iter=3000, rhs_len=lens)
+    _, _, good = oracle_problem(scan)
+    for i, L in enumerate(lens):
+        assert ib[i]["status"] == "MM_OK"
+        xs, is_ = c.solve(tods[i:i + 1], MM.MM_PRECOND_BD, tol=1e-10, max_iter=3000, rhs_len=lens[i:i + 1])
+        assert rel(xb[i], xs[0]) < 1e-8
+        prob, mbd, idx = truncated_problem(scan, int(L), good=good)
+        b = O.rhs(prob, tods[i][idx])
+        xo = _oracle_solution(prob, mbd, b)
+        assert rel(xb[i], xo) < 1e-6
+
+
+def test_device_pointers_and_stepwise_api():
+    torch = pytest.importorskip("torch")
+    scan, d, _ = scan_and_tod(SMALL, seed=14)
+    c = ctx_for(scan)
+    c.build_bd()
+    dt = torch.from_numpy(d).cuda()
+    x_host, info_h = c.solve(d, MM.MM_PRECOND_BD, tol=1e-9)
+    x_dev, info_d = c.solve(dt, MM.MM_PRECOND_BD, tol=1e-9)
+    assert rel(x_dev.cpu().numpy()[0], x_host[0]) < 1e-9
+    c.solve_begin(d, MM.MM_PRECOND_BD, tol=1e-9)
+    done = False
+    steps = 0
+    while not done:
+        done = c.solve_step(3)
+        steps += 1
+    x_step, info_s = c.solve_end()
+    assert rel(x_step[0], x_host[0]) < 1e-9
+    assert info_s[0]["iters"] == info_h[0]["iters"]
+
+
+def test_errors_are_reported():
+    c = MM.Context(0, None, MM.MM_FP64)
+    with pytest.raises(MM.MapMakerError) as e:
+        c.build_bd()
+    assert e.value.status == MM.MM_ERR_STATE
+    scan = synth.make_scan(seed=0, **SMALL)
+    bad = scan.pix.copy()
+    bad[3] = scan.n_pix
+    with pytest.raises(MM.MapMakerError) as e:
+        c.setup_pointing(bad, scan.psi, scan.block_off, scan.block_band, scan.band, scan.n_pix, scan.n_det)
+    assert e.value.status == MM.MM_ERR_ARG
+    with pytest.raises(MM.MapMakerError):
+        c.set_option("filter", 7)

@@ -71,7 +71,12 @@ struct mm_ctx {
 
     // options
     int opt_filter = 0, opt_fft_log2 = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
+    int opt_time_filter = 0;
     double last_apply_ms = 0.0;
+    // CUDA-event pairs around filter launches (when timing is on)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fev;
+    size_t fev_used = 0;
+    bool capturing = false;
 
     // pointing
     bool have_pointing = false;
@@ -339,6 +344,18 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
     a.V = plan->V;
     a.state = st;
     a.tod_is_float = tod_is_float;
+    cudaEvent_t e1 = nullptr;
+    if (ctx->opt_time_filter && !ctx->capturing) {
+        if (ctx->fev_used == ctx->fev.size()) {
+            std::pair<cudaEvent_t, cudaEvent_t> pr;
+            CK(cudaEventCreate(&pr.first));
+            CK(cudaEventCreate(&pr.second));
+            ctx->fev.push_back(pr);
+        }
+        auto& pr = ctx->fev[ctx->fev_used++];
+        CK(cudaEventRecord(pr.first, ctx->stream));
+        e1 = pr.second;
+    }
     if (plan->variant == 2) {
         FftTables& ft = plan->f64 ? ctx->fft64 : ctx->fft32;
         a.H = ft.H.p;
@@ -351,6 +368,7 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         else launch_filter_direct_f32(a, from_tod, ctx->stream);
     }
     CKL();
+    if (e1) CK(cudaEventRecord(e1, ctx->stream));
     return MM_OK;
 }
 
@@ -637,6 +655,10 @@ mm_status mm_destroy(mm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     destroy_graph(ctx);
+    for (auto& pr : ctx->fev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -1207,8 +1229,10 @@ mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done) {
                 TRY(pcg_iteration(ctx));
                 cudaGraph_t g;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                ctx->capturing = true;
                 mm_status s = MM_OK;
                 for (int i = 0; i < n_iter && s == MM_OK; ++i) s = pcg_iteration(ctx);
+                ctx->capturing = false;
                 cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
                 if (s != MM_OK) return s;
                 CK(e);
@@ -1307,6 +1331,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_check_every = v;
     } else if (n == "graphs") {
         ctx->opt_graphs = v ? 1 : 0;
+    } else if (n == "time_filter") {
+        ctx->opt_time_filter = v ? 1 : 0;
+        ctx->fev_used = 0;
     } else {
         return fail(ctx, MM_ERR_ARG, "unknown option " + n);
     }
@@ -1322,6 +1349,20 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "check_every") *value = ctx->opt_check_every;
     else if (n == "graphs") *value = ctx->opt_graphs;
     else if (n == "last_apply_ms") *value = ctx->last_apply_ms;
+    else if (n == "kernel_launches") *value = (double)launches_total();
+    else if (n == "time_filter") *value = ctx->opt_time_filter;
+    else if (n == "filter_ms" || n == "filter_launches") {
+        // total device time of the filter launches timed since the last read; resets the record
+        CK(cudaStreamSynchronize(ctx->stream));
+        double tot = 0.0;
+        for (size_t i = 0; i < ctx->fev_used; ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->fev[i].first, ctx->fev[i].second));
+            tot += ms;
+        }
+        *value = n == "filter_ms" ? tot : (double)ctx->fev_used;
+        if (n == "filter_ms") ctx->fev_used = 0;
+    }
     else if (n == "plan_fft_log2") {
         Plan* p = nullptr;
         if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");

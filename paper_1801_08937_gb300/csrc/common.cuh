@@ -18,6 +18,10 @@
 
 namespace mm {
 
+// Kernels launched by this library since load (every launcher adds its count).
+long long launches_total();
+void count_launches(int n);
+
 template <typename T> struct __align__(sizeof(T) * 4) V4 { T x, y, z, w; };
 template <typename T> struct __align__(sizeof(T) * 2) C2 { T x, y; };
 

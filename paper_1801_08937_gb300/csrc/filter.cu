@@ -19,6 +19,10 @@
 
 namespace mm {
 
+static long long g_launches = 0;
+long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+void count_launches(int n) { __atomic_fetch_add(&g_launches, (long long)n, __ATOMIC_RELAXED); }
+
 constexpr int FFT_NT = 256;
 constexpr int DIRECT_NT = 256;
 
@@ -427,6 +431,7 @@ static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
         configured = sm;
     }
     k_filter_fft<T, FROM_TOD><<<a.n_work, FFT_NT, sm, s>>>(a);
+    count_launches(1);
 }
 template <typename T, bool FROM_TOD>
 static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
@@ -438,6 +443,7 @@ static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
         configured = sm;
     }
     k_filter_direct<T, FROM_TOD><<<a.n_work, DIRECT_NT, sm, s>>>(a);
+    count_launches(1);
 }
 
 void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s) {
@@ -462,12 +468,14 @@ void launch_fft_spectrum(const double* h, double* H_out, double2* work, const do
     if (n_bands <= 0) return;
     k_fft_spectrum<<<n_bands, 256, 0, s>>>(h, H_out, reinterpret_cast<C2<double>*>(work),
                                            reinterpret_cast<const C2<double>*>(tw), L, logL);
+    count_launches(1);
 }
 
 void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t blocks = (n + 255) / 256;
     k_weights64<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(psi, cs, n);
+    count_launches(1);
 }
 
 }  // namespace mm

@@ -103,16 +103,28 @@ static int grid_for(int64_t n) {
     return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
 }
 void launch_map_in(const double* src3, V4<double>* dst4, int64_t n, cudaStream_t s) {
-    if (n > 0) k_map_in<<<grid_for(n), VT, 0, s>>>(src3, dst4, n);
+    if (n > 0) {
+        k_map_in<<<grid_for(n), VT, 0, s>>>(src3, dst4, n);
+        count_launches(1);
+    }
 }
 void launch_map_out(const V4<double>* src4, double* dst3, int64_t n, cudaStream_t s) {
-    if (n > 0) k_map_out<<<grid_for(n), VT, 0, s>>>(src4, dst3, n);
+    if (n > 0) {
+        k_map_out<<<grid_for(n), VT, 0, s>>>(src4, dst3, n);
+        count_launches(1);
+    }
 }
 void launch_to_f32(const V4<double>* src, V4<float>* dst, int64_t n, cudaStream_t s) {
-    if (n > 0) k_to_f32<<<grid_for(n), VT, 0, s>>>(src, dst, n);
+    if (n > 0) {
+        k_to_f32<<<grid_for(n), VT, 0, s>>>(src, dst, n);
+        count_launches(1);
+    }
 }
 void launch_from_f32(const V4<float>* src, V4<double>* dst, int64_t n, cudaStream_t s) {
-    if (n > 0) k_from_f32<<<grid_for(n), VT, 0, s>>>(src, dst, n);
+    if (n > 0) {
+        k_from_f32<<<grid_for(n), VT, 0, s>>>(src, dst, n);
+        count_launches(1);
+    }
 }
 void launch_zero(void* p, size_t bytes, cudaStream_t s) {
     if (bytes) cudaMemsetAsync(p, 0, bytes, s);
@@ -192,7 +204,11 @@ void launch_bd_accumulate(const int32_t* pix, const float* psi, const int64_t* b
     if (n_blocks <= 0) return;
     k_bd_accumulate<<<n_blocks, VT, 0, s>>>(pix, psi, block_off, block_band, band, lam1, n_t, sorted_len, nrhs, sums,
                                             n_pix);
-    if (nrhs > 1) k_bd_prefix<<<grid_for((int64_t)n_pix * 7), VT, 0, s>>>(sums, n_pix, nrhs);
+    count_launches(1);
+    if (nrhs > 1) {
+        k_bd_prefix<<<grid_for((int64_t)n_pix * 7), VT, 0, s>>>(sums, n_pix, nrhs);
+        count_launches(1);
+    }
 }
 
 // Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations.
@@ -273,6 +289,7 @@ void launch_bd_invert(const double* sums, double* bd, uint8_t* good, int* n_drop
                       double rcond_min, int set_good, cudaStream_t s) {
     k_bd_invert<<<grid_for((int64_t)n_pix * nrhs), VT, 0, s>>>(sums, bd, good, n_dropped, n_pix, nrhs, rcond_min,
                                                               set_good);
+    count_launches(1);
 }
 
 __global__ void k_flag_samples(int32_t* pix, const uint8_t* good, int64_t n) {
@@ -282,7 +299,10 @@ __global__ void k_flag_samples(int32_t* pix, const uint8_t* good, int64_t n) {
     }
 }
 void launch_flag_samples(int32_t* pix, const uint8_t* good, int64_t n, cudaStream_t s) {
-    if (n > 0) k_flag_samples<<<grid_for(n), VT, 0, s>>>(pix, good, n);
+    if (n > 0) {
+        k_flag_samples<<<grid_for(n), VT, 0, s>>>(pix, good, n);
+        count_launches(1);
+    }
 }
 
 __global__ void k_bd_apply(const double* bd, int per_rhs, const V4<double>* x, V4<double>* y, int n_pix) {
@@ -296,6 +316,7 @@ void launch_bd_apply(const double* bd, int bd_per_rhs, const V4<double>* x, V4<d
                      cudaStream_t s) {
     dim3 g(grid_for(n_pix), nrhs);
     k_bd_apply<<<g, VT, 0, s>>>(bd, bd_per_rhs, x, y, n_pix);
+    count_launches(1);
 }
 
 // ---------------- PCG ----------------
@@ -546,23 +567,37 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
 
 void launch_pcg_init(const PcgArgs& a, const V4<double>* b, cudaStream_t s) {
     k_pcg_init<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a, b);
+    count_launches(1);
 }
 void launch_pcg_src(const PcgArgs& a, int first, cudaStream_t s) {
     k_pcg_src<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a, first);
+    count_launches(1);
 }
-void launch_pcg_pq(const PcgArgs& a, cudaStream_t s) { k_pcg_pq<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a); }
+void launch_pcg_pq(const PcgArgs& a, cudaStream_t s) {
+    k_pcg_pq<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a);
+    count_launches(1);
+}
 void launch_pcg_update(const PcgArgs& a, int two_level, cudaStream_t s) {
-    if (two_level) k_pcg_update<1><<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a);
-    else k_pcg_update<0><<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a);
+    if (two_level) {
+        k_pcg_update<1><<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a);
+        count_launches(1);
+    }
+    else {
+        k_pcg_update<0><<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a);
+        count_launches(1);
+    }
 }
 void launch_precond_bd_dot(const PcgArgs& a, int finalize_beta, cudaStream_t s) {
     k_bd_dot<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a, finalize_beta);
+    count_launches(1);
 }
 void launch_m2l_ztr(const PcgArgs& a, const V4<double>* v, cudaStream_t s) {
     k_m2l_ztr<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a, v);
+    count_launches(1);
 }
 void launch_m2l_apply(const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta, cudaStream_t s) {
     k_m2l_apply<<<dim3(a.grid_x, a.nrhs), VT, 0, s>>>(a, v, out, finalize_beta);
+    count_launches(1);
 }
 
 // ---------------- tall-skinny float64 products ----------------
@@ -591,6 +626,7 @@ void launch_multidot(const double* X, int64_t ldx, int m, const double* v, int64
                      unsigned* counter, int grid_x, cudaStream_t s) {
     if (m <= 0) return;
     k_multidot<<<grid_x, VT, 0, s>>>(X, ldx, m, v, n, h, partial, counter);
+    count_launches(1);
 }
 
 __global__ void k_sub_combo(const double* X, int64_t ldx, int m, const double* h, double* v, int64_t n) {
@@ -606,6 +642,7 @@ __global__ void k_sub_combo(const double* X, int64_t ldx, int m, const double* h
 void launch_sub_combo(const double* X, int64_t ldx, int m, const double* h, double* v, int64_t n, cudaStream_t s) {
     if (m <= 0) return;
     k_sub_combo<<<grid_for(n), VT, m * sizeof(double), s>>>(X, ldx, m, h, v, n);
+    count_launches(1);
 }
 
 // Y[c][i] = sum_r X[r][i] C[r*kc + c], eight outputs per pass.
@@ -630,6 +667,7 @@ void launch_combo(const double* X, int64_t ldx, int m, const double* C, int kc, 
                   cudaStream_t s) {
     if (kc <= 0) return;
     k_combo<<<grid_for(n), VT, 0, s>>>(X, ldx, m, C, kc, Y, ldy, n);
+    count_launches(1);
 }
 
 void launch_gram(const double* X, int mx, const double* Y, int my, int64_t ld, int64_t n, double* G, double* partial,
@@ -637,6 +675,7 @@ void launch_gram(const double* X, int mx, const double* Y, int my, int64_t ld, i
     // column j of G^T: G[i][j] = X_i . Y_j, as multidots against each Y_j
     for (int j = 0; j < my; ++j) {
         k_multidot<<<grid_x, VT, 0, s>>>(X, ld, mx, Y + (int64_t)j * ld, n, G + (int64_t)j * mx, partial, counter);
+        count_launches(1);
     }
 }
 
@@ -644,7 +683,10 @@ __global__ void k_scale(double* v, int64_t n, double f) {
     for (int64_t i = blockIdx.x * (int64_t)VT + threadIdx.x; i < n; i += (int64_t)gridDim.x * VT) v[i] *= f;
 }
 void launch_scale_host(double* v, int64_t n, double f, cudaStream_t s) {
-    if (n > 0) k_scale<<<grid_for(n), VT, 0, s>>>(v, n, f);
+    if (n > 0) {
+        k_scale<<<grid_for(n), VT, 0, s>>>(v, n, f);
+        count_launches(1);
+    }
 }
 
 }  // namespace mm
@@ -674,6 +716,7 @@ __global__ void k_residual(const V4<double>* b, const V4<double>* q, V4<double>*
 void launch_residual(const V4<double>* b, const V4<double>* q, V4<double>* r_out, double* norms, int n_pix, int nrhs,
                      double* partial, unsigned* counter, int grid_x, cudaStream_t s) {
     k_residual<<<dim3(grid_x, nrhs), VT, 0, s>>>(b, q, r_out, norms, n_pix, nrhs, partial, counter);
+    count_launches(1);
 }
 
 // y += x over n doubles, only for right-hand sides whose mask entry is set.
@@ -687,6 +730,7 @@ __global__ void k_axpy_masked(double* y, const double* x, int64_t n_per, const i
 void launch_axpy_masked(double* y, const double* x, int64_t n_per, int nrhs, const int32_t* mask, cudaStream_t s) {
     if (n_per <= 0 || nrhs <= 0) return;
     k_axpy_masked<<<dim3(grid_for(n_per), nrhs), VT, 0, s>>>(y, x, n_per, mask);
+    count_launches(1);
 }
 
 }  // namespace mm

@@ -113,6 +113,28 @@ template <typename T> struct Dft<T, 16> {
     }
 };
 
+// Powers w^q, q < R, of one twiddle by repeated products of depth <= 4
+// (one table load per butterfly instead of R - 1).
+template <typename T, int R>
+__device__ __forceinline__ void twiddle_powers(C2<T> w1, C2<T>* w) {
+    w[1] = w1;
+    if (R > 2) {
+        w[2] = cmul(w1, w1);
+        w[3] = cmul(w[2], w1);
+    }
+    if (R > 4) {
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[4], w1);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+    if (R > 8) {
+        w[8] = cmul(w[4], w[4]);
+#pragma unroll
+        for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
+    }
+}
+
 // Decimation-in-frequency pass of radix R over spans of 2^logS (in place):
 // for each butterfly j < S/R of each span, DFT_R over elements j + r S/R,
 // then output q times W_S^(j q).  Natural order in, digit-reversed out.
@@ -125,13 +147,17 @@ __device__ __forceinline__ void dif_pass(C2<T>* s, const C2<T>* __restrict__ tw,
         const int g = bf >> logSr;
         const int j = bf & ((1 << logSr) - 1);
         const int base = (g << logS) + j;
+        C2<T> w1{T(1), T(0)};
+        if (logSr > 0) w1 = ldtw(tw, j << tsh);
         C2<T> a[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) a[r] = s[sidx(base + (r << logSr))];
         Dft<T, R>::run(a);
         if (logSr > 0) {
+            C2<T> w[R];
+            twiddle_powers<T, R>(w1, w);
 #pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], ldtw(tw, (j * q) << tsh));
+            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) s[sidx(base + (q << logSr))] = a[q];
@@ -150,12 +176,16 @@ __device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw,
         const int g = bf >> logSr;
         const int j = bf & ((1 << logSr) - 1);
         const int base = (g << logS) + j;
+        C2<T> w1{T(1), T(0)};
+        if (logSr > 0) w1 = ldtw(tw, j << tsh);
         C2<T> a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) a[q] = s[sidx(base + (q << logSr))];
         if (logSr > 0) {
+            C2<T> w[R];
+            twiddle_powers<T, R>(w1, w);
 #pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], ldtw(tw, (j * q) << tsh));
+            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
         }
         Dft<T, R>::run(a);
 #pragma unroll
@@ -222,6 +252,19 @@ __device__ __forceinline__ void weights(const FilterArgs& a, int64_t t, double& 
     s = v.y;
 }
 
+__device__ __forceinline__ void weights_from(const FilterArgs& a, int64_t t, float psi, float& c, float& s) {
+    const float x = fmaf(2.0f, psi, -3.14159265358979323846f);
+    float sn, cs;
+    __sincosf(x, &sn, &cs);
+    c = -cs;
+    s = -sn;
+}
+__device__ __forceinline__ void weights_from(const FilterArgs& a, int64_t t, float, double& c, double& s) {
+    const double2 v = __ldg(a.cs64 + t);
+    c = v.x;
+    s = v.y;
+}
+
 template <typename T>
 __device__ __forceinline__ V4<T> ldmap(const V4<T>* m);
 template <>
@@ -249,6 +292,76 @@ __device__ __forceinline__ T sample_value(const FilterArgs& a, int64_t t, int rh
         weights(a, t, c, s);
         const V4<T> m = ldmap<T>(reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix + p);
         return m.x + c * m.y + s * m.z;
+    }
+}
+
+// Gather of a segment pair into s[i] = (y_A[out0_A - lambda + i], y_B[...]),
+// zero outside each block.  Loads are issued GB iterations at a time (index
+// and angle first, then the map entries) to keep many requests in flight.
+template <typename T, bool FROM_TOD>
+__device__ __forceinline__ void gather_pair(const FilterArgs& a, const Seg& A, const Seg& B, bool actA, bool actB,
+                                            C2<T>* s, int L, int lam) {
+    constexpr int GB = 4;
+    const int nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < L; i0 += nt * GB) {
+        int pa[GB], pb[GB];
+        float fa[GB], fb[GB];
+        T ya[GB], yb[GB];
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int i = i0 + g * nt;
+            const int64_t ta = A.out0 - lam + i, tb = B.out0 - lam + i;
+            const bool va = actA && i < L && ta >= A.lo && ta < A.hi;
+            const bool vb = actB && i < L && tb >= B.lo && tb < B.hi;
+            pa[g] = -1;
+            pb[g] = -1;
+            ya[g] = T(0);
+            yb[g] = T(0);
+            if (FROM_TOD) {
+                if (va) ya[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + A.rhs * a.n_samples + ta))
+                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + A.rhs * a.n_samples + ta));
+                if (vb) yb[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + B.rhs * a.n_samples + tb))
+                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + B.rhs * a.n_samples + tb));
+            } else {
+                if (va) {
+                    pa[g] = __ldg(a.pix + ta);
+                    if (sizeof(T) == 4) fa[g] = __ldg(a.psi + ta);
+                }
+                if (vb) {
+                    pb[g] = __ldg(a.pix + tb);
+                    if (sizeof(T) == 4) fb[g] = __ldg(a.psi + tb);
+                }
+            }
+        }
+        if (!FROM_TOD) {
+            const V4<T>* mapA = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)A.rhs * a.n_pix;
+            const V4<T>* mapB = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)B.rhs * a.n_pix;
+            V4<T> ma[GB], mb[GB];
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+                if (pa[g] >= 0) ma[g] = ldmap<T>(mapA + pa[g]);
+                if (pb[g] >= 0) mb[g] = ldmap<T>(mapB + pb[g]);
+            }
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+                const int i = i0 + g * nt;
+                if (pa[g] >= 0) {
+                    T c, sn;
+                    weights_from(a, A.out0 - lam + i, fa[g], c, sn);
+                    ya[g] = ma[g].x + c * ma[g].y + sn * ma[g].z;
+                }
+                if (pb[g] >= 0) {
+                    T c, sn;
+                    weights_from(a, B.out0 - lam + i, fb[g], c, sn);
+                    yb[g] = mb[g].x + c * mb[g].y + sn * mb[g].z;
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int i = i0 + g * nt;
+            if (i < L) s[sidx(i)] = C2<T>{ya[g], yb[g]};
+        }
     }
 }
 
@@ -316,7 +429,7 @@ __device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
 
 // ---------------- FFT overlap-save variant ----------------
 template <typename T, bool FROM_TOD>
-__global__ void __launch_bounds__(FFT_NT) k_filter_fft(const FilterArgs a) {
+__global__ void __launch_bounds__(FFT_NT, sizeof(T) == 4 ? 3 : 1) k_filter_fft(const FilterArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
     const Seg A = a.segs[2 * blockIdx.x];
@@ -327,18 +440,7 @@ __global__ void __launch_bounds__(FFT_NT) k_filter_fft(const FilterArgs a) {
     const int L = a.L, lam = a.lam, logL = a.logL;
     const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
 
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        T ya = T(0), yb = T(0);
-        if (actA) {
-            const int64_t t = A.out0 - lam + i;
-            if (t >= A.lo && t < A.hi) ya = sample_value<T, FROM_TOD>(a, t, A.rhs);
-        }
-        if (actB) {
-            const int64_t t = B.out0 - lam + i;
-            if (t >= B.lo && t < B.hi) yb = sample_value<T, FROM_TOD>(a, t, B.rhs);
-        }
-        s[sidx(i)] = C2<T>{ya, yb};
-    }
+    gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
     __syncthreads();
     fft_dif<T>(s, tw, logL);
     const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
@@ -352,12 +454,44 @@ __global__ void __launch_bounds__(FFT_NT) k_filter_fft(const FilterArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int vmax = max(actA ? A.n_out : 0, actB ? B.n_out : 0);
-    for (int base = warp * 32; base < vmax; base += nwarp * 32) {
-        const int i = base + lane;
-        const int ii = min(lam + i, L - 1);
-        const C2<T> v = s[sidx(ii)];
-        scatter_one<T>(a, A, actA, i, v.x);
-        scatter_one<T>(a, B, actB, i, -v.y);
+    constexpr int SB = 2;
+    V4<T>* qA = reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(actA ? A.rhs : 0) * a.n_pix;
+    V4<T>* qB = reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(actB ? B.rhs : 0) * a.n_pix;
+    for (int base = warp * 32; base < vmax; base += nwarp * 32 * SB) {
+        int pa[SB], pb[SB];
+        float fa[SB], fb[SB];
+#pragma unroll
+        for (int g = 0; g < SB; ++g) {
+            const int i = base + g * nwarp * 32 + lane;
+            pa[g] = -1;
+            pb[g] = -1;
+            if (actA && i < A.n_out) {
+                pa[g] = __ldg(a.pix + A.out0 + i);
+                if (sizeof(T) == 4) fa[g] = __ldg(a.psi + A.out0 + i);
+            }
+            if (actB && i < B.n_out) {
+                pb[g] = __ldg(a.pix + B.out0 + i);
+                if (sizeof(T) == 4) fb[g] = __ldg(a.psi + B.out0 + i);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < SB; ++g) {
+            const int i = base + g * nwarp * 32 + lane;
+            const C2<T> v = s[sidx(min(lam + i, L - 1))];
+            T c = T(0), sn = T(0), za = T(0), zb = T(0);
+            if (pa[g] >= 0) {
+                weights_from(a, A.out0 + i, fa[g], c, sn);
+                za = v.x;
+            }
+            scatter_warp<T>(pa[g], c, sn, za, qA);
+            c = T(0);
+            sn = T(0);
+            if (pb[g] >= 0) {
+                weights_from(a, B.out0 + i, fb[g], c, sn);
+                zb = -v.y;
+            }
+            scatter_warp<T>(pb[g], c, sn, zb, qB);
+        }
     }
 }
 
@@ -428,6 +562,7 @@ static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
     static size_t configured = 0;
     if (sm > configured) {
         cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured = sm;
     }
     k_filter_fft<T, FROM_TOD><<<a.n_work, FFT_NT, sm, s>>>(a);

@@ -211,6 +211,26 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
 mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done);
 mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem);
 
+/* M_2l applied without allocating device memory during the call (the paper
+ * has no counterpart; this is a deployment variant of mm_apply_precond).
+ * For callers that must not call cudaMalloc/cudaFree while they run: latency-
+ * critical serving loops (allocation can synchronise the device and can fail
+ * under memory pressure) and host applications or plug-ins whose device
+ * memory belongs to another allocator.
+ *  x, y   [nrhs][n_pix][3] float64, DEVICE memory on the context's device,
+ *         owned by the caller; y = M_2l x as mm_apply_precond computes it.
+ *  Needs mm_build_bd and a coarse space (those calls allocate; this one
+ *  does not).  Reduction scratch lives in a fixed 1 MiB device array inside
+ *  the library, held by every GPU that loads it until the process exits.
+ *  Limits: nrhs <= 128, k <= 128 and 2 * nrhs * k + 64 <= 131072; larger
+ *  requests return MM_ERR_ARG.  The first call on a device looks up the
+ *  array's device address (cudaGetSymbolAddress); make that first call
+ *  before any stream capture.  All calls share the array, so calls that
+ *  overlap on the GPU (other streams or threads) race; serialise them.
+ *  Returns after the result is complete.  Errors: MM_ERR_ARG, MM_ERR_STATE,
+ *  MM_ERR_CUDA. */
+mm_status mm_apply_precond_2l_noalloc(mm_ctx* ctx, const double* x, double* y, int32_t nrhs);
+
 /* Device bytes a context needs for a problem of this shape (pointing, maps,
  * PCG state, Arnoldi basis of m_max vectors and k coarse vectors), for
  * admission control.  Pure host arithmetic. */

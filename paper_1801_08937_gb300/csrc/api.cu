@@ -630,6 +630,27 @@ mm_status finish_coarse(mm_ctx* ctx) {
 
 }  // namespace
 
+namespace mm {
+// Read-only view of a context's M_BD and coarse space for other translation units.
+bool ctx_coarse_view(mm_ctx* ctx, CoarseView* v) {
+    if (!ctx) return false;
+    v->device = ctx->device;
+    v->stream = ctx->stream;
+    v->n_pix = ctx->n_pix;
+    v->k = ctx->k;
+    v->grid_x = ctx->grid_x;
+    v->have_bd = ctx->have_bd;
+    v->bd = ctx->d_bd.as<double>();
+    v->Z = ctx->d_Z.as<V4<double>>();
+    v->AZ = ctx->d_AZ.as<V4<double>>();
+    v->Einv = ctx->d_Einv.as<double>();
+    return true;
+}
+void ctx_set_error(mm_ctx* ctx, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+}
+}  // namespace mm
+
 // =====================================================================
 extern "C" {
 

@@ -154,6 +154,18 @@ void launch_residual(const V4<double>* b, const V4<double>* q, V4<double>* r_out
 void launch_axpy_masked(double* y, const double* x, int64_t n_per, int nrhs, const int32_t* mask,
                         cudaStream_t s);
 
+// Read-only view of a context's preconditioner state (defined with the context).
+struct CoarseView {
+    int device;
+    cudaStream_t stream;
+    int n_pix, k, grid_x;
+    bool have_bd;
+    const double* bd;
+    const V4<double>* Z;
+    const V4<double>* AZ;
+    const double* Einv;
+};
+
 // ---------------- host linear algebra ----------------
 // Eigenvalues and right eigenvectors of a real m x m matrix (row-major),
 // via complex shifted QR and inverse iteration.  Returns false on failure.

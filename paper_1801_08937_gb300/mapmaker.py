@@ -53,6 +53,7 @@ SIGNATURES = [
     ("mm_solve_step", C.c_int, [_VP, _I32, C.POINTER(_I32)]),
     ("mm_solve_end", C.c_int, [_VP, _VP, C.POINTER(mm_solve_info), C.c_int]),
     ("mm_estimate_bytes", C.c_int64, [_I64, _I32, _I32, _I32, _I32, _I32, _I32, C.c_int]),
+    ("mm_apply_precond_2l_noalloc", C.c_int, [_VP, _VP, _VP, _I32]),
 ]
 
 _lib = None
@@ -202,6 +203,16 @@ class Context:
         px, m1, k1 = _arg(x, np.float64)
         po, m2, k2 = _arg(out, np.float64, writable=True)
         self._check(self.lib.mm_apply_precond(self.h, int(which), px, po, nrhs, _mem(m1, m2)))
+        return out
+
+    def apply_precond_2l_noalloc(self, x, out):
+        """y = M_2l x into a caller-owned device array; the call allocates no device memory."""
+        nrhs = int(np.prod(x.shape) // (3 * self.n_pix))
+        px, m1, k1 = _arg(x, np.float64)
+        po, m2, k2 = _arg(out, np.float64, writable=True)
+        if m1 != MM_DEVICE or m2 != MM_DEVICE:
+            raise ValueError("apply_precond_2l_noalloc takes device arrays only")
+        self._check(self.lib.mm_apply_precond_2l_noalloc(self.h, px, po, nrhs))
         return out
 
     def build_coarse(self, b=None, m_max=200, eps_arn=1e-8, k=32, eps_lambda=0.2) -> int:

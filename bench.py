@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-bd", action="store_true", help="skip the M_BD comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve"],
+                    help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream")
+    ap.add_argument("--n-rhs", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -190,6 +194,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
+    if args.mode == "mc":
+        return run_mc(args, world, rank, local)
+    if args.mode == "serve":
+        return run_serve(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -387,6 +395,193 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------- batched Monte Carlo (c3) ----------------
+def run_mc(args, world, rank, local):
+    """64 right-hand sides of uneven length on the c1 geometry, one launch per
+    PCG iteration for all of them, iterations replayed from a CUDA graph; the
+    coarse space comes from the master scan once (simplified approach)."""
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    torch.cuda.set_device(local)
+    seed = rank
+    scan = synth.scan_from_config("c3", seed=seed)
+    lens = synth.mc_lengths(args.n_rhs, 1 << 19, 1 << 20, seed)
+    t_gen = time.time()
+    tods = np.empty((args.n_rhs, scan.n_samples), dtype=np.float32)
+    for i in range(args.n_rhs):
+        s_i = 1000 + i + 100000 * seed
+        tods[i] = synth.make_tod(scan, synth.make_sky(scan.n_pix, s_i), synth.make_noise(scan, s_i))
+    t_gen = time.time() - t_gen
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    tod_d = torch.from_numpy(tods).to(dev)
+    ctx = M.Context(local, stream.cuda_stream, M.MM_FP32_MIXED)
+    ctx.set_option("graphs", 1)
+    ctx.set_option("check_every", 8)
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        out = None
+        for _ in range(reps):
+            out = fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps, out
+
+    def setup():
+        ctx.setup_scan(scan)
+        ctx.build_bd(1e-3)
+        b = ctx.rhs(tod_d[0:1])
+        return ctx.build_coarse(b[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
+
+    setup_ms, k_used = timed(setup)
+    out = torch.empty((args.n_rhs, scan.n_pix, 3), dtype=torch.float64, device=dev)
+
+    def batched(precond=M.MM_PRECOND_2L):
+        return ctx.solve(tod_d, precond, tol=args.tol, max_iter=args.max_iter, rhs_len=lens, out=out)[1]
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+    launches0 = ctx.get_option("kernel_launches")
+    ms, infos = timed(batched, args.steps)
+    launches = int(ctx.get_option("kernel_launches") - launches0) // max(1, args.steps)
+    its = [i["iters"] for i in infos]
+    ok = sum(1 for i in infos if i["status"] == "MM_OK")
+    # single right-hand side solves of the same maps, one at a time
+    n_single = min(4, args.n_rhs)
+    one = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
+    single = {}
+    for name, pc in (("m_bd", M.MM_PRECOND_BD), ("two_level", M.MM_PRECOND_2L)):
+        tot, iters = 0.0, []
+        for i in range(n_single):
+            t, inf = timed(lambda: ctx.solve(tod_d[i:i + 1], pc, tol=args.tol, max_iter=args.max_iter,
+                                             rhs_len=lens[i:i + 1], out=one)[1])
+            tot += t
+            iters.append(inf[0]["iters"])
+        single[name] = {"time_per_map_s": tot / n_single / 1e3, "iters_mean": float(np.mean(iters))}
+    value = ms / 1e3 / args.n_rhs
+    line = {"metric": METRIC + " [batched Monte Carlo]", "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"c3: {args.n_rhs} RHS on a 32x32 patch, 8 det x 2^20 master scan, per-RHS "
+                                   f"lengths U[2^19, 2^20] per detector, lambda 512, 4096-sample intervals, "
+                                   f"shared coarse space k={k_used}, CUDA graph of 8 iterations",
+                       "samples_per_batched_Ax": int(np.sum(lens) * scan.n_det)},
+            "batched": {"iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)), "converged": ok,
+                        "kernel_launches_per_batch": launches},
+            "single_rhs": single, "setup_once_s": setup_ms / 1e3, "gen_s": t_gen}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# ---------------- serving (c5) ----------------
+def _gpu_tod(torch, scan, seed, dev):
+    """Timeline d = P s + 1/f noise synthesised on the device (input generation only)."""
+    g = torch.Generator(device=dev).manual_seed(seed)
+    pix = torch.from_numpy(scan.pix).to(dev).long()
+    psi = torch.from_numpy(scan.psi).to(dev).double()
+    sky = torch.randn((scan.n_pix, 3), generator=g, device=dev, dtype=torch.float64)
+    sky[:, 1:] *= 0.1
+    ok = pix >= 0
+    p = pix.clamp(min=0)
+    d = sky[p, 0] + sky[p, 1] * torch.cos(2 * psi) + sky[p, 2] * torch.sin(2 * psi)
+    d = torch.where(ok, d, torch.zeros_like(d))
+    blen = scan.n_t // scan.n_int
+    w = torch.randn((scan.n_det * scan.n_int, blen), generator=g, device=dev, dtype=torch.float64)
+    f = torch.fft.rfftfreq(blen, d=1.0 / 100.0, device=dev, dtype=torch.float64)
+    f[0] = f[1]
+    fk = torch.from_numpy(np.repeat(scan.f_knee, scan.n_int)).to(dev)[:, None]
+    shape = torch.sqrt(1.0 + fk / f[None, :])
+    n = torch.fft.irfft(torch.fft.rfft(w, dim=1) * shape, n=blen, dim=1).reshape(-1)
+    return (d + n).float()
+
+
+def run_serve(args, world, rank, local):
+    """Poisson stream of map requests of mixed sizes, 30% on repeated scans."""
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    from paper_1801_08937_gb300 import serving as S
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(5 + rank)
+    patches = [64, 128, 256]
+    dets = [16, 32, 64, 128]
+    samples = [1 << 18, 1 << 19]
+    n_req = args.requests
+    scans, reqs = [], []
+    for j in range(n_req):
+        if scans and rng.random() < 0.3:
+            sid = int(rng.integers(len(scans)))
+        else:
+            nx = int(rng.choice(patches))
+            nd = int(rng.choice(dets))
+            nt = int(rng.choice(samples))
+            sc = synth.make_scan(nx=nx, ny=nx, n_det=nd, n_t=nt, n_int=nt // 16384, half_bw=512,
+                                 f_knee=(0.1, 2.0), seed=1000 + len(scans))
+            scans.append(sc)
+            sid = len(scans) - 1
+        reqs.append((sid, 7000 + j))
+    specs = [S.ScanSpec(torch.from_numpy(sc.pix).to(dev), torch.from_numpy(sc.psi).to(dev), sc.block_off,
+                        sc.block_band, sc.band, sc.n_pix, sc.n_det) for sc in scans]
+    tods = [_gpu_tod(torch, scans[sid], seed, dev) for sid, seed in reqs]
+    torch.cuda.synchronize()
+    kw = dict(m_max=40, k=16, eps_arn=1e-6)
+
+    # sequential M_BD baseline: each request alone, set-up included, one at a time
+    seq_n = min(12, n_req)
+    t0 = time.perf_counter()
+    for j in range(seq_n):
+        sid, _ = reqs[j]
+        sc = scans[sid]
+        c = M.Context(local, None, M.MM_FP32_MIXED)
+        sp = specs[sid]
+        c.setup_pointing(sp.pix, sp.psi, sc.block_off, sc.block_band, sc.band, sc.n_pix, n_det=sc.n_det)
+        c.build_bd(1e-3)
+        c.solve(tods[j][None], M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter)
+        c.close()
+    torch.cuda.synchronize()
+    seq_s = (time.perf_counter() - t0) / seq_n
+    rate = 0.7 / seq_s
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    srv = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=12, **kw).start()
+    futs = []
+    t_start = time.perf_counter()
+    for j, (sid, _) in enumerate(reqs):
+        delay = t_start + arrivals[j] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(srv.submit(S.MapRequest(f"scan{sid}", specs[sid], tods[j], M.MM_PRECOND_2L, tol=args.tol,
+                                            max_iter=args.max_iter)))
+    res = [f.result(timeout=600) for f in futs]
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.stop()
+    ok = sum(1 for r in res if r.info["status"] == "MM_OK")
+    line = {"metric": METRIC + " [serving]", "value": st["p99_s"], "unit": "s (p99 latency)", "n_gpus": world,
+            "steps": n_req, "warmup": 0, "ms_per_step": wall / n_req * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{n_req} Poisson requests at 0.7x sequential M_BD capacity, patches "
+                                   f"64^2..256^2, 16..128 det x 2^18..2^19 samples, lambda 512, 30% repeat scans",
+                       "unique_scans": len(scans)},
+            "serving": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "maps_per_s": n_req / wall,
+                        "converged": ok, "cache_hits": st["cache_hits"], "evictions": st["evictions"],
+                        "max_concurrent": st["max_concurrent"]},
+            "sequential_m_bd": {"maps_per_s": 1.0 / seq_s, "s_per_map": seq_s, "n": seq_n},
+            "offered_rate_per_s": rate}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -211,6 +211,17 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
 mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done);
 mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem);
 
+/* Non-blocking stepping for a scheduler that drives many contexts from one
+ * host thread.  mm_solve_launch enqueues n_iter PCG iterations and an
+ * asynchronous read-back of the per-RHS state and returns at once;
+ * mm_solve_poll sets *ready to 1 once that read-back has landed (0 while the
+ * device is still busy) and then *done as mm_solve_step would; a finished
+ * inner solve may start a float64 refinement before returning.  Errors:
+ * MM_ERR_STATE (no solve begun, or poll without launch), MM_ERR_ARG,
+ * MM_ERR_CUDA. */
+mm_status mm_solve_launch(mm_ctx* ctx, int32_t n_iter);
+mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done);
+
 /* M_2l applied without allocating device memory during the call (the paper
  * has no counterpart; this is a deployment variant of mm_apply_precond).
  * For callers that must not call cudaMalloc/cudaFree while they run: latency-

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -45,6 +47,8 @@ struct DevBuf {
 struct Plan {
     int variant = 0;   // 1 direct, 2 fft
     int L = 0, logL = 0, V = 0;
+    int whole = 0;     // FFT: one transform per whole block (no overlap-save halo)
+    FftPasses fp{};
     int f64 = 0;
     int nrhs = 0;
     std::vector<int64_t> lens;
@@ -70,8 +74,9 @@ struct mm_ctx {
     std::string err;
 
     // options
-    int opt_filter = 0, opt_fft_log2 = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
+    int opt_filter = 0, opt_fft_log2 = 0, opt_fft_len = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
     int opt_time_filter = 0;
+    int opt_autotune = 1;
     double last_apply_ms = 0.0;
     // CUDA-event pairs around filter launches (when timing is on)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fev;
@@ -122,6 +127,11 @@ struct mm_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;
+    // asynchronous stepping
+    RhsState* h_st_pinned = nullptr;
+    int h_st_pinned_n = 0;
+    cudaEvent_t ev_state = nullptr;
+    bool launched = false;
 };
 
 namespace {
@@ -169,30 +179,92 @@ int64_t max_block_len(const mm_ctx* c) {
     return m;
 }
 
-// FFT length for the overlap-save filter: minimise segments per block times
-// L log L, within the shared-memory limit of the precision.
-int auto_fft_log2(const mm_ctx* c, bool f64) {
-    const int64_t nb = std::max<int64_t>(1, max_block_len(c));
-    const int maxlog = f64 ? 13 : 14;
-    int best = -1;
-    double best_cost = 1e300;
-    for (int lg = 6; lg <= maxlog; ++lg) {
-        const int L = 1 << lg;
-        const int V = L - 2 * c->lam;
-        if (V < 32) continue;
-        const int64_t segs = (nb + V - 1) / V;
-        const double cost = (double)segs * L * lg;
-        if (cost < best_cost * 0.999) {
-            best_cost = cost;
-            best = lg;
-        }
-    }
-    return best;
+// Mixed-radix pass plan for L = 2^a 3^b (b <= 2): a radix-3 or radix-9 pass
+// first, then radix 16 while it divides, then one radix 2, 4 or 8 pass.
+bool fft_passes(int L, FftPasses* fp) {
+    int rest = L, np = 0, span = L;
+    fp->L = L;
+    auto add = [&](int r) {
+        fp->radix[np] = r;
+        fp->span[np] = span;
+        span /= r;
+        rest /= r;
+        ++np;
+    };
+    if (rest % 9 == 0) add(9);
+    else if (rest % 3 == 0) add(3);
+    while (rest % 16 == 0 && np < 8) add(16);
+    if (rest == 8 || rest == 4 || rest == 2) add(rest);
+    fp->npass = np;
+    return rest == 1 && np <= 8;
 }
 
-mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, int L, bool f64) {
+size_t smem_limit_bytes() { return 220 * 1024; }
+
+// FFT length and mode candidates: whole blocks (one block per transform, no
+// halo, when L >= n_b + lambda) or overlap-save segments of V = L - 2 lambda
+// outputs.  Cost model: transform points x passes plus gathered and
+// scattered samples, with a penalty when the grid cannot fill the GPU.
+struct FftCand {
+    int L, whole;
+    double cost;
+};
+
+std::vector<FftCand> fft_candidates(const mm_ctx* c, bool f64, int forced_log2, int forced_len) {
+    const int64_t nb = std::max<int64_t>(1, max_block_len(c));
+    const int lam = c->lam;
+    std::vector<FftCand> out;
+    for (int b3 = 0; b3 <= 2; ++b3) {
+        for (int lg = 5; lg <= 15; ++lg) {
+            const int L = (1 << lg) * (b3 == 0 ? 1 : (b3 == 1 ? 3 : 9));
+            if (L < 64) continue;
+            if (forced_log2 > 0 && L != (1 << forced_log2)) continue;
+            if (forced_len > 0 && L != forced_len) continue;
+            const size_t sm = fft_smem_bytes(L, f64);
+            if (sm > smem_limit_bytes()) continue;
+            FftPasses fp;
+            if (!fft_passes(L, &fp)) continue;
+            double points = 0, gathered = 0, ctas = 0;
+            int whole = 0;
+            if (L >= nb + lam) {
+                whole = 1;
+                points = (double)c->n_blocks * L * 0.5;
+                gathered = (double)c->n_samples;
+                ctas = c->n_blocks * 0.5;
+            } else {
+                const int V = L - 2 * lam;
+                if (V < 32) continue;
+                double segs = 0;
+                for (int b = 0; b < c->n_blocks; ++b) {
+                    const int64_t n = c->block_off[b + 1] - c->block_off[b];
+                    segs += (double)((n + V - 1) / V);
+                }
+                points = segs * L * 0.5;
+                gathered = std::min<double>(segs * L, 2.0 * c->n_samples + segs * 2.0 * lam);
+                ctas = segs * 0.5;
+            }
+            double cost = points * fp.npass * 44.0 + gathered * 40.0 + (double)c->n_samples * 50.0;
+            const double per_sm = std::max(1.0, std::floor(228.0 * 1024 / (double)(sm + 1024)));
+            const double slots = 152.0 * per_sm;
+            if (ctas < slots) cost *= slots / std::max(1.0, ctas);   // idle SMs
+            out.push_back({L, whole, cost});
+        }
+    }
+    std::sort(out.begin(), out.end(), [](const FftCand& a, const FftCand& b) { return a.cost < b.cost; });
+    return out;
+}
+
+bool choose_fft(const mm_ctx* c, bool f64, int forced_log2, int forced_len, int* L_out, int* whole_out) {
+    auto cands = fft_candidates(c, f64, forced_log2, forced_len);
+    if (cands.empty()) return false;
+    *L_out = cands[0].L;
+    *whole_out = cands[0].whole;
+    return true;
+}
+
+mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, bool f64) {
+    const int L = fp.L;
     if (ft.L == L) return MM_OK;
-    const int logL = ilog2(L);
     // twiddles exp(-2 pi i e / L) in float64 on the host
     std::vector<double> tw64(2 * (size_t)L);
     for (int e = 0; e < L; ++e) {
@@ -219,7 +291,7 @@ mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, int L, bool f64) {
     CK(cudaMemcpyAsync(d_tw64.p, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(d_h.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     launch_fft_spectrum(d_h.as<double>(), d_H64.as<double>(), d_work.as<double2>(), d_tw64.as<double2>(),
-                        ctx->n_bands, L, logL, ctx->stream);
+                        ctx->n_bands, fp, ctx->stream);
     CKL();
     if (f64) {
         CK(ft.tw.ensure(tw64.size() * 8));
@@ -244,40 +316,28 @@ mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, int L, bool f64) {
 }
 
 // Segment list: for every block, chunk and right-hand side, pairs of segments
-// that share a band.
-mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
-    int variant = ctx->opt_filter;
-    int L = 0, logL = 0, V = 0;
-    if (variant == 0) variant = (ctx->lam <= 32) ? 1 : 2;
+// that share a band (and halo).
+mm_status make_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, int variant, int L,
+                    int whole, int V, Plan** out) {
+    FftPasses fp{};
+    int logL = 0;
     if (variant == 2) {
-        logL = ctx->opt_fft_log2 > 0 ? ctx->opt_fft_log2 : auto_fft_log2(ctx, f64);
-        if (f64 && logL > 13) logL = 13;
-        if (logL < 6 || (1 << logL) - 2 * ctx->lam < 32) {
-            if (ctx->opt_filter == 2) return fail(ctx, MM_ERR_ARG, "FFT length too short for the band half-width");
-            variant = 1;
-        } else {
-            L = 1 << logL;
-            V = L - 2 * ctx->lam;
-        }
-    }
-    if (variant == 1) {
-        V = std::max(32, ctx->opt_direct_tile);
-        L = 0;
-        logL = 0;
-        const size_t sm = direct_smem_bytes(V, ctx->lam, f64);
-        if (sm > 200 * 1024) return fail(ctx, MM_ERR_ARG, "direct filter tile plus halo exceeds shared memory");
+        fft_passes(L, &fp);
+        logL = ilog2(L);
     }
     for (auto& p : ctx->plans)
-        if (p->variant == variant && p->L == L && p->V == V && p->f64 == (int)f64 && p->nrhs == nrhs && p->lens == lens) {
+        if (p->variant == variant && p->L == L && p->V == V && p->whole == whole && p->f64 == (int)f64 &&
+            p->nrhs == nrhs && p->lens == lens) {
             *out = p.get();
             return MM_OK;
         }
     std::vector<Seg> segs;
     auto push = [&](const Seg& s) {
-        if (segs.size() % 2 == 1 && segs.back().band != s.band) {
+        if (segs.size() % 2 == 1 && (segs.back().band != s.band || segs.back().shift != s.shift)) {
             Seg e{};
             e.n_out = 0;
             e.band = segs.back().band;
+            e.shift = segs.back().shift;
             segs.push_back(e);
         }
         segs.push_back(s);
@@ -285,7 +345,8 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
     for (int b = 0; b < ctx->n_blocks; ++b) {
         const int64_t o0 = ctx->block_off[b], o1 = ctx->block_off[b + 1];
         const int64_t det0 = (o0 / ctx->n_t) * ctx->n_t;
-        for (int64_t c0 = o0; c0 < o1; c0 += V) {
+        const int64_t step = whole ? (o1 - o0) : V;
+        for (int64_t c0 = o0; c0 < o1; c0 += step) {
             for (int r = 0; r < nrhs; ++r) {
                 int64_t hi = o1;
                 if (!lens.empty()) hi = std::min(hi, det0 + lens[r]);
@@ -295,8 +356,9 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
                 s.lo = o0;
                 s.hi = hi;
                 s.rhs = r;
-                s.n_out = (int32_t)std::min<int64_t>(V, hi - c0);
+                s.n_out = (int32_t)std::min<int64_t>(step, hi - c0);
                 s.band = ctx->block_band[b];
+                s.shift = whole ? 0 : ctx->lam;
                 push(s);
             }
         }
@@ -304,6 +366,7 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
     if (segs.size() % 2 == 1) {
         Seg e{};
         e.band = segs.back().band;
+        e.shift = segs.back().shift;
         segs.push_back(e);
     }
     auto p = std::make_unique<Plan>();
@@ -311,6 +374,8 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
     p->L = L;
     p->logL = logL;
     p->V = V;
+    p->whole = whole;
+    p->fp = fp;
     p->f64 = f64;
     p->nrhs = nrhs;
     p->lens = lens;
@@ -319,10 +384,153 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
     if (!segs.empty())
         CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (variant == 2) TRY(build_fft_tables(ctx, f64 ? ctx->fft64 : ctx->fft32, L, f64));
+    if (variant == 2) TRY(build_fft_tables(ctx, f64 ? ctx->fft64 : ctx->fft32, fp, f64));
     ctx->plans.push_back(std::move(p));
     *out = ctx->plans.back().get();
     return MM_OK;
+}
+
+mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, void* dst, const RhsState* st,
+                     int tod_is_float);
+
+// Process-wide record of tuned choices, keyed by problem shape.
+struct TuneKey {
+    int f64, lam, n_blocks, nrhs;
+    int64_t n_samples, max_block, lens_sum;
+    int n_pix;
+    bool operator==(const TuneKey& o) const {
+        return f64 == o.f64 && lam == o.lam && n_blocks == o.n_blocks && nrhs == o.nrhs && n_samples == o.n_samples &&
+               max_block == o.max_block && lens_sum == o.lens_sum && n_pix == o.n_pix;
+    }
+};
+struct TuneVal {
+    int variant, L, whole, V;
+    double ms;
+};
+// Optional persistence: when MM_TUNE_CACHE names a file, tuned choices are
+// read from it at first use and appended to it as JSON lines.
+const char* tune_file() { return std::getenv("MM_TUNE_CACHE"); }
+
+std::vector<std::pair<TuneKey, TuneVal>>& tune_cache() {
+    static std::vector<std::pair<TuneKey, TuneVal>> c;
+    static bool loaded = false;
+    if (!loaded) {
+        loaded = true;
+        if (const char* path = tune_file()) {
+            if (FILE* f = std::fopen(path, "r")) {
+                char line[512];
+                while (std::fgets(line, sizeof line, f)) {
+                    TuneKey k{};
+                    TuneVal v{};
+                    long long ns = 0, mb = 0, ls = 0;
+                    if (std::sscanf(line,
+                                    "{\"f64\": %d, \"lam\": %d, \"n_blocks\": %d, \"nrhs\": %d, \"n_samples\": %lld, "
+                                    "\"max_block\": %lld, \"lens_sum\": %lld, \"n_pix\": %d, \"variant\": %d, \"L\": %d, "
+                                    "\"whole\": %d, \"V\": %d, \"ms\": %lf}",
+                                    &k.f64, &k.lam, &k.n_blocks, &k.nrhs, &ns, &mb, &ls, &k.n_pix, &v.variant, &v.L,
+                                    &v.whole, &v.V, &v.ms) == 13) {
+                        k.n_samples = ns;
+                        k.max_block = mb;
+                        k.lens_sum = ls;
+                        c.push_back({k, v});
+                    }
+                }
+                std::fclose(f);
+            }
+        }
+    }
+    return c;
+}
+
+void tune_record(const TuneKey& k, const TuneVal& v) {
+    tune_cache().push_back({k, v});
+    if (const char* path = tune_file()) {
+        if (FILE* f = std::fopen(path, "a")) {
+            std::fprintf(f,
+                         "{\"f64\": %d, \"lam\": %d, \"n_blocks\": %d, \"nrhs\": %d, \"n_samples\": %lld, "
+                         "\"max_block\": %lld, \"lens_sum\": %lld, \"n_pix\": %d, \"variant\": %d, \"L\": %d, "
+                         "\"whole\": %d, \"V\": %d, \"ms\": %.6f}\n",
+                         k.f64, k.lam, k.n_blocks, k.nrhs, (long long)k.n_samples, (long long)k.max_block,
+                         (long long)k.lens_sum, k.n_pix, v.variant, v.L, v.whole, v.V, v.ms);
+            std::fclose(f);
+        }
+    }
+}
+
+// Time each candidate plan once (after one warm-up launch) on the current
+// pointing and keep the fastest.  Candidates: the six cheapest FFT plans of
+// the cost model and, for narrow bands, the direct band at two tile sizes.
+mm_status autotune_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, TuneVal* best) {
+    struct Opt { int variant, L, whole, V; };
+    std::vector<Opt> opts;
+    auto cands = fft_candidates(ctx, f64, 0, 0);
+    for (size_t i = 0; i < cands.size() && i < 6; ++i)
+        opts.push_back({2, cands[i].L, cands[i].whole, cands[i].whole ? cands[i].L - ctx->lam : cands[i].L - 2 * ctx->lam});
+    if (ctx->lam <= 256)
+        for (int tile : {512, 2048})
+            if (direct_smem_bytes(tile, ctx->lam, f64) <= 200 * 1024) opts.push_back({1, 0, 0, tile});
+    if (opts.empty()) return fail(ctx, MM_ERR_ARG, "no filter plan fits this band");
+    const size_t esz = f64 ? sizeof(V4<double>) : sizeof(V4<float>);
+    const size_t nv = (size_t)ctx->n_pix * nrhs;
+    DevBuf src, dst;
+    CK(src.ensure(nv * esz));
+    CK(dst.ensure(nv * esz));
+    CK(cudaMemsetAsync(src.p, 0, nv * esz, ctx->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    best->ms = 1e300;
+    const int saved_time = ctx->opt_time_filter;
+    ctx->opt_time_filter = 0;
+    for (const Opt& o : opts) {
+        Plan* p = nullptr;
+        TRY(make_plan(ctx, f64, nrhs, lens, o.variant, o.L, o.whole, o.V, &p));
+        TRY(run_filter(ctx, p, false, src.p, dst.p, nullptr, 0));
+        CK(cudaEventRecord(e0, ctx->stream));
+        TRY(run_filter(ctx, p, false, src.p, dst.p, nullptr, 0));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best->ms) *best = TuneVal{o.variant, o.L, o.whole, o.V, (double)ms};
+    }
+    ctx->opt_time_filter = saved_time;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return MM_OK;
+}
+
+mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
+    int variant = ctx->opt_filter;
+    int L = 0, V = 0, whole = 0;
+    if (variant == 0 && ctx->opt_fft_len == 0 && ctx->opt_fft_log2 == 0 && ctx->opt_autotune && !ctx->capturing) {
+        TuneKey key{(int)f64, ctx->lam, ctx->n_blocks, nrhs, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
+        for (auto v : lens) key.lens_sum += v;
+        for (auto& kv : tune_cache())
+            if (kv.first == key) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
+                                                  kv.second.whole, kv.second.V, out);
+        TuneVal best{};
+        TRY(autotune_plan(ctx, f64, nrhs, lens, &best));
+        tune_record(key, best);
+        return make_plan(ctx, f64, nrhs, lens, best.variant, best.L, best.whole, best.V, out);
+    }
+    if (variant == 0) variant = (ctx->lam <= 32) ? 1 : 2;
+    if (variant == 2) {
+        if (!choose_fft(ctx, f64, ctx->opt_fft_log2, ctx->opt_fft_len, &L, &whole)) {
+            if (ctx->opt_filter == 2) return fail(ctx, MM_ERR_ARG, "no FFT length fits the band half-width");
+            variant = 1;
+        } else {
+            V = whole ? L - ctx->lam : L - 2 * ctx->lam;
+        }
+    }
+    if (variant == 1) {
+        V = std::max(32, ctx->opt_direct_tile);
+        L = 0;
+        whole = 0;
+        const size_t sm = direct_smem_bytes(V, ctx->lam, f64);
+        if (sm > 200 * 1024) return fail(ctx, MM_ERR_ARG, "direct filter tile plus halo exceeds shared memory");
+    }
+    return make_plan(ctx, f64, nrhs, lens, variant, L, whole, V, out);
 }
 
 // dst (V4<T>[nrhs][n_pix], zeroed by the caller) += P^T W (P src | d).
@@ -342,6 +550,7 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
     a.L = plan->L;
     a.logL = plan->logL;
     a.V = plan->V;
+    a.fp = plan->fp;
     a.state = st;
     a.tod_is_float = tod_is_float;
     cudaEvent_t e1 = nullptr;
@@ -680,6 +889,8 @@ mm_status mm_destroy(mm_ctx* ctx) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    if (ctx->h_st_pinned) cudaFreeHost(ctx->h_st_pinned);
+    if (ctx->ev_state) cudaEventDestroy(ctx->ev_state);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -1234,6 +1445,41 @@ static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
     return MM_OK;
 }
 
+static mm_status launch_iters(mm_ctx* ctx, int32_t n_iter) {
+    if (n_iter <= 0) return MM_OK;
+    if (ctx->opt_graphs && n_iter == ctx->opt_check_every) {
+        if (!ctx->graph_exec) {
+            // one eager iteration first so every kernel attribute is configured
+            TRY(pcg_iteration(ctx));
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            ctx->capturing = true;
+            mm_status s = MM_OK;
+            for (int i = 0; i < n_iter && s == MM_OK; ++i) s = pcg_iteration(ctx);
+            ctx->capturing = false;
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (s != MM_OK) return s;
+            CK(e);
+            CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+            cudaGraphDestroy(g);
+            ctx->graph_iters = n_iter;
+        }
+        CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    } else {
+        for (int i = 0; i < n_iter; ++i) TRY(pcg_iteration(ctx));
+    }
+    return MM_OK;
+}
+
+static mm_status evaluate_state(mm_ctx* ctx, int32_t* done) {
+    bool any = false;
+    for (int i = 0; i < ctx->nrhs; ++i) any = any || ctx->h_st[i].active;
+    int32_t d = 0;
+    if (!any) TRY(finish_inner(ctx, &d, true));
+    if (done) *done = d;
+    return MM_OK;
+}
+
 mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done) {
     if (!ctx) return MM_ERR_ARG;
     if (ctx->phase == PH_DONE) {
@@ -1242,36 +1488,49 @@ mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done) {
     }
     if (ctx->phase != PH_INNER) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
     CK(cudaSetDevice(ctx->device));
-    int32_t d = 0;
-    if (n_iter > 0) {
-        if (ctx->opt_graphs && n_iter == ctx->opt_check_every) {
-            if (!ctx->graph_exec) {
-                // one eager iteration first so every kernel attribute is configured
-                TRY(pcg_iteration(ctx));
-                cudaGraph_t g;
-                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-                ctx->capturing = true;
-                mm_status s = MM_OK;
-                for (int i = 0; i < n_iter && s == MM_OK; ++i) s = pcg_iteration(ctx);
-                ctx->capturing = false;
-                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-                if (s != MM_OK) return s;
-                CK(e);
-                CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
-                cudaGraphDestroy(g);
-                ctx->graph_iters = n_iter;
-            }
-            CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
-        } else {
-            for (int i = 0; i < n_iter; ++i) TRY(pcg_iteration(ctx));
-        }
-    }
+    TRY(launch_iters(ctx, n_iter));
     TRY(read_state(ctx));
-    bool any = false;
-    for (int i = 0; i < ctx->nrhs; ++i) any = any || ctx->h_st[i].active;
-    if (!any) TRY(finish_inner(ctx, &d, true));
-    if (done) *done = d;
+    return evaluate_state(ctx, done);
+}
+
+mm_status mm_solve_launch(mm_ctx* ctx, int32_t n_iter) {
+    if (!ctx) return MM_ERR_ARG;
+    if (ctx->phase == PH_DONE) return MM_OK;
+    if (ctx->phase != PH_INNER) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
+    if (n_iter < 0) return fail(ctx, MM_ERR_ARG, "n_iter must be >= 0");
+    CK(cudaSetDevice(ctx->device));
+    TRY(launch_iters(ctx, n_iter));
+    if (!ctx->h_st_pinned || ctx->h_st_pinned_n < ctx->nrhs) {
+        if (ctx->h_st_pinned) cudaFreeHost(ctx->h_st_pinned);
+        ctx->h_st_pinned = nullptr;
+        CK(cudaMallocHost(reinterpret_cast<void**>(&ctx->h_st_pinned), ctx->nrhs * sizeof(RhsState)));
+        ctx->h_st_pinned_n = ctx->nrhs;
+    }
+    if (!ctx->ev_state) CK(cudaEventCreateWithFlags(&ctx->ev_state, cudaEventDisableTiming));
+    CK(cudaMemcpyAsync(ctx->h_st_pinned, ctx->s_st.p, ctx->nrhs * sizeof(RhsState), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaEventRecord(ctx->ev_state, ctx->stream));
+    ctx->launched = true;
     return MM_OK;
+}
+
+mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done) {
+    if (!ctx || !ready || !done) return MM_ERR_ARG;
+    *ready = 0;
+    *done = 0;
+    if (ctx->phase == PH_DONE) {
+        *ready = *done = 1;
+        return MM_OK;
+    }
+    if (ctx->phase != PH_INNER || !ctx->launched) return fail(ctx, MM_ERR_STATE, "mm_solve_launch first");
+    CK(cudaSetDevice(ctx->device));
+    const cudaError_t q = cudaEventQuery(ctx->ev_state);
+    if (q == cudaErrorNotReady) return MM_OK;
+    CK(q);
+    ctx->launched = false;
+    ctx->h_st.assign(ctx->h_st_pinned, ctx->h_st_pinned + ctx->nrhs);
+    *ready = 1;
+    return evaluate_state(ctx, done);
 }
 
 mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem) {
@@ -1344,6 +1603,10 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
     } else if (n == "fft_log2") {
         if (v != 0 && (v < 6 || v > 14)) return fail(ctx, MM_ERR_ARG, "fft_log2 must be 0 or in [6, 14]");
         ctx->opt_fft_log2 = v;
+    } else if (n == "fft_len") {
+        FftPasses fp;
+        if (v != 0 && (v < 64 || !fft_passes(v, &fp))) return fail(ctx, MM_ERR_ARG, "fft_len must be 0 or 2^a 3^b >= 64, b <= 2");
+        ctx->opt_fft_len = v;
     } else if (n == "direct_tile") {
         if (v < 32 || v > 65536) return fail(ctx, MM_ERR_ARG, "direct_tile must lie in [32, 65536]");
         ctx->opt_direct_tile = v;
@@ -1352,6 +1615,8 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_check_every = v;
     } else if (n == "graphs") {
         ctx->opt_graphs = v ? 1 : 0;
+    } else if (n == "autotune") {
+        ctx->opt_autotune = v ? 1 : 0;
     } else if (n == "time_filter") {
         ctx->opt_time_filter = v ? 1 : 0;
         ctx->fev_used = 0;
@@ -1366,12 +1631,14 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     const std::string n(name);
     if (n == "filter") *value = ctx->opt_filter;
     else if (n == "fft_log2") *value = ctx->opt_fft_log2;
+    else if (n == "fft_len") *value = ctx->opt_fft_len;
     else if (n == "direct_tile") *value = ctx->opt_direct_tile;
     else if (n == "check_every") *value = ctx->opt_check_every;
     else if (n == "graphs") *value = ctx->opt_graphs;
     else if (n == "last_apply_ms") *value = ctx->last_apply_ms;
     else if (n == "kernel_launches") *value = (double)launches_total();
     else if (n == "time_filter") *value = ctx->opt_time_filter;
+    else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "filter_ms" || n == "filter_launches") {
         // total device time of the filter launches timed since the last read; resets the record
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1389,6 +1656,11 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
         if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");
         TRY(get_plan(ctx, !is_f32(ctx), 1, {}, &p));
         *value = p->variant == 2 ? p->logL : 0;
+    } else if (n == "plan_fft_len" || n == "plan_whole") {
+        Plan* p = nullptr;
+        if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");
+        TRY(get_plan(ctx, !is_f32(ctx), 1, {}, &p));
+        *value = n == "plan_whole" ? p->whole : (p->variant == 2 ? p->L : 0);
     } else if (n == "device_bytes") {
         size_t f = 0, t = 0;
         cudaMemGetInfo(&f, &t);

@@ -38,7 +38,15 @@ struct Seg {
     int32_t rhs;
     int32_t n_out;
     int32_t band;
-    int32_t pad;
+    int32_t shift;   // left halo in the transform buffer: lambda, or 0 for a whole block
+};
+
+// Mixed-radix FFT plan: L = product of radix[p]; pass p works on spans of
+// span[p] points (span[0] = L, span[p+1] = span[p] / radix[p]).
+struct FftPasses {
+    int L, npass;
+    int radix[8];
+    int span[8];
 };
 
 // Per-right-hand-side PCG scalars kept on the device (float64).
@@ -70,6 +78,7 @@ struct FilterArgs {
     const void* tw;        // FFT: [L] twiddles exp(-2 pi i e / L)
     const void* band;      // direct: [n_bands][lambda+1]
     int L, logL, lam, V;
+    FftPasses fp;
     const RhsState* state; // may be null: all right-hand sides active
     int tod_is_float;      // src TOD element type when from_tod (1: float, 0: double)
 };
@@ -83,7 +92,7 @@ size_t fft_smem_bytes(int L, bool f64);
 size_t direct_smem_bytes(int V, int lam, bool f64);
 // H = DIF(h) for each band in float64 through global scratch; h [n_bands][L].
 void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw,
-                         int n_bands, int L, int logL, cudaStream_t s);
+                         int n_bands, const FftPasses& fp, cudaStream_t s);
 void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s);
 
 // ---------------- vectors, preconditioners, reductions ----------------

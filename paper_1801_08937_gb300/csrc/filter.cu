@@ -23,7 +23,6 @@ static long long g_launches = 0;
 long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 void count_launches(int n) { __atomic_fetch_add(&g_launches, (long long)n, __ATOMIC_RELAXED); }
 
-constexpr int FFT_NT = 256;
 constexpr int DIRECT_NT = 256;
 
 // Padded shared-memory index: one spare element every 16 keeps the strided
@@ -84,6 +83,41 @@ template <typename T> struct Dft<T, 8> {
         for (int i = 0; i < 8; ++i) a[i] = o[i];
     }
 };
+template <typename T> __device__ __forceinline__ void dft3(C2<T>& a0, C2<T>& a1, C2<T>& a2) {
+    const T h = T(0.86602540378443864676);   // sin(2 pi / 3)
+    const C2<T> t1 = cadd(a1, a2);
+    const C2<T> u{a0.x - T(0.5) * t1.x, a0.y - T(0.5) * t1.y};
+    const C2<T> v{h * (a1.x - a2.x), h * (a1.y - a2.y)};
+    a0 = cadd(a0, t1);
+    a1 = C2<T>{u.x + v.y, u.y - v.x};   // u - i v
+    a2 = C2<T>{u.x - v.y, u.y + v.x};   // u + i v
+}
+template <typename T> struct Dft<T, 3> {
+    static __device__ __forceinline__ void run(C2<T>* a) { dft3(a[0], a[1], a[2]); }
+};
+template <typename T> struct Dft<T, 9> {
+    static __device__ __forceinline__ void run(C2<T>* a) {
+        // n = 3 n1 + n2, k = k1 + 3 k2; W9^m = (cos 2 pi m / 9, -sin 2 pi m / 9)
+        const T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);
+        const T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);
+        const T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);
+#pragma unroll
+        for (int n2 = 0; n2 < 3; ++n2) dft3(a[n2], a[n2 + 3], a[n2 + 6]);
+        a[4] = cmul(a[4], C2<T>{c1, -s1});
+        a[7] = cmul(a[7], C2<T>{c2, -s2});
+        a[5] = cmul(a[5], C2<T>{c2, -s2});
+        a[8] = cmul(a[8], C2<T>{c4, -s4});
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) dft3(a[3 * k1], a[3 * k1 + 1], a[3 * k1 + 2]);
+        C2<T> o[9];
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) o[k1 + 3 * k2] = a[3 * k1 + k2];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) a[i] = o[i];
+    }
+};
 template <typename T> struct Dft<T, 16> {
     static __device__ __forceinline__ void run(C2<T>* a) {
         const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
@@ -113,75 +147,67 @@ template <typename T> struct Dft<T, 16> {
     }
 };
 
-// Powers w^q, q < R, of one twiddle by repeated products of depth <= 4
-// (one table load per butterfly instead of R - 1).
+// Powers w^q, q < R, of one twiddle, each a product of two earlier powers
+// (depth <= 4), from a single table load per butterfly.
 template <typename T, int R>
 __device__ __forceinline__ void twiddle_powers(C2<T> w1, C2<T>* w) {
     w[1] = w1;
-    if (R > 2) {
-        w[2] = cmul(w1, w1);
-        w[3] = cmul(w[2], w1);
-    }
-    if (R > 4) {
-        w[4] = cmul(w[2], w[2]);
-        w[5] = cmul(w[4], w1);
-        w[6] = cmul(w[4], w[2]);
-        w[7] = cmul(w[4], w[3]);
-    }
-    if (R > 8) {
-        w[8] = cmul(w[4], w[4]);
 #pragma unroll
-        for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
+    for (int q = 2; q < R; ++q) {
+        int hi = 1;
+        while (hi * 2 <= q) hi *= 2;
+        w[q] = (hi == q) ? cmul(w[q / 2], w[q / 2]) : cmul(w[hi], w[q - hi]);
     }
 }
 
-// Decimation-in-frequency pass of radix R over spans of 2^logS (in place):
+// Decimation-in-frequency pass of radix R over spans of S points (in place):
 // for each butterfly j < S/R of each span, DFT_R over elements j + r S/R,
-// then output q times W_S^(j q).  Natural order in, digit-reversed out.
-template <typename T, int R, int LOGR>
-__device__ __forceinline__ void dif_pass(C2<T>* s, const C2<T>* __restrict__ tw, int logL, int logS) {
-    const int logSr = logS - LOGR;
-    const int nbf = 1 << (logL - LOGR);
-    const int tsh = logL - logS;
+// then output q times W_S^(j q) = W_L^(j q L/S).  After all passes the
+// transform sits in mixed-radix digit-reversed order.
+template <typename T, int R>
+__device__ __forceinline__ void dif_pass(C2<T>* s, const C2<T>* __restrict__ tw, int L, int S) {
+    const int Sr = S / R;
+    const int nbf = L / R;
+    const int tstep = L / S;
     for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-        const int g = bf >> logSr;
-        const int j = bf & ((1 << logSr) - 1);
-        const int base = (g << logS) + j;
+        const int g = bf / Sr;
+        const int j = bf - g * Sr;
+        const int base = g * S + j;
         C2<T> w1{T(1), T(0)};
-        if (logSr > 0) w1 = ldtw(tw, j << tsh);
+        if (Sr > 1) w1 = ldtw(tw, j * tstep);
         C2<T> a[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + (r << logSr))];
+        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + r * Sr)];
         Dft<T, R>::run(a);
-        if (logSr > 0) {
+        if (Sr > 1) {
             C2<T> w[R];
             twiddle_powers<T, R>(w1, w);
 #pragma unroll
             for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) s[sidx(base + (q << logSr))] = a[q];
+        for (int q = 0; q < R; ++q) s[sidx(base + q * Sr)] = a[q];
     }
 }
 
 // The matching decimation-in-time pass in the conjugate domain: element q
 // times W_S^(j q), then DFT_R.  Run on conj(X) in the reverse pass order it
 // yields L * conj(x): the exact inverse of the DIF passes.
-template <typename T, int R, int LOGR>
-__device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw, int logL, int logS) {
-    const int logSr = logS - LOGR;
-    const int nbf = 1 << (logL - LOGR);
-    const int tsh = logL - logS;
+template <typename T, int R>
+__device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw, int L, int S) {
+    const int Sr = S / R;
+    const int nbf = L / R;
+    const int tstep = L / S;
     for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-        const int g = bf >> logSr;
-        const int j = bf & ((1 << logSr) - 1);
-        const int base = (g << logS) + j;
+        const int g = bf / Sr;
+        const int j = bf - g * Sr;
+        const int base = g * S + j;
         C2<T> w1{T(1), T(0)};
-        if (logSr > 0) w1 = ldtw(tw, j << tsh);
+        if (Sr > 1) w1 = ldtw(tw, j * tstep);
         C2<T> a[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) a[q] = s[sidx(base + (q << logSr))];
-        if (logSr > 0) {
+        for (int q = 0; q < R; ++q) a[q] = s[sidx(base + q * Sr)];
+        if (Sr > 1) {
             C2<T> w[R];
             twiddle_powers<T, R>(w1, w);
 #pragma unroll
@@ -189,49 +215,34 @@ __device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw,
         }
         Dft<T, R>::run(a);
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[sidx(base + (r << logSr))] = a[r];
+        for (int r = 0; r < R; ++r) s[sidx(base + r * Sr)] = a[r];
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void tail_dif(C2<T>* s, const C2<T>* tw, int logL, int rem) {
-    if (rem == 1) dif_pass<T, 2, 1>(s, tw, logL, 1);
-    else if (rem == 2) dif_pass<T, 4, 2>(s, tw, logL, 2);
-    else if (rem == 3) dif_pass<T, 8, 3>(s, tw, logL, 3);
-}
-template <typename T>
-__device__ __forceinline__ void tail_dit(C2<T>* s, const C2<T>* tw, int logL, int rem) {
-    if (rem == 1) dit_pass<T, 2, 1>(s, tw, logL, 1);
-    else if (rem == 2) dit_pass<T, 4, 2>(s, tw, logL, 2);
-    else if (rem == 3) dit_pass<T, 8, 3>(s, tw, logL, 3);
+template <typename T, bool DIT>
+__device__ __forceinline__ void run_pass(C2<T>* s, const C2<T>* tw, int L, int R, int S) {
+    switch (R) {
+        case 16: DIT ? dit_pass<T, 16>(s, tw, L, S) : dif_pass<T, 16>(s, tw, L, S); break;
+        case 9: DIT ? dit_pass<T, 9>(s, tw, L, S) : dif_pass<T, 9>(s, tw, L, S); break;
+        case 8: DIT ? dit_pass<T, 8>(s, tw, L, S) : dif_pass<T, 8>(s, tw, L, S); break;
+        case 4: DIT ? dit_pass<T, 4>(s, tw, L, S) : dif_pass<T, 4>(s, tw, L, S); break;
+        case 3: DIT ? dit_pass<T, 3>(s, tw, L, S) : dif_pass<T, 3>(s, tw, L, S); break;
+        default: DIT ? dit_pass<T, 2>(s, tw, L, S) : dif_pass<T, 2>(s, tw, L, S); break;
+    }
 }
 
-// Forward transform: radix-16 passes from span L down, then one radix-2^rem pass.
+// Forward transform: the plan's passes in order (spans shrink from L).
 template <typename T>
-__device__ void fft_dif(C2<T>* s, const C2<T>* tw, int logL) {
-    const int n16 = logL >> 2, rem = logL & 3;
-    int logS = logL;
-    for (int p = 0; p < n16; ++p) {
-        dif_pass<T, 16, 4>(s, tw, logL, logS);
-        logS -= 4;
-        __syncthreads();
-    }
-    if (rem) {
-        tail_dif<T>(s, tw, logL, rem);
+__device__ void fft_dif(C2<T>* s, const C2<T>* tw, const FftPasses& fp) {
+    for (int p = 0; p < fp.npass; ++p) {
+        run_pass<T, false>(s, tw, fp.L, fp.radix[p], fp.span[p]);
         __syncthreads();
     }
 }
 template <typename T>
-__device__ void fft_dit_conj(C2<T>* s, const C2<T>* tw, int logL) {
-    const int n16 = logL >> 2, rem = logL & 3;
-    if (rem) {
-        tail_dit<T>(s, tw, logL, rem);
-        __syncthreads();
-    }
-    int logS = rem + 4;
-    for (int p = 0; p < n16; ++p) {
-        dit_pass<T, 16, 4>(s, tw, logL, logS);
-        logS += 4;
+__device__ void fft_dit_conj(C2<T>* s, const C2<T>* tw, const FftPasses& fp) {
+    for (int p = fp.npass - 1; p >= 0; --p) {
+        run_pass<T, true>(s, tw, fp.L, fp.radix[p], fp.span[p]);
         __syncthreads();
     }
 }
@@ -428,8 +439,8 @@ __device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
 }
 
 // ---------------- FFT overlap-save variant ----------------
-template <typename T, bool FROM_TOD>
-__global__ void __launch_bounds__(FFT_NT, sizeof(T) == 4 ? 3 : 1) k_filter_fft(const FilterArgs a) {
+template <typename T, bool FROM_TOD, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_filter_fft(const FilterArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
     const Seg A = a.segs[2 * blockIdx.x];
@@ -437,12 +448,13 @@ __global__ void __launch_bounds__(FFT_NT, sizeof(T) == 4 ? 3 : 1) k_filter_fft(c
     const bool actA = seg_active<T>(a, A);
     const bool actB = seg_active<T>(a, B);
     if (!actA && !actB) return;
-    const int L = a.L, lam = a.lam, logL = a.logL;
+    const int L = a.L;
+    const int lam = actA ? A.shift : B.shift;   // left halo of this pair (lambda, or 0 for whole blocks)
     const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
 
     gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
     __syncthreads();
-    fft_dif<T>(s, tw, logL);
+    fft_dif<T>(s, tw, a.fp);
     const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const C2<T> v = s[sidx(i)];
@@ -450,7 +462,7 @@ __global__ void __launch_bounds__(FFT_NT, sizeof(T) == 4 ? 3 : 1) k_filter_fft(c
         s[sidx(i)] = C2<T>{v.x * h, -v.y * h};
     }
     __syncthreads();
-    fft_dit_conj<T>(s, tw, logL);
+    fft_dit_conj<T>(s, tw, a.fp);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int vmax = max(actA ? A.n_out : 0, actB ? B.n_out : 0);
@@ -530,13 +542,14 @@ __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a)
 }
 
 // ---------------- setup kernels ----------------
-__global__ void k_fft_spectrum(const double* h, double* H, C2<double>* work, const C2<double>* tw, int L,
-                               int logL) {
+__global__ void k_fft_spectrum(const double* h, double* H, C2<double>* work, const C2<double>* tw,
+                               const FftPasses fp) {
+    const int L = fp.L;
     C2<double>* s = work + (int64_t)blockIdx.x * (L + (L >> 4));
     const double* hb = h + (int64_t)blockIdx.x * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) s[sidx(i)] = C2<double>{hb[i], 0.0};
     __syncthreads();
-    fft_dif<double>(s, tw, logL);
+    fft_dif<double>(s, tw, fp);
     const double inv = 1.0 / (double)L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) H[(int64_t)blockIdx.x * L + i] = s[sidx(i)].x * inv;
 }
@@ -555,18 +568,26 @@ size_t direct_smem_bytes(int V, int lam, bool f64) {
     return (size_t)(((lam + 2) & ~1) + V + 2 * lam) * (f64 ? 8 : 4);
 }
 
+template <typename T, bool FROM_TOD, int NT>
+static void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configured = sm;
+    }
+    k_filter_fft<T, FROM_TOD, NT><<<a.n_work, NT, sm, s>>>(a);
+    count_launches(1);
+}
+
+// 512 threads when one CTA fills an SM's shared memory (large float32
+// transforms), 256 otherwise.
 template <typename T, bool FROM_TOD>
 static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
     if (a.n_work <= 0) return;
     const size_t sm = fft_smem_bytes(a.L, sizeof(T) == 8);
-    static size_t configured = 0;
-    if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured = sm;
-    }
-    k_filter_fft<T, FROM_TOD><<<a.n_work, FFT_NT, sm, s>>>(a);
-    count_launches(1);
+    if (sizeof(T) == 4 && sm > 110 * 1024) launch_fft_nt<T, FROM_TOD, 512>(a, sm, s);
+    else launch_fft_nt<T, FROM_TOD, 256>(a, sm, s);
 }
 template <typename T, bool FROM_TOD>
 static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
@@ -598,11 +619,11 @@ void launch_filter_direct_f64(const FilterArgs& a, bool from_tod, cudaStream_t s
     else launch_direct_t<double, false>(a, s);
 }
 
-void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw, int n_bands, int L,
-                         int logL, cudaStream_t s) {
+void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw, int n_bands,
+                         const FftPasses& fp, cudaStream_t s) {
     if (n_bands <= 0) return;
     k_fft_spectrum<<<n_bands, 256, 0, s>>>(h, H_out, reinterpret_cast<C2<double>*>(work),
-                                           reinterpret_cast<const C2<double>*>(tw), L, logL);
+                                           reinterpret_cast<const C2<double>*>(tw), fp);
     count_launches(1);
 }
 

@@ -54,6 +54,8 @@ SIGNATURES = [
     ("mm_solve_end", C.c_int, [_VP, _VP, C.POINTER(mm_solve_info), C.c_int]),
     ("mm_estimate_bytes", C.c_int64, [_I64, _I32, _I32, _I32, _I32, _I32, _I32, C.c_int]),
     ("mm_apply_precond_2l_noalloc", C.c_int, [_VP, _VP, _VP, _I32]),
+    ("mm_solve_launch", C.c_int, [_VP, _I32]),
+    ("mm_solve_poll", C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32)]),
 ]
 
 _lib = None
@@ -261,6 +263,15 @@ class Context:
         done = C.c_int32(0)
         self._check(self.lib.mm_solve_step(self.h, int(n_iter), C.byref(done)))
         return bool(done.value)
+
+    def solve_launch(self, n_iter: int):
+        self._check(self.lib.mm_solve_launch(self.h, int(n_iter)))
+
+    def solve_poll(self):
+        """(ready, done): ready once the last launch's state read-back has landed."""
+        r, d = C.c_int32(0), C.c_int32(0)
+        self._check(self.lib.mm_solve_poll(self.h, C.byref(r), C.byref(d)))
+        return bool(r.value), bool(d.value)
 
     def solve_end(self, out=None, like=None):
         out = self._map_out(like, self._nrhs) if out is None else out

@@ -22,11 +22,13 @@ TOL64 = 1e-11
 TOL32 = 1e-5
 
 
-def ctx_for(scan, prec=MM.MM_FP64, filt=0, fft_log2=0):
+def ctx_for(scan, prec=MM.MM_FP64, filt=0, fft_log2=0, fft_len=0):
     c = MM.Context(0, None, prec)
     c.set_option("filter", filt)
     if fft_log2:
         c.set_option("fft_log2", fft_log2)
+    if fft_len:
+        c.set_option("fft_len", fft_len)
     c.setup_scan(scan)
     return c
 
@@ -52,12 +54,14 @@ def ragged(scan, seed=0, min_len=40):
 SMALL = dict(nx=8, ny=8, n_det=4, n_t=4096, n_int=4, half_bw=64, f_knee=1.0)
 
 
-@pytest.mark.parametrize("filt,fft_log2", [(1, 0), (2, 0), (2, 8), (2, 10)])
+@pytest.mark.parametrize("filt,fft_len", [(1, 0), (2, 0), (2, 256), (2, 1024), (2, 576), (2, 768), (2, 1152),
+                                          (2, 2304), (2, 4608)])
 @pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
-def test_apply_A_matches_oracle(filt, fft_log2, prec):
+def test_apply_A_matches_oracle(filt, fft_len, prec):
+    """Direct band, overlap-save segments (L < n_b + lambda) and whole blocks, radix 2..16, 3 and 9."""
     scan = ragged(synth.make_scan(seed=1, flag_frac=0.01, **SMALL), seed=1)
     prob = O.Problem.from_scan(scan)
-    c = ctx_for(scan, prec, filt, fft_log2)
+    c = ctx_for(scan, prec, filt, fft_len=fft_len)
     x = np.random.default_rng(2).standard_normal((2, scan.n_pix, 3))
     y = c.apply_A(x)
     for r in range(2):

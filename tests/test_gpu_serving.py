@@ -1,0 +1,99 @@
+"""Continuous-batching server: each map is the same alone and in the mix.
+
+Requests on a handful of scans (some repeated, so their coarse space is
+reused) arrive while others are still iterating; every result must match
+the same request solved alone through the plain C ABI within the solve
+tolerance, and must match the FP64 oracle on the small scans.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from helpers import oracle_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_1801_08937_gb300")
+MM = P.mapmaker
+from paper_1801_08937_gb300 import serving as S  # noqa: E402
+
+
+def _scan(i):
+    shapes = [dict(nx=8, ny=8, n_det=4, n_t=2048, n_int=2, half_bw=64, f_knee=1.0),
+              dict(nx=12, ny=12, n_det=3, n_t=4096, n_int=4, half_bw=32, f_knee=0.5),
+              dict(nx=6, ny=6, n_det=2, n_t=3072, n_int=3, half_bw=100, f_knee=2.0)]
+    return synth.make_scan(seed=40 + i, **shapes[i % 3])
+
+
+def _spec(scan):
+    return S.ScanSpec(scan.pix, scan.psi, scan.block_off, scan.block_band, scan.band, scan.n_pix, scan.n_det)
+
+
+def _alone(scan, tod, precision, precond, k, m_max):
+    c = MM.Context(0, None, precision)
+    c.setup_scan(scan)
+    c.build_bd(1e-3)
+    if precond == MM.MM_PRECOND_2L:
+        c.build_coarse(c.rhs(tod)[0], m_max=m_max, eps_arn=1e-6, k=k)
+    x, info = c.solve(tod, precond, tol=1e-9, max_iter=800)
+    c.close()
+    return x[0], info[0]
+
+
+@pytest.mark.parametrize("precision", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_results_same_alone_and_in_mix(precision):
+    scans = [_scan(i) for i in range(3)]
+    dtype = np.float32 if precision == MM.MM_FP32_MIXED else np.float64
+    reqs = []
+    for j in range(9):
+        i = j % 3
+        sc = scans[i]
+        tod = synth.make_tod(sc, synth.make_sky(sc.n_pix, 100 + j), synth.make_noise(sc, 100 + j)).astype(dtype)
+        reqs.append((f"scan{i}", sc, tod))
+    srv = S.MapServer(device=0, precision=precision, iters_per_tick=3, m_max=30, k=6, reserve_bytes=0).start()
+    futs = []
+    for j, (sid, sc, tod) in enumerate(reqs):
+        futs.append(srv.submit(S.MapRequest(sid, _spec(sc), tod, MM.MM_PRECOND_2L, tol=1e-9, max_iter=800)))
+        time.sleep(0.002 * (j % 2))     # arrivals spread while earlier solves run
+    res = [f.result(timeout=120) for f in futs]
+    st = srv.stats()
+    srv.stop()
+    assert st["completed"] == 9 and st["cache_hits"] >= 6
+    assert st["max_concurrent"] >= 2
+    for (sid, sc, tod), r in zip(reqs, res):
+        assert r.info["status"] == "MM_OK"
+        # the coarse space of a repeated scan comes from its first request's b, so
+        # compare against the exact solution rather than bit-for-bit
+        prob, mbd, good = oracle_problem(sc)
+        b = O.rhs(prob, tod.astype(np.float64)).reshape(-1)
+        xo = O.pcg(lambda v: O.apply_A(prob, v).reshape(-1), lambda v: O.bd_apply(mbd, v).reshape(-1), b,
+                   tol=1e-13, max_iter=5000)[0]
+        assert rel(r.map, xo) < 1e-6
+    # the first request of each scan has exactly the set-up of a standalone solve
+    for j in range(3):
+        sid, sc, tod = reqs[j]
+        xa, ia = _alone(sc, tod, precision, MM.MM_PRECOND_2L, 6, 30)
+        assert rel(res[j].map, xa) < 1e-7
+
+
+def test_admission_waits_for_memory_and_evicts_idle_scans():
+    scans = [_scan(i) for i in range(3)]
+    per_scan = max(MM.estimate_bytes(s.n_samples, s.n_pix, s.n_bands, s.half_bw, 1, 30, 6, MM.MM_FP64)
+                   for s in scans)
+    # room for about two resident scans: the third must wait and evict
+    srv = S.MapServer(device=0, precision=MM.MM_FP64, iters_per_tick=4, m_max=30, k=6, reserve_bytes=0,
+                      budget_bytes=int(2.5 * per_scan)).start()
+    futs = []
+    for j in range(6):
+        sc = scans[j % 3]
+        tod = synth.make_tod(sc, synth.make_sky(sc.n_pix, 200 + j), synth.make_noise(sc, 200 + j))
+        futs.append(srv.submit(S.MapRequest(f"s{j % 3}", _spec(sc), tod, MM.MM_PRECOND_BD, tol=1e-9)))
+    res = [f.result(timeout=120) for f in futs]
+    st = srv.stats()
+    srv.stop()
+    assert all(r.info["status"] == "MM_OK" for r in res)
+    assert st["evictions"] >= 1

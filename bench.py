@@ -418,7 +418,8 @@ def run_mc(args, world, rank, local):
         tods[i] = synth.make_tod(scan, synth.make_sky(scan.n_pix, s_i), synth.make_noise(scan, s_i))
     t_gen = time.time() - t_gen
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)      # graphs are captured on a created stream
+    torch.cuda.set_stream(stream)
     tod_d = torch.from_numpy(tods).to(dev)
     ctx = M.Context(local, stream.cuda_stream, M.MM_FP32_MIXED)
     ctx.set_option("graphs", 1)

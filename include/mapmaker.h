@@ -157,6 +157,21 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
 mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, double eps_arn,
                           int32_t k, double eps_lambda, int32_t* k_out, int mem);
 
+/* Coarse space from the last M_BD solve instead of a separate Arnoldi run.
+ * With option "harvest" = m > 0, a solve with M_BD keeps, for its first
+ * right-hand side and first inner PCG run, the vectors v_j = z_j / sqrt(r_j^T z_j)
+ * (z_j = M_BD r_j) and the coefficients alpha_j, beta_j for j < m.  PCG with
+ * M_BD is the Lanczos process of B = M_BD A in the M_BD^-1 inner product, so
+ * B V = V T_m + (rank one) with T_m tridiagonal, diagonal
+ * 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j.
+ * Ritz pairs of T_m (Appendix A, Eq. ritz, in its symmetric form) give the
+ * deflation basis: the k smallest (or, if k <= 0, those below eps_lambda)
+ * form Z = V S, then Z is orthonormalised and AZ, E = Z^T A Z formed as in
+ * mm_build_coarse.  *k_out (may be NULL) receives dim Z.
+ * Errors: MM_ERR_STATE (no harvested solve), MM_ERR_ARG, MM_ERR_SINGULAR,
+ * MM_ERR_CUDA. */
+mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, int32_t* k_out);
+
 /* Install a deflation basis Z [k][n_pix][3] float64 (`mem`) instead of
  * building one: the paper's "simplified" reuse of a basis computed on another
  * data subset (Sect. 7).  AZ and E = Z^T A Z are formed with this context's A.
@@ -187,16 +202,28 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
                    const int64_t* rhs_len_or_null, mm_precond precond, double tol,
                    int32_t max_iter, mm_solve_info* info, int mem);
 
-/* Tuning knobs, by name.  "filter": 0 auto, 1 direct band, 2 FFT
- * overlap-save; "fft_log2": FFT length 2^v for the FFT filter (0 = auto);
- * "direct_tile": outputs per CTA of the direct filter; "check_every": PCG
- * iterations between host convergence checks; "graphs": 1 to replay captured
- * CUDA graphs of PCG iterations.  Errors: MM_ERR_ARG for an unknown name or
- * value. */
+/* Tuning knobs, by name.  "filter": 0 auto, 1 direct band, 2 FFT;
+ * "fft_len": FFT length 2^a 3^b (b <= 2) of the FFT filter, 0 = choose;
+ * "fft_log2": FFT length 2^v (0 = choose); "autotune": 1 (default) times the
+ * candidate filter plans on first use of a problem shape and keeps the
+ * fastest (cached per process, and in the JSON-lines file named by the
+ * environment variable MM_TUNE_CACHE when set); "direct_tile": outputs per
+ * CTA of the direct filter; "check_every": PCG iterations between host
+ * convergence checks; "graphs": 1 to replay a captured CUDA graph of
+ * check_every PCG iterations (only on a created stream, not the legacy
+ * default stream); "harvest": Lanczos vectors kept from M_BD solves (see
+ * mm_build_coarse_from_solve); "time_filter": 1 records CUDA events around
+ * every filter launch.  Errors: MM_ERR_ARG for an unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
-/* Read back a tuning knob or statistic ("filter", "fft_log2", "direct_tile",
- * "check_every", "graphs", "last_apply_ms", "device_bytes").  Errors: MM_ERR_ARG. */
+/* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"
+ * (device time of the last mm_apply_A), "filter_launches" and "filter_ms"
+ * (filter launches timed since the last read of "filter_ms", and their total
+ * device time; reading "filter_ms" resets both), "kernel_launches" (kernels
+ * launched by the library since load), "plan_fft_len", "plan_fft_log2",
+ * "plan_whole" (the plan a single-RHS product uses), "harvested" (Lanczos
+ * vectors kept by the last M_BD solve), "device_bytes" (device memory in use).
+ * Errors: MM_ERR_ARG, MM_ERR_STATE. */
 mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value);
 
 /* Stepwise solve for schedulers that interleave many solves (continuous

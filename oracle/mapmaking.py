@@ -32,7 +32,7 @@ __all__ = [
     "weights", "apply_P", "apply_Pt", "apply_Ninv", "apply_A", "rhs",
     "bd_blocks", "select_pixels", "flag_samples", "bd_inverse", "bd_apply",
     "pcg", "arnoldi", "ritz_basis", "coarse_space", "m2l_apply",
-    "dense_P", "dense_Ninv", "dense_A", "apply_A_rows", "Problem",
+    "dense_P", "dense_Ninv", "dense_A", "apply_A_rows", "Problem", "pcg_lanczos", "lanczos_ritz",
 ]
 
 
@@ -216,6 +216,54 @@ def pcg(apply_A_fn, apply_M_fn, b, tol: float = 1e-8, max_iter: int = 500):
         p = z + beta * p
     true = float(np.linalg.norm(b - apply_A_fn(x)) / bn)
     return x, dict(iters=it, hist=hist, true_rel_res=true, converged=converged)
+
+
+def pcg_lanczos(apply_A_fn, apply_M_fn, b, m: int):
+    """m steps of PCG (x_0 = 0) recording alpha_j, beta_j and v_j = z_j / sqrt(r_j^T z_j).
+
+    Same recurrences as ``pcg``; the recorded quantities are the Lanczos
+    description of B = M A that PCG builds as a by-product (used for the
+    deflation basis instead of a separate Arnoldi run).
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    r = b.copy()
+    z = apply_M_fn(r)
+    p = z.copy()
+    rz = float(r @ z)
+    alphas, betas, V = [], [], []
+    for _ in range(m):
+        V.append(z / np.sqrt(rz))
+        q = apply_A_fn(p)
+        alpha = rz / float(p @ q)
+        r = r - alpha * q
+        z = apply_M_fn(r)
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        rz = rz_new
+        p = z + beta * p
+    return np.array(alphas), np.array(betas), np.stack(V, axis=1)
+
+
+def lanczos_ritz(alphas, betas, V, k: int):
+    """Ritz pairs of B = M A from the PCG coefficients.
+
+    T_m has diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal
+    -sqrt(beta_j)/alpha_j; B V_m = V_m T_m + (a multiple of v_{m+1} e_m^T), the
+    symmetric counterpart of Eq. factoriz (Appendix A).  Returns the k
+    smallest Ritz values and the orthonormalised Ritz vectors V_m S.
+    """
+    m = len(alphas)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = -np.sqrt(betas[j]) / alphas[j]
+    lam, S = np.linalg.eigh(T)
+    Z = V[:, :m] @ S[:, :k]
+    Q, _ = np.linalg.qr(Z)
+    return lam[:k], Q, T
 
 
 def arnoldi(apply_B_fn, r0, m_max: int, tol: float):

@@ -44,7 +44,13 @@ struct DevBuf {
     template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+struct FftTables {
+    int L = 0;
+    DevBuf tw, H;
+};
+
 struct Plan {
+    FftTables ft;      // twiddles and band spectra for this plan's L
     int variant = 0;   // 1 direct, 2 fft
     int L = 0, logL = 0, V = 0;
     int whole = 0;     // FFT: one transform per whole block (no overlap-save halo)
@@ -54,11 +60,6 @@ struct Plan {
     std::vector<int64_t> lens;
     DevBuf segs;
     int n_work = 0;
-};
-
-struct FftTables {
-    int L = 0;
-    DevBuf tw, H;
 };
 
 enum Phase { PH_IDLE = 0, PH_INNER = 1, PH_DONE = 2 };
@@ -77,6 +78,7 @@ struct mm_ctx {
     int opt_filter = 0, opt_fft_log2 = 0, opt_fft_len = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
     int opt_time_filter = 0;
     int opt_autotune = 1;
+    int opt_harvest = 0;           // Lanczos vectors kept from an M_BD solve (0: off)
     double last_apply_ms = 0.0;
     // CUDA-event pairs around filter launches (when timing is on)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fev;
@@ -91,7 +93,6 @@ struct mm_ctx {
     std::vector<int32_t> block_band;
     std::vector<double> band;
     DevBuf d_pix, d_psi, d_cs64, d_block_off, d_block_band, d_band64, d_band32;
-    FftTables fft32, fft64;
     std::vector<std::unique_ptr<Plan>> plans;
 
     // M_BD
@@ -127,6 +128,14 @@ struct mm_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;
+    // Lanczos harvest of the last M_BD solve (right-hand side 0)
+    bool harvest_on = false;
+    int harvest_count = 0;
+    DevBuf d_harv, d_ahist, d_bhist;
+    std::vector<double> harv_alpha, harv_beta;
+    // per right-hand-side coarse operators for batches of uneven length
+    bool coarse_per_rhs = false;
+    DevBuf d_AZr, d_Einvr;
     // asynchronous stepping
     RhsState* h_st_pinned = nullptr;
     int h_st_pinned_n = 0;
@@ -384,7 +393,7 @@ mm_status make_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>&
     if (!segs.empty())
         CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (variant == 2) TRY(build_fft_tables(ctx, f64 ? ctx->fft64 : ctx->fft32, fp, f64));
+    if (variant == 2) TRY(build_fft_tables(ctx, p->ft, fp, f64));
     ctx->plans.push_back(std::move(p));
     *out = ctx->plans.back().get();
     return MM_OK;
@@ -566,7 +575,7 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         e1 = pr.second;
     }
     if (plan->variant == 2) {
-        FftTables& ft = plan->f64 ? ctx->fft64 : ctx->fft32;
+        FftTables& ft = plan->ft;
         a.H = ft.H.p;
         a.tw = ft.tw.p;
         if (plan->f64) launch_filter_fft_f64(a, from_tod, ctx->stream);
@@ -650,6 +659,18 @@ PcgArgs pcg_args(mm_ctx* ctx) {
     a.hist = ctx->s_hist.as<double>();
     a.hist_stride = ctx->max_iter + 1;
     a.grid_x = ctx->grid_x;
+    if (ctx->coarse_per_rhs && ctx->precond == MM_PRECOND_2L) {
+        a.AZ = ctx->d_AZr.as<V4<double>>();
+        a.Einv = ctx->d_Einvr.as<double>();
+        a.az_stride = (int64_t)ctx->k * ctx->n_pix;
+        a.einv_stride = ctx->k * ctx->k;
+    }
+    if (ctx->harvest_on) {
+        a.ahist = ctx->d_ahist.as<double>();
+        a.bhist = ctx->d_bhist.as<double>();
+        a.harvest = ctx->d_harv.as<V4<double>>();
+        a.harvest_m = ctx->opt_harvest;
+    }
     return a;
 }
 
@@ -673,6 +694,8 @@ mm_status pcg_iteration(mm_ctx* ctx) {
     if (two) {
         launch_m2l_ztr(a, a.r, ctx->stream);
         launch_m2l_apply(a, a.r, a.z, 1, ctx->stream);
+    } else if (ctx->harvest_on) {
+        launch_harvest(a, ctx->stream);
     }
     CKL();
     return MM_OK;
@@ -690,6 +713,7 @@ mm_status pcg_start(mm_ctx* ctx, const V4<double>* b, const std::vector<double>&
     PcgArgs a = pcg_args(ctx);
     launch_pcg_init(a, b, ctx->stream);
     precond_step(ctx, a, 0);
+    if (ctx->harvest_on && ctx->precond == MM_PRECOND_BD) launch_harvest(a, ctx->stream);
     CKL();
     return MM_OK;
 }
@@ -839,6 +863,55 @@ mm_status finish_coarse(mm_ctx* ctx) {
 
 }  // namespace
 
+namespace {
+// Per right-hand side coarse operators for a batch of uneven lengths: the
+// basis Z is shared, AZ_i = A_i Z and E_i = Z^T A_i Z use each right-hand
+// side's own A_i (its first rhs_len[i] samples per detector), so that
+// M_2l,i A_i Z = Z holds for every i (Sect. 3.2, Eq. ident).
+mm_status coarse_for_lens(mm_ctx* ctx) {
+    const int k = ctx->k, R = ctx->nrhs;
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    const bool f64 = !is_f32(ctx);
+    std::vector<int64_t> lens_rep;
+    for (int r = 0; r < R; ++r)
+        for (int c = 0; c < k; ++c) lens_rep.push_back(ctx->lens[r]);
+    DevBuf zrep;
+    CK(zrep.ensure((size_t)R * k * n * 8));
+    for (int r = 0; r < R; ++r)
+        CK(cudaMemcpyAsync(zrep.as<double>() + (size_t)r * k * n, ctx->d_Z.p, (size_t)k * n * 8,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(ctx->d_AZr.ensure((size_t)R * k * n * 8));
+    Plan* plan = nullptr;
+    TRY(get_plan(ctx, f64, R * k, lens_rep, &plan));
+    TRY(apply_A_dev(ctx, f64, zrep.as<V4<double>>(), ctx->d_AZr.as<V4<double>>(), R * k, plan));
+    DevBuf dG;
+    CK(dG.ensure((size_t)R * k * k * 8));
+    CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(k, 2) * sizeof(double) + 64));
+    for (int r = 0; r < R; ++r)
+        launch_gram(ctx->d_Z.as<double>(), k, ctx->d_AZr.as<double>() + (size_t)r * k * n, k, n, n,
+                    dG.as<double>() + (size_t)r * k * k, ctx->w_partial.as<double>(), ctx->w_counter.as<unsigned>(),
+                    ctx->grid_x, ctx->stream);
+    CKL();
+    std::vector<double> G((size_t)R * k * k), Einv_all((size_t)R * k * k);
+    CK(cudaMemcpyAsync(G.data(), dG.p, G.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < R; ++r) {
+        const double* g = &G[(size_t)r * k * k];
+        std::vector<double> E((size_t)k * k), Einv;
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) E[(size_t)i * k + j] = 0.5 * (g[(size_t)j * k + i] + g[(size_t)i * k + j]);
+        if (!host_cholesky(E, k)) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not SPD");
+        host_spd_inverse_from_chol(E, k, Einv);
+        std::copy(Einv.begin(), Einv.end(), Einv_all.begin() + (size_t)r * k * k);
+    }
+    CK(ctx->d_Einvr.ensure(Einv_all.size() * 8));
+    CK(cudaMemcpyAsync(ctx->d_Einvr.p, Einv_all.data(), Einv_all.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->coarse_per_rhs = true;
+    return MM_OK;
+}
+}  // namespace
+
 namespace mm {
 // Read-only view of a context's M_BD and coarse space for other translation units.
 bool ctx_coarse_view(mm_ctx* ctx, CoarseView* v) {
@@ -931,7 +1004,6 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     ctx->k = 0;
     ctx->have_lastb = false;
     ctx->plans.clear();
-    ctx->fft32.L = ctx->fft64.L = 0;
     ctx->n_samples = n_samples;
     ctx->n_det = n_det;
     ctx->n_t = n_t;
@@ -1267,6 +1339,63 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     return MM_OK;
 }
 
+mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, int32_t* k_out) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (ctx->harvest_count < 2) return fail(ctx, MM_ERR_STATE, "no harvested M_BD solve (set option harvest > 1)");
+    if (k > 128) return fail(ctx, MM_ERR_ARG, "k must be at most 128");
+    CK(cudaSetDevice(ctx->device));
+    const int m = ctx->harvest_count;
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    // T: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal -sqrt(beta_j)/alpha_j
+    std::vector<double> T((size_t)m * m, 0.0);
+    const auto& al = ctx->harv_alpha;
+    const auto& be = ctx->harv_beta;
+    for (int j = 0; j < m; ++j) {
+        T[(size_t)j * m + j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+        if (j + 1 < m) {
+            const double off = -std::sqrt(std::max(0.0, be[j])) / al[j];
+            T[(size_t)j * m + j + 1] = off;
+            T[(size_t)(j + 1) * m + j] = off;
+        }
+    }
+    std::vector<double> wr, wi, vr, vi;
+    if (!host_eig(T, m, wr, wi, vr, vi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
+    const int kwant = k > 0 ? std::min(k, m) : m;
+    std::vector<int> sel;
+    std::vector<double> vals;
+    for (int idx : order) {
+        if ((int)sel.size() >= kwant) break;
+        if (k <= 0 && !(wr[idx] < eps_lambda)) break;
+        sel.push_back(idx);
+        vals.push_back(wr[idx]);
+    }
+    const int ksel = (int)sel.size();
+    if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
+    std::vector<double> C((size_t)m * ksel);
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < ksel; ++c) C[(size_t)r * ksel + c] = vr[(size_t)r * m + sel[c]];
+    DevBuf dC;
+    CK(dC.ensure(C.size() * 8));
+    CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->k = 0;
+    TRY(ensure_work(ctx, 1, 128));
+    CK(ctx->d_Z.ensure((size_t)ksel * n * 8));
+    launch_combo(ctx->d_harv.as<double>(), n, m, dC.as<double>(), ksel, ctx->d_Z.as<double>(), n, n, ctx->stream);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    int kk = 0;
+    TRY(orthonormalise(ctx, ctx->d_Z, ksel, &kk));
+    ctx->k = kk;
+    ctx->ritz.assign(vals.begin(), vals.begin() + std::min<size_t>(vals.size(), kk));
+    TRY(finish_coarse(ctx));
+    if (k_out) *k_out = ctx->k;
+    return MM_OK;
+}
+
 mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
@@ -1352,6 +1481,16 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     CK(ctx->s_u.ensure((size_t)nrhs * std::max(1, ctx->k) * 8));
     CK(ctx->s_mask.ensure((size_t)nrhs * 4 + 16));
     if (ctx->use_lens) TRY(bd_for_lens(ctx));
+    ctx->harvest_on = false;
+    if (ctx->opt_harvest > 0 && precond == MM_PRECOND_BD) {
+        CK(ctx->d_harv.ensure((size_t)ctx->opt_harvest * ctx->n_pix * sizeof(V4<double>)));
+        CK(ctx->d_ahist.ensure((size_t)nrhs * (max_iter + 1) * 8));
+        CK(ctx->d_bhist.ensure((size_t)nrhs * (max_iter + 1) * 8));
+        ctx->harvest_on = true;
+        ctx->harvest_count = 0;
+    }
+    ctx->coarse_per_rhs = false;
+    if (ctx->use_lens && precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx));
     TRY(get_plan(ctx, !f32, nrhs, ctx->lens, &ctx->plan_op));
     TRY(get_plan(ctx, true, nrhs, ctx->lens, &ctx->plan_64));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -1401,6 +1540,19 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
 static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
     // all inner PCG runs have stopped: accumulate and (mixed) refine
     const int R = ctx->nrhs;
+    if (ctx->harvest_on) {
+        // the Lanczos sequence is the first inner solve's; restarts would begin a new one
+        ctx->harvest_on = false;
+        const int m = std::min(ctx->h_st[0].iters, ctx->opt_harvest);
+        ctx->harvest_count = m;
+        ctx->harv_alpha.assign(m, 0.0);
+        ctx->harv_beta.assign(m, 0.0);
+        if (m > 0) {
+            CK(cudaMemcpyAsync(ctx->harv_alpha.data(), ctx->d_ahist.p, m * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->harv_beta.data(), ctx->d_bhist.p, m * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
     std::vector<int32_t> mask(R, 1);
     for (int i = 0; i < R; ++i) {
         ctx->tot_iters[i] += ctx->h_st[i].iters;
@@ -1447,7 +1599,9 @@ static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
 
 static mm_status launch_iters(mm_ctx* ctx, int32_t n_iter) {
     if (n_iter <= 0) return MM_OK;
-    if (ctx->opt_graphs && n_iter == ctx->opt_check_every) {
+    const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy &&
+                            ctx->stream != cudaStreamPerThread;
+    if (ctx->opt_graphs && capturable && n_iter == ctx->opt_check_every) {
         if (!ctx->graph_exec) {
             // one eager iteration first so every kernel attribute is configured
             TRY(pcg_iteration(ctx));
@@ -1617,6 +1771,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_graphs = v ? 1 : 0;
     } else if (n == "autotune") {
         ctx->opt_autotune = v ? 1 : 0;
+    } else if (n == "harvest") {
+        if (v < 0 || v > 4096) return fail(ctx, MM_ERR_ARG, "harvest must lie in [0, 4096]");
+        ctx->opt_harvest = v;
     } else if (n == "time_filter") {
         ctx->opt_time_filter = v ? 1 : 0;
         ctx->fev_used = 0;
@@ -1639,6 +1796,8 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "kernel_launches") *value = (double)launches_total();
     else if (n == "time_filter") *value = ctx->opt_time_filter;
     else if (n == "autotune") *value = ctx->opt_autotune;
+    else if (n == "harvest") *value = ctx->opt_harvest;
+    else if (n == "harvested") *value = ctx->harvest_count;
     else if (n == "filter_ms" || n == "filter_launches") {
         // total device time of the filter launches timed since the last read; resets the record
         CK(cudaStreamSynchronize(ctx->stream));

@@ -134,6 +134,14 @@ struct PcgArgs {
     double* hist;            // [nrhs][hist_stride]
     int hist_stride;
     int grid_x;
+    // per right-hand-side coarse operators (0 strides: shared)
+    int64_t az_stride;       // in V4<double> units
+    int einv_stride;         // in doubles
+    // Lanczos harvest from an M_BD run (null when off)
+    double* ahist;           // [nrhs][hist_stride] alpha_j
+    double* bhist;           // [nrhs][hist_stride] beta_j
+    V4<double>* harvest;     // [harvest_m][n_pix] z_j / sqrt(r_j^T z_j) of right-hand side 0
+    int harvest_m;
 };
 void launch_pcg_init(const PcgArgs& a, const V4<double>* b, cudaStream_t s);
 void launch_pcg_src(const PcgArgs& a, int first, cudaStream_t s);
@@ -143,6 +151,7 @@ void launch_precond_bd_dot(const PcgArgs& a, int finalize_beta, cudaStream_t s);
 void launch_m2l_ztr(const PcgArgs& a, const V4<double>* v, cudaStream_t s);
 void launch_m2l_apply(const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta,
                       cudaStream_t s);
+void launch_harvest(const PcgArgs& a, cudaStream_t s);
 
 // Tall-skinny float64 products over vectors of n doubles (n = 4 n_pix).
 // h[i] = sum_n X[i][n] v[n] for i < m  (deterministic two-phase reduction)

@@ -425,6 +425,7 @@ __global__ void k_pcg_pq(const PcgArgs a) {
             } else {
                 st.alpha = st.rz / pq;
             }
+            if (a.ahist) a.ahist[(int64_t)rhs * a.hist_stride + st.iters] = st.alpha;
             a.counter[rhs] = 0;
         }
     }
@@ -480,6 +481,7 @@ __global__ void k_pcg_update(const PcgArgs a) {
                 const double rz = gather_partial<2>(a.partial, gridDim.x, a.nrhs, rhs, 1);
                 st.beta = rz / st.rz;
                 st.rz = rz;
+                if (a.bhist) a.bhist[(int64_t)rhs * a.hist_stride + st.iters - 1] = st.beta;
             }
             a.counter[rhs] = 0;
         }
@@ -512,9 +514,10 @@ __global__ void k_m2l_ztr(const PcgArgs a, const V4<double>* v) {
             t[c] = s;
         }
         __syncthreads();
+        const double* Einv = a.Einv + (int64_t)rhs * a.einv_stride;
         for (int c = threadIdx.x; c < k; c += VT) {
             double s = 0.0;
-            for (int j = 0; j < k; ++j) s += a.Einv[c * k + j] * t[j];
+            for (int j = 0; j < k; ++j) s += Einv[c * k + j] * t[j];
             a.u[(int64_t)rhs * k + c] = s;
         }
         if (threadIdx.x == 0) a.counter[rhs] = 0;
@@ -531,11 +534,12 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
     for (int c = threadIdx.x; c < a.k; c += VT) u[c] = a.u[(int64_t)rhs * a.k + c];
     __syncthreads();
     double acc[1] = {0.0};
+    const V4<double>* AZ = a.AZ + (int64_t)rhs * a.az_stride;
     PIX_LOOP(i) {
         V4<double> y = v[off + i];
         V4<double> zu{0, 0, 0, 0};
         for (int c = 0; c < a.k; ++c) {
-            const V4<double> azc = a.AZ[(int64_t)c * a.n_pix + i];
+            const V4<double> azc = AZ[(int64_t)c * a.n_pix + i];
             const V4<double> zc = a.Z[(int64_t)c * a.n_pix + i];
             const double uc = u[c];
             y.x -= azc.x * uc;
@@ -563,6 +567,23 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
             a.counter[rhs] = 0;
         }
     }
+}
+
+// Lanczos vectors of M_BD A from PCG with M_BD: v_j = z_j / sqrt(r_j^T z_j)
+// (right-hand side 0), stored while j < harvest_m.
+__global__ void k_harvest(const PcgArgs a) {
+    const RhsState st = a.st[0];
+    if (!st.active || st.iters >= a.harvest_m) return;
+    const double sc = 1.0 / sqrt(st.rz);
+    V4<double>* w = a.harvest + (int64_t)st.iters * a.n_pix;
+    for (int i = blockIdx.x * VT + threadIdx.x; i < a.n_pix; i += gridDim.x * VT) {
+        const V4<double> z = a.z[i];
+        w[i] = V4<double>{z.x * sc, z.y * sc, z.z * sc, 0.0};
+    }
+}
+void launch_harvest(const PcgArgs& a, cudaStream_t s) {
+    k_harvest<<<a.grid_x, VT, 0, s>>>(a);
+    count_launches(1);
 }
 
 void launch_pcg_init(const PcgArgs& a, const V4<double>* b, cudaStream_t s) {

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("mm_estimate_bytes", C.c_int64, [_I64, _I32, _I32, _I32, _I32, _I32, _I32, C.c_int]),
     ("mm_apply_precond_2l_noalloc", C.c_int, [_VP, _VP, _VP, _I32]),
     ("mm_solve_launch", C.c_int, [_VP, _I32]),
+    ("mm_build_coarse_from_solve", C.c_int, [_VP, _I32, _D, C.POINTER(_I32)]),
     ("mm_solve_poll", C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32)]),
 ]
 
@@ -222,6 +223,11 @@ class Context:
         pb, m1, kb = _arg(b, np.float64)
         self._check(self.lib.mm_build_coarse(self.h, pb, int(m_max), float(eps_arn), int(k),
                                              float(eps_lambda), C.byref(kout), m1))
+        return kout.value
+
+    def build_coarse_from_solve(self, k=32, eps_lambda=0.2) -> int:
+        kout = C.c_int32(0)
+        self._check(self.lib.mm_build_coarse_from_solve(self.h, int(k), float(eps_lambda), C.byref(kout)))
         return kout.value
 
     def set_coarse(self, Z):

@@ -271,3 +271,78 @@ def test_errors_are_reported():
     assert e.value.status == MM.MM_ERR_ARG
     with pytest.raises(MM.MapMakerError):
         c.set_option("filter", 7)
+
+
+def test_graph_replay_matches_eager():
+    torch = pytest.importorskip("torch")
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=8192, n_int=8, half_bw=32, f_knee=1.0)
+    scan = synth.make_scan(seed=15, **cfg)
+    lens = np.array([8192, 5000, 7000], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 300 + i), synth.make_noise(scan, 300 + i))
+                     for i in range(3)])
+    stream = torch.cuda.Stream()
+    res = []
+    for graphs in (0, 1):
+        c = MM.Context(0, stream.cuda_stream, MM.MM_FP64)
+        c.set_option("graphs", graphs)
+        c.set_option("check_every", 5)
+        c.setup_scan(scan)
+        c.build_bd()
+        c.build_coarse(c.rhs(tods[:1])[0], m_max=20, eps_arn=1e-8, k=4)
+        x, info = c.solve(tods, MM.MM_PRECOND_2L, tol=1e-10, max_iter=500, rhs_len=lens)
+        res.append((x, info))
+        c.close()
+    for i in range(3):
+        assert res[1][1][i]["status"] == "MM_OK"
+        assert res[1][1][i]["iters"] == res[0][1][i]["iters"]
+        assert rel(res[1][0][i], res[0][0][i]) < 1e-9
+
+
+def test_harvested_lanczos_coarse_space_matches_oracle():
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=2048, n_int=2, half_bw=64, f_knee=2.0)
+    scan, d, _ = scan_and_tod(cfg, seed=17)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan)
+    c.build_bd()
+    m = 14
+    c.set_option("harvest", m)
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=2000)
+    assert info[0]["iters"] > m and c.get_option("harvested") == m
+    k = c.build_coarse_from_solve(k=5)
+    assert k == 5
+    Z, ritz = c.get_coarse()
+    A_fn = lambda v: O.apply_A(prob, v).reshape(-1)  # noqa: E731
+    M_fn = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+    al, be, V = O.pcg_lanczos(A_fn, M_fn, O.rhs(prob, d).reshape(-1), m)
+    vals, Zo, T = O.lanczos_ritz(al, be, V, 5)
+    np.testing.assert_allclose(np.sort(ritz), np.sort(vals), rtol=1e-8, atol=1e-10)
+    Zg = Z.reshape(k, -1).T
+    assert np.linalg.norm(Zg @ Zg.T - Zo @ Zo.T) < 1e-6
+    AZ = c.apply_A(Z)
+    assert rel(c.apply_precond(MM.MM_PRECOND_2L, AZ), Z) < 1e-10
+    x2, i2 = c.solve(d, MM.MM_PRECOND_2L, tol=1e-10, max_iter=2000)
+    assert i2[0]["status"] == "MM_OK" and i2[0]["iters"] < info[0]["iters"]
+    assert rel(x2[0], x[0]) < 1e-7
+
+
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_batched_two_level_uneven_lengths(prec):
+    """Shared basis Z, per right-hand side AZ_i and E_i: every map matches its own problem."""
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=8192, n_int=8, half_bw=64, f_knee=2.0)
+    scan = synth.make_scan(seed=18, **cfg)
+    lens = np.array([8192, 4500, 6000, 7333], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 400 + i), synth.make_noise(scan, 400 + i))
+                     for i in range(len(lens))])
+    c = ctx_for(scan, prec)
+    c.build_bd()
+    tt = tods.astype(c.tod_dtype)
+    c.build_coarse(c.rhs(tt[:1])[0], m_max=40, eps_arn=1e-8, k=8)
+    xb, ib = c.solve(tt, MM.MM_PRECOND_2L, tol=1e-9, max_iter=2000, rhs_len=lens)
+    xbd, ibd = c.solve(tt, MM.MM_PRECOND_BD, tol=1e-9, max_iter=2000, rhs_len=lens)
+    _, _, good = oracle_problem(scan)
+    for i, L in enumerate(lens):
+        assert ib[i]["status"] == "MM_OK"
+        assert ib[i]["iters"] <= ibd[i]["iters"]
+        prob, mbd, idx = truncated_problem(scan, int(L), good=good)
+        xo = _oracle_solution(prob, mbd, O.rhs(prob, tt[i][idx].astype(np.float64)))
+        assert rel(xb[i], xo) < 1e-6

@@ -420,3 +420,59 @@ def test_planted_shifted_band_is_caught(monkeypatch):
     monkeypatch.setattr(O.mapmaking, "apply_Ninv", shifted)
     x = np.random.default_rng(14).standard_normal(prob.n)
     assert not np.allclose(O.mapmaking.apply_A(prob, x).reshape(-1), A @ x, rtol=1e-6)
+
+
+# ---------------- Lanczos vectors from an M_BD PCG run ----------------
+
+def test_pcg_lanczos_relation_and_full_spectrum():
+    prob, mbd, gi, A_fn, M_fn, b = _B_setup(16)
+    n_good = int(gi.sum())
+    m = 10
+    al, be, V = O.pcg_lanczos(A_fn, M_fn, b, m)
+    vals, Z, T = O.lanczos_ritz(al, be, V, m)
+    # v_j are orthonormal in the M^-1 inner product: v_i^T A-free check via r = M^-1 z
+    Minv = np.zeros((prob.n, prob.n))
+    for p in range(prob.n_pix):
+        if gi[3 * p]:
+            Minv[3 * p:3 * p + 3, 3 * p:3 * p + 3] = np.linalg.inv(mbd[p])
+    G = V.T @ Minv @ V
+    np.testing.assert_allclose(G, np.eye(m), atol=1e-9)
+    # B V_m = V_m T_m apart from the last column (the symmetric form of Eq. factoriz)
+    BV = np.stack([M_fn(A_fn(V[:, j])) for j in range(m)], axis=1)
+    R = BV - V @ T
+    assert np.linalg.norm(R[:, :m - 1]) <= 1e-9 * np.linalg.norm(BV)
+    # Ritz residual (the symmetric counterpart of Eq. ritz): for T_m s = theta s,
+    # ||B V_m s - theta V_m s||_{M^-1} = |t_{m+1,m}| |e_m^T s|, t_{m+1,m} = -sqrt(beta_{m-1})/alpha_{m-1}
+    al, be, V = O.pcg_lanczos(A_fn, M_fn, b, m + 1)
+    _, _, T = O.lanczos_ritz(al[:m], be[:m], V[:, :m], m)
+    th, S = np.linalg.eigh(T)
+    t_next = np.sqrt(be[m - 1]) / al[m - 1]
+    for i in (0, 1, m - 1):
+        y = V[:, :m] @ S[:, i]
+        res = M_fn(A_fn(y)) - th[i] * y
+        lhs = np.sqrt(res @ Minv @ res)
+        assert lhs == pytest.approx(t_next * abs(S[-1, i]), rel=1e-6, abs=1e-12)
+    # a long run: Ritz values stay inside the spectrum of M_BD A and the extremes converge
+    al, be, V = O.pcg_lanczos(A_fn, M_fn, b, n_good)
+    vals, Z, T = O.lanczos_ritz(al, be, V, n_good)
+    A = O.dense_A(prob)
+    MA = np.zeros_like(A)
+    for p in range(prob.n_pix):
+        MA[3 * p:3 * p + 3] = mbd[p] @ A[3 * p:3 * p + 3]
+    ev = np.sort(np.linalg.eigvals(MA[np.ix_(gi, gi)]).real)
+    assert vals.min() >= ev[0] - 1e-9 and vals.max() <= ev[-1] + 1e-9
+    assert abs(vals.min() - ev[0]) < 1e-9 and abs(vals.max() - ev[-1]) < 1e-9
+
+
+def test_lanczos_deflation_satisfies_m2l_identity():
+    prob, mbd, gi, A_fn, M_fn, b = _B_setup(17)
+    al, be, V = O.pcg_lanczos(A_fn, M_fn, b, 25)
+    vals, Z, T = O.lanczos_ritz(al, be, V, 6)
+    AZ, E, L = O.coarse_space(A_fn, Z)
+    for i in range(Z.shape[1]):
+        np.testing.assert_allclose(O.m2l_apply(A_fn(Z[:, i]), M_fn, Z, AZ, L), Z[:, i], atol=1e-10)
+    # the smallest Ritz pairs are accurate eigenpairs of B after 25 steps
+    for i in range(2):
+        y = Z[:, i]
+        th = (y @ M_fn(A_fn(y))) / (y @ y)
+        assert np.linalg.norm(M_fn(A_fn(y)) - th * y) < 1e-3 * np.linalg.norm(y) * abs(th) + 1e-6

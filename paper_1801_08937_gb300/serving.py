@@ -116,6 +116,7 @@ class MapServer:
         self.rejected = 0
         self.max_concurrent = 0
         self.t0 = None
+        self.error = None
 
     # ---------------- public API ----------------
     def start(self):
@@ -165,12 +166,14 @@ class MapServer:
         esz = 4 if self.precision == M.MM_FP32_MIXED else 8
         return spec.n_samples * esz + spec.n_pix * 32 * 16
 
-    def _evict_idle(self, need: int) -> bool:
+    def _evict_idle(self, need: int, keep_id: str | None = None) -> bool:
         for sid in list(self._scans.keys()):
             if self._free_bytes() >= need:
                 return True
+            if sid == keep_id:
+                continue
             e = self._scans[sid]
-            if not e.busy and e.ready:
+            if not e.busy and e.ready and sid not in self._setting_up:
                 e.ctx.close()
                 del self._scans[sid]
                 self.evictions += 1
@@ -212,7 +215,7 @@ class MapServer:
                 fut.set_exception(e.error)
                 continue
             need = self._solve_bytes(req.scan) + (0 if e is not None else self._scan_bytes(req.scan))
-            if self._free_bytes() < need and not self._evict_idle(need):
+            if self._free_bytes() < need and not self._evict_idle(need, keep_id=req.scan_id):
                 keep.append((req, fut))
                 continue
             if e is None:
@@ -284,11 +287,33 @@ class MapServer:
         self._active = still
         return progressed
 
+    def _fail_all(self, ex):
+        with self._lock:
+            pending = list(self._pending)
+            self._pending.clear()
+        for _, fut in pending:
+            if not fut.done():
+                fut.set_exception(ex)
+        for a in self._active:
+            if not a.fut.done():
+                a.fut.set_exception(ex)
+        for waiting in self._setting_up.values():
+            for _, fut in waiting:
+                if not fut.done():
+                    fut.set_exception(ex)
+        self._active = []
+        self._setting_up = {}
+
     def _loop(self):
         self.torch.cuda.set_device(self.device)
         while not self._stop.is_set():
-            self._finish_setups()
-            self._admit()
-            progressed = self._tick() if self._active else False
+            try:
+                self._finish_setups()
+                self._admit()
+                progressed = self._tick() if self._active else False
+            except Exception as ex:   # a scheduler fault fails every request instead of hanging them
+                self._fail_all(ex)
+                self.error = ex
+                return
             if not progressed:
                 time.sleep(0.0002)

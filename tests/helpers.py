@@ -44,7 +44,12 @@ def truncated_problem(scan, length, rcond_min=1e-3, good=None):
     prob = O.Problem(pix[idx], scan.psi[idx], new_off, scan.band, np.array(bands), scan.n_pix)
     blocks, hits = O.bd_blocks(prob)
     g = good if good is not None else O.select_pixels(blocks, hits, rcond_min)
-    mbd = O.bd_inverse(blocks, g & (hits > 0))
+    # a pixel kept on the full scan but numerically singular in this prefix
+    # gets a zero M_BD block (as in the library), so PCG leaves it at zero
+    ev = np.linalg.eigvalsh(blocks)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rc = np.where(ev[:, 2] > 0, ev[:, 0] / ev[:, 2], 0.0)
+    mbd = O.bd_inverse(blocks, g & (hits > 0) & (rc > 1e-12))
     return prob, mbd, idx
 
 

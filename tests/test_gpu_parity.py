@@ -344,5 +344,6 @@ def test_batched_two_level_uneven_lengths(prec):
         assert ib[i]["status"] == "MM_OK"
         assert ib[i]["iters"] <= ibd[i]["iters"]
         prob, mbd, idx = truncated_problem(scan, int(L), good=good)
-        xo = _oracle_solution(prob, mbd, O.rhs(prob, tt[i][idx].astype(np.float64)))
-        assert rel(xb[i], xo) < 1e-6
+        xo = _oracle_solution(prob, mbd, O.rhs(prob, tt[i][idx].astype(np.float64))).reshape(-1, 3)
+        well = np.abs(mbd).reshape(scan.n_pix, -1).sum(axis=1) > 0   # pixels this prefix determines
+        assert rel(xb[i][well], xo[well]) < 1e-6

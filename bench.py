@@ -285,11 +285,8 @@ def main():
     launches = int(ctx.get_option("kernel_launches") - launches0)
     ctx.set_option("time_filter", 0)
     info2l = dict(info_last["info"])
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    from paper_1801_08937_gb300 import sharding as SH
+    ms_max = SH.max_over_ranks(ms, dist)
     maps = args.steps * world
     value = ms_max / 1e3 / maps
 

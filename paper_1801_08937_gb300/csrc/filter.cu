@@ -247,6 +247,79 @@ __device__ void fft_dit_conj(C2<T>* s, const C2<T>* tw, const FftPasses& fp) {
     }
 }
 
+// ---- compile-time plans for the lengths the planner uses most ----
+// Same pass order as the host planner: a radix-9 or radix-3 pass, radix-16
+// passes, then one radix 2, 4 or 8 pass; all spans and index divisors are
+// constants, so the butterfly addressing folds to shifts and multiplies.
+struct CtPlan {
+    int np;
+    int r[8];
+    int s[8];
+};
+__host__ __device__ constexpr CtPlan make_ct_plan(int L) {
+    CtPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int rest = L, span = L;
+    if (rest % 9 == 0) {
+        p.r[p.np] = 9; p.s[p.np] = span; span /= 9; rest /= 9; ++p.np;
+    } else if (rest % 3 == 0) {
+        p.r[p.np] = 3; p.s[p.np] = span; span /= 3; rest /= 3; ++p.np;
+    }
+    while (rest % 16 == 0 && p.np < 8) {
+        p.r[p.np] = 16; p.s[p.np] = span; span /= 16; rest /= 16; ++p.np;
+    }
+    if (rest == 8 || rest == 4 || rest == 2) {
+        p.r[p.np] = rest; p.s[p.np] = span; ++p.np;
+    }
+    return p;
+}
+
+template <typename T, int R, int S, int L, int NT, bool DIT>
+__device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) {
+    constexpr int Sr = S / R;
+    constexpr int nbf = L / R;
+    constexpr int tstep = L / S;
+#pragma unroll 1
+    for (int bf = threadIdx.x; bf < nbf; bf += NT) {
+        const int g = bf / Sr;
+        const int j = bf - g * Sr;
+        const int base = g * S + j;
+        C2<T> w1{T(1), T(0)};
+        if (Sr > 1) w1 = ldtw(tw, j * tstep);
+        C2<T> a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + r * Sr)];
+        if (!DIT) Dft<T, R>::run(a);
+        if (Sr > 1) {
+            C2<T> w[R];
+            twiddle_powers<T, R>(w1, w);
+#pragma unroll
+            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
+        }
+        if (DIT) Dft<T, R>::run(a);
+#pragma unroll
+        for (int q = 0; q < R; ++q) s[sidx(base + q * Sr)] = a[q];
+    }
+}
+
+template <typename T, int L, int NT, int P>
+__device__ __forceinline__ void ct_dif(C2<T>* s, const C2<T>* tw) {
+    constexpr CtPlan pl = make_ct_plan(L);
+    if constexpr (P < pl.np) {
+        ct_pass<T, pl.r[P], pl.s[P], L, NT, false>(s, tw);
+        __syncthreads();
+        ct_dif<T, L, NT, P + 1>(s, tw);
+    }
+}
+template <typename T, int L, int NT, int P>
+__device__ __forceinline__ void ct_dit(C2<T>* s, const C2<T>* tw) {
+    constexpr CtPlan pl = make_ct_plan(L);
+    if constexpr (P >= 0) {
+        ct_pass<T, pl.r[P], pl.s[P], L, NT, true>(s, tw);
+        __syncthreads();
+        ct_dit<T, L, NT, P - 1>(s, tw);
+    }
+}
+
 // ---- pointing weights ----
 // float32: __sincosf on 2 psi - pi in [-pi, pi), where its error stays near
 // 4e-7; cos 2psi = -cos(2psi - pi), sin 2psi = -sin(2psi - pi).
@@ -439,7 +512,7 @@ __device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
 }
 
 // ---------------- FFT overlap-save variant ----------------
-template <typename T, bool FROM_TOD, int NT>
+template <typename T, bool FROM_TOD, int NT, int LCT>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_filter_fft(const FilterArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
@@ -448,13 +521,14 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     const bool actA = seg_active<T>(a, A);
     const bool actB = seg_active<T>(a, B);
     if (!actA && !actB) return;
-    const int L = a.L;
+    const int L = LCT > 0 ? LCT : a.L;
     const int lam = actA ? A.shift : B.shift;   // left halo of this pair (lambda, or 0 for whole blocks)
     const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
 
     gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
     __syncthreads();
-    fft_dif<T>(s, tw, a.fp);
+    if constexpr (LCT > 0) ct_dif<T, LCT, NT, 0>(s, tw);
+    else fft_dif<T>(s, tw, a.fp);
     const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const C2<T> v = s[sidx(i)];
@@ -462,7 +536,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
         s[sidx(i)] = C2<T>{v.x * h, -v.y * h};
     }
     __syncthreads();
-    fft_dit_conj<T>(s, tw, a.fp);
+    if constexpr (LCT > 0) ct_dit<T, LCT, NT, make_ct_plan(LCT > 0 ? LCT : 64).np - 1>(s, tw);
+    else fft_dit_conj<T>(s, tw, a.fp);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int vmax = max(actA ? A.n_out : 0, actB ? B.n_out : 0);
@@ -568,26 +643,50 @@ size_t direct_smem_bytes(int V, int lam, bool f64) {
     return (size_t)(((lam + 2) & ~1) + V + 2 * lam) * (f64 ? 8 : 4);
 }
 
-template <typename T, bool FROM_TOD, int NT>
+template <typename T, bool FROM_TOD, int NT, int LCT>
 static void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
     static size_t configured = 0;
     if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured = sm;
     }
-    k_filter_fft<T, FROM_TOD, NT><<<a.n_work, NT, sm, s>>>(a);
+    k_filter_fft<T, FROM_TOD, NT, LCT><<<a.n_work, NT, sm, s>>>(a);
     count_launches(1);
 }
 
 // 512 threads when one CTA fills an SM's shared memory (large float32
-// transforms), 256 otherwise.
+// transforms), 256 otherwise; compile-time transforms for the common lengths.
 template <typename T, bool FROM_TOD>
 static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
     if (a.n_work <= 0) return;
     const size_t sm = fft_smem_bytes(a.L, sizeof(T) == 8);
-    if (sizeof(T) == 4 && sm > 110 * 1024) launch_fft_nt<T, FROM_TOD, 512>(a, sm, s);
-    else launch_fft_nt<T, FROM_TOD, 256>(a, sm, s);
+    if constexpr (sizeof(T) == 4 && !FROM_TOD) {
+        switch (a.L) {
+            case 18432: return launch_fft_nt<T, FROM_TOD, 512, 18432>(a, sm, s);
+            case 16384: return launch_fft_nt<T, FROM_TOD, 512, 16384>(a, sm, s);
+            case 12288: return launch_fft_nt<T, FROM_TOD, 512, 12288>(a, sm, s);
+            case 9216: return launch_fft_nt<T, FROM_TOD, 256, 9216>(a, sm, s);
+            case 8192: return launch_fft_nt<T, FROM_TOD, 256, 8192>(a, sm, s);
+            case 4608: return launch_fft_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
+            case 4096: return launch_fft_nt<T, FROM_TOD, 256, 4096>(a, sm, s);
+            case 2048: return launch_fft_nt<T, FROM_TOD, 256, 2048>(a, sm, s);
+            default: break;
+        }
+    }
+    if constexpr (sizeof(T) == 8) {
+        switch (a.L) {
+            case 12288: return launch_fft_nt<T, FROM_TOD, 256, 12288>(a, sm, s);
+            case 9216: return launch_fft_nt<T, FROM_TOD, 256, 9216>(a, sm, s);
+            case 8192: return launch_fft_nt<T, FROM_TOD, 256, 8192>(a, sm, s);
+            case 4608: return launch_fft_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
+            default: break;
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (sm > 110 * 1024) return launch_fft_nt<T, FROM_TOD, 512, 0>(a, sm, s);
+    }
+    launch_fft_nt<T, FROM_TOD, 256, 0>(a, sm, s);
 }
 template <typename T, bool FROM_TOD>
 static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {

@@ -69,6 +69,23 @@ def test_apply_A_matches_oracle(filt, fft_len, prec):
         assert rel(y[r], ref) < (TOL64 if prec == MM.MM_FP64 else TOL32)
 
 
+CT_LENGTHS = [2048, 4096, 4608, 8192, 9216, 12288, 16384, 18432]
+
+
+@pytest.mark.parametrize("L", CT_LENGTHS)
+@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+def test_apply_A_compile_time_lengths(L, prec):
+    """Every compile-time transform, as whole blocks (short blocks) and as segments (long blocks)."""
+    if prec == MM.MM_FP64 and L > 12288:
+        pytest.skip("float64 transform of this length exceeds shared memory")
+    for cfg in (SMALL, dict(nx=8, ny=8, n_det=2, n_t=40960, n_int=2, half_bw=200, f_knee=1.0)):
+        scan = synth.make_scan(seed=19, flag_frac=0.01, **cfg)
+        prob = O.Problem.from_scan(scan)
+        c = ctx_for(scan, prec, 2, fft_len=L)
+        x = np.random.default_rng(19).standard_normal((scan.n_pix, 3))
+        assert rel(c.apply_A(x)[0], O.apply_A(prob, x)) < (TOL64 if prec == MM.MM_FP64 else TOL32)
+
+
 @pytest.mark.parametrize("lam,blen", [(0, 512), (3, 512), (150, 100), (64, 65), (200, 4096)])
 def test_apply_A_band_edges(lam, blen):
     """Bands wider than blocks, zero bands, one-tap bands: truncation at block edges."""

@@ -92,7 +92,9 @@ struct mm_ctx {
     std::vector<int64_t> block_off;
     std::vector<int32_t> block_band;
     std::vector<double> band;
-    DevBuf d_pix, d_psi, d_cs64, d_block_off, d_block_band, d_band64, d_band32;
+    DevBuf d_pix, d_psi, d_cs64, d_block_off, d_block_band, d_band64, d_band32, d_banddf, d_csdf;
+    bool have_csdf = false;
+    int p64 = 1;   // precision of the float64-accurate products: 1 native, 2 double-float
     std::vector<std::unique_ptr<Plan>> plans;
 
     // M_BD
@@ -219,7 +221,7 @@ struct FftCand {
     double cost;
 };
 
-std::vector<FftCand> fft_candidates(const mm_ctx* c, bool f64, int forced_log2, int forced_len) {
+std::vector<FftCand> fft_candidates(const mm_ctx* c, int f64, int forced_log2, int forced_len) {
     const int64_t nb = std::max<int64_t>(1, max_block_len(c));
     const int lam = c->lam;
     std::vector<FftCand> out;
@@ -229,7 +231,7 @@ std::vector<FftCand> fft_candidates(const mm_ctx* c, bool f64, int forced_log2, 
             if (L < 64) continue;
             if (forced_log2 > 0 && L != (1 << forced_log2)) continue;
             if (forced_len > 0 && L != forced_len) continue;
-            const size_t sm = fft_smem_bytes(L, f64);
+            const size_t sm = fft_smem_bytes(L, f64 != 0);
             if (sm > smem_limit_bytes()) continue;
             FftPasses fp;
             if (!fft_passes(L, &fp)) continue;
@@ -263,7 +265,7 @@ std::vector<FftCand> fft_candidates(const mm_ctx* c, bool f64, int forced_log2, 
     return out;
 }
 
-bool choose_fft(const mm_ctx* c, bool f64, int forced_log2, int forced_len, int* L_out, int* whole_out) {
+bool choose_fft(const mm_ctx* c, int f64, int forced_log2, int forced_len, int* L_out, int* whole_out) {
     auto cands = fft_candidates(c, f64, forced_log2, forced_len);
     if (cands.empty()) return false;
     *L_out = cands[0].L;
@@ -271,7 +273,7 @@ bool choose_fft(const mm_ctx* c, bool f64, int forced_log2, int forced_len, int*
     return true;
 }
 
-mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, bool f64) {
+mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, int f64) {
     const int L = fp.L;
     if (ft.L == L) return MM_OK;
     // twiddles exp(-2 pi i e / L) in float64 on the host
@@ -302,11 +304,27 @@ mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, bool
     launch_fft_spectrum(d_h.as<double>(), d_H64.as<double>(), d_work.as<double2>(), d_tw64.as<double2>(),
                         ctx->n_bands, fp, ctx->stream);
     CKL();
-    if (f64) {
+    if (f64 == 1) {
         CK(ft.tw.ensure(tw64.size() * 8));
         CK(ft.H.ensure(h.size() * 8));
         CK(cudaMemcpyAsync(ft.tw.p, d_tw64.p, tw64.size() * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ft.H.p, d_H64.p, h.size() * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else if (f64 == 2) {
+        // double-float: each value as (hi, lo) float32 pair
+        std::vector<double> H64(h.size());
+        CK(cudaMemcpyAsync(H64.data(), d_H64.p, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::vector<float> Hdf(2 * h.size()), twdf(2 * tw64.size());
+        auto split = [](double d, float* o) {
+            o[0] = (float)d;
+            o[1] = (float)(d - (double)o[0]);
+        };
+        for (size_t i = 0; i < h.size(); ++i) split(H64[i], &Hdf[2 * i]);
+        for (size_t i = 0; i < tw64.size(); ++i) split(tw64[i], &twdf[2 * i]);
+        CK(ft.tw.ensure(twdf.size() * 4));
+        CK(ft.H.ensure(Hdf.size() * 4));
+        CK(cudaMemcpyAsync(ft.tw.p, twdf.data(), twdf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.H.p, Hdf.data(), Hdf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     } else {
         std::vector<double> H64(h.size());
         CK(cudaMemcpyAsync(H64.data(), d_H64.p, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -326,7 +344,7 @@ mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, bool
 
 // Segment list: for every block, chunk and right-hand side, pairs of segments
 // that share a band (and halo).
-mm_status make_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, int variant, int L,
+mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, int variant, int L,
                     int whole, int V, Plan** out) {
     FftPasses fp{};
     int logL = 0;
@@ -335,7 +353,7 @@ mm_status make_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>&
         logL = ilog2(L);
     }
     for (auto& p : ctx->plans)
-        if (p->variant == variant && p->L == L && p->V == V && p->whole == whole && p->f64 == (int)f64 &&
+        if (p->variant == variant && p->L == L && p->V == V && p->whole == whole && p->f64 == f64 &&
             p->nrhs == nrhs && p->lens == lens) {
             *out = p.get();
             return MM_OK;
@@ -394,6 +412,12 @@ mm_status make_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>&
         CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (variant == 2) TRY(build_fft_tables(ctx, p->ft, fp, f64));
+    if (f64 == 2 && !ctx->have_csdf) {
+        CK(ctx->d_csdf.ensure((size_t)ctx->n_samples * 16));
+        launch_weights_df(ctx->d_cs64.as<double2>(), ctx->d_csdf.as<float4>(), ctx->n_samples, ctx->stream);
+        CKL();
+        ctx->have_csdf = true;
+    }
     ctx->plans.push_back(std::move(p));
     *out = ctx->plans.back().get();
     return MM_OK;
@@ -469,7 +493,7 @@ void tune_record(const TuneKey& k, const TuneVal& v) {
 // Time each candidate plan once (after one warm-up launch) on the current
 // pointing and keep the fastest.  Candidates: the six cheapest FFT plans of
 // the cost model and, for narrow bands, the direct band at two tile sizes.
-mm_status autotune_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, TuneVal* best) {
+mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, TuneVal* best) {
     struct Opt { int variant, L, whole, V; };
     std::vector<Opt> opts;
     auto cands = fft_candidates(ctx, f64, 0, 0);
@@ -477,9 +501,9 @@ mm_status autotune_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64
         opts.push_back({2, cands[i].L, cands[i].whole, cands[i].whole ? cands[i].L - ctx->lam : cands[i].L - 2 * ctx->lam});
     if (ctx->lam <= 256)
         for (int tile : {512, 2048})
-            if (direct_smem_bytes(tile, ctx->lam, f64) <= 200 * 1024) opts.push_back({1, 0, 0, tile});
+            if (direct_smem_bytes(tile, ctx->lam, f64 != 0) <= 200 * 1024) opts.push_back({1, 0, 0, tile});
     if (opts.empty()) return fail(ctx, MM_ERR_ARG, "no filter plan fits this band");
-    const size_t esz = f64 ? sizeof(V4<double>) : sizeof(V4<float>);
+    const size_t esz = f64 ? sizeof(V4<double>) : sizeof(V4<float>);   // V4<df> is 32 bytes too
     const size_t nv = (size_t)ctx->n_pix * nrhs;
     DevBuf src, dst;
     CK(src.ensure(nv * esz));
@@ -509,11 +533,11 @@ mm_status autotune_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64
     return MM_OK;
 }
 
-mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
+mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
     int variant = ctx->opt_filter;
     int L = 0, V = 0, whole = 0;
     if (variant == 0 && ctx->opt_fft_len == 0 && ctx->opt_fft_log2 == 0 && ctx->opt_autotune && !ctx->capturing) {
-        TuneKey key{(int)f64, ctx->lam, ctx->n_blocks, nrhs, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
+        TuneKey key{f64, ctx->lam, ctx->n_blocks, nrhs, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
         for (auto v : lens) key.lens_sum += v;
         for (auto& kv : tune_cache())
             if (kv.first == key) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
@@ -536,7 +560,7 @@ mm_status get_plan(mm_ctx* ctx, bool f64, int nrhs, const std::vector<int64_t>& 
         V = std::max(32, ctx->opt_direct_tile);
         L = 0;
         whole = 0;
-        const size_t sm = direct_smem_bytes(V, ctx->lam, f64);
+        const size_t sm = direct_smem_bytes(V, ctx->lam, f64 != 0);
         if (sm > 200 * 1024) return fail(ctx, MM_ERR_ARG, "direct filter tile plus halo exceeds shared memory");
     }
     return make_plan(ctx, f64, nrhs, lens, variant, L, whole, V, out);
@@ -574,15 +598,18 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         CK(cudaEventRecord(pr.first, ctx->stream));
         e1 = pr.second;
     }
+    a.csdf = ctx->d_csdf.as<float4>();
     if (plan->variant == 2) {
         FftTables& ft = plan->ft;
         a.H = ft.H.p;
         a.tw = ft.tw.p;
-        if (plan->f64) launch_filter_fft_f64(a, from_tod, ctx->stream);
+        if (plan->f64 == 2) launch_filter_fft_df(a, from_tod, ctx->stream);
+        else if (plan->f64 == 1) launch_filter_fft_f64(a, from_tod, ctx->stream);
         else launch_filter_fft_f32(a, from_tod, ctx->stream);
     } else {
-        a.band = plan->f64 ? ctx->d_band64.p : ctx->d_band32.p;
-        if (plan->f64) launch_filter_direct_f64(a, from_tod, ctx->stream);
+        a.band = plan->f64 == 2 ? ctx->d_banddf.p : (plan->f64 ? ctx->d_band64.p : ctx->d_band32.p);
+        if (plan->f64 == 2) launch_filter_direct_df(a, from_tod, ctx->stream);
+        else if (plan->f64 == 1) launch_filter_direct_f64(a, from_tod, ctx->stream);
         else launch_filter_direct_f32(a, from_tod, ctx->stream);
     }
     CKL();
@@ -608,15 +635,19 @@ mm_status ensure_work(mm_ctx* ctx, int nrhs, int kmax) {
 
 // out (V4<double>) = A in (V4<double>) for nrhs vectors, operator precision
 // f64 or the context's.
-mm_status apply_A_dev(mm_ctx* ctx, bool f64, const V4<double>* in, V4<double>* out, int nrhs, const Plan* forced = nullptr) {
+mm_status apply_A_dev(mm_ctx* ctx, int f64, const V4<double>* in, V4<double>* out, int nrhs, const Plan* forced = nullptr) {
     Plan* plan = nullptr;
     if (forced) plan = const_cast<Plan*>(forced);
     else TRY(get_plan(ctx, f64, nrhs, {}, &plan));
     TRY(ensure_work(ctx, nrhs, ctx->k));
     const int64_t nv = (int64_t)ctx->n_pix * nrhs;
-    if (f64) {
+    if (f64 == 1) {
         CK(cudaMemsetAsync(out, 0, nv * sizeof(V4<double>), ctx->stream));
         TRY(run_filter(ctx, plan, false, in, out, nullptr, 0));
+    } else if (f64 == 2) {
+        launch_map_to_df(in, ctx->w_src.p, nv, ctx->stream);
+        CK(cudaMemsetAsync(out, 0, nv * sizeof(V4<double>), ctx->stream));
+        TRY(run_filter(ctx, plan, false, ctx->w_src.p, out, nullptr, 0));
     } else {
         V4<float>* src = ctx->w_src.as<V4<float>>();
         V4<float>* q = ctx->w_q.as<V4<float>>();
@@ -728,7 +759,7 @@ mm_status read_state(mm_ctx* ctx) {
 // float64 residual b - A x per right-hand side (x in s_xtot or s_x), written to
 // s_rtrue; norms to host.
 mm_status true_residual(mm_ctx* ctx, const V4<double>* x, std::vector<double>& rr) {
-    TRY(apply_A_dev(ctx, true, x, ctx->s_q64.as<V4<double>>(), ctx->nrhs, ctx->plan_64));
+    TRY(apply_A_dev(ctx, ctx->p64, x, ctx->s_q64.as<V4<double>>(), ctx->nrhs, ctx->plan_64));
     launch_residual(ctx->s_b.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), ctx->s_rtrue.as<V4<double>>(),
                     ctx->w_norms.as<double>(), ctx->n_pix, ctx->nrhs, ctx->w_partial.as<double>(),
                     ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
@@ -947,6 +978,7 @@ mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision pr
     ctx->device = device;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     ctx->prec = prec;
+    ctx->p64 = prec == MM_FP32_MIXED ? 2 : 1;
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
     *out = ctx;
@@ -1033,6 +1065,14 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     CK(ctx->d_band32.ensure(b32.size() * 4));
     CK(cudaMemcpyAsync(ctx->d_band64.p, ctx->band.data(), ctx->band.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_band32.p, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float> bdf(2 * ctx->band.size());
+    for (size_t i = 0; i < ctx->band.size(); ++i) {
+        bdf[2 * i] = (float)ctx->band[i];
+        bdf[2 * i + 1] = (float)(ctx->band[i] - (double)bdf[2 * i]);
+    }
+    CK(ctx->d_banddf.ensure(bdf.size() * 4));
+    CK(cudaMemcpyAsync(ctx->d_banddf.p, bdf.data(), bdf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->have_csdf = false;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_pointing = true;
     return MM_OK;
@@ -1084,7 +1124,7 @@ mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int 
         src = d_tod.p;
     }
     Plan* plan = nullptr;
-    TRY(get_plan(ctx, true, nrhs, {}, &plan));
+    TRY(get_plan(ctx, ctx->p64, nrhs, {}, &plan));
     TRY(ensure_work(ctx, nrhs, ctx->k));
     DevBuf q;
     CK(q.ensure((size_t)nrhs * ctx->n_pix * sizeof(V4<double>)));
@@ -1492,7 +1532,7 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     ctx->coarse_per_rhs = false;
     if (ctx->use_lens && precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx));
     TRY(get_plan(ctx, !f32, nrhs, ctx->lens, &ctx->plan_op));
-    TRY(get_plan(ctx, true, nrhs, ctx->lens, &ctx->plan_64));
+    TRY(get_plan(ctx, ctx->p64, nrhs, ctx->lens, &ctx->plan_64));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     const size_t esz = f32 ? 4 : 8;
     const void* src = tod;
@@ -1771,6 +1811,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_graphs = v ? 1 : 0;
     } else if (n == "autotune") {
         ctx->opt_autotune = v ? 1 : 0;
+    } else if (n == "fp64_products") {
+        if (v != 1 && v != 2) return fail(ctx, MM_ERR_ARG, "fp64_products must be 1 (float64) or 2 (double-float)");
+        ctx->p64 = v;
     } else if (n == "harvest") {
         if (v < 0 || v > 4096) return fail(ctx, MM_ERR_ARG, "harvest must lie in [0, 4096]");
         ctx->opt_harvest = v;
@@ -1797,6 +1840,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "time_filter") *value = ctx->opt_time_filter;
     else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "harvest") *value = ctx->opt_harvest;
+    else if (n == "fp64_products") *value = ctx->p64;
     else if (n == "harvested") *value = ctx->harvest_count;
     else if (n == "filter_ms" || n == "filter_launches") {
         // total device time of the filter launches timed since the last read; resets the record

@@ -70,6 +70,7 @@ struct FilterArgs {
     const int32_t* pix;
     const float* psi;
     const double2* cs64;   // float64 weights, may be null for float32
+    const float4* csdf;    // double-float weights (hi, lo of cos 2psi; hi, lo of sin 2psi)
     const void* src;       // maps [nrhs][n_pix] (V4<T>) or TOD [nrhs][n_samples] (T)
     int64_t n_samples;
     void* dst;             // accumulators [nrhs][n_pix] (V4<T>)
@@ -88,6 +89,11 @@ void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s);
 void launch_filter_fft_f64(const FilterArgs& a, bool from_tod, cudaStream_t s);
 void launch_filter_direct_f32(const FilterArgs& a, bool from_tod, cudaStream_t s);
 void launch_filter_direct_f64(const FilterArgs& a, bool from_tod, cudaStream_t s);
+// Double-float (float32 pairs) variants: maps V4<df> in, float64 accumulators out.
+void launch_filter_fft_df(const FilterArgs& a, bool from_tod, cudaStream_t s);
+void launch_filter_direct_df(const FilterArgs& a, bool from_tod, cudaStream_t s);
+void launch_weights_df(const double2* cs, float4* out, int64_t n, cudaStream_t s);
+void launch_map_to_df(const V4<double>* src, void* dst, int64_t n, cudaStream_t s);
 size_t fft_smem_bytes(int L, bool f64);
 size_t direct_smem_bytes(int V, int lam, bool f64);
 // H = DIF(h) for each band in float64 through global scratch; h [n_bands][L].

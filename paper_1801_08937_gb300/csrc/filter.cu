@@ -1,620 +1,11 @@
-// Fused A x = P^T W P x and b = P^T W d kernels.
-//
-// One CTA handles one pair of output segments (see Seg).  Per pair it
-//   1. gathers y_t = I_p + Q_p cos 2psi_t + U_p sin 2psi_t over the segment
-//      plus a lambda halo on each side, clipped to the block (Sect. 2,
-//      Eq. datamodel), or reads d_t for the right-hand side;
-//   2. applies the block's banded Toeplitz weight W (Sect. 2, Eq. estimator)
-//      -- FFT variant: both segments ride in one complex FFT of length L
-//      (real part / imaginary part), are multiplied by the real spectrum of
-//      the symmetric band and transformed back (overlap-save: the central
-//      L - 2 lambda outputs are exact linear-convolution values);
-//      -- direct variant: the band sum in shared memory;
-//   3. scatters z_t (1, cos 2psi_t, sin 2psi_t) into the map (P^T), first
-//      summing runs of equal consecutive pixels inside each warp so one
-//      atomic carries a whole run.
-#include <cuda_runtime.h>
-
-#include "common.cuh"
+// Set-up kernels of the filter (spectra, pointing weights) and the launch counter.
+#include "filter_impl.cuh"
 
 namespace mm {
 
 static long long g_launches = 0;
 long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 void count_launches(int n) { __atomic_fetch_add(&g_launches, (long long)n, __ATOMIC_RELAXED); }
-
-constexpr int DIRECT_NT = 256;
-
-// Padded shared-memory index: one spare element every 16 keeps the strided
-// butterfly accesses of the late passes spread over the banks.
-__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
-
-template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
-template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
-template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-
-__device__ __forceinline__ C2<float> ldtw(const C2<float>* tw, int e) {
-    float2 v = __ldg(reinterpret_cast<const float2*>(tw) + e);
-    return {v.x, v.y};
-}
-__device__ __forceinline__ C2<double> ldtw(const C2<double>* tw, int e) {
-    double2 v = __ldg(reinterpret_cast<const double2*>(tw) + e);
-    return {v.x, v.y};
-}
-
-// ---- small forward DFTs in registers, natural order in and out, W_R = e^{-2 pi i / R} ----
-template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
-    const C2<T> s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-    a0 = cadd(s02, s13);
-    a2 = csub(s02, s13);
-    a1 = {d02.x + d13.y, d02.y - d13.x};   // d02 - i d13
-    a3 = {d02.x - d13.y, d02.y + d13.x};   // d02 + i d13
-}
-
-template <typename T, int R> struct Dft;
-template <typename T> struct Dft<T, 2> {
-    static __device__ __forceinline__ void run(C2<T>* a) {
-        const C2<T> t = a[0];
-        a[0] = cadd(t, a[1]);
-        a[1] = csub(t, a[1]);
-    }
-};
-template <typename T> struct Dft<T, 4> {
-    static __device__ __forceinline__ void run(C2<T>* a) { dft4(a[0], a[1], a[2], a[3]); }
-};
-template <typename T> struct Dft<T, 8> {
-    static __device__ __forceinline__ void run(C2<T>* a) {
-        const T r2 = T(0.70710678118654752440);
-        // n = 2 n1 + n2, k = k1 + 4 k2
-        dft4(a[0], a[2], a[4], a[6]);
-        dft4(a[1], a[3], a[5], a[7]);
-        a[3] = cmul(a[3], C2<T>{r2, -r2});
-        a[5] = C2<T>{a[5].y, -a[5].x};
-        a[7] = cmul(a[7], C2<T>{-r2, -r2});
-        C2<T> o[8];
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            o[k1] = cadd(a[2 * k1], a[2 * k1 + 1]);
-            o[k1 + 4] = csub(a[2 * k1], a[2 * k1 + 1]);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = o[i];
-    }
-};
-template <typename T> __device__ __forceinline__ void dft3(C2<T>& a0, C2<T>& a1, C2<T>& a2) {
-    const T h = T(0.86602540378443864676);   // sin(2 pi / 3)
-    const C2<T> t1 = cadd(a1, a2);
-    const C2<T> u{a0.x - T(0.5) * t1.x, a0.y - T(0.5) * t1.y};
-    const C2<T> v{h * (a1.x - a2.x), h * (a1.y - a2.y)};
-    a0 = cadd(a0, t1);
-    a1 = C2<T>{u.x + v.y, u.y - v.x};   // u - i v
-    a2 = C2<T>{u.x - v.y, u.y + v.x};   // u + i v
-}
-template <typename T> struct Dft<T, 3> {
-    static __device__ __forceinline__ void run(C2<T>* a) { dft3(a[0], a[1], a[2]); }
-};
-template <typename T> struct Dft<T, 9> {
-    static __device__ __forceinline__ void run(C2<T>* a) {
-        // n = 3 n1 + n2, k = k1 + 3 k2; W9^m = (cos 2 pi m / 9, -sin 2 pi m / 9)
-        const T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);
-        const T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);
-        const T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);
-#pragma unroll
-        for (int n2 = 0; n2 < 3; ++n2) dft3(a[n2], a[n2 + 3], a[n2 + 6]);
-        a[4] = cmul(a[4], C2<T>{c1, -s1});
-        a[7] = cmul(a[7], C2<T>{c2, -s2});
-        a[5] = cmul(a[5], C2<T>{c2, -s2});
-        a[8] = cmul(a[8], C2<T>{c4, -s4});
-#pragma unroll
-        for (int k1 = 0; k1 < 3; ++k1) dft3(a[3 * k1], a[3 * k1 + 1], a[3 * k1 + 2]);
-        C2<T> o[9];
-#pragma unroll
-        for (int k1 = 0; k1 < 3; ++k1)
-#pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) o[k1 + 3 * k2] = a[3 * k1 + k2];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a[i] = o[i];
-    }
-};
-template <typename T> struct Dft<T, 16> {
-    static __device__ __forceinline__ void run(C2<T>* a) {
-        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
-        const T r2 = T(0.70710678118654752440);
-        // n = 4 n1 + n2, k = k1 + 4 k2
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
-        // a[n2 + 4 k1] *= W16^(n2 k1)
-        a[5] = cmul(a[5], C2<T>{c1, -s1});
-        a[9] = cmul(a[9], C2<T>{r2, -r2});
-        a[13] = cmul(a[13], C2<T>{s1, -c1});
-        a[6] = cmul(a[6], C2<T>{r2, -r2});
-        a[10] = C2<T>{a[10].y, -a[10].x};
-        a[14] = cmul(a[14], C2<T>{-r2, -r2});
-        a[7] = cmul(a[7], C2<T>{s1, -c1});
-        a[11] = cmul(a[11], C2<T>{-r2, -r2});
-        a[15] = cmul(a[15], C2<T>{-c1, s1});
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
-        C2<T> o[16];
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = a[4 * k1 + k2];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) a[i] = o[i];
-    }
-};
-
-// Powers w^q, q < R, of one twiddle, each a product of two earlier powers
-// (depth <= 4), from a single table load per butterfly.
-template <typename T, int R>
-__device__ __forceinline__ void twiddle_powers(C2<T> w1, C2<T>* w) {
-    w[1] = w1;
-#pragma unroll
-    for (int q = 2; q < R; ++q) {
-        int hi = 1;
-        while (hi * 2 <= q) hi *= 2;
-        w[q] = (hi == q) ? cmul(w[q / 2], w[q / 2]) : cmul(w[hi], w[q - hi]);
-    }
-}
-
-// Decimation-in-frequency pass of radix R over spans of S points (in place):
-// for each butterfly j < S/R of each span, DFT_R over elements j + r S/R,
-// then output q times W_S^(j q) = W_L^(j q L/S).  After all passes the
-// transform sits in mixed-radix digit-reversed order.
-template <typename T, int R>
-__device__ __forceinline__ void dif_pass(C2<T>* s, const C2<T>* __restrict__ tw, int L, int S) {
-    const int Sr = S / R;
-    const int nbf = L / R;
-    const int tstep = L / S;
-    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-        const int g = bf / Sr;
-        const int j = bf - g * Sr;
-        const int base = g * S + j;
-        C2<T> w1{T(1), T(0)};
-        if (Sr > 1) w1 = ldtw(tw, j * tstep);
-        C2<T> a[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + r * Sr)];
-        Dft<T, R>::run(a);
-        if (Sr > 1) {
-            C2<T> w[R];
-            twiddle_powers<T, R>(w1, w);
-#pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) s[sidx(base + q * Sr)] = a[q];
-    }
-}
-
-// The matching decimation-in-time pass in the conjugate domain: element q
-// times W_S^(j q), then DFT_R.  Run on conj(X) in the reverse pass order it
-// yields L * conj(x): the exact inverse of the DIF passes.
-template <typename T, int R>
-__device__ __forceinline__ void dit_pass(C2<T>* s, const C2<T>* __restrict__ tw, int L, int S) {
-    const int Sr = S / R;
-    const int nbf = L / R;
-    const int tstep = L / S;
-    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-        const int g = bf / Sr;
-        const int j = bf - g * Sr;
-        const int base = g * S + j;
-        C2<T> w1{T(1), T(0)};
-        if (Sr > 1) w1 = ldtw(tw, j * tstep);
-        C2<T> a[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) a[q] = s[sidx(base + q * Sr)];
-        if (Sr > 1) {
-            C2<T> w[R];
-            twiddle_powers<T, R>(w1, w);
-#pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
-        }
-        Dft<T, R>::run(a);
-#pragma unroll
-        for (int r = 0; r < R; ++r) s[sidx(base + r * Sr)] = a[r];
-    }
-}
-
-template <typename T, bool DIT>
-__device__ __forceinline__ void run_pass(C2<T>* s, const C2<T>* tw, int L, int R, int S) {
-    switch (R) {
-        case 16: DIT ? dit_pass<T, 16>(s, tw, L, S) : dif_pass<T, 16>(s, tw, L, S); break;
-        case 9: DIT ? dit_pass<T, 9>(s, tw, L, S) : dif_pass<T, 9>(s, tw, L, S); break;
-        case 8: DIT ? dit_pass<T, 8>(s, tw, L, S) : dif_pass<T, 8>(s, tw, L, S); break;
-        case 4: DIT ? dit_pass<T, 4>(s, tw, L, S) : dif_pass<T, 4>(s, tw, L, S); break;
-        case 3: DIT ? dit_pass<T, 3>(s, tw, L, S) : dif_pass<T, 3>(s, tw, L, S); break;
-        default: DIT ? dit_pass<T, 2>(s, tw, L, S) : dif_pass<T, 2>(s, tw, L, S); break;
-    }
-}
-
-// Forward transform: the plan's passes in order (spans shrink from L).
-template <typename T>
-__device__ void fft_dif(C2<T>* s, const C2<T>* tw, const FftPasses& fp) {
-    for (int p = 0; p < fp.npass; ++p) {
-        run_pass<T, false>(s, tw, fp.L, fp.radix[p], fp.span[p]);
-        __syncthreads();
-    }
-}
-template <typename T>
-__device__ void fft_dit_conj(C2<T>* s, const C2<T>* tw, const FftPasses& fp) {
-    for (int p = fp.npass - 1; p >= 0; --p) {
-        run_pass<T, true>(s, tw, fp.L, fp.radix[p], fp.span[p]);
-        __syncthreads();
-    }
-}
-
-// ---- compile-time plans for the lengths the planner uses most ----
-// Same pass order as the host planner: a radix-9 or radix-3 pass, radix-16
-// passes, then one radix 2, 4 or 8 pass; all spans and index divisors are
-// constants, so the butterfly addressing folds to shifts and multiplies.
-struct CtPlan {
-    int np;
-    int r[8];
-    int s[8];
-};
-__host__ __device__ constexpr CtPlan make_ct_plan(int L) {
-    CtPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
-    int rest = L, span = L;
-    if (rest % 9 == 0) {
-        p.r[p.np] = 9; p.s[p.np] = span; span /= 9; rest /= 9; ++p.np;
-    } else if (rest % 3 == 0) {
-        p.r[p.np] = 3; p.s[p.np] = span; span /= 3; rest /= 3; ++p.np;
-    }
-    while (rest % 16 == 0 && p.np < 8) {
-        p.r[p.np] = 16; p.s[p.np] = span; span /= 16; rest /= 16; ++p.np;
-    }
-    if (rest == 8 || rest == 4 || rest == 2) {
-        p.r[p.np] = rest; p.s[p.np] = span; ++p.np;
-    }
-    return p;
-}
-
-template <typename T, int R, int S, int L, int NT, bool DIT>
-__device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) {
-    constexpr int Sr = S / R;
-    constexpr int nbf = L / R;
-    constexpr int tstep = L / S;
-#pragma unroll 1
-    for (int bf = threadIdx.x; bf < nbf; bf += NT) {
-        const int g = bf / Sr;
-        const int j = bf - g * Sr;
-        const int base = g * S + j;
-        C2<T> w1{T(1), T(0)};
-        if (Sr > 1) w1 = ldtw(tw, j * tstep);
-        C2<T> a[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + r * Sr)];
-        if (!DIT) Dft<T, R>::run(a);
-        if (Sr > 1) {
-            C2<T> w[R];
-            twiddle_powers<T, R>(w1, w);
-#pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
-        }
-        if (DIT) Dft<T, R>::run(a);
-#pragma unroll
-        for (int q = 0; q < R; ++q) s[sidx(base + q * Sr)] = a[q];
-    }
-}
-
-template <typename T, int L, int NT, int P>
-__device__ __forceinline__ void ct_dif(C2<T>* s, const C2<T>* tw) {
-    constexpr CtPlan pl = make_ct_plan(L);
-    if constexpr (P < pl.np) {
-        ct_pass<T, pl.r[P], pl.s[P], L, NT, false>(s, tw);
-        __syncthreads();
-        ct_dif<T, L, NT, P + 1>(s, tw);
-    }
-}
-template <typename T, int L, int NT, int P>
-__device__ __forceinline__ void ct_dit(C2<T>* s, const C2<T>* tw) {
-    constexpr CtPlan pl = make_ct_plan(L);
-    if constexpr (P >= 0) {
-        ct_pass<T, pl.r[P], pl.s[P], L, NT, true>(s, tw);
-        __syncthreads();
-        ct_dit<T, L, NT, P - 1>(s, tw);
-    }
-}
-
-// ---- pointing weights ----
-// float32: __sincosf on 2 psi - pi in [-pi, pi), where its error stays near
-// 4e-7; cos 2psi = -cos(2psi - pi), sin 2psi = -sin(2psi - pi).
-__device__ __forceinline__ void weights(const FilterArgs& a, int64_t t, float& c, float& s) {
-    const float x = fmaf(2.0f, __ldg(a.psi + t), -3.14159265358979323846f);
-    float sn, cs;
-    __sincosf(x, &sn, &cs);
-    c = -cs;
-    s = -sn;
-}
-__device__ __forceinline__ void weights(const FilterArgs& a, int64_t t, double& c, double& s) {
-    const double2 v = __ldg(a.cs64 + t);
-    c = v.x;
-    s = v.y;
-}
-
-__device__ __forceinline__ void weights_from(const FilterArgs& a, int64_t t, float psi, float& c, float& s) {
-    const float x = fmaf(2.0f, psi, -3.14159265358979323846f);
-    float sn, cs;
-    __sincosf(x, &sn, &cs);
-    c = -cs;
-    s = -sn;
-}
-__device__ __forceinline__ void weights_from(const FilterArgs& a, int64_t t, float, double& c, double& s) {
-    const double2 v = __ldg(a.cs64 + t);
-    c = v.x;
-    s = v.y;
-}
-
-template <typename T>
-__device__ __forceinline__ V4<T> ldmap(const V4<T>* m);
-template <>
-__device__ __forceinline__ V4<float> ldmap(const V4<float>* m) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(m));
-    return {v.x, v.y, v.z, v.w};
-}
-template <>
-__device__ __forceinline__ V4<double> ldmap(const V4<double>* m) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(m));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(m) + 1);
-    return {a.x, a.y, b.x, b.y};
-}
-
-// y_t of right-hand side `rhs`: (P x)_t, or d_t when FROM_TOD.
-template <typename T, bool FROM_TOD>
-__device__ __forceinline__ T sample_value(const FilterArgs& a, int64_t t, int rhs) {
-    if (FROM_TOD) {
-        if (a.tod_is_float) return T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t));
-        return T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t));
-    } else {
-        const int p = __ldg(a.pix + t);
-        if (p < 0) return T(0);
-        T c, s;
-        weights(a, t, c, s);
-        const V4<T> m = ldmap<T>(reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix + p);
-        return m.x + c * m.y + s * m.z;
-    }
-}
-
-// Gather of a segment pair into s[i] = (y_A[out0_A - lambda + i], y_B[...]),
-// zero outside each block.  Loads are issued GB iterations at a time (index
-// and angle first, then the map entries) to keep many requests in flight.
-template <typename T, bool FROM_TOD>
-__device__ __forceinline__ void gather_pair(const FilterArgs& a, const Seg& A, const Seg& B, bool actA, bool actB,
-                                            C2<T>* s, int L, int lam) {
-    constexpr int GB = 4;
-    const int nt = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < L; i0 += nt * GB) {
-        int pa[GB], pb[GB];
-        float fa[GB], fb[GB];
-        T ya[GB], yb[GB];
-#pragma unroll
-        for (int g = 0; g < GB; ++g) {
-            const int i = i0 + g * nt;
-            const int64_t ta = A.out0 - lam + i, tb = B.out0 - lam + i;
-            const bool va = actA && i < L && ta >= A.lo && ta < A.hi;
-            const bool vb = actB && i < L && tb >= B.lo && tb < B.hi;
-            pa[g] = -1;
-            pb[g] = -1;
-            ya[g] = T(0);
-            yb[g] = T(0);
-            if (FROM_TOD) {
-                if (va) ya[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + A.rhs * a.n_samples + ta))
-                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + A.rhs * a.n_samples + ta));
-                if (vb) yb[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + B.rhs * a.n_samples + tb))
-                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + B.rhs * a.n_samples + tb));
-            } else {
-                if (va) {
-                    pa[g] = __ldg(a.pix + ta);
-                    if (sizeof(T) == 4) fa[g] = __ldg(a.psi + ta);
-                }
-                if (vb) {
-                    pb[g] = __ldg(a.pix + tb);
-                    if (sizeof(T) == 4) fb[g] = __ldg(a.psi + tb);
-                }
-            }
-        }
-        if (!FROM_TOD) {
-            const V4<T>* mapA = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)A.rhs * a.n_pix;
-            const V4<T>* mapB = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)B.rhs * a.n_pix;
-            V4<T> ma[GB], mb[GB];
-#pragma unroll
-            for (int g = 0; g < GB; ++g) {
-                if (pa[g] >= 0) ma[g] = ldmap<T>(mapA + pa[g]);
-                if (pb[g] >= 0) mb[g] = ldmap<T>(mapB + pb[g]);
-            }
-#pragma unroll
-            for (int g = 0; g < GB; ++g) {
-                const int i = i0 + g * nt;
-                if (pa[g] >= 0) {
-                    T c, sn;
-                    weights_from(a, A.out0 - lam + i, fa[g], c, sn);
-                    ya[g] = ma[g].x + c * ma[g].y + sn * ma[g].z;
-                }
-                if (pb[g] >= 0) {
-                    T c, sn;
-                    weights_from(a, B.out0 - lam + i, fb[g], c, sn);
-                    yb[g] = mb[g].x + c * mb[g].y + sn * mb[g].z;
-                }
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < GB; ++g) {
-            const int i = i0 + g * nt;
-            if (i < L) s[sidx(i)] = C2<T>{ya[g], yb[g]};
-        }
-    }
-}
-
-__device__ __forceinline__ void atomic_add3(V4<float>* q, float a, float b, float c) {
-#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
-    atomicAdd(reinterpret_cast<float4*>(q), make_float4(a, b, c, 0.0f));
-#else
-    atomicAdd(&q->x, a);
-    atomicAdd(&q->y, b);
-    atomicAdd(&q->z, c);
-#endif
-}
-__device__ __forceinline__ void atomic_add3(V4<double>* q, double a, double b, double c) {
-    atomicAdd(&q->x, a);
-    atomicAdd(&q->y, b);
-    atomicAdd(&q->z, c);
-}
-
-// Warp-cooperative P^T: every lane holds one sample (p < 0: nothing).
-// Consecutive lanes with equal p form a run; a suffix sum inside each run
-// leaves the run total on its first lane, which issues one atomic.
-template <typename T>
-__device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<T>* q) {
-    const unsigned FULL = 0xffffffffu;
-    const unsigned lane = threadIdx.x & 31u;
-    const int pprev = __shfl_up_sync(FULL, p, 1);
-    const bool head = (lane == 0) || (p != pprev);
-    const unsigned heads = __ballot_sync(FULL, head);
-    const unsigned above = heads & ~((2u << lane) - 1u);
-    const int end = above ? (__ffs(above) - 1) : 32;
-    T v0 = z, v1 = z * c, v2 = z * s;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const T o0 = __shfl_down_sync(FULL, v0, d);
-        const T o1 = __shfl_down_sync(FULL, v1, d);
-        const T o2 = __shfl_down_sync(FULL, v2, d);
-        if ((int)lane + d < end) {
-            v0 += o0;
-            v1 += o1;
-            v2 += o2;
-        }
-    }
-    if (head && p >= 0) atomic_add3(q + p, v0, v1, v2);
-}
-
-template <typename T>
-__device__ __forceinline__ void scatter_one(const FilterArgs& a, const Seg& S, bool act, int i, T zval) {
-    int p = -1;
-    T c = T(0), s = T(0), z = T(0);
-    if (act && i < S.n_out) {
-        const int64_t t = S.out0 + i;
-        p = __ldg(a.pix + t);
-        if (p >= 0) {
-            weights(a, t, c, s);
-            z = zval;
-        }
-    }
-    scatter_warp<T>(p, c, s, z, reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(act ? S.rhs : 0) * a.n_pix);
-}
-
-template <typename T>
-__device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
-    return S.n_out > 0 && (a.state == nullptr || a.state[S.rhs].active);
-}
-
-// ---------------- FFT overlap-save variant ----------------
-template <typename T, bool FROM_TOD, int NT, int LCT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_filter_fft(const FilterArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
-    const Seg A = a.segs[2 * blockIdx.x];
-    const Seg B = a.segs[2 * blockIdx.x + 1];
-    const bool actA = seg_active<T>(a, A);
-    const bool actB = seg_active<T>(a, B);
-    if (!actA && !actB) return;
-    const int L = LCT > 0 ? LCT : a.L;
-    const int lam = actA ? A.shift : B.shift;   // left halo of this pair (lambda, or 0 for whole blocks)
-    const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
-
-    gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
-    __syncthreads();
-    if constexpr (LCT > 0) ct_dif<T, LCT, NT, 0>(s, tw);
-    else fft_dif<T>(s, tw, a.fp);
-    const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const C2<T> v = s[sidx(i)];
-        const T h = __ldg(H + i);
-        s[sidx(i)] = C2<T>{v.x * h, -v.y * h};
-    }
-    __syncthreads();
-    if constexpr (LCT > 0) ct_dit<T, LCT, NT, make_ct_plan(LCT > 0 ? LCT : 64).np - 1>(s, tw);
-    else fft_dit_conj<T>(s, tw, a.fp);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const int vmax = max(actA ? A.n_out : 0, actB ? B.n_out : 0);
-    constexpr int SB = 2;
-    V4<T>* qA = reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(actA ? A.rhs : 0) * a.n_pix;
-    V4<T>* qB = reinterpret_cast<V4<T>*>(a.dst) + (int64_t)(actB ? B.rhs : 0) * a.n_pix;
-    for (int base = warp * 32; base < vmax; base += nwarp * 32 * SB) {
-        int pa[SB], pb[SB];
-        float fa[SB], fb[SB];
-#pragma unroll
-        for (int g = 0; g < SB; ++g) {
-            const int i = base + g * nwarp * 32 + lane;
-            pa[g] = -1;
-            pb[g] = -1;
-            if (actA && i < A.n_out) {
-                pa[g] = __ldg(a.pix + A.out0 + i);
-                if (sizeof(T) == 4) fa[g] = __ldg(a.psi + A.out0 + i);
-            }
-            if (actB && i < B.n_out) {
-                pb[g] = __ldg(a.pix + B.out0 + i);
-                if (sizeof(T) == 4) fb[g] = __ldg(a.psi + B.out0 + i);
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < SB; ++g) {
-            const int i = base + g * nwarp * 32 + lane;
-            const C2<T> v = s[sidx(min(lam + i, L - 1))];
-            T c = T(0), sn = T(0), za = T(0), zb = T(0);
-            if (pa[g] >= 0) {
-                weights_from(a, A.out0 + i, fa[g], c, sn);
-                za = v.x;
-            }
-            scatter_warp<T>(pa[g], c, sn, za, qA);
-            c = T(0);
-            sn = T(0);
-            if (pb[g] >= 0) {
-                weights_from(a, B.out0 + i, fb[g], c, sn);
-                zb = -v.y;
-            }
-            scatter_warp<T>(pb[g], c, sn, zb, qB);
-        }
-    }
-}
-
-// ---------------- direct band variant ----------------
-template <typename T, bool FROM_TOD>
-__global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int lam = a.lam;
-    T* c = reinterpret_cast<T*>(smraw);
-    T* y = c + ((lam + 1 + 1) & ~1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-        const Seg S = a.segs[2 * blockIdx.x + half];
-        if (!seg_active<T>(a, S)) continue;   // uniform across the CTA
-        const T* band = reinterpret_cast<const T*>(a.band) + (int64_t)S.band * (lam + 1);
-        for (int k = threadIdx.x; k <= lam; k += blockDim.x) c[k] = band[k];
-        const int nin = S.n_out + 2 * lam;
-        for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-            const int64_t t = S.out0 - lam + i;
-            y[i] = (t >= S.lo && t < S.hi) ? sample_value<T, FROM_TOD>(a, t, S.rhs) : T(0);
-        }
-        __syncthreads();
-        for (int base = warp * 32; base < S.n_out; base += nwarp * 32) {
-            const int i = base + lane;
-            T z = T(0);
-            if (i < S.n_out) {
-                const T* yc = y + lam + i;
-                z = c[0] * yc[0];
-                for (int k = 1; k <= lam; ++k) z += c[k] * (yc[-k] + yc[k]);
-            }
-            scatter_one<T>(a, S, true, i, z);
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------- setup kernels ----------------
 __global__ void k_fft_spectrum(const double* h, double* H, C2<double>* work, const C2<double>* tw,
@@ -637,86 +28,27 @@ __global__ void k_weights64(const float* psi, double2* cs, int64_t n) {
     }
 }
 
+// Double-float weights (cos 2psi, sin 2psi) from the float64 table.
+__global__ void k_weights_df(const double2* cs, float4* out, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = cs[t];
+        const df c(v.x), s(v.y);
+        out[t] = make_float4(c.hi, c.lo, s.hi, s.lo);
+    }
+}
+__global__ void k_map_to_df(const V4<double>* src, V4<df>* dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V4<double> v = src[i];
+        dst[i] = V4<df>{df(v.x), df(v.y), df(v.z), df(0.0)};
+    }
+}
+
 // ---------------- launchers ----------------
 size_t fft_smem_bytes(int L, bool f64) { return (size_t)(L + (L >> 4)) * (f64 ? 16 : 8); }
 size_t direct_smem_bytes(int V, int lam, bool f64) {
     return (size_t)(((lam + 2) & ~1) + V + 2 * lam) * (f64 ? 8 : 4);
 }
 
-template <typename T, bool FROM_TOD, int NT, int LCT>
-static void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
-    static size_t configured = 0;
-    if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured = sm;
-    }
-    k_filter_fft<T, FROM_TOD, NT, LCT><<<a.n_work, NT, sm, s>>>(a);
-    count_launches(1);
-}
-
-// 512 threads when one CTA fills an SM's shared memory (large float32
-// transforms), 256 otherwise; compile-time transforms for the common lengths.
-template <typename T, bool FROM_TOD>
-static void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
-    if (a.n_work <= 0) return;
-    const size_t sm = fft_smem_bytes(a.L, sizeof(T) == 8);
-    if constexpr (sizeof(T) == 4 && !FROM_TOD) {
-        switch (a.L) {
-            case 18432: return launch_fft_nt<T, FROM_TOD, 512, 18432>(a, sm, s);
-            case 16384: return launch_fft_nt<T, FROM_TOD, 512, 16384>(a, sm, s);
-            case 12288: return launch_fft_nt<T, FROM_TOD, 512, 12288>(a, sm, s);
-            case 9216: return launch_fft_nt<T, FROM_TOD, 256, 9216>(a, sm, s);
-            case 8192: return launch_fft_nt<T, FROM_TOD, 256, 8192>(a, sm, s);
-            case 4608: return launch_fft_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
-            case 4096: return launch_fft_nt<T, FROM_TOD, 256, 4096>(a, sm, s);
-            case 2048: return launch_fft_nt<T, FROM_TOD, 256, 2048>(a, sm, s);
-            default: break;
-        }
-    }
-    if constexpr (sizeof(T) == 8) {
-        switch (a.L) {
-            case 12288: return launch_fft_nt<T, FROM_TOD, 256, 12288>(a, sm, s);
-            case 9216: return launch_fft_nt<T, FROM_TOD, 256, 9216>(a, sm, s);
-            case 8192: return launch_fft_nt<T, FROM_TOD, 256, 8192>(a, sm, s);
-            case 4608: return launch_fft_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
-            default: break;
-        }
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (sm > 110 * 1024) return launch_fft_nt<T, FROM_TOD, 512, 0>(a, sm, s);
-    }
-    launch_fft_nt<T, FROM_TOD, 256, 0>(a, sm, s);
-}
-template <typename T, bool FROM_TOD>
-static void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
-    if (a.n_work <= 0) return;
-    const size_t sm = direct_smem_bytes(a.V, a.lam, sizeof(T) == 8);
-    static size_t configured = 0;
-    if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_direct<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        configured = sm;
-    }
-    k_filter_direct<T, FROM_TOD><<<a.n_work, DIRECT_NT, sm, s>>>(a);
-    count_launches(1);
-}
-
-void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s) {
-    if (from_tod) launch_fft_t<float, true>(a, s);
-    else launch_fft_t<float, false>(a, s);
-}
-void launch_filter_fft_f64(const FilterArgs& a, bool from_tod, cudaStream_t s) {
-    if (from_tod) launch_fft_t<double, true>(a, s);
-    else launch_fft_t<double, false>(a, s);
-}
-void launch_filter_direct_f32(const FilterArgs& a, bool from_tod, cudaStream_t s) {
-    if (from_tod) launch_direct_t<float, true>(a, s);
-    else launch_direct_t<float, false>(a, s);
-}
-void launch_filter_direct_f64(const FilterArgs& a, bool from_tod, cudaStream_t s) {
-    if (from_tod) launch_direct_t<double, true>(a, s);
-    else launch_direct_t<double, false>(a, s);
-}
 
 void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw, int n_bands,
                          const FftPasses& fp, cudaStream_t s) {
@@ -726,6 +58,18 @@ void launch_fft_spectrum(const double* h, double* H_out, double2* work, const do
     count_launches(1);
 }
 
+void launch_weights_df(const double2* cs, float4* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    k_weights_df<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(cs, out, n);
+    count_launches(1);
+}
+void launch_map_to_df(const V4<double>* src, void* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    k_map_to_df<<<(int)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, s>>>(src, reinterpret_cast<V4<df>*>(dst), n);
+    count_launches(1);
+}
 void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t blocks = (n + 255) / 256;

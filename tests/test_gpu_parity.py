@@ -110,11 +110,14 @@ def test_apply_A_c1_full_size():
         assert rel(c.apply_A(x)[0], ref) < tol
 
 
-@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
-def test_rhs_matches_oracle(prec):
+@pytest.mark.parametrize("prec,products", [(MM.MM_FP64, 1), (MM.MM_FP32_MIXED, 1), (MM.MM_FP32_MIXED, 2)])
+@pytest.mark.parametrize("fft_len", [0, 1152, 4608, 8192])
+def test_rhs_matches_oracle(prec, products, fft_len):
+    """b = P^T W d to float64 accuracy: native float64 or double-float products."""
     scan, d, _ = scan_and_tod(SMALL, seed=5, flag_frac=0.01)
     prob = O.Problem.from_scan(scan)
-    c = ctx_for(scan, prec)
+    c = ctx_for(scan, prec, 2 if fft_len else 0, fft_len=fft_len)
+    c.set_option("fp64_products", products)
     tod = d.astype(c.tod_dtype)
     b = c.rhs(tod)
     ref = O.rhs(prob, tod.astype(np.float64))

@@ -120,11 +120,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def fft_flops_per_point(logL):
-    """Real flops per point of one transform as the kernel computes it."""
-    per_pass = {4: 266 / 16, 3: 102 / 8, 2: 34 / 4, 1: 10 / 2}
-    n16, rem = logL // 4, logL % 4
-    return n16 * per_pass[4] + (per_pass[rem] if rem else 0.0)
+def fft_passes(L):
+    """Radix sequence of the library's planner for L = 2^a 3^b: 9 or 3, then 16s, then 8/4/2."""
+    rs, rest = [], L
+    if rest % 9 == 0:
+        rs.append(9)
+        rest //= 9
+    elif rest % 3 == 0:
+        rs.append(3)
+        rest //= 3
+    while rest % 16 == 0:
+        rs.append(16)
+        rest //= 16
+    if rest in (2, 4, 8):
+        rs.append(rest)
+    return rs
+
+
+# real flops per point of one pass (butterfly + pass twiddles), as the kernel computes them
+FLOPS_PER_POINT = {16: 266 / 16, 9: 168 / 9, 8: 102 / 8, 4: 34 / 4, 3: 28 / 3, 2: 10 / 2}
+
+
+def fft_flops_per_point(L):
+    return sum(FLOPS_PER_POINT[r] for r in fft_passes(L))
 
 
 def dist_setup():
@@ -291,14 +309,13 @@ def main():
     value = ms_max / 1e3 / maps
 
     # ---- the dominant kernel: float32 fused gather/filter/scatter, A x alone ----
-    plan_log2 = int(ctx.get_option("plan_fft_log2"))
+    L = int(ctx.get_option("plan_fft_len"))
+    whole = int(ctx.get_option("plan_whole"))
     lam = scan.half_bw
-    L = 1 << plan_log2 if plan_log2 else 0
     n_work = 0
     if L:
-        V = L - 2 * lam
         blen = scan.n_t // scan.n_int
-        segs_per_block = -(-blen // V)
+        segs_per_block = 1 if whole else -(-blen // (L - 2 * lam))
         n_work = -(-(scan.n_blocks * segs_per_block) // 2)
     xin = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
     yout = torch.empty_like(xin)
@@ -311,7 +328,7 @@ def main():
         ctx.apply_A(xin, out=yout)
     ax_ms = ctx.get_option("filter_ms") / reps
     ctx.set_option("time_filter", 0)
-    flops_per_launch = n_work * (2 * fft_flops_per_point(plan_log2) * L + 2 * L) if L else 0.0
+    flops_per_launch = n_work * (2 * fft_flops_per_point(L) * L + 2 * L) if L else 0.0
     bytes_per_launch = 8.0 * scan.n_samples
     peaks = {}
     try:
@@ -328,7 +345,8 @@ def main():
                           % ("float" if prec == M.MM_FP32_MIXED else "double"),
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec == M.MM_FP32_MIXED
                                 else "nominal GB300 FP64 rate"),
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": ax_ms, "fft_log2": plan_log2,
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": ax_ms, "fft_len": L,
+                "fft_radices": fft_passes(L) if L else None, "whole_blocks": bool(whole),
                 "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "of": "measured",
                              "frac": achieved_gbs / hbm_peak, "algorithmic_bytes": "8 B/sample (pix + psi)"},
                 "step_filter_ms": filter_ms / max(1, args.steps), "step_filter_launches": n_filter / max(1, args.steps)}
@@ -553,7 +571,8 @@ def run_serve(args, world, rank, local):
     seq_s = (time.perf_counter() - t0) / seq_n
     rate = 0.7 / seq_s
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    srv = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=12, **kw).start()
+    srv = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=12,
+                      coarse="harvest", **kw).start()
     futs = []
     t_start = time.perf_counter()
     for j, (sid, _) in enumerate(reqs):

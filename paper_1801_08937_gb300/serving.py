@@ -72,6 +72,7 @@ class _ScanEntry:
         self.ready = False
         self.error = None
         self.has_coarse = False
+        self.harvesting = False
         self.last_used = time.perf_counter()
 
 
@@ -90,7 +91,12 @@ class MapServer:
 
     def __init__(self, device: int = 0, precision: int = M.MM_FP32_MIXED, budget_bytes: int | None = None,
                  iters_per_tick: int = 4, max_active: int = 16, m_max: int = 60, k: int = 16,
-                 eps_arn: float = 1e-6, setup_workers: int = 2, reserve_bytes: int = 2 << 30):
+                 eps_arn: float = 1e-6, setup_workers: int = 2, reserve_bytes: int = 2 << 30,
+                 coarse: str = "arnoldi"):
+        """coarse: "arnoldi" builds each new scan's deflation basis before its
+        first solve; "harvest" solves the first request of a scan with M_BD,
+        keeping the Lanczos vectors of that run, and builds the basis from
+        them afterwards, so later requests on the scan use M_2l."""
         import torch
         self.torch = torch
         self.device = device
@@ -98,6 +104,7 @@ class MapServer:
         self.iters_per_tick = iters_per_tick
         self.max_active = max_active
         self.m_max, self.k, self.eps_arn = m_max, k, eps_arn
+        self.coarse_mode = coarse
         self.reserve = reserve_bytes
         self.budget = budget_bytes
         self._pending = collections.deque()
@@ -189,7 +196,7 @@ class MapServer:
                 s = entry.spec
                 entry.ctx.setup_pointing(s.pix, s.psi, s.block_off, s.block_band, s.band, s.n_pix, n_det=s.n_det)
                 entry.ctx.build_bd(1e-3)
-                if want_coarse:
+                if want_coarse and self.coarse_mode == "arnoldi":
                     b = entry.ctx.rhs(tod)
                     entry.ctx.build_coarse(b[0], m_max=self.m_max, eps_arn=self.eps_arn, k=self.k)
                     entry.has_coarse = True
@@ -197,6 +204,17 @@ class MapServer:
         except Exception as ex:  # reported to every waiting request
             entry.error = ex
         entry.ready = True
+
+    def _coarse_from_solve(self, entry: _ScanEntry):
+        try:
+            self.torch.cuda.set_device(self.device)
+            if entry.ctx.get_option("harvested") >= 2:
+                entry.ctx.build_coarse_from_solve(k=self.k)
+                entry.has_coarse = True
+            entry.stream.synchronize()
+        except Exception:
+            entry.has_coarse = False   # later requests fall back to M_BD
+        entry.busy = False
 
     # ---------------- scheduler ----------------
     def _admit(self):
@@ -239,7 +257,9 @@ class MapServer:
         e.last_used = time.perf_counter()
         self._scans.move_to_end(req.scan_id)
         precond = req.precond if (req.precond != M.MM_PRECOND_2L or e.has_coarse) else M.MM_PRECOND_BD
+        e.harvesting = (req.precond == M.MM_PRECOND_2L and not e.has_coarse and self.coarse_mode == "harvest")
         try:
+            e.ctx.set_option("harvest", self.m_max if e.harvesting else 0)
             e.ctx.solve_begin(req.tod, precond, tol=req.tol, max_iter=req.max_iter)
         except Exception as ex:
             e.busy = False
@@ -277,7 +297,12 @@ class MapServer:
             if done:
                 x, info = a.entry.ctx.solve_end()
                 now = time.perf_counter()
-                a.entry.busy = False
+                if a.entry.harvesting:
+                    # deflation basis from this M_BD run's Lanczos vectors, off the critical path
+                    a.entry.harvesting = False
+                    self._pool.submit(self._coarse_from_solve, a.entry)
+                else:
+                    a.entry.busy = False
                 a.entry.last_used = now
                 self.latencies.append(now - a.req.arrival)
                 self.completed += 1

@@ -54,11 +54,12 @@ def test_results_same_alone_and_in_mix(precision):
         sc = scans[i]
         tod = synth.make_tod(sc, synth.make_sky(sc.n_pix, 100 + j), synth.make_noise(sc, 100 + j)).astype(dtype)
         reqs.append((f"scan{i}", sc, tod))
-    srv = S.MapServer(device=0, precision=precision, iters_per_tick=3, m_max=30, k=6, reserve_bytes=0).start()
+    srv = S.MapServer(device=0, precision=precision, iters_per_tick=1, m_max=30, k=6, reserve_bytes=0).start()
     futs = []
     for j, (sid, sc, tod) in enumerate(reqs):
         futs.append(srv.submit(S.MapRequest(sid, _spec(sc), tod, MM.MM_PRECOND_2L, tol=1e-9, max_iter=800)))
-        time.sleep(0.002 * (j % 2))     # arrivals spread while earlier solves run
+        if j == 5:
+            time.sleep(0.01)            # later arrivals join while earlier solves run
     res = [f.result(timeout=120) for f in futs]
     st = srv.stats()
     srv.stop()
@@ -97,3 +98,24 @@ def test_admission_waits_for_memory_and_evicts_idle_scans():
     srv.stop()
     assert all(r.info["status"] == "MM_OK" for r in res)
     assert st["evictions"] >= 1
+
+
+def test_harvest_mode_first_request_bd_then_two_level():
+    """A new scan's first request runs M_BD and seeds the coarse space for the next ones."""
+    sc = _scan(0)
+    tods = [synth.make_tod(sc, synth.make_sky(sc.n_pix, 500 + j), synth.make_noise(sc, 500 + j)) for j in range(3)]
+    srv = S.MapServer(device=0, precision=MM.MM_FP64, iters_per_tick=2, m_max=40, k=6, reserve_bytes=0,
+                      coarse="harvest").start()
+    first = srv.submit(S.MapRequest("h", _spec(sc), tods[0], MM.MM_PRECOND_2L, tol=1e-9)).result(timeout=120)
+    time.sleep(0.05)
+    later = [srv.submit(S.MapRequest("h", _spec(sc), t, MM.MM_PRECOND_2L, tol=1e-9)) for t in tods[1:]]
+    later = [f.result(timeout=120) for f in later]
+    srv.stop()
+    prob, mbd, good = oracle_problem(sc)
+    for t, r in zip(tods, [first] + later):
+        assert r.info["status"] == "MM_OK"
+        b = O.rhs(prob, t).reshape(-1)
+        xo = O.pcg(lambda v: O.apply_A(prob, v).reshape(-1), lambda v: O.bd_apply(mbd, v).reshape(-1), b,
+                   tol=1e-13, max_iter=5000)[0]
+        assert rel(r.map, xo) < 1e-6
+    assert all(r.info["iters"] < first.info["iters"] for r in later)

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-bd", action="store_true", help="skip the M_BD comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
+                    help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream")
     ap.add_argument("--n-rhs", type=int, default=64)
@@ -250,10 +252,15 @@ def main():
     info_last = {}
 
     def setup_scan(pointing=(pix_d, psi_d), tod_in=tod_d):
-        """One-time per scan: pointing, M_BD and the coarse space."""
+        """One-time per scan: pointing, M_BD and the coarse space (from a first M_BD run by default)."""
         ctx.setup_pointing(pointing[0], pointing[1], scan.block_off, scan.block_band, scan.band, scan.n_pix,
                            n_det=scan.n_det)
         ctx.build_bd(1e-3)
+        if args.coarse == "lanczos":
+            ctx.set_option("harvest", args.m_max)
+            ctx.solve(tod_in, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=x_d)
+            ctx.set_option("harvest", 0)
+            return ctx.build_coarse_from_solve(k=args.k)
         b = ctx.rhs(tod_in)
         return ctx.build_coarse(b[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
 
@@ -394,7 +401,8 @@ def main():
                        "replicas": world},
             "two_level": {"iters": info2l["iters"], "true_rel_res": info2l["true_rel_res"],
                           "refinements": info2l["refinements"], "k": k_used, "status": info2l["status"],
-                          "setup_once_s": setup_ms / 1e3, "m_max": args.m_max, "eps_arn": args.eps_arn},
+                          "setup_once_s": setup_ms / 1e3, "coarse_from": args.coarse, "m_max": args.m_max,
+                          "eps_arn": args.eps_arn if args.coarse == "arnoldi" else None},
             "m_bd": bd,
             "apply_A": {"samples_per_s": scan.n_samples / (ax_ms * 1e-3) if ax_ms > 0 else None,
                         "kernel_ms": ax_ms,

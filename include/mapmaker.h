@@ -126,8 +126,9 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
  * Errors: MM_ERR_STATE (no pointing), MM_ERR_ARG, MM_ERR_CUDA. */
 mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out);
 
-/* b = P^T W d (Sect. 3, Eq. linearsystem) for nrhs timelines, computed in
- * float64 whatever the context precision.  tod [nrhs][n_samples] (element
+/* b = P^T W d (Sect. 3, Eq. linearsystem) for nrhs timelines, computed to
+ * float64 accuracy whatever the context precision (native float64, or
+ * double-float arithmetic, see option "fp64_products").  tod [nrhs][n_samples] (element
  * type per context precision), b_out [nrhs][n_pix][3] float64, both in `mem`.
  * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int mem);
@@ -213,7 +214,11 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * check_every PCG iterations (only on a created stream, not the legacy
  * default stream); "harvest": Lanczos vectors kept from M_BD solves (see
  * mm_build_coarse_from_solve); "time_filter": 1 records CUDA events around
- * every filter launch.  Errors: MM_ERR_ARG for an unknown name or value. */
+ * every filter launch; "fp64_products": 1 native float64 or 2 (default for
+ * MM_FP32_MIXED) double-float arithmetic (float32 pairs, about 44 bits) for
+ * b and the refinement residuals; "apply_precision": precision of
+ * mm_apply_A (0 context, 1 float64, 2 double-float).  Errors: MM_ERR_ARG for
+ * an unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
 /* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"

@@ -79,6 +79,7 @@ struct mm_ctx {
     int opt_time_filter = 0;
     int opt_autotune = 1;
     int opt_harvest = 0;           // Lanczos vectors kept from an M_BD solve (0: off)
+    int opt_apply_prec = 0;        // mm_apply_A precision: 0 context, 1 float64, 2 double-float
     double last_apply_ms = 0.0;
     // CUDA-event pairs around filter launches (when timing is on)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fev;
@@ -1166,9 +1167,10 @@ mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int 
     launch_map_in(xsrc, in4.as<V4<double>>(), nv, ctx->stream);
     CKL();
     Plan* plan = nullptr;
-    TRY(get_plan(ctx, !is_f32(ctx), nrhs, {}, &plan));
+    const int aprec = ctx->opt_apply_prec ? ctx->opt_apply_prec : (is_f32(ctx) ? 0 : 1);
+    TRY(get_plan(ctx, aprec, nrhs, {}, &plan));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    TRY(apply_A_dev(ctx, !is_f32(ctx), in4.as<V4<double>>(), out4.as<V4<double>>(), nrhs, plan));
+    TRY(apply_A_dev(ctx, aprec, in4.as<V4<double>>(), out4.as<V4<double>>(), nrhs, plan));
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     if (mem == MM_HOST) {
         DevBuf o;
@@ -1811,6 +1813,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_graphs = v ? 1 : 0;
     } else if (n == "autotune") {
         ctx->opt_autotune = v ? 1 : 0;
+    } else if (n == "apply_precision") {
+        if (v < 0 || v > 2) return fail(ctx, MM_ERR_ARG, "apply_precision must be 0, 1 or 2");
+        ctx->opt_apply_prec = v;
     } else if (n == "fp64_products") {
         if (v != 1 && v != 2) return fail(ctx, MM_ERR_ARG, "fp64_products must be 1 (float64) or 2 (double-float)");
         ctx->p64 = v;
@@ -1841,6 +1846,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;
+    else if (n == "apply_precision") *value = ctx->opt_apply_prec;
     else if (n == "harvested") *value = ctx->harvest_count;
     else if (n == "filter_ms" || n == "filter_launches") {
         // total device time of the filter launches timed since the last read; resets the record

@@ -100,6 +100,19 @@ def test_apply_A_band_edges(lam, blen):
         assert rel(c.apply_A(x)[0], ref) < TOL64
 
 
+@pytest.mark.parametrize("fft_len", [0, 4608, 8192, 12288])
+def test_apply_A_double_float_matches_oracle(fft_len):
+    """Double-float products reach float64-level agreement with the oracle."""
+    scan = ragged(synth.make_scan(seed=20, flag_frac=0.01, **SMALL), seed=20)
+    prob = O.Problem.from_scan(scan)
+    c = ctx_for(scan, MM.MM_FP32_MIXED, 2 if fft_len else 0, fft_len=fft_len)
+    c.set_option("apply_precision", 2)
+    x = np.random.default_rng(20).standard_normal((2, scan.n_pix, 3))
+    y = c.apply_A(x)
+    for r in range(2):
+        assert rel(y[r], O.apply_A(prob, x[r])) < TOL64
+
+
 def test_apply_A_c1_full_size():
     scan = synth.scan_from_config("c1", seed=0)
     prob = O.Problem.from_scan(scan)

@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-bd", action="store_true", help="skip the M_BD comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--inner-tol", type=float, default=2e-6)
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve"],
@@ -248,6 +249,8 @@ def main():
     tod_d = torch.from_numpy(tod_np).to(dev)
     x_d = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
     ctx = M.Context(local, stream.cuda_stream, prec)
+    if prec == M.MM_FP32_MIXED:
+        ctx.set_option("inner_tol", args.inner_tol)
 
     info_last = {}
 

@@ -217,8 +217,10 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * every filter launch; "fp64_products": 1 native float64 or 2 (default for
  * MM_FP32_MIXED) double-float arithmetic (float32 pairs, about 44 bits) for
  * b and the refinement residuals; "apply_precision": precision of
- * mm_apply_A (0 context, 1 float64, 2 double-float).  Errors: MM_ERR_ARG for
- * an unknown name or value. */
+ * mm_apply_A (0 context, 1 float64, 2 double-float); "inner_tol": in
+ * MM_FP32_MIXED, the smallest relative tolerance asked of a float32-operator
+ * PCG run between float64-accurate refinements (default 2e-6).  Errors:
+ * MM_ERR_ARG for an unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
 /* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"

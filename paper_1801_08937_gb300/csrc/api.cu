@@ -80,6 +80,7 @@ struct mm_ctx {
     int opt_autotune = 1;
     int opt_harvest = 0;           // Lanczos vectors kept from an M_BD solve (0: off)
     int opt_apply_prec = 0;        // mm_apply_A precision: 0 context, 1 float64, 2 double-float
+    double opt_inner_tol = 2e-6;   // floor of the float32-operator PCG tolerance between refinements
     double last_apply_ms = 0.0;
     // CUDA-event pairs around filter launches (when timing is on)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fev;
@@ -1573,7 +1574,7 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     }
     std::vector<double> tols(nrhs);
     std::vector<int> budgets(nrhs, max_iter);
-    for (int i = 0; i < nrhs; ++i) tols[i] = f32 ? std::max(tol, 2e-6) : tol;
+    for (int i = 0; i < nrhs; ++i) tols[i] = f32 ? std::max(tol, ctx->opt_inner_tol) : tol;
     TRY(pcg_start(ctx, ctx->s_b.as<V4<double>>(), tols, budgets));
     ctx->phase = PH_INNER;
     return MM_OK;
@@ -1618,7 +1619,7 @@ static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
         if (allow_refine && ctx->true_res[i] > ctx->tol && left > 0 && ctx->outer < 8 && rr[i] > 0) {
             again = true;
             budgets[i] = left;
-            tols[i] = std::max(0.5 * ctx->tol * ctx->bnorm[i] / rr[i], 2e-6);
+            tols[i] = std::max(0.5 * ctx->tol * ctx->bnorm[i] / rr[i], ctx->opt_inner_tol);
         }
     }
     if (again) {
@@ -1813,6 +1814,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_graphs = v ? 1 : 0;
     } else if (n == "autotune") {
         ctx->opt_autotune = v ? 1 : 0;
+    } else if (n == "inner_tol") {
+        if (!(value > 0.0) || value > 1e-2) return fail(ctx, MM_ERR_ARG, "inner_tol must lie in (0, 1e-2]");
+        ctx->opt_inner_tol = value;
     } else if (n == "apply_precision") {
         if (v < 0 || v > 2) return fail(ctx, MM_ERR_ARG, "apply_precision must be 0, 1 or 2");
         ctx->opt_apply_prec = v;
@@ -1847,6 +1851,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;
     else if (n == "apply_precision") *value = ctx->opt_apply_prec;
+    else if (n == "inner_tol") *value = ctx->opt_inner_tol;
     else if (n == "harvested") *value = ctx->harvest_count;
     else if (n == "filter_ms" || n == "filter_launches") {
         // total device time of the filter launches timed since the last read; resets the record

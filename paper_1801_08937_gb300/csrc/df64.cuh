@@ -15,6 +15,7 @@ struct df {
     df() = default;
     __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ constexpr df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr df(float f) : hi(f), lo(0.0f) {}
     __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.0f) {}
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };

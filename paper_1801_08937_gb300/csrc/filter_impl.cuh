@@ -83,7 +83,7 @@ template <typename T> struct Dft<T, 4> {
 };
 template <typename T> struct Dft<T, 8> {
     static __device__ __forceinline__ void run(C2<T>* a) {
-        const T r2 = T(0.70710678118654752440);
+        constexpr T r2 = T(0.70710678118654752440);
         // n = 2 n1 + n2, k = k1 + 4 k2
         dft4(a[0], a[2], a[4], a[6]);
         dft4(a[1], a[3], a[5], a[7]);
@@ -101,9 +101,10 @@ template <typename T> struct Dft<T, 8> {
     }
 };
 template <typename T> __device__ __forceinline__ void dft3(C2<T>& a0, C2<T>& a1, C2<T>& a2) {
-    const T h = T(0.86602540378443864676);   // sin(2 pi / 3)
+    constexpr T h = T(0.86602540378443864676);   // sin(2 pi / 3)
+    constexpr T half = T(0.5);
     const C2<T> t1 = cadd(a1, a2);
-    const C2<T> u{a0.x - T(0.5) * t1.x, a0.y - T(0.5) * t1.y};
+    const C2<T> u{a0.x - half * t1.x, a0.y - half * t1.y};
     const C2<T> v{h * (a1.x - a2.x), h * (a1.y - a2.y)};
     a0 = cadd(a0, t1);
     a1 = C2<T>{u.x + v.y, u.y - v.x};   // u - i v
@@ -115,9 +116,9 @@ template <typename T> struct Dft<T, 3> {
 template <typename T> struct Dft<T, 9> {
     static __device__ __forceinline__ void run(C2<T>* a) {
         // n = 3 n1 + n2, k = k1 + 3 k2; W9^m = (cos 2 pi m / 9, -sin 2 pi m / 9)
-        const T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);
-        const T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);
-        const T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);
+        constexpr T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);
+        constexpr T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);
+        constexpr T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);
 #pragma unroll
         for (int n2 = 0; n2 < 3; ++n2) dft3(a[n2], a[n2 + 3], a[n2 + 6]);
         a[4] = cmul(a[4], C2<T>{c1, -s1});
@@ -137,8 +138,8 @@ template <typename T> struct Dft<T, 9> {
 };
 template <typename T> struct Dft<T, 16> {
     static __device__ __forceinline__ void run(C2<T>* a) {
-        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
-        const T r2 = T(0.70710678118654752440);
+        constexpr T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
+        constexpr T r2 = T(0.70710678118654752440);
         // n = 4 n1 + n2, k = k1 + 4 k2
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);

@@ -60,8 +60,12 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=2e-6)
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve"],
-                    help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream")
+    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply"],
+                    help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
+                         "apply: A x alone (profiling)")
+    ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
+    ap.add_argument("--fft-len", type=int, default=0, help="apply mode: forced transform length (0: autotuned)")
+    ap.add_argument("--apply-precision", default="f32", choices=["f32", "f64", "df"])
     ap.add_argument("--n-rhs", type=int, default=64)
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -219,6 +223,8 @@ def main():
         return run_mc(args, world, rank, local)
     if args.mode == "serve":
         return run_serve(args, world, rank, local)
+    if args.mode == "apply":
+        return run_apply(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -421,6 +427,42 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------- A x alone (profiling) ----------------
+def run_apply(args, world, rank, local):
+    """mm_apply_A on the config's scan (optionally fewer detectors), timed with the filter's CUDA events."""
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    torch.cuda.set_device(local)
+    over = {"n_det": args.n_det} if args.n_det else {}
+    scan = synth.scan_from_config(args.config, seed=rank, **over)
+    prec = M.MM_FP64 if args.apply_precision == "f64" else M.MM_FP32_MIXED
+    ctx = M.Context(local, torch.cuda.current_stream().cuda_stream, prec)
+    if args.fft_len:
+        ctx.set_option("filter", 2)
+        ctx.set_option("fft_len", args.fft_len)
+    if args.apply_precision == "df":
+        ctx.set_option("apply_precision", 2)
+    ctx.setup_scan(scan)
+    x = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(max(1, args.warmup)):
+        ctx.apply_A(x, out=y)
+    ctx.set_option("time_filter", 1)
+    ctx.get_option("filter_ms")
+    for _ in range(args.steps):
+        ctx.apply_A(x, out=y)
+    ms = ctx.get_option("filter_ms") / args.steps
+    if rank == 0:
+        print(json.dumps({"mode": "apply", "config": args.config, "n_det": scan.n_det, "samples": scan.n_samples,
+                          "precision": args.apply_precision, "fft_len": int(ctx.get_option("plan_fft_len")),
+                          "whole_blocks": bool(ctx.get_option("plan_whole")), "filter_ms": ms,
+                          "samples_per_s": scan.n_samples / (ms * 1e-3)}), flush=True)
+    ctx.close()
 
 
 # ---------------- batched Monte Carlo (c3) ----------------

@@ -410,11 +410,8 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     p->lens = lens;
     p->n_work = (int)(segs.size() / 2);
     CK(p->segs.ensure(std::max<size_t>(1, segs.size()) * sizeof(Seg)));
-    if (!segs.empty()) {
+    if (!segs.empty())
         CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
-        launch_seg_windows(p->segs.as<Seg>(), (int)segs.size(), ctx->d_pix.as<int32_t>(), ctx->stream);
-        CKL();
-    }
     CK(cudaStreamSynchronize(ctx->stream));
     if (variant == 2) TRY(build_fft_tables(ctx, p->ft, fp, f64));
     if (f64 == 2 && !ctx->have_csdf) {

@@ -39,8 +39,6 @@ struct Seg {
     int32_t n_out;
     int32_t band;
     int32_t shift;   // left halo in the transform buffer: lambda, or 0 for a whole block
-    int32_t pmin;    // smallest pixel index its outputs hit
-    int32_t pcount;  // pixel window size (largest - smallest + 1; 0 if none)
 };
 
 // Mixed-radix FFT plan: L = product of radix[p]; pass p works on spans of
@@ -84,7 +82,6 @@ struct FilterArgs {
     FftPasses fp;
     const RhsState* state; // may be null: all right-hand sides active
     int tod_is_float;      // src TOD element type when from_tod (1: float, 0: double)
-    int hist_max;          // shared-memory scatter window per segment (0: warp-aggregated atomics only)
 };
 
 // T = float or double; from_tod selects b = P^T W d (src is a TOD).
@@ -103,8 +100,6 @@ size_t direct_smem_bytes(int V, int lam, bool f64);
 void launch_fft_spectrum(const double* h, double* H_out, double2* work, const double2* tw,
                          int n_bands, const FftPasses& fp, cudaStream_t s);
 void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s);
-// Fill Seg::pmin / Seg::pcount (pixel window of each segment's outputs).
-void launch_seg_windows(Seg* segs, int n_segs, const int32_t* pix, cudaStream_t s);
 
 // ---------------- vectors, preconditioners, reductions ----------------
 void launch_map_in(const double* src3, V4<double>* dst4, int64_t n_vec, cudaStream_t s);

@@ -43,38 +43,6 @@ __global__ void k_map_to_df(const V4<double>* src, V4<df>* dst, int64_t n) {
     }
 }
 
-// Pixel window of each segment's outputs (one CTA per segment).
-__global__ void k_seg_windows(Seg* segs, const int32_t* pix) {
-    Seg& S = segs[blockIdx.x];
-    int lo = INT32_MAX, hi = -1;
-    for (int i = threadIdx.x; i < S.n_out; i += blockDim.x) {
-        const int p = pix[S.out0 + i];
-        if (p >= 0) {
-            lo = min(lo, p);
-            hi = max(hi, p);
-        }
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        lo = min(lo, __shfl_down_sync(0xffffffffu, lo, d));
-        hi = max(hi, __shfl_down_sync(0xffffffffu, hi, d));
-    }
-    __shared__ int slo[32], shi[32];
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        slo[w] = lo;
-        shi[w] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
-            lo = min(lo, slo[j]);
-            hi = max(hi, shi[j]);
-        }
-        S.pmin = hi >= 0 ? lo : 0;
-        S.pcount = hi >= 0 ? hi - lo + 1 : 0;
-    }
-}
-
 // ---------------- launchers ----------------
 size_t fft_smem_bytes(int L, bool f64) { return (size_t)(L + (L >> 4)) * (f64 ? 16 : 8); }
 size_t direct_smem_bytes(int V, int lam, bool f64) {
@@ -100,11 +68,6 @@ void launch_map_to_df(const V4<double>* src, void* dst, int64_t n, cudaStream_t 
     if (n <= 0) return;
     const int64_t blocks = (n + 255) / 256;
     k_map_to_df<<<(int)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, s>>>(src, reinterpret_cast<V4<df>*>(dst), n);
-    count_launches(1);
-}
-void launch_seg_windows(Seg* segs, int n_segs, const int32_t* pix, cudaStream_t s) {
-    if (n_segs <= 0) return;
-    k_seg_windows<<<n_segs, 256, 0, s>>>(segs, pix);
     count_launches(1);
 }
 void launch_weights64(const float* psi, double2* cs, int64_t n, cudaStream_t s) {

@@ -566,14 +566,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     const int L = LCT > 0 ? LCT : a.L;
     const int lam = actA ? A.shift : B.shift;   // left halo of this pair (lambda, or 0 for whole blocks)
     const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
-    // Shared-memory scatter: each segment's outputs hit a pixel window small
-    // enough to accumulate in shared memory, flushed with one atomic per pixel.
-    constexpr bool HIST_OK = (sizeof(T) == 4);
-    const bool use_hist = HIST_OK && a.hist_max > 0 && (!actA || A.pcount <= a.hist_max) &&
-                          (!actB || B.pcount <= a.hist_max);
-    float* hist = reinterpret_cast<float*>(smraw + (size_t)(L + (L >> 4)) * sizeof(C2<T>));
-    if (use_hist)
-        for (int i = threadIdx.x; i < 6 * a.hist_max; i += blockDim.x) hist[i] = 0.0f;
 
     gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
     __syncthreads();
@@ -595,56 +587,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     using Acc = typename AccT<T>::type;
     V4<Acc>* qA = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)(actA ? A.rhs : 0) * a.n_pix;
     V4<Acc>* qB = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)(actB ? B.rhs : 0) * a.n_pix;
-    if constexpr (HIST_OK) {
-        if (use_hist) {
-            float* hA = hist;
-            float* hB = hist + 3 * a.hist_max;
-            for (int i0 = threadIdx.x; i0 < vmax; i0 += 2 * NT) {
-                int pa[2], pb[2];
-                float fa[2], fb[2];
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const int i = i0 + g * NT;
-                    pa[g] = (actA && i < A.n_out) ? __ldg(a.pix + A.out0 + i) : -1;
-                    pb[g] = (actB && i < B.n_out) ? __ldg(a.pix + B.out0 + i) : -1;
-                    fa[g] = pa[g] >= 0 ? __ldg(a.psi + A.out0 + i) : 0.0f;
-                    fb[g] = pb[g] >= 0 ? __ldg(a.psi + B.out0 + i) : 0.0f;
-                }
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const int i = i0 + g * NT;
-                    if (pa[g] < 0 && pb[g] < 0) continue;
-                    const C2<T> v = s[sidx(min(lam + i, L - 1))];
-                    if (pa[g] >= 0) {
-                        T c, sn;
-                        weights_from(a, A.out0 + i, fa[g], c, sn);
-                        float* h = hA + 3 * (pa[g] - A.pmin);
-                        atomicAdd(h, v.x);
-                        atomicAdd(h + 1, v.x * c);
-                        atomicAdd(h + 2, v.x * sn);
-                    }
-                    if (pb[g] >= 0) {
-                        T c, sn;
-                        weights_from(a, B.out0 + i, fb[g], c, sn);
-                        float* h = hB + 3 * (pb[g] - B.pmin);
-                        atomicAdd(h, -v.y);
-                        atomicAdd(h + 1, -v.y * c);
-                        atomicAdd(h + 2, -v.y * sn);
-                    }
-                }
-            }
-            __syncthreads();
-            for (int l = threadIdx.x; l < (actA ? A.pcount : 0); l += NT) {
-                const float v0 = hA[3 * l], v1 = hA[3 * l + 1], v2 = hA[3 * l + 2];
-                if (v0 != 0.0f || v1 != 0.0f || v2 != 0.0f) atomic_add3(qA + A.pmin + l, v0, v1, v2);
-            }
-            for (int l = threadIdx.x; l < (actB ? B.pcount : 0); l += NT) {
-                const float v0 = hB[3 * l], v1 = hB[3 * l + 1], v2 = hB[3 * l + 2];
-                if (v0 != 0.0f || v1 != 0.0f || v2 != 0.0f) atomic_add3(qB + B.pmin + l, v0, v1, v2);
-            }
-            return;
-        }
-    }
     for (int base = warp * 32; base < vmax; base += nwarp * 32 * SB) {
         int pa[SB], pb[SB];
         float fa[SB], fb[SB];
@@ -718,17 +660,8 @@ __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a)
 }
 
 
-constexpr int HIST_PIXELS = 1536;   // shared-memory scatter window per segment (float32, 512 threads)
-
 template <typename T, bool FROM_TOD, int NT, int LCT>
-inline void launch_fft_nt(const FilterArgs& a0, size_t sm, cudaStream_t s) {
-    FilterArgs a = a0;
-    if (sizeof(T) == 4 && NT == 512 && sm + (size_t)6 * HIST_PIXELS * sizeof(float) <= 227 * 1024) {
-        a.hist_max = HIST_PIXELS;
-        sm += (size_t)6 * HIST_PIXELS * sizeof(float);
-    } else {
-        a.hist_max = 0;
-    }
+inline void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
     static size_t configured = 0;
     if (sm > configured) {
         cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -32,7 +32,7 @@ __all__ = [
     "weights", "apply_P", "apply_Pt", "apply_Ninv", "apply_A", "rhs",
     "bd_blocks", "select_pixels", "flag_samples", "bd_inverse", "bd_apply",
     "pcg", "arnoldi", "ritz_basis", "coarse_space", "m2l_apply",
-    "dense_P", "dense_Ninv", "dense_A", "apply_A_rows", "Problem", "pcg_lanczos", "lanczos_ritz",
+    "dense_P", "dense_Ninv", "dense_A", "apply_A_rows", "rhs_rows", "Problem", "pcg_lanczos", "lanczos_ritz",
 ]
 
 
@@ -389,22 +389,15 @@ def dense_A(prob: Problem) -> np.ndarray:
 
 # -------- sampled rows for full-size checks --------
 
-def apply_A_rows(prob: Problem, x, pixels) -> np.ndarray:
-    """Rows (A x)_p for the listed pixels only, by the definition.
-
-    (A x)_p = sum_{t: p_t = p} w_t z_t with z_t = sum_{|k|<=lambda, t-k in block} c_|k| y_{t-k}
-    and y = P x.  Returns [len(pixels), 3].
-    """
-    y = apply_P(prob.pix, prob.psi, x)
+def _rows_of_W(prob: Problem, y, pixels) -> np.ndarray:
+    """sum_{t: p_t = p} w_t (W y)_t for the listed pixels, W y evaluated only where needed."""
     lam = prob.band.shape[1] - 1
-    blk = np.searchsorted(prob.block_off, np.arange(prob.pix.shape[0]), side="right") - 1 \
-        if prob.pix.shape[0] < (1 << 22) else None
     out = np.zeros((len(pixels), 3))
     for i, p in enumerate(pixels):
         ts = np.nonzero(prob.pix == p)[0]
         if ts.size == 0:
             continue
-        bs = blk[ts] if blk is not None else np.searchsorted(prob.block_off, ts, side="right") - 1
+        bs = np.searchsorted(prob.block_off, ts, side="right") - 1
         w = weights(prob.psi[ts])
         for t, b, wt in zip(ts, bs, w):
             o0, o1 = int(prob.block_off[b]), int(prob.block_off[b + 1])
@@ -413,3 +406,17 @@ def apply_A_rows(prob: Problem, x, pixels) -> np.ndarray:
             zt = float(c[np.abs(np.arange(j0, j1) - t)] @ y[j0:j1])
             out[i] += zt * wt
     return out
+
+
+def apply_A_rows(prob: Problem, x, pixels) -> np.ndarray:
+    """Rows (A x)_p for the listed pixels only, by the definition.
+
+    (A x)_p = sum_{t: p_t = p} w_t z_t with z_t = sum_{|k|<=lambda, t-k in block} c_|k| y_{t-k}
+    and y = P x.  Returns [len(pixels), 3].
+    """
+    return _rows_of_W(prob, apply_P(prob.pix, prob.psi, x), pixels)
+
+
+def rhs_rows(prob: Problem, d, pixels) -> np.ndarray:
+    """Rows b_p of b = P^T W d for the listed pixels only.  Returns [len(pixels), 3]."""
+    return _rows_of_W(prob, np.asarray(d, dtype=np.float64), pixels)

@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=2e-6)
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
                          "apply: A x alone (profiling)")
     ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
@@ -225,6 +225,8 @@ def main():
         return run_serve(args, world, rank, local)
     if args.mode == "apply":
         return run_apply(args, world, rank, local)
+    if args.mode == "scale":
+        return run_scale(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -427,6 +429,85 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------- mixed precision at scale (c4) ----------------
+def run_scale(args, world, rank, local):
+    """c4: 512x512 patch, 1024 det x 2^20 samples.  Mixed-precision two-level map
+    (coarse space k=64 from a first M_BD run) against the float64 GPU path,
+    and sampled rows of A x against the oracle on a 1/64 subset (16 detectors)."""
+    import torch
+    import oracle as O
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t_gen = time.time()
+    scan = synth.scan_from_config("c4", seed=rank)
+    tod = synth.make_tod(scan, synth.make_sky(scan.n_pix, rank), synth.make_noise(scan, rank))
+    t_gen = time.time() - t_gen
+    pix_d = torch.from_numpy(scan.pix).to(dev)
+    psi_d = torch.from_numpy(scan.psi).to(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        out = fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / 1e3, out
+
+    res = {}
+    maps = {}
+    for name, prec in (("mixed", M.MM_FP32_MIXED), ("fp64", M.MM_FP64)):
+        ctx = M.Context(local, stream.cuda_stream, prec)
+        tod_d = torch.from_numpy(tod.astype(np.float32 if prec == M.MM_FP32_MIXED else np.float64)).to(dev)
+        out = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
+        ctx.setup_pointing(pix_d, psi_d, scan.block_off, scan.block_band, scan.band, scan.n_pix, n_det=scan.n_det)
+        ctx.build_bd(1e-3)
+        if name == "mixed":
+            ctx.set_option("inner_tol", args.inner_tol)
+            ctx.set_option("harvest", args.m_max)
+            t_bd, (_, ibd) = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter,
+                                                     out=out))
+            ctx.set_option("harvest", 0)
+            t_c, k = timed(lambda: ctx.build_coarse_from_solve(k=64))
+            t_2l, (_, i2l) = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.max_iter,
+                                                     out=out))
+            res[name] = {"m_bd_s": t_bd, "m_bd_iters": ibd[0]["iters"], "coarse_s": t_c, "k": k,
+                         "two_level_s": t_2l, "two_level_iters": i2l[0]["iters"],
+                         "true_rel_res": i2l[0]["true_rel_res"]}
+        else:
+            t_bd, (_, ibd) = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter,
+                                                     out=out))
+            res[name] = {"m_bd_s": t_bd, "m_bd_iters": ibd[0]["iters"], "true_rel_res": ibd[0]["true_rel_res"]}
+        maps[name] = out.cpu().numpy()[0]
+        ctx.close()
+        del tod_d
+        torch.cuda.empty_cache()
+    err = float(np.linalg.norm(maps["mixed"] - maps["fp64"]) / np.linalg.norm(maps["fp64"]))
+    # 1/64 subset: 16 detectors of the same scan, sampled rows of A x against the oracle
+    sub = synth.scan_from_config("c4", seed=rank, n_det=16)
+    prob = O.Problem.from_scan(sub)
+    rng = np.random.default_rng(9)
+    pixels = [int(p) for p in rng.integers(0, sub.n_pix, 6)]
+    x = rng.standard_normal((sub.n_pix, 3))
+    ref = O.apply_A_rows(prob, x, pixels)
+    ctx = M.Context(local, stream.cuda_stream, M.MM_FP32_MIXED)
+    ctx.setup_scan(sub)
+    y = ctx.apply_A(torch.from_numpy(x[None]).to(dev)).cpu().numpy()[0]
+    ctx.close()
+    sub_err = float(np.linalg.norm(y[pixels] - ref) / np.linalg.norm(ref))
+    line = {"mode": "scale", "config": "c4: 512x512 patch, 1024 det x 2^20 samples, lambda 2048, 64 intervals, k=64",
+            "samples": scan.n_samples, "mixed": res["mixed"], "fp64": res["fp64"],
+            "map_rel_err_mixed_vs_fp64": err, "subset_Ax_rows_rel_err_vs_oracle": sub_err, "gen_s": t_gen}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # ---------------- A x alone (profiling) ----------------

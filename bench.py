@@ -470,6 +470,9 @@ def run_scale(args, world, rank, local):
         out = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
         ctx.setup_pointing(pix_d, psi_d, scan.block_off, scan.block_band, scan.band, scan.n_pix, n_det=scan.n_det)
         ctx.build_bd(1e-3)
+        # first use of each plan shape runs the autotuner: do it before timing
+        ctx.rhs(tod_d)
+        ctx.apply_A(out, out=torch.empty_like(out))
         if name == "mixed":
             ctx.set_option("inner_tol", args.inner_tol)
             ctx.set_option("harvest", args.m_max)

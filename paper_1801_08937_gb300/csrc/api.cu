@@ -194,7 +194,9 @@ int64_t max_block_len(const mm_ctx* c) {
 
 // Mixed-radix pass plan for L = 2^a 3^b (b <= 2): a radix-3 or radix-9 pass
 // first, then radix 16 while it divides, then one radix 2, 4 or 8 pass.
-bool fft_passes(int L, FftPasses* fp) {
+// maxr: largest power-of-two radix (8 for double-float plans, 16 otherwise),
+// the same rule as the kernels' compile-time plans.
+bool fft_passes(int L, FftPasses* fp, int maxr = 16) {
     int rest = L, np = 0, span = L;
     fp->L = L;
     auto add = [&](int r) {
@@ -206,8 +208,8 @@ bool fft_passes(int L, FftPasses* fp) {
     };
     if (rest % 9 == 0) add(9);
     else if (rest % 3 == 0) add(3);
-    while (rest % 16 == 0 && np < 8) add(16);
-    if (rest == 8 || rest == 4 || rest == 2) add(rest);
+    while (rest % maxr == 0 && np < 8) add(maxr);
+    if (rest > 1 && rest < maxr && (rest == 8 || rest == 4 || rest == 2)) add(rest);
     fp->npass = np;
     return rest == 1 && np <= 8;
 }
@@ -236,7 +238,7 @@ std::vector<FftCand> fft_candidates(const mm_ctx* c, int f64, int forced_log2, i
             const size_t sm = fft_smem_bytes(L, f64 != 0);
             if (sm > smem_limit_bytes()) continue;
             FftPasses fp;
-            if (!fft_passes(L, &fp)) continue;
+            if (!fft_passes(L, &fp, f64 == 2 ? 8 : 16)) continue;
             double points = 0, gathered = 0, ctas = 0;
             int whole = 0;
             if (L >= nb + lam) {
@@ -351,7 +353,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     FftPasses fp{};
     int logL = 0;
     if (variant == 2) {
-        fft_passes(L, &fp);
+        fft_passes(L, &fp, f64 == 2 ? 8 : 16);
         logL = ilog2(L);
     }
     for (auto& p : ctx->plans)

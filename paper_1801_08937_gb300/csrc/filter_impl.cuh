@@ -16,6 +16,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "df64.cuh"
 
@@ -274,7 +276,8 @@ struct CtPlan {
     int r[8];
     int s[8];
 };
-__host__ __device__ constexpr CtPlan make_ct_plan(int L) {
+// MAXR: largest power-of-two radix (16, or 8 where registers are scarce).
+__host__ __device__ constexpr CtPlan make_ct_plan(int L, int MAXR = 16) {
     CtPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
     int rest = L, span = L;
     if (rest % 9 == 0) {
@@ -282,10 +285,10 @@ __host__ __device__ constexpr CtPlan make_ct_plan(int L) {
     } else if (rest % 3 == 0) {
         p.r[p.np] = 3; p.s[p.np] = span; span /= 3; rest /= 3; ++p.np;
     }
-    while (rest % 16 == 0 && p.np < 8) {
-        p.r[p.np] = 16; p.s[p.np] = span; span /= 16; rest /= 16; ++p.np;
+    while (rest % MAXR == 0 && p.np < 8) {
+        p.r[p.np] = MAXR; p.s[p.np] = span; span /= MAXR; rest /= MAXR; ++p.np;
     }
-    if (rest == 8 || rest == 4 || rest == 2) {
+    if (rest > 1 && rest < MAXR && (rest == 8 || rest == 4 || rest == 2)) {
         p.r[p.np] = rest; p.s[p.np] = span; ++p.np;
     }
     return p;
@@ -319,22 +322,22 @@ __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) 
     }
 }
 
-template <typename T, int L, int NT, int P>
+template <typename T, int L, int NT, int MAXR, int P>
 __device__ __forceinline__ void ct_dif(C2<T>* s, const C2<T>* tw) {
-    constexpr CtPlan pl = make_ct_plan(L);
+    constexpr CtPlan pl = make_ct_plan(L, MAXR);
     if constexpr (P < pl.np) {
         ct_pass<T, pl.r[P], pl.s[P], L, NT, false>(s, tw);
         __syncthreads();
-        ct_dif<T, L, NT, P + 1>(s, tw);
+        ct_dif<T, L, NT, MAXR, P + 1>(s, tw);
     }
 }
-template <typename T, int L, int NT, int P>
+template <typename T, int L, int NT, int MAXR, int P>
 __device__ __forceinline__ void ct_dit(C2<T>* s, const C2<T>* tw) {
-    constexpr CtPlan pl = make_ct_plan(L);
+    constexpr CtPlan pl = make_ct_plan(L, MAXR);
     if constexpr (P >= 0) {
         ct_pass<T, pl.r[P], pl.s[P], L, NT, true>(s, tw);
         __syncthreads();
-        ct_dit<T, L, NT, P - 1>(s, tw);
+        ct_dit<T, L, NT, MAXR, P - 1>(s, tw);
     }
 }
 
@@ -553,6 +556,12 @@ __device__ __forceinline__ bool seg_active(const FilterArgs& a, const Seg& S) {
 }
 
 // ---------------- FFT overlap-save variant ----------------
+// Largest power-of-two radix of the compile-time transforms: 8 for
+// double-float (register pressure at 512 threads), 16 otherwise.  The host
+// planner uses the same rule, so the spectra share the digit order.
+template <typename T> struct MaxRadix { static constexpr int value = 16; };
+template <> struct MaxRadix<df> { static constexpr int value = 8; };
+
 template <typename T, bool FROM_TOD, int NT, int LCT>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_filter_fft(const FilterArgs a) {
     static_assert(sizeof(C2<T>) == 2 * sizeof(T), "complex layout");
@@ -569,7 +578,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
 
     gather_pair<T, FROM_TOD>(a, A, B, actA, actB, s, L, lam);
     __syncthreads();
-    if constexpr (LCT > 0) ct_dif<T, LCT, NT, 0>(s, tw);
+    if constexpr (LCT > 0) ct_dif<T, LCT, NT, MaxRadix<T>::value, 0>(s, tw);
     else fft_dif<T>(s, tw, a.fp);
     const T* H = reinterpret_cast<const T*>(a.H) + (int64_t)(actA ? A.band : B.band) * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -578,7 +587,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
         s[sidx(i)] = C2<T>{v.x * h, -v.y * h};
     }
     __syncthreads();
-    if constexpr (LCT > 0) ct_dit<T, LCT, NT, make_ct_plan(LCT > 0 ? LCT : 64).np - 1>(s, tw);
+    if constexpr (LCT > 0)
+        ct_dit<T, LCT, NT, MaxRadix<T>::value, make_ct_plan(LCT > 0 ? LCT : 64, MaxRadix<T>::value).np - 1>(s, tw);
     else fft_dit_conj<T>(s, tw, a.fp);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -691,7 +701,16 @@ inline void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
             default: break;
         }
     }
-    if constexpr (sizeof(T) == 8) {   // double and double-float
+    if constexpr (std::is_same<T, df>::value) {   // double-float: 512 threads, radix <= 8
+        switch (a.L) {
+            case 12288: return launch_fft_nt<T, FROM_TOD, 512, 12288>(a, sm, s);
+            case 9216: return launch_fft_nt<T, FROM_TOD, 512, 9216>(a, sm, s);
+            case 8192: return launch_fft_nt<T, FROM_TOD, 512, 8192>(a, sm, s);
+            case 4608: return launch_fft_nt<T, FROM_TOD, 512, 4608>(a, sm, s);
+            default: break;
+        }
+        return launch_fft_nt<T, FROM_TOD, 512, 0>(a, sm, s);
+    } else if constexpr (sizeof(T) == 8) {
         switch (a.L) {
             case 12288: return launch_fft_nt<T, FROM_TOD, 256, 12288>(a, sm, s);
             case 9216: return launch_fft_nt<T, FROM_TOD, 256, 9216>(a, sm, s);

@@ -512,7 +512,7 @@ __device__ __forceinline__ void atomic_add3(V4<double>* q, df a, df b, df c) {
 // Consecutive lanes with equal p form a run; a suffix sum inside each run
 // leaves the run total on its first lane, which issues one atomic.
 template <typename T>
-__device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename AccT<T>::type>* q) {
+__device__ __forceinline__ void scatter_vals(int p, T v0, T v1, T v2, V4<typename AccT<T>::type>* q) {
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const int pprev = __shfl_up_sync(FULL, p, 1);
@@ -520,7 +520,6 @@ __device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename A
     const unsigned heads = __ballot_sync(FULL, head);
     const unsigned above = heads & ~((2u << lane) - 1u);
     const int end = above ? (__ffs(above) - 1) : 32;
-    T v0 = z, v1 = z * c, v2 = z * s;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const T o0 = shfl_down_t(v0, d);
@@ -533,6 +532,93 @@ __device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename A
         }
     }
     if (head && p >= 0) atomic_add3(q + p, v0, v1, v2);
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename AccT<T>::type>* q) {
+    scatter_vals<T>(p, z, z * c, z * s, q);
+}
+
+// float32 scatter of one segment with four consecutive outputs per lane:
+// runs of equal pixels are summed in registers first, a lane's leading run
+// joins the previous lane's trailing run when they share a pixel, runs
+// strictly inside a lane's four samples go out directly, and the trailing
+// runs go through the warp-segmented reduction.  Every output is counted once.
+__device__ __forceinline__ void scatter4_f32(const FilterArgs& a, const Seg& S, bool act, int i0, const C2<float>* sm,
+                                             int lam, int L, bool imag, V4<float>* q) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    int p[4];
+    float ps[4];
+    const int64_t t0 = S.out0 + i0;
+    if (act && i0 + 3 < S.n_out && (t0 & 3) == 0) {
+        const int4 pv = __ldg(reinterpret_cast<const int4*>(a.pix + t0));
+        const float4 fv = __ldg(reinterpret_cast<const float4*>(a.psi + t0));
+        p[0] = pv.x; p[1] = pv.y; p[2] = pv.z; p[3] = pv.w;
+        ps[0] = fv.x; ps[1] = fv.y; ps[2] = fv.z; ps[3] = fv.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool ok = act && i0 + j < S.n_out;
+            p[j] = ok ? __ldg(a.pix + t0 + j) : -1;
+            ps[j] = ok ? __ldg(a.psi + t0 + j) : 0.0f;
+        }
+    }
+    float v0[4], v1[4], v2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float z = 0.0f, c = 0.0f, sn = 0.0f;
+        if (p[j] >= 0) {
+            const C2<float> v = sm[sidx(min(lam + i0 + j, L - 1))];
+            z = imag ? -v.y : v.x;
+            weights_from(a, t0 + j, ps[j], c, sn);
+        }
+        v0[j] = z;
+        v1[j] = z * c;
+        v2[j] = z * sn;
+    }
+    // runs inside the lane
+    int kf = p[0], cur = p[0];
+    float f0 = v0[0], f1 = v1[0], f2 = v2[0];
+    float c0 = v0[0], c1 = v1[0], c2 = v2[0];
+    bool first_done = false;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        if (p[j] == cur) {
+            c0 += v0[j];
+            c1 += v1[j];
+            c2 += v2[j];
+        } else {
+            if (!first_done) {
+                kf = cur;
+                f0 = c0;
+                f1 = c1;
+                f2 = c2;
+                first_done = true;
+            } else if (cur >= 0) {
+                atomic_add3(q + cur, c0, c1, c2);   // a run strictly inside the lane
+            }
+            cur = p[j];
+            c0 = v0[j];
+            c1 = v1[j];
+            c2 = v2[j];
+        }
+    }
+    const bool multi = first_done;
+    // a lane's leading run continues the previous lane's trailing run?
+    const int prev_last = __shfl_up_sync(FULL, cur, 1);
+    const bool give = multi && lane > 0 && kf == prev_last;
+    const float r0 = __shfl_down_sync(FULL, f0, 1);
+    const float r1 = __shfl_down_sync(FULL, f1, 1);
+    const float r2 = __shfl_down_sync(FULL, f2, 1);
+    const int rgive = __shfl_down_sync(FULL, (int)give, 1);
+    if (lane < 31 && rgive) {
+        c0 += r0;
+        c1 += r1;
+        c2 += r2;
+    }
+    if (multi && !give && kf >= 0) atomic_add3(q + kf, f0, f1, f2);
+    scatter_vals<float>(cur, c0, c1, c2, q);
 }
 
 template <typename T>
@@ -597,6 +683,14 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     using Acc = typename AccT<T>::type;
     V4<Acc>* qA = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)(actA ? A.rhs : 0) * a.n_pix;
     V4<Acc>* qB = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)(actB ? B.rhs : 0) * a.n_pix;
+    if constexpr (std::is_same<T, float>::value) {
+        for (int base = warp * 128; base < vmax; base += nwarp * 128) {
+            const int i0 = base + 4 * lane;
+            scatter4_f32(a, A, actA, i0, s, lam, L, false, qA);
+            scatter4_f32(a, B, actB, i0, s, lam, L, true, qB);
+        }
+        return;
+    }
     for (int base = warp * 32; base < vmax; base += nwarp * 32 * SB) {
         int pa[SB], pb[SB];
         float fa[SB], fb[SB];

@@ -258,10 +258,12 @@ std::vector<FftCand> fft_candidates(const mm_ctx* c, int f64, int forced_log2, i
                 gathered = std::min<double>(segs * L, 2.0 * c->n_samples + segs * 2.0 * lam);
                 ctas = segs * 0.5;
             }
-            double cost = points * fp.npass * 44.0 + gathered * 40.0 + (double)c->n_samples * 50.0;
+            // waves of CTAs times the work of one CTA (transform passes plus its gathers and scatters)
             const double per_sm = std::max(1.0, std::floor(228.0 * 1024 / (double)(sm + 1024)));
             const double slots = 152.0 * per_sm;
-            if (ctas < slots) cost *= slots / std::max(1.0, ctas);   // idle SMs
+            const double per_cta = (double)L * fp.npass * 44.0 + (gathered + (double)c->n_samples) / std::max(1.0, ctas) * 45.0;
+            const double waves = std::ceil(std::max(1.0, ctas) / slots);
+            double cost = waves * per_cta + 1e-3 * (points * fp.npass * 44.0);
             out.push_back({L, whole, cost});
         }
     }
@@ -523,13 +525,19 @@ mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_
         Plan* p = nullptr;
         TRY(make_plan(ctx, f64, nrhs, lens, o.variant, o.L, o.whole, o.V, &p));
         TRY(run_filter(ctx, p, false, src.p, dst.p, nullptr, 0));
-        CK(cudaEventRecord(e0, ctx->stream));
-        TRY(run_filter(ctx, p, false, src.p, dst.p, nullptr, 0));
-        CK(cudaEventRecord(e1, ctx->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best->ms) *best = TuneVal{o.variant, o.L, o.whole, o.V, (double)ms};
+        // best of up to three timed launches (one when a launch is long)
+        double ms_best = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(e0, ctx->stream));
+            TRY(run_filter(ctx, p, false, src.p, dst.p, nullptr, 0));
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms_best = std::min(ms_best, (double)ms);
+            if (ms > 2.0) break;
+        }
+        if (ms_best < best->ms) *best = TuneVal{o.variant, o.L, o.whole, o.V, ms_best};
     }
     ctx->opt_time_filter = saved_time;
     cudaEventDestroy(e0);

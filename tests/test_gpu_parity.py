@@ -380,3 +380,61 @@ def test_batched_two_level_uneven_lengths(prec):
         xo = _oracle_solution(prob, mbd, O.rhs(prob, tt[i][idx].astype(np.float64))).reshape(-1, 3)
         well = np.abs(mbd).reshape(scan.n_pix, -1).sum(axis=1) > 0   # pixels this prefix determines
         assert rel(xb[i][well], xo[well]) < 1e-6
+
+
+def test_status_codes_not_converged_and_breakdown():
+    scan, d, _ = scan_and_tod(SMALL, seed=23)
+    c = ctx_for(scan)
+    c.build_bd()
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-14, max_iter=3)
+    assert info[0]["status"] == "MM_ERR_NOT_CONVERGED" and info[0]["iters"] == 3
+    assert np.isfinite(x).all()
+    # an indefinite weight (negative diagonal) makes p^T A p <= 0: reported, not hidden
+    bad = synth.make_scan(seed=24, **dict(SMALL, half_bw=4))
+    bad.band = -np.abs(bad.band)
+    cb = ctx_for(bad)
+    cb.build_bd(0.0)
+    with pytest.raises(MM.MapMakerError) as e:
+        cb.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=50)
+    assert e.value.status == MM.MM_ERR_BREAKDOWN
+
+
+def test_argument_and_state_errors():
+    c = MM.Context(0, None, MM.MM_FP64)
+    scan = synth.make_scan(seed=25, **SMALL)
+    with pytest.raises(MM.MapMakerError) as e:
+        c.solve(np.zeros(scan.n_samples), MM.MM_PRECOND_BD)
+    assert e.value.status == MM.MM_ERR_STATE
+    bo = scan.block_off.copy()
+    bo[1] = bo[2]                                         # empty block
+    with pytest.raises(MM.MapMakerError) as e:
+        c.setup_pointing(scan.pix, scan.psi, bo, scan.block_band, scan.band, scan.n_pix, scan.n_det)
+    assert e.value.status == MM.MM_ERR_ARG
+    c.setup_scan(scan)
+    c.build_bd()
+    with pytest.raises(MM.MapMakerError) as e:
+        c.solve(np.zeros(scan.n_samples), MM.MM_PRECOND_2L)   # no coarse space yet
+    assert e.value.status == MM.MM_ERR_STATE
+    with pytest.raises(MM.MapMakerError) as e:
+        c.build_coarse(None, m_max=10, k=200)
+    assert e.value.status == MM.MM_ERR_ARG
+    # an all-zero timeline solves to the zero map at once
+    x, info = c.solve(np.zeros(scan.n_samples), MM.MM_PRECOND_BD, tol=1e-8)
+    assert info[0]["iters"] == 0 and np.all(x == 0)
+
+
+def test_single_pixel_single_block_extremes():
+    """n_pix = 1, one detector, one block, band wider than the block."""
+    rng = np.random.default_rng(26)
+    n = 300
+    pix = np.zeros(n, dtype=np.int32)
+    psi = (rng.random(n) * np.pi).astype(np.float32)
+    band = synth.toeplitz_band(400, 1.0)[None, :]
+    prob = O.Problem(pix, psi, np.array([0, n]), band, np.array([0]), 1)
+    x = rng.standard_normal((1, 3))
+    for filt in (1, 2):
+        c = MM.Context(0, None, MM.MM_FP64)
+        c.set_option("filter", filt)
+        c.setup_pointing(pix, psi, np.array([0, n]), np.array([0]), band, 1, 1)
+        assert rel(c.apply_A(x)[0], O.apply_A(prob, x)) < TOL64
+        c.close()

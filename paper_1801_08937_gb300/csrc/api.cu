@@ -549,13 +549,14 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
     int variant = ctx->opt_filter;
     int L = 0, V = 0, whole = 0;
     if (variant == 0 && ctx->opt_fft_len == 0 && ctx->opt_fft_log2 == 0 && ctx->opt_autotune && !ctx->capturing) {
-        TuneKey key{f64, ctx->lam, ctx->n_blocks, nrhs, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
-        for (auto v : lens) key.lens_sum += v;
+        // tuned once per precision and geometry on a single right-hand side: the
+        // per-CTA work of a plan does not depend on how many right-hand sides share it
+        TuneKey key{f64, ctx->lam, ctx->n_blocks, 1, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
         for (auto& kv : tune_cache())
             if (kv.first == key) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
                                                   kv.second.whole, kv.second.V, out);
         TuneVal best{};
-        TRY(autotune_plan(ctx, f64, nrhs, lens, &best));
+        TRY(autotune_plan(ctx, f64, 1, {}, &best));
         tune_record(key, best);
         return make_plan(ctx, f64, nrhs, lens, best.variant, best.L, best.whole, best.V, out);
     }

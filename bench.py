@@ -64,6 +64,8 @@ def parse():
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
                          "apply: A x alone (profiling)")
     ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
+    ap.add_argument("--half-bw", type=int, default=-1, help="apply mode: band half-width override")
+    ap.add_argument("--filter", type=int, default=0, help="apply mode: 0 autotuned, 1 direct band, 2 FFT")
     ap.add_argument("--fft-len", type=int, default=0, help="apply mode: forced transform length (0: autotuned)")
     ap.add_argument("--apply-precision", default="f32", choices=["f32", "f64", "df"])
     ap.add_argument("--n-rhs", type=int, default=64)
@@ -523,9 +525,13 @@ def run_apply(args, world, rank, local):
     from paper_1801_08937_gb300 import mapmaker as M
     torch.cuda.set_device(local)
     over = {"n_det": args.n_det} if args.n_det else {}
+    if args.half_bw >= 0:
+        over["half_bw"] = args.half_bw
     scan = synth.scan_from_config(args.config, seed=rank, **over)
     prec = M.MM_FP64 if args.apply_precision == "f64" else M.MM_FP32_MIXED
     ctx = M.Context(local, torch.cuda.current_stream().cuda_stream, prec)
+    if args.filter:
+        ctx.set_option("filter", args.filter)
     if args.fft_len:
         ctx.set_option("filter", 2)
         ctx.set_option("fft_len", args.fft_len)
@@ -542,10 +548,19 @@ def run_apply(args, world, rank, local):
         ctx.apply_A(x, out=y)
     ms = ctx.get_option("filter_ms") / args.steps
     if rank == 0:
-        print(json.dumps({"mode": "apply", "config": args.config, "n_det": scan.n_det, "samples": scan.n_samples,
-                          "precision": args.apply_precision, "fft_len": int(ctx.get_option("plan_fft_len")),
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        gbs = 8.0 * scan.n_samples / (ms * 1e-3) / 1e9
+        print(json.dumps({"mode": "apply", "config": args.config, "n_det": scan.n_det, "half_bw": scan.half_bw,
+                          "samples": scan.n_samples, "precision": args.apply_precision,
+                          "fft_len": int(ctx.get_option("plan_fft_len")),
                           "whole_blocks": bool(ctx.get_option("plan_whole")), "filter_ms": ms,
-                          "samples_per_s": scan.n_samples / (ms * 1e-3)}), flush=True)
+                          "samples_per_s": scan.n_samples / (ms * 1e-3), "hbm_gbs_8B_per_sample": gbs,
+                          "hbm_frac_of_measured": gbs / hbm}), flush=True)
     ctx.close()
 
 

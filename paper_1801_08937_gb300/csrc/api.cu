@@ -506,7 +506,7 @@ mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_
     for (size_t i = 0; i < cands.size() && i < 6; ++i)
         opts.push_back({2, cands[i].L, cands[i].whole, cands[i].whole ? cands[i].L - ctx->lam : cands[i].L - 2 * ctx->lam});
     if (ctx->lam <= 256)
-        for (int tile : {512, 2048})
+        for (int tile : {1024, 2048})
             if (direct_smem_bytes(tile, ctx->lam, f64 != 0) <= 200 * 1024) opts.push_back({1, 0, 0, tile});
     if (opts.empty()) return fail(ctx, MM_ERR_ARG, "no filter plan fits this band");
     const size_t esz = f64 ? sizeof(V4<double>) : sizeof(V4<float>);   // V4<df> is 32 bytes too

@@ -539,45 +539,15 @@ __device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename A
     scatter_vals<T>(p, z, z * c, z * s, q);
 }
 
-// float32 scatter of one segment with four consecutive outputs per lane:
-// runs of equal pixels are summed in registers first, a lane's leading run
-// joins the previous lane's trailing run when they share a pixel, runs
-// strictly inside a lane's four samples go out directly, and the trailing
-// runs go through the warp-segmented reduction.  Every output is counted once.
-__device__ __forceinline__ void scatter4_f32(const FilterArgs& a, const Seg& S, bool act, int i0, const C2<float>* sm,
-                                             int lam, int L, bool imag, V4<float>* q) {
+// float32 scatter of four consecutive outputs per lane: runs of equal pixels
+// are summed in registers first, a lane's leading run joins the previous
+// lane's trailing run when they share a pixel, runs strictly inside a lane's
+// four samples go out directly, and the trailing runs go through the
+// warp-segmented reduction.  Every output is counted once.
+__device__ __forceinline__ void scatter4_vals(const int (&p)[4], const float (&v0)[4], const float (&v1)[4],
+                                              const float (&v2)[4], V4<float>* q) {
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
-    int p[4];
-    float ps[4];
-    const int64_t t0 = S.out0 + i0;
-    if (act && i0 + 3 < S.n_out && (t0 & 3) == 0) {
-        const int4 pv = __ldg(reinterpret_cast<const int4*>(a.pix + t0));
-        const float4 fv = __ldg(reinterpret_cast<const float4*>(a.psi + t0));
-        p[0] = pv.x; p[1] = pv.y; p[2] = pv.z; p[3] = pv.w;
-        ps[0] = fv.x; ps[1] = fv.y; ps[2] = fv.z; ps[3] = fv.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const bool ok = act && i0 + j < S.n_out;
-            p[j] = ok ? __ldg(a.pix + t0 + j) : -1;
-            ps[j] = ok ? __ldg(a.psi + t0 + j) : 0.0f;
-        }
-    }
-    float v0[4], v1[4], v2[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float z = 0.0f, c = 0.0f, sn = 0.0f;
-        if (p[j] >= 0) {
-            const C2<float> v = sm[sidx(min(lam + i0 + j, L - 1))];
-            z = imag ? -v.y : v.x;
-            weights_from(a, t0 + j, ps[j], c, sn);
-        }
-        v0[j] = z;
-        v1[j] = z * c;
-        v2[j] = z * sn;
-    }
-    // runs inside the lane
     int kf = p[0], cur = p[0];
     float f0 = v0[0], f1 = v1[0], f2 = v2[0];
     float c0 = v0[0], c1 = v1[0], c2 = v2[0];
@@ -605,7 +575,6 @@ __device__ __forceinline__ void scatter4_f32(const FilterArgs& a, const Seg& S, 
         }
     }
     const bool multi = first_done;
-    // a lane's leading run continues the previous lane's trailing run?
     const int prev_last = __shfl_up_sync(FULL, cur, 1);
     const bool give = multi && lane > 0 && kf == prev_last;
     const float r0 = __shfl_down_sync(FULL, f0, 1);
@@ -619,6 +588,47 @@ __device__ __forceinline__ void scatter4_f32(const FilterArgs& a, const Seg& S, 
     }
     if (multi && !give && kf >= 0) atomic_add3(q + kf, f0, f1, f2);
     scatter_vals<float>(cur, c0, c1, c2, q);
+}
+
+// Pixel and angle of four consecutive samples t0..t0+3 (vector loads when
+// aligned); samples at or beyond `limit` (segment end) come back flagged.
+__device__ __forceinline__ void load4(const FilterArgs& a, int64_t t0, bool act, int count, int (&p)[4],
+                                      float (&ps)[4]) {
+    if (act && count >= 4 && (t0 & 3) == 0) {
+        const int4 pv = __ldg(reinterpret_cast<const int4*>(a.pix + t0));
+        const float4 fv = __ldg(reinterpret_cast<const float4*>(a.psi + t0));
+        p[0] = pv.x; p[1] = pv.y; p[2] = pv.z; p[3] = pv.w;
+        ps[0] = fv.x; ps[1] = fv.y; ps[2] = fv.z; ps[3] = fv.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool ok = act && j < count;
+            p[j] = ok ? __ldg(a.pix + t0 + j) : -1;
+            ps[j] = ok ? __ldg(a.psi + t0 + j) : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ void scatter4_f32(const FilterArgs& a, const Seg& S, bool act, int i0, const C2<float>* sm,
+                                             int lam, int L, bool imag, V4<float>* q) {
+    int p[4];
+    float ps[4];
+    const int64_t t0 = S.out0 + i0;
+    load4(a, t0, act, S.n_out - i0, p, ps);
+    float v0[4], v1[4], v2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float z = 0.0f, c = 0.0f, sn = 0.0f;
+        if (p[j] >= 0) {
+            const C2<float> v = sm[sidx(min(lam + i0 + j, L - 1))];
+            z = imag ? -v.y : v.x;
+            weights_from(a, t0 + j, ps[j], c, sn);
+        }
+        v0[j] = z;
+        v1[j] = z * c;
+        v2[j] = z * sn;
+    }
+    scatter4_vals(p, v0, v1, v2, q);
 }
 
 template <typename T>
@@ -729,6 +739,89 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     }
 }
 
+// ---------------- direct band variant, float32, four samples per thread ----------------
+// For narrow bands the product is gather + scatter bound: each thread owns
+// four consecutive outputs in both phases, so the pixel indices and pointing
+// weights loaded for the gather stay in registers for the scatter.  The
+// gathered y (with its lambda halo) is staged in shared memory for the band.
+template <bool FROM_TOD, int GPT>
+__global__ void __launch_bounds__(DIRECT_NT) k_filter_direct4(const FilterArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lam = a.lam;
+    float* c = reinterpret_cast<float*>(smraw);
+    float* y = c + ((lam + 1 + 3) & ~3);
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const Seg S = a.segs[2 * blockIdx.x + half];
+        if (!seg_active<float>(a, S)) continue;   // uniform across the CTA
+        const float* band = reinterpret_cast<const float*>(a.band) + (int64_t)S.band * (lam + 1);
+        for (int k = threadIdx.x; k <= lam; k += blockDim.x) c[k] = band[k];
+        V4<float>* q = reinterpret_cast<V4<float>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
+        const V4<float>* xm = reinterpret_cast<const V4<float>*>(a.src) + (int64_t)S.rhs * a.n_pix;
+        int p[GPT][4];
+        float cw[GPT][4], sw[GPT][4];
+        // outputs of this thread: groups g = threadIdx.x + k * NT, samples out0 + 4g .. +3
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
+            float ps[4];
+            load4(a, S.out0 + i0, i0 < S.n_out, S.n_out - i0, p[k], ps);
+            float yv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cw[k][j] = 0.0f;
+                sw[k][j] = 0.0f;
+                yv[j] = 0.0f;
+                if (p[k][j] >= 0) weights_from(a, S.out0 + i0 + j, ps[j], cw[k][j], sw[k][j]);
+            }
+            if (FROM_TOD) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j < S.n_out)
+                        yv[j] = a.tod_is_float ? __ldg(reinterpret_cast<const float*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j)
+                                               : (float)__ldg(reinterpret_cast<const double*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j);
+            } else {
+                V4<float> m[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (p[k][j] >= 0) m[j] = ldmap<float>(xm + p[k][j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (p[k][j] >= 0) yv[j] = m[j].x + cw[k][j] * m[j].y + sw[k][j] * m[j].z;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j < S.n_out) y[lam + i0 + j] = yv[j];
+        }
+        // halo of lambda samples on each side, clipped to the block
+        for (int h = threadIdx.x; h < 2 * lam; h += blockDim.x) {
+            const int i = h < lam ? h : lam + S.n_out + (h - lam);
+            const int64_t t = S.out0 - lam + i;
+            y[i] = (t >= S.lo && t < S.hi) ? sample_value<float, FROM_TOD>(a, t, S.rhs) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
+            float v0[4], v1[4], v2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float z = 0.0f;
+                if (p[k][j] >= 0) {
+                    const float* yc = y + lam + i0 + j;
+                    z = c[0] * yc[0];
+                    for (int kk = 1; kk <= lam; ++kk) z += c[kk] * (yc[-kk] + yc[kk]);
+                }
+                v0[j] = z;
+                v1[j] = z * cw[k][j];
+                v2[j] = z * sw[k][j];
+            }
+            scatter4_vals(p[k], v0, v1, v2, q);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------- direct band variant ----------------
 template <typename T, bool FROM_TOD>
 __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a) {
@@ -821,6 +914,30 @@ inline void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
 template <typename T, bool FROM_TOD>
 inline void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
     if (a.n_work <= 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+        // lean kernel: tile = 4 * DIRECT_NT * GPT outputs
+        const size_t sm = (size_t)(((a.lam + 1 + 3) & ~3) + a.V + 2 * a.lam) * sizeof(float);
+        if (a.V == 4 * DIRECT_NT * 2) {
+            static size_t configured = 0;
+            if (sm > configured) {
+                cudaFuncSetAttribute(k_filter_direct4<FROM_TOD, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                configured = sm;
+            }
+            k_filter_direct4<FROM_TOD, 2><<<a.n_work, DIRECT_NT, sm, s>>>(a);
+            count_launches(1);
+            return;
+        }
+        if (a.V == 4 * DIRECT_NT) {
+            static size_t configured1 = 0;
+            if (sm > configured1) {
+                cudaFuncSetAttribute(k_filter_direct4<FROM_TOD, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                configured1 = sm;
+            }
+            k_filter_direct4<FROM_TOD, 1><<<a.n_work, DIRECT_NT, sm, s>>>(a);
+            count_launches(1);
+            return;
+        }
+    }
     const size_t sm = direct_smem_bytes(a.V, a.lam, sizeof(T) == 8);
     static size_t configured = 0;
     if (sm > configured) {

@@ -86,6 +86,26 @@ def test_apply_A_compile_time_lengths(L, prec):
         assert rel(c.apply_A(x)[0], O.apply_A(prob, x)) < (TOL64 if prec == MM.MM_FP64 else TOL32)
 
 
+@pytest.mark.parametrize("tile", [1024, 2048])
+@pytest.mark.parametrize("lam", [0, 5, 16])
+@pytest.mark.parametrize("prec", [MM.MM_FP32_MIXED, MM.MM_FP64])
+def test_apply_A_direct_tiles(tile, lam, prec):
+    """Direct band with the lean four-samples-per-thread float32 kernel (and float64), ragged blocks, flags."""
+    scan = ragged(synth.make_scan(seed=27, flag_frac=0.02, **dict(SMALL, half_bw=lam)), seed=27)
+    prob = O.Problem.from_scan(scan)
+    c = ctx_for(scan, prec, 1)
+    c.set_option("direct_tile", tile)
+    x = np.random.default_rng(27).standard_normal((2, scan.n_pix, 3))
+    y = c.apply_A(x)
+    tol = TOL64 if prec == MM.MM_FP64 else TOL32
+    for r in range(2):
+        assert rel(y[r], O.apply_A(prob, x[r])) < tol
+    d = synth.make_tod(scan, synth.make_sky(scan.n_pix, 27), synth.make_noise(scan, 27))
+    c.build_bd()
+    xs, info = c.solve(d.astype(c.tod_dtype), MM.MM_PRECOND_BD, tol=1e-10)
+    assert info[0]["status"] == "MM_OK"
+
+
 @pytest.mark.parametrize("lam,blen", [(0, 512), (3, 512), (150, 100), (64, 65), (200, 4096)])
 def test_apply_A_band_edges(lam, blen):
     """Bands wider than blocks, zero bands, one-tap bands: truncation at block edges."""

@@ -744,42 +744,46 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
 // four consecutive outputs in both phases, so the pixel indices and pointing
 // weights loaded for the gather stay in registers for the scatter.  The
 // gathered y (with its lambda halo) is staged in shared memory for the band.
-template <bool FROM_TOD, int GPT>
+template <bool FROM_TOD, int GPT, int LMAX>
 __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct4(const FilterArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int lam = a.lam;
-    float* c = reinterpret_cast<float*>(smraw);
-    float* y = c + ((lam + 1 + 3) & ~3);
+    const int lam = a.lam;   // <= LMAX
+    float* c = reinterpret_cast<float*>(smraw);                    // LMAX + 1 (zero beyond lam), padded to 4
+    float* y = c + ((LMAX + 1 + 3) & ~3);                          // [LMAX + 4*NT*GPT + LMAX], aligned to 16 B
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         const Seg S = a.segs[2 * blockIdx.x + half];
         if (!seg_active<float>(a, S)) continue;   // uniform across the CTA
         const float* band = reinterpret_cast<const float*>(a.band) + (int64_t)S.band * (lam + 1);
-        for (int k = threadIdx.x; k <= lam; k += blockDim.x) c[k] = band[k];
+        for (int k = threadIdx.x; k <= LMAX; k += blockDim.x) c[k] = k <= lam ? band[k] : 0.0f;
         V4<float>* q = reinterpret_cast<V4<float>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
         const V4<float>* xm = reinterpret_cast<const V4<float>*>(a.src) + (int64_t)S.rhs * a.n_pix;
         int p[GPT][4];
-        float cw[GPT][4], sw[GPT][4];
+        float cw[GPT][4], sw[GPT][4], yv[GPT][4];
         // outputs of this thread: groups g = threadIdx.x + k * NT, samples out0 + 4g .. +3
 #pragma unroll
         for (int k = 0; k < GPT; ++k) {
             const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
             float ps[4];
             load4(a, S.out0 + i0, i0 < S.n_out, S.n_out - i0, p[k], ps);
-            float yv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 cw[k][j] = 0.0f;
                 sw[k][j] = 0.0f;
-                yv[j] = 0.0f;
+                yv[k][j] = 0.0f;
                 if (p[k][j] >= 0) weights_from(a, S.out0 + i0 + j, ps[j], cw[k][j], sw[k][j]);
             }
+        }
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
             if (FROM_TOD) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (i0 + j < S.n_out)
-                        yv[j] = a.tod_is_float ? __ldg(reinterpret_cast<const float*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j)
-                                               : (float)__ldg(reinterpret_cast<const double*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j);
+                        yv[k][j] = a.tod_is_float
+                                       ? __ldg(reinterpret_cast<const float*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j)
+                                       : (float)__ldg(reinterpret_cast<const double*>(a.src) + S.rhs * a.n_samples + S.out0 + i0 + j);
             } else {
                 V4<float> m[4];
 #pragma unroll
@@ -787,31 +791,65 @@ __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct4(const FilterArgs a
                     if (p[k][j] >= 0) m[j] = ldmap<float>(xm + p[k][j]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (p[k][j] >= 0) yv[j] = m[j].x + cw[k][j] * m[j].y + sw[k][j] * m[j].z;
+                    if (p[k][j] >= 0) yv[k][j] = m[j].x + cw[k][j] * m[j].y + sw[k][j] * m[j].z;
             }
+        }
+        if constexpr (LMAX > 0) {
+            // stage y with its halo, then each thread slides over a register window
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (i0 + j < S.n_out) y[lam + i0 + j] = yv[j];
+            for (int k = 0; k < GPT; ++k) {
+                const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
+                *reinterpret_cast<float4*>(y + LMAX + i0) = make_float4(yv[k][0], yv[k][1], yv[k][2], yv[k][3]);
+            }
+            __syncthreads();   // the right halo overlaps the stores of tile positions past the segment end
+            for (int h = threadIdx.x; h < 2 * LMAX; h += blockDim.x) {
+                // left halo y[0 .. LMAX), right halo after the segment's outputs
+                const int i = h < LMAX ? h : LMAX + S.n_out + (h - LMAX);
+                const int64_t t = S.out0 - LMAX + i;
+                y[i] = (t >= S.lo && t < S.hi && (h < LMAX ? LMAX - h <= lam : h - LMAX < lam))
+                           ? sample_value<float, FROM_TOD>(a, t, S.rhs) : 0.0f;
+            }
+            // outputs inside the tile but past the segment end read zeros
+            for (int i = S.n_out + threadIdx.x; i < 4 * DIRECT_NT * GPT; i += blockDim.x)
+                if (i >= S.n_out + LMAX) y[LMAX + i] = 0.0f;
+            __syncthreads();
+            float cr[LMAX + 1];
+#pragma unroll
+            for (int kk = 0; kk <= LMAX; ++kk) cr[kk] = c[kk];
+#pragma unroll
+            for (int k = 0; k < GPT; ++k) {
+                const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
+                float w[4 + 2 * LMAX];
+#pragma unroll
+                for (int e = 0; e < (4 + 2 * LMAX) / 4; ++e) {
+                    const float4 v = *reinterpret_cast<const float4*>(y + i0 + 4 * e);
+                    w[4 * e] = v.x;
+                    w[4 * e + 1] = v.y;
+                    w[4 * e + 2] = v.z;
+                    w[4 * e + 3] = v.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float z = cr[0] * w[LMAX + j];
+#pragma unroll
+                    for (int kk = 1; kk <= LMAX; ++kk) z += cr[kk] * (w[LMAX + j - kk] + w[LMAX + j + kk]);
+                    yv[k][j] = z;
+                }
+            }
+        } else {
+            __syncthreads();
+            const float c0 = c[0];
+#pragma unroll
+            for (int k = 0; k < GPT; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) yv[k][j] *= c0;
         }
-        // halo of lambda samples on each side, clipped to the block
-        for (int h = threadIdx.x; h < 2 * lam; h += blockDim.x) {
-            const int i = h < lam ? h : lam + S.n_out + (h - lam);
-            const int64_t t = S.out0 - lam + i;
-            y[i] = (t >= S.lo && t < S.hi) ? sample_value<float, FROM_TOD>(a, t, S.rhs) : 0.0f;
-        }
-        __syncthreads();
 #pragma unroll
         for (int k = 0; k < GPT; ++k) {
-            const int i0 = 4 * (threadIdx.x + k * DIRECT_NT);
             float v0[4], v1[4], v2[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float z = 0.0f;
-                if (p[k][j] >= 0) {
-                    const float* yc = y + lam + i0 + j;
-                    z = c[0] * yc[0];
-                    for (int kk = 1; kk <= lam; ++kk) z += c[kk] * (yc[-kk] + yc[kk]);
-                }
+                const float z = p[k][j] >= 0 ? yv[k][j] : 0.0f;
                 v0[j] = z;
                 v1[j] = z * cw[k][j];
                 v2[j] = z * sw[k][j];
@@ -915,26 +953,26 @@ template <typename T, bool FROM_TOD>
 inline void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
     if (a.n_work <= 0) return;
     if constexpr (std::is_same<T, float>::value) {
-        // lean kernel: tile = 4 * DIRECT_NT * GPT outputs
-        const size_t sm = (size_t)(((a.lam + 1 + 3) & ~3) + a.V + 2 * a.lam) * sizeof(float);
-        if (a.V == 4 * DIRECT_NT * 2) {
-            static size_t configured = 0;
-            if (sm > configured) {
-                cudaFuncSetAttribute(k_filter_direct4<FROM_TOD, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                configured = sm;
+        // lean kernel: tile = 4 * DIRECT_NT * GPT outputs, bands up to 16 taps each side
+        if ((a.V == 4 * DIRECT_NT * 2 || a.V == 4 * DIRECT_NT) && a.lam <= 16) {
+            const int gpt = a.V / (4 * DIRECT_NT);
+            const int lmax = a.lam == 0 ? 0 : (a.lam <= 4 ? 4 : (a.lam <= 8 ? 8 : 16));
+            const size_t sm = (size_t)(((lmax + 1 + 3) & ~3) + a.V + 2 * lmax + 4) * sizeof(float);
+            auto go = [&](auto kern) {
+                kern<<<a.n_work, DIRECT_NT, sm, s>>>(a);
+                count_launches(1);
+            };
+            if (gpt == 2) {
+                if (lmax == 0) go(k_filter_direct4<FROM_TOD, 2, 0>);
+                else if (lmax == 4) go(k_filter_direct4<FROM_TOD, 2, 4>);
+                else if (lmax == 8) go(k_filter_direct4<FROM_TOD, 2, 8>);
+                else go(k_filter_direct4<FROM_TOD, 2, 16>);
+            } else {
+                if (lmax == 0) go(k_filter_direct4<FROM_TOD, 1, 0>);
+                else if (lmax == 4) go(k_filter_direct4<FROM_TOD, 1, 4>);
+                else if (lmax == 8) go(k_filter_direct4<FROM_TOD, 1, 8>);
+                else go(k_filter_direct4<FROM_TOD, 1, 16>);
             }
-            k_filter_direct4<FROM_TOD, 2><<<a.n_work, DIRECT_NT, sm, s>>>(a);
-            count_launches(1);
-            return;
-        }
-        if (a.V == 4 * DIRECT_NT) {
-            static size_t configured1 = 0;
-            if (sm > configured1) {
-                cudaFuncSetAttribute(k_filter_direct4<FROM_TOD, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                configured1 = sm;
-            }
-            k_filter_direct4<FROM_TOD, 1><<<a.n_work, DIRECT_NT, sm, s>>>(a);
-            count_launches(1);
             return;
         }
     }

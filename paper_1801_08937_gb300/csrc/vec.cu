@@ -53,11 +53,36 @@ __device__ __forceinline__ bool last_block(unsigned* counter, int rhs) {
     return is_last;
 }
 
+// Sum of the CTA partials of value d for slice rhs, by the whole (last) CTA:
+// strided per-thread sums, then warp and CTA trees -- a fixed order, so the
+// result is deterministic.  Every thread of the CTA must call it; the sum is
+// returned to all threads.
 template <int D>
 __device__ __forceinline__ double gather_partial(const double* partial, int nblk, int nrhs, int rhs, int d) {
+    __shared__ double red[VT / 32];
+    __shared__ double total;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += __ldcg(partial + ((int64_t)b * nrhs + rhs) * D + d);
-    return s;
+    for (int b = threadIdx.x; b < nblk; b += VT) s += __ldcg(partial + ((int64_t)b * nrhs + rhs) * D + d);
+    s = warp_sum(s);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < VT / 32; ++w) t += red[w];
+        total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Warp w sums partials of the values c = w, w + 8, ... (k values per slice).
+__device__ __forceinline__ double warp_gather(const double* partial, int nblk, int64_t stride, int64_t off) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += __ldcg(partial + (int64_t)b * stride + off);
+    s = warp_sum(s);
+    return __shfl_sync(0xffffffffu, s, 0);
 }
 
 __device__ __forceinline__ V4<double> ld4(const V4<double>* p) { return *p; }
@@ -340,8 +365,8 @@ __global__ void k_pcg_init(const PcgArgs a, const V4<double>* b) {
     double* part = a.partial + ((int64_t)blockIdx.x * a.nrhs + rhs) * 1;
     block_partials<1>(acc, part);
     if (last_block(a.counter, rhs)) {
+        const double bb = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
         if (threadIdx.x == 0) {
-            const double bb = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
             RhsState& st = a.st[rhs];
             st.bnorm = sqrt(bb);
             st.relres = 1.0;
@@ -370,8 +395,8 @@ __global__ void k_bd_dot(const PcgArgs a, int finalize_beta) {
     }
     block_partials<1>(acc, a.partial + ((int64_t)blockIdx.x * a.nrhs + rhs));
     if (last_block(a.counter, rhs)) {
+        const double rz = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
         if (threadIdx.x == 0) {
-            const double rz = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
             RhsState& st = a.st[rhs];
             st.beta = finalize_beta ? rz / st.rz : 0.0;
             st.rz = rz;
@@ -414,8 +439,8 @@ __global__ void k_pcg_pq(const PcgArgs a) {
     PIX_LOOP(i) acc[0] += dot3(a.p[off + i], load_q(a, off + i));
     block_partials<1>(acc, a.partial + ((int64_t)blockIdx.x * a.nrhs + rhs));
     if (last_block(a.counter, rhs)) {
+        const double pq = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
         if (threadIdx.x == 0) {
-            const double pq = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
             RhsState& st = a.st[rhs];
             st.pq = pq;
             if (!(pq > 0.0) || !isfinite(pq) || !isfinite(st.rz)) {
@@ -462,8 +487,9 @@ __global__ void k_pcg_update(const PcgArgs a) {
     }
     block_partials<2>(acc, a.partial + ((int64_t)blockIdx.x * a.nrhs + rhs) * 2);
     if (last_block(a.counter, rhs)) {
+        const double rr = gather_partial<2>(a.partial, gridDim.x, a.nrhs, rhs, 0);
+        const double rz_new = TWO_LEVEL ? 0.0 : gather_partial<2>(a.partial, gridDim.x, a.nrhs, rhs, 1);
         if (threadIdx.x == 0) {
-            const double rr = gather_partial<2>(a.partial, gridDim.x, a.nrhs, rhs, 0);
             RhsState& st = a.st[rhs];
             st.iters += 1;
             st.relres = sqrt(rr) / st.bnorm;
@@ -478,7 +504,7 @@ __global__ void k_pcg_update(const PcgArgs a) {
                 st.active = 0;
             }
             if (!TWO_LEVEL) {
-                const double rz = gather_partial<2>(a.partial, gridDim.x, a.nrhs, rhs, 1);
+                const double rz = rz_new;
                 st.beta = rz / st.rz;
                 st.rz = rz;
                 if (a.bhist) a.bhist[(int64_t)rhs * a.hist_stride + st.iters - 1] = st.beta;
@@ -508,10 +534,9 @@ __global__ void k_m2l_ztr(const PcgArgs a, const V4<double>* v) {
     }
     if (last_block(a.counter, rhs)) {
         __shared__ double t[128];
-        for (int c = threadIdx.x; c < k; c += VT) {
-            double s = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(a.partial + ((int64_t)b * a.nrhs + rhs) * k + c);
-            t[c] = s;
+        for (int c = warp; c < k; c += nw) {
+            const double s = warp_gather(a.partial, gridDim.x, (int64_t)a.nrhs * k, (int64_t)rhs * k + c);
+            if (lane == 0) t[c] = s;
         }
         __syncthreads();
         const double* Einv = a.Einv + (int64_t)rhs * a.einv_stride;
@@ -559,8 +584,8 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
     if (finalize_beta < 0) return;
     block_partials<1>(acc, a.partial + ((int64_t)blockIdx.x * a.nrhs + rhs));
     if (last_block(a.counter, rhs)) {
+        const double rz = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
         if (threadIdx.x == 0) {
-            const double rz = gather_partial<1>(a.partial, gridDim.x, a.nrhs, rhs, 0);
             RhsState& st = a.st[rhs];
             st.beta = finalize_beta ? rz / st.rz : 0.0;
             st.rz = rz;
@@ -635,10 +660,9 @@ __global__ void k_multidot(const double* X, int64_t ldx, int m, const double* v,
         if (lane == 0) partial[(int64_t)blockIdx.x * m + r] = s;
     }
     if (last_block(counter, 0)) {
-        for (int r = threadIdx.x; r < m; r += VT) {
-            double s = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (int64_t)b * m + r);
-            h[r] = s;
+        for (int r = warp; r < m; r += nw) {
+            const double s = warp_gather(partial, gridDim.x, m, r);
+            if (lane == 0) h[r] = s;
         }
         if (threadIdx.x == 0) counter[0] = 0;
     }
@@ -728,8 +752,9 @@ __global__ void k_residual(const V4<double>* b, const V4<double>* q, V4<double>*
     }
     block_partials<1>(acc, partial + ((int64_t)blockIdx.x * nrhs + rhs));
     if (last_block(counter, rhs)) {
+        const double v = gather_partial<1>(partial, gridDim.x, nrhs, rhs, 0);
         if (threadIdx.x == 0) {
-            norms[rhs] = gather_partial<1>(partial, gridDim.x, nrhs, rhs, 0);
+            norms[rhs] = v;
             counter[rhs] = 0;
         }
     }

@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--filter", type=int, default=0, help="apply mode: 0 autotuned, 1 direct band, 2 FFT")
     ap.add_argument("--fft-len", type=int, default=0, help="apply mode: forced transform length (0: autotuned)")
     ap.add_argument("--apply-precision", default="f32", choices=["f32", "f64", "df"])
+    ap.add_argument("--half", type=int, default=1, choices=[0, 1],
+                    help="apply mode: allow whole blocks as half-length complex transforms")
     ap.add_argument("--n-rhs", type=int, default=64)
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -333,10 +335,11 @@ def main():
     whole = int(ctx.get_option("plan_whole"))
     lam = scan.half_bw
     n_work = 0
+    T = L // 2 if whole == 2 else L          # complex points per transform
     if L:
         blen = scan.n_t // scan.n_int
         segs_per_block = 1 if whole else -(-blen // (L - 2 * lam))
-        n_work = -(-(scan.n_blocks * segs_per_block) // 2)
+        n_work = scan.n_blocks if whole == 2 else -(-(scan.n_blocks * segs_per_block) // 2)
     xin = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
     yout = torch.empty_like(xin)
     for _ in range(3):
@@ -348,7 +351,9 @@ def main():
         ctx.apply_A(xin, out=yout)
     ax_ms = ctx.get_option("filter_ms") / reps
     ctx.set_option("time_filter", 0)
-    flops_per_launch = n_work * (2 * fft_flops_per_point(L) * L + 2 * L) if L else 0.0
+    # forward + inverse transform, plus the spectrum step (2 flop per point; 8 per point for the
+    # paired real-spectrum step of half-length transforms)
+    flops_per_launch = n_work * (2 * fft_flops_per_point(T) * T + (8 if whole == 2 else 2) * T) if L else 0.0
     bytes_per_launch = 8.0 * scan.n_samples
     peaks = {}
     try:
@@ -361,12 +366,14 @@ def main():
     achieved_tf = flops_per_launch / (ax_ms * 1e-3) / 1e12 if ax_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / alu_peak if alu_peak else None, "traffic": None,
-                "kernel": "k_filter_fft<%s> (gather + overlap-save FFT Toeplitz + scatter)"
-                          % ("float" if prec == M.MM_FP32_MIXED else "double"),
+                "kernel": "%s<%s> (gather + FFT Toeplitz + scatter)"
+                          % ("k_filter_half" if whole == 2 else "k_filter_fft",
+                             "float" if prec == M.MM_FP32_MIXED else "double"),
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec == M.MM_FP32_MIXED
                                 else "nominal GB300 FP64 rate"),
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": ax_ms, "fft_len": L,
-                "fft_radices": fft_passes(L) if L else None, "whole_blocks": bool(whole),
+                "fft_radices": fft_passes(T) if L else None, "whole_blocks": bool(whole),
+                "half_length_transform": whole == 2,
                 "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "of": "measured",
                              "frac": achieved_gbs / hbm_peak, "algorithmic_bytes": "8 B/sample (pix + psi)"},
                 "step_filter_ms": filter_ms / max(1, args.steps), "step_filter_launches": n_filter / max(1, args.steps)}
@@ -537,6 +544,7 @@ def run_apply(args, world, rank, local):
         ctx.set_option("fft_len", args.fft_len)
     if args.apply_precision == "df":
         ctx.set_option("apply_precision", 2)
+    ctx.set_option("half_transform", args.half)
     ctx.setup_scan(scan)
     x = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
@@ -558,7 +566,7 @@ def run_apply(args, world, rank, local):
         print(json.dumps({"mode": "apply", "config": args.config, "n_det": scan.n_det, "half_bw": scan.half_bw,
                           "samples": scan.n_samples, "precision": args.apply_precision,
                           "fft_len": int(ctx.get_option("plan_fft_len")),
-                          "whole_blocks": bool(ctx.get_option("plan_whole")), "filter_ms": ms,
+                          "plan_whole": int(ctx.get_option("plan_whole")), "filter_ms": ms,
                           "samples_per_s": scan.n_samples / (ms * 1e-3), "hbm_gbs_8B_per_sample": gbs,
                           "hbm_frac_of_measured": gbs / hbm}), flush=True)
     ctx.close()

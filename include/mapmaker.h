@@ -219,8 +219,11 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * b and the refinement residuals; "apply_precision": precision of
  * mm_apply_A (0 context, 1 float64, 2 double-float); "inner_tol": in
  * MM_FP32_MIXED, the smallest relative tolerance asked of a float32-operator
- * PCG run between float64-accurate refinements (default 2e-6).  Errors:
- * MM_ERR_ARG for an unknown name or value. */
+ * PCG run between float64-accurate refinements (default 2e-6);
+ * "half_transform": 1 (default) lets a whole block of N real samples run as
+ * one N/2-point complex transform per CTA (paired real-spectrum step), 0
+ * keeps two blocks per N-point transform.  Errors: MM_ERR_ARG for an
+ * unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
 /* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"
@@ -228,7 +231,9 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
  * (filter launches timed since the last read of "filter_ms", and their total
  * device time; reading "filter_ms" resets both), "kernel_launches" (kernels
  * launched by the library since load), "plan_fft_len", "plan_fft_log2",
- * "plan_whole" (the plan a single-RHS product uses), "harvested" (Lanczos
+ * "plan_whole" (the plan a single-RHS product uses: 0 overlap-save segments,
+ * 1 whole blocks two per transform, 2 whole blocks as half-length complex
+ * transforms), "harvested" (Lanczos
  * vectors kept by the last M_BD solve), "device_bytes" (device memory in use).
  * Errors: MM_ERR_ARG, MM_ERR_STATE. */
 mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value);

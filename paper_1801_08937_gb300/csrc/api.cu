@@ -47,13 +47,15 @@ struct DevBuf {
 struct FftTables {
     int L = 0;
     DevBuf tw, H;
+    DevBuf pairs;      // half-length real transforms: positions of k and M - k
 };
 
 struct Plan {
     FftTables ft;      // twiddles and band spectra for this plan's L
     int variant = 0;   // 1 direct, 2 fft
     int L = 0, logL = 0, V = 0;
-    int whole = 0;     // FFT: one transform per whole block (no overlap-save halo)
+    int whole = 0;     // FFT: 1 one transform per whole block (no overlap-save halo), two blocks
+                       // per CTA; 2 one block per CTA as an L/2-point complex transform
     FftPasses fp{};
     int f64 = 0;
     int nrhs = 0;
@@ -78,6 +80,7 @@ struct mm_ctx {
     int opt_filter = 0, opt_fft_log2 = 0, opt_fft_len = 0, opt_direct_tile = 1024, opt_check_every = 8, opt_graphs = 0;
     int opt_time_filter = 0;
     int opt_autotune = 1;
+    int opt_half = 1;              // allow whole blocks as half-length complex transforms
     int opt_harvest = 0;           // Lanczos vectors kept from an M_BD solve (0: off)
     int opt_apply_prec = 0;        // mm_apply_A precision: 0 context, 1 float64, 2 double-float
     double opt_inner_tol = 2e-6;   // floor of the float32-operator PCG tolerance between refinements
@@ -235,6 +238,18 @@ std::vector<FftCand> fft_candidates(const mm_ctx* c, int f64, int forced_log2, i
             if (L < 64) continue;
             if (forced_log2 > 0 && L != (1 << forced_log2)) continue;
             if (forced_len > 0 && L != forced_len) continue;
+            // a whole block as an L/2-point complex transform, one block per CTA
+            FftPasses fh;
+            if (L >= nb + lam && c->opt_half && L % 4 == 0 && L / 2 <= 65535 &&
+                fft_smem_bytes(L / 2, f64 != 0) <= smem_limit_bytes() && fft_passes(L / 2, &fh, f64 == 2 ? 8 : 16)) {
+                const size_t smh = fft_smem_bytes(L / 2, f64 != 0);
+                const double fit = std::floor(228.0 * 1024 / (double)(smh + 1024));
+                const double per_smh = std::max(1.0, std::min(fit, f64 ? 1.0 : 2.0));
+                const double ctash = c->n_blocks;
+                const double per_ctah = (double)(L / 2) * fh.npass * 44.0 + 2.0 * (double)c->n_samples / ctash * 45.0;
+                const double wavesh = std::ceil(ctash / (152.0 * per_smh));
+                out.push_back({L, 2, wavesh * per_ctah + 1e-3 * ((double)c->n_blocks * (L / 2) * fh.npass * 44.0)});
+            }
             const size_t sm = fft_smem_bytes(L, f64 != 0);
             if (sm > smem_limit_bytes()) continue;
             FftPasses fp;
@@ -348,6 +363,135 @@ mm_status build_fft_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fp, int 
     return MM_OK;
 }
 
+// Frequency index held at each position after the DIF passes of fp: with
+// position p = sum_i d_i (span_i / radix_i), the frequency is
+// d_0 + radix_0 (d_1 + radix_1 (d_2 + ...)) (mixed-radix digit reversal).
+std::vector<int> dif_frequency(const FftPasses& fp) {
+    std::vector<int> k(fp.L);
+    for (int p = 0; p < fp.L; ++p) {
+        int rem = p, mult = 1, f = 0;
+        for (int i = 0; i < fp.npass; ++i) {
+            const int sr = fp.span[i] / fp.radix[i];
+            const int d = rem / sr;
+            rem -= d * sr;
+            f += d * mult;
+            mult *= fp.radix[i];
+        }
+        k[p] = f;
+    }
+    return k;
+}
+
+// Tables of a whole-block plan run as an M = N/2 point complex transform:
+// twiddles of length M, the pair positions (k, M - k) and, per band, the
+// coefficients (alpha_k, alpha_{M-k}, beta_k) of the paired real-spectrum
+// filter, from the band's length-N spectrum, with 1/M folded in.
+mm_status build_half_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fpM, int N, int f64) {
+    const int M = fpM.L;
+    if (ft.L == M && ft.pairs.p) return MM_OK;
+    FftPasses fpN;
+    if (!fft_passes(N, &fpN, 16)) return fail(ctx, MM_ERR_ARG, "no transform plan for the block spectrum");
+    // length-N spectra of the bands (digit-reversed, scaled by 1/N) on the device
+    std::vector<double> twN(2 * (size_t)N);
+    for (int e = 0; e < N; ++e) {
+        const double ang = -2.0 * M_PI * (double)e / (double)N;
+        twN[2 * e] = std::cos(ang);
+        twN[2 * e + 1] = std::sin(ang);
+    }
+    std::vector<double> h((size_t)ctx->n_bands * N, 0.0);
+    for (int b = 0; b < ctx->n_bands; ++b) {
+        const double* c = &ctx->band[(size_t)b * (ctx->lam + 1)];
+        double* hb = &h[(size_t)b * N];
+        hb[0] = c[0];
+        for (int i = 1; i <= ctx->lam; ++i) {
+            hb[i] = c[i];
+            hb[N - i] = c[i];
+        }
+    }
+    std::vector<double> Hp(h.size());
+    {
+        DevBuf d_tw, d_h, d_H, d_work;
+        CK(d_tw.ensure(twN.size() * 8));
+        CK(d_h.ensure(h.size() * 8));
+        CK(d_H.ensure(h.size() * 8));
+        CK(d_work.ensure((size_t)ctx->n_bands * (N + (N >> 4)) * 16));
+        CK(cudaMemcpyAsync(d_tw.p, twN.data(), twN.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(d_h.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        launch_fft_spectrum(d_h.as<double>(), d_H.as<double>(), d_work.as<double2>(), d_tw.as<double2>(),
+                            ctx->n_bands, fpN, ctx->stream);
+        CKL();
+        CK(cudaMemcpyAsync(Hp.data(), d_H.p, Hp.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    const std::vector<int> kN = dif_frequency(fpN), kM = dif_frequency(fpM);
+    std::vector<int> posM(M);
+    for (int p = 0; p < M; ++p) posM[kM[p]] = p;
+    const int np = M / 2 + 1;
+    std::vector<uint32_t> pairs(np);
+    for (int k = 0; k < np; ++k) pairs[k] = (uint32_t)posM[k] | ((uint32_t)posM[(M - k) % M] << 16);
+    // coefficients in float64: H_k / M = 2 (H_k / N)
+    std::vector<double> coef((size_t)ctx->n_bands * np * 3);
+    std::vector<double> Hn(N);
+    for (int b = 0; b < ctx->n_bands; ++b) {
+        for (int p = 0; p < N; ++p) Hn[kN[p]] = 2.0 * Hp[(size_t)b * N + p];
+        for (int k = 0; k < np; ++k) {
+            const double h1 = Hn[k], h2 = Hn[M - k];
+            const double th = 2.0 * M_PI * (double)k / (double)N;
+            const double sn = std::sin(th), cs = std::cos(th);
+            double* o = &coef[((size_t)b * np + k) * 3];
+            o[0] = 0.5 * ((h1 + h2) + (h2 - h1) * sn);
+            o[1] = 0.5 * ((h1 + h2) - (h2 - h1) * sn);
+            o[2] = -0.5 * (h2 - h1) * cs;
+        }
+    }
+    std::vector<double> twM(2 * (size_t)M);
+    for (int e = 0; e < M; ++e) {
+        const double ang = -2.0 * M_PI * (double)e / (double)M;
+        twM[2 * e] = std::cos(ang);
+        twM[2 * e + 1] = std::sin(ang);
+    }
+    const size_t nc = (size_t)ctx->n_bands * np;
+    if (f64 == 1) {
+        std::vector<double> C(nc * 4, 0.0);
+        for (size_t i = 0; i < nc; ++i)
+            for (int j = 0; j < 3; ++j) C[4 * i + j] = coef[3 * i + j];
+        CK(ft.H.ensure(C.size() * 8));
+        CK(ft.tw.ensure(twM.size() * 8));
+        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.tw.p, twM.data(), twM.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else if (f64 == 2) {
+        auto split = [](double d, float* o) {
+            o[0] = (float)d;
+            o[1] = (float)(d - (double)o[0]);
+        };
+        std::vector<float> C(nc * 8, 0.0f), tw(2 * twM.size());
+        for (size_t i = 0; i < nc; ++i)
+            for (int j = 0; j < 3; ++j) split(coef[3 * i + j], &C[8 * i + 2 * j]);
+        for (size_t i = 0; i < twM.size(); ++i) split(twM[i], &tw[2 * i]);
+        CK(ft.H.ensure(C.size() * 4));
+        CK(ft.tw.ensure(tw.size() * 4));
+        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.tw.p, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::vector<float> C(nc * 4, 0.0f), tw(twM.size());
+        for (size_t i = 0; i < nc; ++i)
+            for (int j = 0; j < 3; ++j) C[4 * i + j] = (float)coef[3 * i + j];
+        for (size_t i = 0; i < twM.size(); ++i) tw[i] = (float)twM[i];
+        CK(ft.H.ensure(C.size() * 4));
+        CK(ft.tw.ensure(tw.size() * 4));
+        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ft.tw.p, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    CK(ft.pairs.ensure(pairs.size() * 4));
+    CK(cudaMemcpyAsync(ft.pairs.p, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ft.L = M;
+    return MM_OK;
+}
+
 // Segment list: for every block, chunk and right-hand side, pairs of segments
 // that share a band (and halo).
 mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, int variant, int L,
@@ -355,8 +499,8 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     FftPasses fp{};
     int logL = 0;
     if (variant == 2) {
-        fft_passes(L, &fp, f64 == 2 ? 8 : 16);
-        logL = ilog2(L);
+        fft_passes(whole == 2 ? L / 2 : L, &fp, f64 == 2 ? 8 : 16);
+        logL = ilog2(whole == 2 ? L / 2 : L);
     }
     for (auto& p : ctx->plans)
         if (p->variant == variant && p->L == L && p->V == V && p->whole == whole && p->f64 == f64 &&
@@ -365,8 +509,9 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
             return MM_OK;
         }
     std::vector<Seg> segs;
+    const bool single = (variant == 2 && whole == 2);   // one segment per CTA
     auto push = [&](const Seg& s) {
-        if (segs.size() % 2 == 1 && (segs.back().band != s.band || segs.back().shift != s.shift)) {
+        if (!single && segs.size() % 2 == 1 && (segs.back().band != s.band || segs.back().shift != s.shift)) {
             Seg e{};
             e.n_out = 0;
             e.band = segs.back().band;
@@ -396,7 +541,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
             }
         }
     }
-    if (segs.size() % 2 == 1) {
+    if (!single && segs.size() % 2 == 1) {
         Seg e{};
         e.band = segs.back().band;
         e.shift = segs.back().shift;
@@ -412,12 +557,13 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     p->f64 = f64;
     p->nrhs = nrhs;
     p->lens = lens;
-    p->n_work = (int)(segs.size() / 2);
+    p->n_work = (int)(single ? segs.size() : segs.size() / 2);
     CK(p->segs.ensure(std::max<size_t>(1, segs.size()) * sizeof(Seg)));
     if (!segs.empty())
         CK(cudaMemcpyAsync(p->segs.p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (variant == 2) TRY(build_fft_tables(ctx, p->ft, fp, f64));
+    if (variant == 2 && whole == 2) TRY(build_half_tables(ctx, p->ft, fp, L, f64));
+    else if (variant == 2) TRY(build_fft_tables(ctx, p->ft, fp, f64));
     if (f64 == 2 && !ctx->have_csdf) {
         CK(ctx->d_csdf.ensure((size_t)ctx->n_samples * 16));
         launch_weights_df(ctx->d_cs64.as<double2>(), ctx->d_csdf.as<float4>(), ctx->n_samples, ctx->stream);
@@ -553,7 +699,7 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
         // per-CTA work of a plan does not depend on how many right-hand sides share it
         TuneKey key{f64, ctx->lam, ctx->n_blocks, 1, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
         for (auto& kv : tune_cache())
-            if (kv.first == key) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
+            if (kv.first == key && (ctx->opt_half || kv.second.whole != 2)) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
                                                   kv.second.whole, kv.second.V, out);
         TuneVal best{};
         TRY(autotune_plan(ctx, f64, 1, {}, &best));
@@ -616,6 +762,11 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         FftTables& ft = plan->ft;
         a.H = ft.H.p;
         a.tw = ft.tw.p;
+        if (plan->whole == 2) {
+            a.half = 1;
+            a.L = plan->L / 2;
+            a.pairs = ft.pairs.as<uint32_t>();
+        }
         if (plan->f64 == 2) launch_filter_fft_df(a, from_tod, ctx->stream);
         else if (plan->f64 == 1) launch_filter_fft_f64(a, from_tod, ctx->stream);
         else launch_filter_fft_f32(a, from_tod, ctx->stream);
@@ -1825,6 +1976,8 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_graphs = v ? 1 : 0;
     } else if (n == "autotune") {
         ctx->opt_autotune = v ? 1 : 0;
+    } else if (n == "half_transform") {
+        ctx->opt_half = v ? 1 : 0;
     } else if (n == "inner_tol") {
         if (!(value > 0.0) || value > 1e-2) return fail(ctx, MM_ERR_ARG, "inner_tol must lie in (0, 1e-2]");
         ctx->opt_inner_tol = value;
@@ -1859,6 +2012,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "kernel_launches") *value = (double)launches_total();
     else if (n == "time_filter") *value = ctx->opt_time_filter;
     else if (n == "autotune") *value = ctx->opt_autotune;
+    else if (n == "half_transform") *value = ctx->opt_half;
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;
     else if (n == "apply_precision") *value = ctx->opt_apply_prec;

@@ -65,7 +65,7 @@ struct RhsState {
 
 // ---------------- filter (A x, b) ----------------
 struct FilterArgs {
-    const Seg* segs;       // [2 * n_work]
+    const Seg* segs;       // [2 * n_work] (pairs), or [n_work] for half-length real transforms
     int n_work;
     const int32_t* pix;
     const float* psi;
@@ -75,8 +75,11 @@ struct FilterArgs {
     int64_t n_samples;
     void* dst;             // accumulators [nrhs][n_pix] (V4<T>)
     int n_pix;
-    const void* H;         // FFT: [n_bands][L] real spectrum (digit-reversed, 1/L folded in)
+    const void* H;         // FFT: [n_bands][L] real spectrum (digit-reversed, 1/L folded in);
+                           // half: [n_bands][L/2 + 1] pair coefficients (alpha_k, alpha_{L-k}, beta_k)
     const void* tw;        // FFT: [L] twiddles exp(-2 pi i e / L)
+    const uint32_t* pairs; // half: [L/2 + 1] digit-reversed positions of k (low 16 bits) and L - k
+    int half;              // 1: one whole block per CTA as L = N/2 complex points
     const void* band;      // direct: [n_bands][lambda+1]
     int L, logL, lam, V;
     FftPasses fp;

@@ -294,6 +294,25 @@ __host__ __device__ constexpr CtPlan make_ct_plan(int L, int MAXR = 16) {
     return p;
 }
 
+// Padded index of point base + r Sr of a butterfly, as sidx(base) plus a
+// compile-time offset.  Exact when the butterfly's points keep their place
+// within 16-point groups: Sr a multiple of 16 (whole groups apart), S a
+// multiple of 16 with Sr dividing 16 (the points of one group stay in it),
+// or S dividing 16 (the whole butterfly inside one group).
+template <int S, int Sr>
+__host__ __device__ constexpr bool pad_const() {
+    return Sr % 16 == 0 || (S % 16 == 0 && 16 % Sr == 0) || 16 % S == 0;
+}
+template <int S, int Sr>
+__host__ __device__ constexpr int pad_offset(int r) {
+    return Sr % 16 == 0 ? r * (Sr + Sr / 16) : (S % 16 == 0 ? r * Sr + ((r * Sr) >> 4) : r * Sr);
+}
+template <int S, int Sr>
+__device__ __forceinline__ int pad_index(int b0, int base, int r) {
+    if constexpr (pad_const<S, Sr>()) return b0 + pad_offset<S, Sr>(r);
+    else return sidx(base + r * Sr);
+}
+
 template <typename T, int R, int S, int L, int NT, bool DIT>
 __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) {
     constexpr int Sr = S / R;
@@ -304,11 +323,12 @@ __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) 
         const int g = bf / Sr;
         const int j = bf - g * Sr;
         const int base = g * S + j;
+        const int b0 = sidx(base);
         C2<T> w1{T(1), T(0)};
         if (Sr > 1) w1 = ldtw(tw, j * tstep);
         C2<T> a[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = s[sidx(base + r * Sr)];
+        for (int r = 0; r < R; ++r) a[r] = s[pad_index<S, Sr>(b0, base, r)];
         if (!DIT) Dft<T, R>::run(a);
         if (Sr > 1) {
             C2<T> w[R];
@@ -318,7 +338,7 @@ __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) 
         }
         if (DIT) Dft<T, R>::run(a);
 #pragma unroll
-        for (int q = 0; q < R; ++q) s[sidx(base + q * Sr)] = a[q];
+        for (int q = 0; q < R; ++q) s[pad_index<S, Sr>(b0, base, q)] = a[q];
     }
 }
 
@@ -739,6 +759,226 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
     }
 }
 
+// ---------------- whole block as a half-length complex transform ----------------
+// One CTA per block.  The block's real samples y_0..y_{N-1} (zero beyond the
+// block, N >= n_b + lambda, so the circular product equals the band product)
+// ride as M = N/2 complex points z_m = y_{2m} + i y_{2m+1}.  With Z = DFT_M(z)
+// and H the length-N spectrum of the band (real and even), the filtered
+// sequence y' = W y has, for every k and its partner M - k (mod M),
+//   Z'_k = alpha_k Z_k + i beta_k conj(Z_{M-k}),
+//   alpha_k = ((H_k + H_{M-k}) + (H_{M-k} - H_k) sin theta_k) / 2,
+//   beta_k  = -(H_{M-k} - H_k) cos theta_k / 2,   theta_k = 2 pi k / N,
+// which follows from Y_k = (Z_k + conj Z_{M-k}) / 2 - i e^{-i theta_k}
+// (Z_k - conj Z_{M-k}) / 2 and its inverse.  The coefficient table holds,
+// per pair k = 0..M/2, (alpha_k, alpha_{M-k}, beta_k) with 1/M folded in;
+// the pair table holds the digit-reversed positions of k and M - k.  Half
+// the shared memory of a two-segment transform, so two CTAs share an SM and
+// one's gather and scatter overlap the other's butterflies.
+
+__device__ __forceinline__ void ld_coef(const void* C, int64_t e, float& aa, float& ab, float& be) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(C) + e);
+    aa = v.x;
+    ab = v.y;
+    be = v.z;
+}
+__device__ __forceinline__ void ld_coef(const void* C, int64_t e, double& aa, double& ab, double& be) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(C) + 2 * e);
+    const double2 v = __ldg(reinterpret_cast<const double2*>(C) + 2 * e + 1);
+    aa = u.x;
+    ab = u.y;
+    be = v.x;
+}
+__device__ __forceinline__ void ld_coef(const void* C, int64_t e, df& aa, df& ab, df& be) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(C) + 2 * e);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(C) + 2 * e + 1);
+    aa = df(u.x, u.y);
+    ab = df(u.z, u.w);
+    be = df(v.x, v.y);
+}
+
+// Four consecutive timeline values d_{t0..t0+3} of a segment (zero past n_out).
+__device__ __forceinline__ void load4_tod(const FilterArgs& a, const Seg& S, int i0, bool act, float (&y)[4]) {
+    const int64_t t0 = (int64_t)S.rhs * a.n_samples + S.out0 + i0;
+    const int count = S.n_out - i0;
+    if (act && a.tod_is_float && count >= 4 && (t0 & 3) == 0) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(a.src) + (t0 >> 2));
+        y[0] = v.x;
+        y[1] = v.y;
+        y[2] = v.z;
+        y[3] = v.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float v = 0.0f;
+            if (act && j < count)
+                v = a.tod_is_float ? __ldg(reinterpret_cast<const float*>(a.src) + t0 + j)
+                                   : (float)__ldg(reinterpret_cast<const double*>(a.src) + t0 + j);
+            y[j] = v;
+        }
+    }
+}
+
+// Loads in flight per thread in the float32 gather (groups of four samples)
+// and in the scatter (warp iterations of 128 samples).
+constexpr int HALF_GB = 2;
+constexpr int HALF_SU = 2;
+
+// float32 gather: each thread fills two complex points (four samples) per
+// group, GB groups in flight.
+template <bool FROM_TOD, int NT>
+__device__ __forceinline__ void half_gather_f32(const FilterArgs& a, const Seg& S, C2<float>* s, int M) {
+    constexpr int GB = HALF_GB;
+    const int ng = M >> 1;
+    const V4<float>* map = reinterpret_cast<const V4<float>*>(a.src) + (int64_t)S.rhs * a.n_pix;
+    for (int u0 = threadIdx.x; u0 < ng; u0 += NT * GB) {
+        int p[GB][4];
+        float ps[GB][4], y[GB][4];
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int u = u0 + g * NT;
+            const int i0 = 4 * u;
+            const bool act = u < ng && i0 < S.n_out;
+            if (FROM_TOD) load4_tod(a, S, i0, act, y[g]);
+            else load4(a, S.out0 + i0, act, S.n_out - i0, p[g], ps[g]);
+        }
+        if (!FROM_TOD) {
+            V4<float> m[GB][4];
+#pragma unroll
+            for (int g = 0; g < GB; ++g)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (p[g][j] >= 0) m[g][j] = ldmap<float>(map + p[g][j]);
+#pragma unroll
+            for (int g = 0; g < GB; ++g)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float v = 0.0f;
+                    if (p[g][j] >= 0) {
+                        float c, sn;
+                        weights_from(a, 0, ps[g][j], c, sn);
+                        v = m[g][j].x + c * m[g][j].y + sn * m[g][j].z;
+                    }
+                    y[g][j] = v;
+                }
+        }
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int u = u0 + g * NT;
+            if (u < ng) {
+                s[sidx(2 * u)] = C2<float>{y[g][0], y[g][1]};
+                s[sidx(2 * u + 1)] = C2<float>{y[g][2], y[g][3]};
+            }
+        }
+    }
+}
+
+template <typename T, bool FROM_TOD, int NT>
+__device__ __forceinline__ void half_gather_t(const FilterArgs& a, const Seg& S, C2<T>* s, int M) {
+    for (int m = threadIdx.x; m < M; m += NT) {
+        const int i = 2 * m;
+        const T y0 = i < S.n_out ? sample_value<T, FROM_TOD>(a, S.out0 + i, S.rhs) : T(0);
+        const T y1 = i + 1 < S.n_out ? sample_value<T, FROM_TOD>(a, S.out0 + i + 1, S.rhs) : T(0);
+        s[sidx(m)] = C2<T>{y0, y1};
+    }
+}
+
+// After the conjugate-domain inverse, point m holds conj(z'_m):
+// y'_{2m} = Re, y'_{2m+1} = -Im.
+template <int NT>
+__device__ __forceinline__ void half_scatter_f32(const FilterArgs& a, const Seg& S, const C2<float>* s, int M) {
+    constexpr int NW = NT / 32, SU = HALF_SU;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V4<float>* q = reinterpret_cast<V4<float>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
+    for (int base = warp * 128; base < S.n_out; base += NW * 128 * SU) {
+        int p[SU][4];
+        float ps[SU][4];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int i0 = base + u * NW * 128 + 4 * lane;
+            load4(a, S.out0 + i0, i0 < S.n_out, S.n_out - i0, p[u], ps[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int i0 = base + u * NW * 128 + 4 * lane;
+            const int m0 = min(i0 >> 1, M - 2);
+            const C2<float> e0 = s[sidx(m0)], e1 = s[sidx(m0 + 1)];
+            const float z[4] = {e0.x, -e0.y, e1.x, -e1.y};
+            float v0[4], v1[4], v2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float zz = 0.0f, c = 0.0f, sn = 0.0f;
+                if (p[u][j] >= 0) {
+                    zz = z[j];
+                    weights_from(a, 0, ps[u][j], c, sn);
+                }
+                v0[j] = zz;
+                v1[j] = zz * c;
+                v2[j] = zz * sn;
+            }
+            scatter4_vals(p[u], v0, v1, v2, q);
+        }
+    }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void half_scatter_t(const FilterArgs& a, const Seg& S, const C2<T>* s) {
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    using Acc = typename AccT<T>::type;
+    V4<Acc>* q = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
+    for (int base = warp * 32; base < S.n_out; base += NW * 32) {
+        const int i = base + lane;
+        int p = -1;
+        T c = T(0), sn = T(0), z = T(0);
+        if (i < S.n_out) {
+            const int64_t t = S.out0 + i;
+            p = __ldg(a.pix + t);
+            if (p >= 0) {
+                weights(a, t, c, sn);
+                const C2<T> e = s[sidx(i >> 1)];
+                z = (i & 1) ? -e.y : e.x;
+            }
+        }
+        scatter_warp<T>(p, c, sn, z, q);
+    }
+}
+
+template <typename T> struct HalfMinBlocks { static constexpr int value = 1; };
+template <> struct HalfMinBlocks<float> { static constexpr int value = 2; };
+
+template <typename T, bool FROM_TOD, int NT, int MCT>
+__global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(const FilterArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* s = reinterpret_cast<C2<T>*>(smraw);
+    const Seg S = a.segs[blockIdx.x];
+    if (!seg_active<T>(a, S)) return;
+    const int M = MCT > 0 ? MCT : a.L;
+    const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
+    if constexpr (std::is_same<T, float>::value) half_gather_f32<FROM_TOD, NT>(a, S, s, M);
+    else half_gather_t<T, FROM_TOD, NT>(a, S, s, M);
+    __syncthreads();
+    if constexpr (MCT > 0) ct_dif<T, MCT, NT, MaxRadix<T>::value, 0>(s, tw);
+    else fft_dif<T>(s, tw, a.fp);
+    // paired real-spectrum filter, written conjugated for the inverse
+    const int np = M / 2 + 1;
+    const int64_t cb = (int64_t)S.band * np;
+    for (int e = threadIdx.x; e < np; e += NT) {
+        const uint32_t pr = __ldg(a.pairs + e);
+        const int pa = (int)(pr & 0xffffu), pb = (int)(pr >> 16);
+        T aa, ab, be;
+        ld_coef(a.H, cb + e, aa, ab, be);
+        const C2<T> A = s[sidx(pa)], B = s[sidx(pb)];
+        s[sidx(pa)] = C2<T>{aa * A.x + be * B.y, -(aa * A.y + be * B.x)};
+        s[sidx(pb)] = C2<T>{ab * B.x + be * A.y, -(ab * B.y + be * A.x)};
+    }
+    __syncthreads();
+    if constexpr (MCT > 0)
+        ct_dit<T, MCT, NT, MaxRadix<T>::value, make_ct_plan(MCT > 0 ? MCT : 64, MaxRadix<T>::value).np - 1>(s, tw);
+    else fft_dit_conj<T>(s, tw, a.fp);
+    if constexpr (std::is_same<T, float>::value) half_scatter_f32<NT>(a, S, s, M);
+    else half_scatter_t<T, NT>(a, S, s);
+}
+
 // ---------------- direct band variant, float32, four samples per thread ----------------
 // For narrow bands the product is gather + scatter bound: each thread owns
 // four consecutive outputs in both phases, so the pixel indices and pointing
@@ -949,6 +1189,46 @@ inline void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
     }
     launch_fft_nt<T, FROM_TOD, 256, 0>(a, sm, s);
 }
+template <typename T, bool FROM_TOD, int NT, int MCT>
+inline void launch_half_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaFuncSetAttribute(k_filter_half<T, FROM_TOD, NT, MCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_filter_half<T, FROM_TOD, NT, MCT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configured = sm;
+    }
+    k_filter_half<T, FROM_TOD, NT, MCT><<<a.n_work, NT, sm, s>>>(a);
+    count_launches(1);
+}
+
+// Half-length real transforms (a.L = M complex points): float32 with two
+// CTAs per SM (384 threads for the large transforms, 256 otherwise);
+// double-float with 512 threads; float64 with 256.  Compile-time transforms
+// for the common block shapes.
+template <typename T, bool FROM_TOD>
+inline void launch_half_t(const FilterArgs& a, cudaStream_t s) {
+    if (a.n_work <= 0) return;
+    const size_t sm = fft_smem_bytes(a.L, sizeof(T) == 8);
+    if constexpr (std::is_same<T, float>::value) {
+        if constexpr (!FROM_TOD) {
+            switch (a.L) {
+                case 9216: return launch_half_nt<T, FROM_TOD, 384, 9216>(a, sm, s);
+                case 8192: return launch_half_nt<T, FROM_TOD, 384, 8192>(a, sm, s);
+                case 4608: return launch_half_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
+                case 2304: return launch_half_nt<T, FROM_TOD, 256, 2304>(a, sm, s);
+                default: break;
+            }
+        }
+        return launch_half_nt<T, FROM_TOD, 256, 0>(a, sm, s);
+    } else if constexpr (std::is_same<T, df>::value) {
+        if (a.L == 9216) return launch_half_nt<T, FROM_TOD, 512, 9216>(a, sm, s);
+        return launch_half_nt<T, FROM_TOD, 512, 0>(a, sm, s);
+    } else {
+        if (a.L == 9216) return launch_half_nt<T, FROM_TOD, 256, 9216>(a, sm, s);
+        return launch_half_nt<T, FROM_TOD, 256, 0>(a, sm, s);
+    }
+}
+
 template <typename T, bool FROM_TOD>
 inline void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
     if (a.n_work <= 0) return;

@@ -22,9 +22,10 @@ TOL64 = 1e-11
 TOL32 = 1e-5
 
 
-def ctx_for(scan, prec=MM.MM_FP64, filt=0, fft_log2=0, fft_len=0):
+def ctx_for(scan, prec=MM.MM_FP64, filt=0, fft_log2=0, fft_len=0, half=1):
     c = MM.Context(0, None, prec)
     c.set_option("filter", filt)
+    c.set_option("half_transform", half)
     if fft_log2:
         c.set_option("fft_log2", fft_log2)
     if fft_len:
@@ -75,15 +76,60 @@ CT_LENGTHS = [2048, 4096, 4608, 8192, 9216, 12288, 16384, 18432]
 @pytest.mark.parametrize("L", CT_LENGTHS)
 @pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
 def test_apply_A_compile_time_lengths(L, prec):
-    """Every compile-time transform, as whole blocks (short blocks) and as segments (long blocks)."""
+    """Every compile-time transform of the two-segment kernel, as whole blocks (short blocks) and
+    as segments (long blocks)."""
     if prec == MM.MM_FP64 and L > 12288:
         pytest.skip("float64 transform of this length exceeds shared memory")
     for cfg in (SMALL, dict(nx=8, ny=8, n_det=2, n_t=40960, n_int=2, half_bw=200, f_knee=1.0)):
         scan = synth.make_scan(seed=19, flag_frac=0.01, **cfg)
         prob = O.Problem.from_scan(scan)
-        c = ctx_for(scan, prec, 2, fft_len=L)
+        c = ctx_for(scan, prec, 2, fft_len=L, half=0)
         x = np.random.default_rng(19).standard_normal((scan.n_pix, 3))
         assert rel(c.apply_A(x)[0], O.apply_A(prob, x)) < (TOL64 if prec == MM.MM_FP64 else TOL32)
+
+
+HALF_LENGTHS = [1152, 2048, 4608, 6144, 9216, 16384, 18432]
+
+
+@pytest.mark.parametrize("L", HALF_LENGTHS)
+@pytest.mark.parametrize("prec", ["f64", "f32", "df"])
+def test_apply_A_half_length_transform(L, prec):
+    """Whole blocks as L/2-point complex transforms with the paired real-spectrum step, against the
+    oracle and the two-segment kernel: ragged blocks with unaligned starts and lengths, flagged
+    samples, compile-time (L/2 = 2304, 4608, 8192, 9216) and run-time plans."""
+    n_t = L - 64 - 7                     # every block fits one transform with its band
+    scan = ragged(synth.make_scan(seed=31, flag_frac=0.01, nx=8, ny=8, n_det=3, n_t=n_t, n_int=1,
+                                  half_bw=64, f_knee=1.0), seed=31)
+    prob = O.Problem.from_scan(scan)
+    x = np.random.default_rng(31).standard_normal((2, scan.n_pix, 3))
+    tol = TOL32 if prec == "f32" else TOL64
+    halves = (1,) if (prec != "f32" and L > 12288) else (1, 0)   # two segments of 16-byte points do not fit
+    for half in halves:
+        c = ctx_for(scan, MM.MM_FP64 if prec == "f64" else MM.MM_FP32_MIXED, 2, fft_len=L, half=half)
+        if prec == "df":
+            c.set_option("apply_precision", 2)
+        y = c.apply_A(x)
+        if prec != "df":
+            assert c.get_option("plan_whole") == (2 if half else 1)
+        for r in range(2):
+            assert rel(y[r], O.apply_A(prob, x[r])) < tol
+        c.close()
+
+
+@pytest.mark.parametrize("L", [4608, 18432])
+@pytest.mark.parametrize("products", [1, 2])
+def test_rhs_half_length_transform(L, products):
+    """b = P^T W d through the half-length transform (float64 and double-float), ragged blocks."""
+    n_t = L - 64 - 7
+    scan = ragged(synth.make_scan(seed=33, flag_frac=0.01, nx=8, ny=8, n_det=3, n_t=n_t, n_int=1,
+                                  half_bw=64, f_knee=1.0), seed=33)
+    d = synth.make_tod(scan, synth.make_sky(scan.n_pix, 33), synth.make_noise(scan, 33))
+    prob = O.Problem.from_scan(scan)
+    c = ctx_for(scan, MM.MM_FP32_MIXED, 2, fft_len=L)
+    c.set_option("fp64_products", products)
+    tod = d.astype(c.tod_dtype)
+    assert rel(c.rhs(tod)[0], O.rhs(prob, tod.astype(np.float64))) < TOL64
+    c.close()
 
 
 @pytest.mark.parametrize("tile", [1024, 2048])

@@ -427,18 +427,28 @@ mm_status build_half_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fpM, in
     std::vector<int> posM(M);
     for (int p = 0; p < M; ++p) posM[kM[p]] = p;
     const int np = M / 2 + 1;
+    // pairs in the order of their first position: neighbouring threads then
+    // touch neighbouring points (the frequency order would stride by M/r_0
+    // and put a warp's accesses on one bank)
+    std::vector<int> order(np);
+    for (int k = 0; k < np; ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return posM[x] < posM[y]; });
     std::vector<uint32_t> pairs(np);
-    for (int k = 0; k < np; ++k) pairs[k] = (uint32_t)posM[k] | ((uint32_t)posM[(M - k) % M] << 16);
+    for (int e = 0; e < np; ++e) {
+        const int k = order[e];
+        pairs[e] = (uint32_t)posM[k] | ((uint32_t)posM[(M - k) % M] << 16);
+    }
     // coefficients in float64: H_k / M = 2 (H_k / N)
     std::vector<double> coef((size_t)ctx->n_bands * np * 3);
     std::vector<double> Hn(N);
     for (int b = 0; b < ctx->n_bands; ++b) {
         for (int p = 0; p < N; ++p) Hn[kN[p]] = 2.0 * Hp[(size_t)b * N + p];
-        for (int k = 0; k < np; ++k) {
+        for (int e = 0; e < np; ++e) {
+            const int k = order[e];
             const double h1 = Hn[k], h2 = Hn[M - k];
             const double th = 2.0 * M_PI * (double)k / (double)N;
             const double sn = std::sin(th), cs = std::cos(th);
-            double* o = &coef[((size_t)b * np + k) * 3];
+            double* o = &coef[((size_t)b * np + e) * 3];
             o[0] = 0.5 * ((h1 + h2) + (h2 - h1) * sn);
             o[1] = 0.5 * ((h1 + h2) - (h2 - h1) * sn);
             o[2] = -0.5 * (h2 - h1) * cs;

@@ -1,9 +1,9 @@
 // Double-float arithmetic: a value is an unevaluated sum hi + lo of two
-// float32 numbers (|lo| <= ulp(hi) / 2), giving about 44 bits of precision
+// float32 numbers (|lo| of the order of ulp(hi)), giving about 44 bits of precision
 // from float32 units.  Addition uses the error-free two-sum of Knuth and
 // Moller; multiplication uses the error-free product through a fused
-// multiply-add (Dekker's product with FMA).  Both renormalise with the
-// fast two-sum of Dekker.  GB300 issues float32 at 64 times its float64
+// multiply-add (Dekker's product with FMA).  Sums renormalise with the
+// fast two-sum of Dekker; products leave that to the next sum.  GB300 issues float32 at 64 times its float64
 // rate, so float64-accurate products run several times faster this way.
 #pragma once
 #include <cuda_runtime.h>
@@ -38,12 +38,14 @@ __device__ __forceinline__ df operator+(df a, df b) {
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+// The product is returned as (p, e) without renormalising: a product cannot
+// cancel, so |e| stays within a few ulp of p, and the next sum renormalises.
 __device__ __forceinline__ df operator*(df a, df b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
+    return df(p, e);
 }
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 __device__ __forceinline__ df& operator-=(df& a, df b) { return a = a - b; }

@@ -770,8 +770,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 256) ? 3 : 1) k_f
 //   beta_k  = -(H_{M-k} - H_k) cos theta_k / 2,   theta_k = 2 pi k / N,
 // which follows from Y_k = (Z_k + conj Z_{M-k}) / 2 - i e^{-i theta_k}
 // (Z_k - conj Z_{M-k}) / 2 and its inverse.  The coefficient table holds,
-// per pair k = 0..M/2, (alpha_k, alpha_{M-k}, beta_k) with 1/M folded in;
-// the pair table holds the digit-reversed positions of k and M - k.  Half
+// per pair (k, M - k), k = 0..M/2, (alpha_k, alpha_{M-k}, beta_k) with 1/M
+// folded in; the pair table holds the digit-reversed positions of k and
+// M - k; both list the pairs in the order of the position of k.  Half
 // the shared memory of a two-segment transform, so two CTAs share an SM and
 // one's gather and scatter overlap the other's butterflies.
 
@@ -959,17 +960,31 @@ __global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(con
     __syncthreads();
     if constexpr (MCT > 0) ct_dif<T, MCT, NT, MaxRadix<T>::value, 0>(s, tw);
     else fft_dif<T>(s, tw, a.fp);
-    // paired real-spectrum filter, written conjugated for the inverse
+    // paired real-spectrum filter, written conjugated for the inverse; the
+    // table loads of PU pairs are issued together
+    constexpr int PU = sizeof(T) == 4 ? 4 : 2;
     const int np = M / 2 + 1;
     const int64_t cb = (int64_t)S.band * np;
-    for (int e = threadIdx.x; e < np; e += NT) {
-        const uint32_t pr = __ldg(a.pairs + e);
-        const int pa = (int)(pr & 0xffffu), pb = (int)(pr >> 16);
-        T aa, ab, be;
-        ld_coef(a.H, cb + e, aa, ab, be);
-        const C2<T> A = s[sidx(pa)], B = s[sidx(pb)];
-        s[sidx(pa)] = C2<T>{aa * A.x + be * B.y, -(aa * A.y + be * B.x)};
-        s[sidx(pb)] = C2<T>{ab * B.x + be * A.y, -(ab * B.y + be * A.x)};
+    for (int e0 = threadIdx.x; e0 < np; e0 += NT * PU) {
+        uint32_t pr[PU];
+        T aa[PU], ab[PU], be[PU];
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+            const int e = e0 + u * NT;
+            if (e < np) {
+                pr[u] = __ldg(a.pairs + e);
+                ld_coef(a.H, cb + e, aa[u], ab[u], be[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+            if (e0 + u * NT < np) {
+                const int pa = (int)(pr[u] & 0xffffu), pb = (int)(pr[u] >> 16);
+                const C2<T> A = s[sidx(pa)], B = s[sidx(pb)];
+                s[sidx(pa)] = C2<T>{aa[u] * A.x + be[u] * B.y, -(aa[u] * A.y + be[u] * B.x)};
+                s[sidx(pb)] = C2<T>{ab[u] * B.x + be[u] * A.y, -(ab[u] * B.y + be[u] * A.x)};
+            }
+        }
     }
     __syncthreads();
     if constexpr (MCT > 0)

@@ -16,6 +16,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "common.cuh"
@@ -615,8 +617,15 @@ __device__ __forceinline__ void scatter4_vals(const int (&p)[4], const float (&v
 __device__ __forceinline__ void load4(const FilterArgs& a, int64_t t0, bool act, int count, int (&p)[4],
                                       float (&ps)[4]) {
     if (act && count >= 4 && (t0 & 3) == 0) {
-        const int4 pv = __ldg(reinterpret_cast<const int4*>(a.pix + t0));
-        const float4 fv = __ldg(reinterpret_cast<const float4*>(a.psi + t0));
+        // streamed past L1 (no allocation), so the map entries and tables stay cached there
+        int4 pv;
+        float4 fv;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(pv.x), "=r"(pv.y), "=r"(pv.z), "=r"(pv.w)
+                     : "l"(a.pix + t0));
+        asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(fv.x), "=f"(fv.y), "=f"(fv.z), "=f"(fv.w)
+                     : "l"(a.psi + t0));
         p[0] = pv.x; p[1] = pv.y; p[2] = pv.z; p[3] = pv.w;
         ps[0] = fv.x; ps[1] = fv.y; ps[2] = fv.z; ps[3] = fv.w;
     } else {
@@ -821,34 +830,61 @@ __device__ __forceinline__ void load4_tod(const FilterArgs& a, const Seg& S, int
 
 // Loads in flight per thread in the float32 gather (groups of four samples)
 // and in the scatter (warp iterations of 128 samples).
-constexpr int HALF_GB = 2;
-constexpr int HALF_SU = 2;
+constexpr int HALF_GB = 1;
+constexpr int HALF_SU = 1;
 
 // float32 gather: each thread fills two complex points (four samples) per
-// group, GB groups in flight.
+// group, GB groups per iteration.  The pointing of the next iteration is
+// requested before the map entries of the current one, so its DRAM latency
+// overlaps the L2 latency and arithmetic of this iteration.
 template <bool FROM_TOD, int NT>
 __device__ __forceinline__ void half_gather_f32(const FilterArgs& a, const Seg& S, C2<float>* s, int M) {
     constexpr int GB = HALF_GB;
     const int ng = M >> 1;
-    const V4<float>* map = reinterpret_cast<const V4<float>*>(a.src) + (int64_t)S.rhs * a.n_pix;
-    for (int u0 = threadIdx.x; u0 < ng; u0 += NT * GB) {
-        int p[GB][4];
-        float ps[GB][4], y[GB][4];
+    auto store = [&](int u0, const float (&y)[GB][4]) {
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             const int u = u0 + g * NT;
-            const int i0 = 4 * u;
-            const bool act = u < ng && i0 < S.n_out;
-            if (FROM_TOD) load4_tod(a, S, i0, act, y[g]);
-            else load4(a, S.out0 + i0, act, S.n_out - i0, p[g], ps[g]);
+            if (u < ng) {
+                s[sidx(2 * u)] = C2<float>{y[g][0], y[g][1]};
+                s[sidx(2 * u + 1)] = C2<float>{y[g][2], y[g][3]};
+            }
         }
-        if (!FROM_TOD) {
+    };
+    if constexpr (FROM_TOD) {
+        for (int u0 = threadIdx.x; u0 < ng; u0 += NT * GB) {
+            float y[GB][4];
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+                const int u = u0 + g * NT;
+                load4_tod(a, S, 4 * u, u < ng && 4 * u < S.n_out, y[g]);
+            }
+            store(u0, y);
+        }
+    } else {
+        const V4<float>* map = reinterpret_cast<const V4<float>*>(a.src) + (int64_t)S.rhs * a.n_pix;
+        auto pointing = [&](int u0, int (&p)[GB][4], float (&ps)[GB][4]) {
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+                const int u = u0 + g * NT;
+                const int i0 = 4 * u;
+                load4(a, S.out0 + i0, u < ng && i0 < S.n_out, S.n_out - i0, p[g], ps[g]);
+            }
+        };
+        int p[GB][4];
+        float ps[GB][4];
+        pointing(threadIdx.x, p, ps);
+        for (int u0 = threadIdx.x; u0 < ng; u0 += NT * GB) {
+            int pn[GB][4];
+            float psn[GB][4];
+            pointing(u0 + NT * GB, pn, psn);
             V4<float> m[GB][4];
 #pragma unroll
             for (int g = 0; g < GB; ++g)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (p[g][j] >= 0) m[g][j] = ldmap<float>(map + p[g][j]);
+            float y[GB][4];
 #pragma unroll
             for (int g = 0; g < GB; ++g)
 #pragma unroll
@@ -861,14 +897,14 @@ __device__ __forceinline__ void half_gather_f32(const FilterArgs& a, const Seg& 
                     }
                     y[g][j] = v;
                 }
-        }
+            store(u0, y);
 #pragma unroll
-        for (int g = 0; g < GB; ++g) {
-            const int u = u0 + g * NT;
-            if (u < ng) {
-                s[sidx(2 * u)] = C2<float>{y[g][0], y[g][1]};
-                s[sidx(2 * u + 1)] = C2<float>{y[g][2], y[g][3]};
-            }
+            for (int g = 0; g < GB; ++g)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    p[g][j] = pn[g][j];
+                    ps[g][j] = psn[g][j];
+                }
         }
     }
 }
@@ -890,14 +926,21 @@ __device__ __forceinline__ void half_scatter_f32(const FilterArgs& a, const Seg&
     constexpr int NW = NT / 32, SU = HALF_SU;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V4<float>* q = reinterpret_cast<V4<float>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
-    for (int base = warp * 128; base < S.n_out; base += NW * 128 * SU) {
-        int p[SU][4];
-        float ps[SU][4];
+    // pointing of the next iteration requested before this one is reduced
+    auto pointing = [&](int base, int (&p)[SU][4], float (&ps)[SU][4]) {
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
             const int i0 = base + u * NW * 128 + 4 * lane;
             load4(a, S.out0 + i0, i0 < S.n_out, S.n_out - i0, p[u], ps[u]);
         }
+    };
+    int p[SU][4];
+    float ps[SU][4];
+    pointing(warp * 128, p, ps);
+    for (int base = warp * 128; base < S.n_out; base += NW * 128 * SU) {
+        int pn[SU][4];
+        float psn[SU][4];
+        pointing(base + NW * 128 * SU, pn, psn);
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
             const int i0 = base + u * NW * 128 + 4 * lane;
@@ -918,6 +961,13 @@ __device__ __forceinline__ void half_scatter_f32(const FilterArgs& a, const Seg&
             }
             scatter4_vals(p[u], v0, v1, v2, q);
         }
+#pragma unroll
+        for (int u = 0; u < SU; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                p[u][j] = pn[u][j];
+                ps[u][j] = psn[u][j];
+            }
     }
 }
 
@@ -1150,12 +1200,32 @@ __global__ void __launch_bounds__(DIRECT_NT) k_filter_direct(const FilterArgs a)
 }
 
 
+// Dynamic shared memory of a filter kernel, and a carveout (percent of the
+// 228 KB per SM) just large enough for the CTAs that registers, threads and
+// shared memory let reside together (1 KB reserved per CTA); the rest of the
+// 256 KB stays L1 for the map entries, twiddles and tables.
+template <typename K>
+inline void configure_smem(K kern, size_t sm, int nt) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kern);
+    const int warps = (nt + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int ctas = (int)((228u * 1024u) / (sm + 1024));
+    ctas = std::min(ctas, 2048 / nt);
+    if (regs_warp > 0) ctas = std::min(ctas, 65536 / (regs_warp * warps));
+    ctas = std::max(ctas, 1);
+    const double need = (double)ctas * (double)(sm + 1024);
+    int pct = (int)std::ceil(100.0 * need / (228.0 * 1024.0));
+    pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 template <typename T, bool FROM_TOD, int NT, int LCT>
 inline void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
     static size_t configured = 0;
     if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_filter_fft<T, FROM_TOD, NT, LCT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configure_smem(k_filter_fft<T, FROM_TOD, NT, LCT>, sm, NT);
         configured = sm;
     }
     k_filter_fft<T, FROM_TOD, NT, LCT><<<a.n_work, NT, sm, s>>>(a);
@@ -1208,8 +1278,7 @@ template <typename T, bool FROM_TOD, int NT, int MCT>
 inline void launch_half_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
     static size_t configured = 0;
     if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_half<T, FROM_TOD, NT, MCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_filter_half<T, FROM_TOD, NT, MCT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configure_smem(k_filter_half<T, FROM_TOD, NT, MCT>, sm, NT);
         configured = sm;
     }
     k_filter_half<T, FROM_TOD, NT, MCT><<<a.n_work, NT, sm, s>>>(a);
@@ -1217,7 +1286,7 @@ inline void launch_half_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
 }
 
 // Half-length real transforms (a.L = M complex points): float32 with two
-// CTAs per SM (384 threads for the large transforms, 256 otherwise);
+// CTAs per SM (512 threads for the large transforms, 256 otherwise);
 // double-float with 512 threads; float64 with 256.  Compile-time transforms
 // for the common block shapes.
 template <typename T, bool FROM_TOD>
@@ -1227,8 +1296,8 @@ inline void launch_half_t(const FilterArgs& a, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) {
         if constexpr (!FROM_TOD) {
             switch (a.L) {
-                case 9216: return launch_half_nt<T, FROM_TOD, 384, 9216>(a, sm, s);
-                case 8192: return launch_half_nt<T, FROM_TOD, 384, 8192>(a, sm, s);
+                case 9216: return launch_half_nt<T, FROM_TOD, 512, 9216>(a, sm, s);
+                case 8192: return launch_half_nt<T, FROM_TOD, 512, 8192>(a, sm, s);
                 case 4608: return launch_half_nt<T, FROM_TOD, 256, 4608>(a, sm, s);
                 case 2304: return launch_half_nt<T, FROM_TOD, 256, 2304>(a, sm, s);
                 default: break;

@@ -48,6 +48,8 @@ struct FftTables {
     int L = 0;
     DevBuf tw, H;
     DevBuf pairs;      // half-length real transforms: positions of k and M - k
+    DevBuf items, Hi;  // the same coefficients by butterfly pair of the last pass (fused spectrum step)
+    DevBuf twp;        // per-pass twiddle powers W_S^(j q) of the compile-time transforms
 };
 
 struct Plan {
@@ -438,21 +440,54 @@ mm_status build_half_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fpM, in
         const int k = order[e];
         pairs[e] = (uint32_t)posM[k] | ((uint32_t)posM[(M - k) % M] << 16);
     }
+    // The last pass of radix R works on butterflies c of R consecutive
+    // positions; butterfly c holds the frequencies kc + (M/R) q and its partner
+    // c' (frequency digits M/R - kc) holds their mirror images M - k, at output
+    // R - 1 - q (kc = 0 and kc = M/(2R) pair with themselves).  One item per
+    // pair {c, c'}, kc = 0 .. M/(2R).
+    const int R = fpM.radix[fpM.npass - 1];
+    const int NB = M / R;
+    const bool fused = fpM.span[fpM.npass - 1] == R && NB % 2 == 0 && 16 % R == 0;
+    const int ni = fused ? NB / 2 + 1 : 0;
+    std::vector<uint32_t> items(std::max(ni, 1), 0u);
+    std::vector<int> item_kc;
+    if (fused) {
+        std::vector<int> bfly(NB, -1);
+        for (int c = 0; c < NB; ++c) {
+            const int kc = kM[c * R];
+            for (int q = 0; q < R; ++q)
+                if (kM[c * R + q] != kc + NB * q) return fail(ctx, MM_ERR_STATE, "unexpected digit order of the last pass");
+            bfly[kc] = c;
+        }
+        // items in the order of their first butterfly's position: neighbouring
+        // threads then touch neighbouring points (2-way bank conflicts at most),
+        // where the frequency order would put a warp on one bank; bit 31 marks
+        // the kc = 0 item
+        std::vector<int> kcs(ni);
+        for (int i = 0; i < ni; ++i) kcs[i] = i;
+        std::sort(kcs.begin(), kcs.end(), [&](int x, int y) { return bfly[x] < bfly[y]; });
+        for (int i = 0; i < ni; ++i) {
+            const int kc = kcs[i];
+            items[i] = (uint32_t)bfly[kc] | ((uint32_t)bfly[(NB - kc) % NB] << 16) | (kc == 0 ? 0x80000000u : 0u);
+        }
+        item_kc.swap(kcs);
+    }
     // coefficients in float64: H_k / M = 2 (H_k / N)
-    std::vector<double> coef((size_t)ctx->n_bands * np * 3);
+    std::vector<double> coef((size_t)ctx->n_bands * np * 3), coefi((size_t)ctx->n_bands * std::max(ni, 1) * R * 3);
     std::vector<double> Hn(N);
+    auto pair_coef = [&](int k, double* o) {
+        const double h1 = Hn[k], h2 = Hn[M - k];
+        const double th = 2.0 * M_PI * (double)k / (double)N;
+        const double sn = std::sin(th), cs = std::cos(th);
+        o[0] = 0.5 * ((h1 + h2) + (h2 - h1) * sn);
+        o[1] = 0.5 * ((h1 + h2) - (h2 - h1) * sn);
+        o[2] = -0.5 * (h2 - h1) * cs;
+    };
     for (int b = 0; b < ctx->n_bands; ++b) {
         for (int p = 0; p < N; ++p) Hn[kN[p]] = 2.0 * Hp[(size_t)b * N + p];
-        for (int e = 0; e < np; ++e) {
-            const int k = order[e];
-            const double h1 = Hn[k], h2 = Hn[M - k];
-            const double th = 2.0 * M_PI * (double)k / (double)N;
-            const double sn = std::sin(th), cs = std::cos(th);
-            double* o = &coef[((size_t)b * np + e) * 3];
-            o[0] = 0.5 * ((h1 + h2) + (h2 - h1) * sn);
-            o[1] = 0.5 * ((h1 + h2) - (h2 - h1) * sn);
-            o[2] = -0.5 * (h2 - h1) * cs;
-        }
+        for (int e = 0; e < np; ++e) pair_coef(order[e], &coef[((size_t)b * np + e) * 3]);
+        for (int i = 0; i < ni; ++i)
+            for (int q = 0; q < R; ++q) pair_coef(item_kc[i] + NB * q, &coefi[(((size_t)b * ni + i) * R + q) * 3]);
     }
     std::vector<double> twM(2 * (size_t)M);
     for (int e = 0; e < M; ++e) {
@@ -460,40 +495,95 @@ mm_status build_half_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fpM, in
         twM[2 * e] = std::cos(ang);
         twM[2 * e + 1] = std::sin(ang);
     }
-    const size_t nc = (size_t)ctx->n_bands * np;
+    // device layouts per element type: float64 (a, b, c, 0) as two double2;
+    // double-float (hi, lo) pairs as two float4; float32 (a, b, c, 0) as float4
+    auto upload = [&](DevBuf& dst, const std::vector<double>& src) -> cudaError_t {
+        const size_t n = src.size() / 3;
+        if (f64 == 1) {
+            std::vector<double> C(n * 4, 0.0);
+            for (size_t i = 0; i < n; ++i)
+                for (int j = 0; j < 3; ++j) C[4 * i + j] = src[3 * i + j];
+            cudaError_t e = dst.ensure(C.size() * 8);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            return e;
+        } else if (f64 == 2) {
+            std::vector<float> C(n * 8, 0.0f);
+            for (size_t i = 0; i < n; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double d = src[3 * i + j];
+                    C[8 * i + 2 * j] = (float)d;
+                    C[8 * i + 2 * j + 1] = (float)(d - (double)(float)d);
+                }
+            cudaError_t e = dst.ensure(C.size() * 4);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            return e;
+        }
+        std::vector<float> C(n * 4, 0.0f);
+        for (size_t i = 0; i < n; ++i)
+            for (int j = 0; j < 3; ++j) C[4 * i + j] = (float)src[3 * i + j];
+        cudaError_t e = dst.ensure(C.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        return e;
+    };
+    CK(upload(ft.H, coef));
+    if (fused) CK(upload(ft.Hi, coefi));
     if (f64 == 1) {
-        std::vector<double> C(nc * 4, 0.0);
-        for (size_t i = 0; i < nc; ++i)
-            for (int j = 0; j < 3; ++j) C[4 * i + j] = coef[3 * i + j];
-        CK(ft.H.ensure(C.size() * 8));
         CK(ft.tw.ensure(twM.size() * 8));
-        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ft.tw.p, twM.data(), twM.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
     } else if (f64 == 2) {
-        auto split = [](double d, float* o) {
-            o[0] = (float)d;
-            o[1] = (float)(d - (double)o[0]);
-        };
-        std::vector<float> C(nc * 8, 0.0f), tw(2 * twM.size());
-        for (size_t i = 0; i < nc; ++i)
-            for (int j = 0; j < 3; ++j) split(coef[3 * i + j], &C[8 * i + 2 * j]);
-        for (size_t i = 0; i < twM.size(); ++i) split(twM[i], &tw[2 * i]);
-        CK(ft.H.ensure(C.size() * 4));
+        std::vector<float> tw(2 * twM.size());
+        for (size_t i = 0; i < twM.size(); ++i) {
+            tw[2 * i] = (float)twM[i];
+            tw[2 * i + 1] = (float)(twM[i] - (double)(float)twM[i]);
+        }
         CK(ft.tw.ensure(tw.size() * 4));
-        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ft.tw.p, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
     } else {
-        std::vector<float> C(nc * 4, 0.0f), tw(twM.size());
-        for (size_t i = 0; i < nc; ++i)
-            for (int j = 0; j < 3; ++j) C[4 * i + j] = (float)coef[3 * i + j];
+        std::vector<float> tw(twM.size());
         for (size_t i = 0; i < twM.size(); ++i) tw[i] = (float)twM[i];
-        CK(ft.H.ensure(C.size() * 4));
         CK(ft.tw.ensure(tw.size() * 4));
-        CK(cudaMemcpyAsync(ft.H.p, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ft.tw.p, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    // per-pass twiddle powers: pass p (radix R, span S, Sr = S/R > 1) holds
+    // W_S^(j q) at [(q - 1) Sr + j], passes concatenated in order
+    {
+        std::vector<double> t;
+        for (int i = 0; i < fpM.npass; ++i) {
+            const int Rp = fpM.radix[i], S = fpM.span[i], Sr = S / Rp;
+            for (int q = 1; q < Rp; ++q)
+                for (int j = 0; j < Sr; ++j) {
+                    const double ang = -2.0 * M_PI * (double)((int64_t)j * q % S) / (double)S;
+                    t.push_back(std::cos(ang));
+                    t.push_back(std::sin(ang));
+                }
+        }
+        if (t.empty()) t.assign(2, 0.0);
+        if (f64 == 1) {
+            CK(ft.twp.ensure(t.size() * 8));
+            CK(cudaMemcpyAsync(ft.twp.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            const bool dfp = f64 == 2;
+            std::vector<float> tf(t.size() * (dfp ? 2 : 1));
+            for (size_t i = 0; i < t.size(); ++i) {
+                if (dfp) {
+                    tf[2 * i] = (float)t[i];
+                    tf[2 * i + 1] = (float)(t[i] - (double)(float)t[i]);
+                } else {
+                    tf[i] = (float)t[i];
+                }
+            }
+            CK(ft.twp.ensure(tf.size() * 4));
+            CK(cudaMemcpyAsync(ft.twp.p, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        }
         CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (fused) {
+        CK(ft.items.ensure(items.size() * 4));
+        CK(cudaMemcpyAsync(ft.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     }
     CK(ft.pairs.ensure(pairs.size() * 4));
     CK(cudaMemcpyAsync(ft.pairs.p, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
@@ -776,6 +866,9 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
             a.half = 1;
             a.L = plan->L / 2;
             a.pairs = ft.pairs.as<uint32_t>();
+            a.items = ft.items.as<uint32_t>();
+            a.Hi = ft.Hi.p;
+            a.twp = ft.twp.p;
         }
         if (plan->f64 == 2) launch_filter_fft_df(a, from_tod, ctx->stream);
         else if (plan->f64 == 1) launch_filter_fft_f64(a, from_tod, ctx->stream);

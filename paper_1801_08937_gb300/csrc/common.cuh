@@ -79,6 +79,9 @@ struct FilterArgs {
                            // half: [n_bands][L/2 + 1] pair coefficients (alpha_k, alpha_{L-k}, beta_k)
     const void* tw;        // FFT: [L] twiddles exp(-2 pi i e / L)
     const uint32_t* pairs; // half: [L/2 + 1] digit-reversed positions of k (low 16 bits) and L - k
+    const uint32_t* items; // half, fused last pass: [L/(2R) + 1] butterfly c (low 16 bits) and its partner c'
+    const void* Hi;        // half, fused last pass: [n_bands][items][R] coefficients (alpha_k, alpha_{L-k}, beta_k)
+    const void* twp;       // half: per-pass twiddles W_S^(j q), pass by pass, [q - 1][j] within a pass; may be null
     int half;              // 1: one whole block per CTA as L = N/2 complex points
     const void* band;      // direct: [n_bands][lambda+1]
     int L, logL, lam, V;

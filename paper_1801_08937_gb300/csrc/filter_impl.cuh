@@ -277,10 +277,11 @@ struct CtPlan {
     int np;
     int r[8];
     int s[8];
+    int toff[8];   // offset of pass p in the per-pass twiddle table (see ct_pass)
 };
 // MAXR: largest power-of-two radix (16, or 8 where registers are scarce).
 __host__ __device__ constexpr CtPlan make_ct_plan(int L, int MAXR = 16) {
-    CtPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    CtPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
     int rest = L, span = L;
     if (rest % 9 == 0) {
         p.r[p.np] = 9; p.s[p.np] = span; span /= 9; rest /= 9; ++p.np;
@@ -293,7 +294,21 @@ __host__ __device__ constexpr CtPlan make_ct_plan(int L, int MAXR = 16) {
     if (rest > 1 && rest < MAXR && (rest == 8 || rest == 4 || rest == 2)) {
         p.r[p.np] = rest; p.s[p.np] = span; ++p.np;
     }
+    int off = 0;
+    for (int i = 0; i < p.np; ++i) {
+        p.toff[i] = off;
+        off += (p.r[i] - 1) * (p.s[i] / p.r[i]);
+    }
     return p;
+}
+
+// Passes whose twiddle powers come from the per-pass table instead of being
+// formed from one twiddle: every pass for float64 and double-float, where a
+// complex product costs tens of float32 instructions; none for float32, where
+// the table loads of a radix-16 butterfly do not fit the register budget of
+// two 512-thread CTAs per SM.
+template <typename T> __host__ __device__ constexpr bool table_twiddles(int) {
+    return sizeof(T) != 4;
 }
 
 // Padded index of point base + r Sr of a butterfly, as sidx(base) plus a
@@ -315,8 +330,13 @@ __device__ __forceinline__ int pad_index(int b0, int base, int r) {
     else return sidx(base + r * Sr);
 }
 
-template <typename T, int R, int S, int L, int NT, bool DIT>
-__device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) {
+// One pass of radix R over spans of S points.  Twiddle powers W_S^(j q):
+// formed from W_L^(j L/S) (one table load), or, with TAB, read from the
+// pass's table ptab[(q - 1) Sr + j] (neighbouring butterflies read
+// neighbouring entries).
+template <typename T, int R, int S, int L, int NT, bool DIT, bool TAB = false>
+__device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw,
+                                        const C2<T>* __restrict__ ptab = nullptr) {
     constexpr int Sr = S / R;
     constexpr int nbf = L / R;
     constexpr int tstep = L / S;
@@ -327,16 +347,21 @@ __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) 
         const int base = g * S + j;
         const int b0 = sidx(base);
         C2<T> w1{T(1), T(0)};
-        if (Sr > 1) w1 = ldtw(tw, j * tstep);
+        if (Sr > 1 && !TAB) w1 = ldtw(tw, j * tstep);
         C2<T> a[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) a[r] = s[pad_index<S, Sr>(b0, base, r)];
         if (!DIT) Dft<T, R>::run(a);
         if (Sr > 1) {
-            C2<T> w[R];
-            twiddle_powers<T, R>(w1, w);
+            if constexpr (TAB) {
 #pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
+                for (int q = 1; q < R; ++q) a[q] = cmul(a[q], ldtw(ptab, (q - 1) * Sr + j));
+            } else {
+                C2<T> w[R];
+                twiddle_powers<T, R>(w1, w);
+#pragma unroll
+                for (int q = 1; q < R; ++q) a[q] = cmul(a[q], w[q]);
+            }
         }
         if (DIT) Dft<T, R>::run(a);
 #pragma unroll
@@ -344,22 +369,27 @@ __device__ __forceinline__ void ct_pass(C2<T>* s, const C2<T>* __restrict__ tw) 
     }
 }
 
-template <typename T, int L, int NT, int MAXR, int P>
-__device__ __forceinline__ void ct_dif(C2<T>* s, const C2<T>* tw) {
+// Passes P .. PEND - 1 of the forward transform (PEND < 0: to the last pass).
+// tt: the per-pass twiddle table (null: powers formed from tw in every pass).
+template <typename T, int L, int NT, int MAXR, int P, int PEND = -1>
+__device__ __forceinline__ void ct_dif(C2<T>* s, const C2<T>* tw, const C2<T>* tt = nullptr) {
     constexpr CtPlan pl = make_ct_plan(L, MAXR);
-    if constexpr (P < pl.np) {
-        ct_pass<T, pl.r[P], pl.s[P], L, NT, false>(s, tw);
+    constexpr int end = PEND < 0 ? pl.np : PEND;
+    if constexpr (P < end) {
+        if (tt && table_twiddles<T>(P)) ct_pass<T, pl.r[P], pl.s[P], L, NT, false, true>(s, tw, tt + pl.toff[P]);
+        else ct_pass<T, pl.r[P], pl.s[P], L, NT, false>(s, tw);
         __syncthreads();
-        ct_dif<T, L, NT, MAXR, P + 1>(s, tw);
+        ct_dif<T, L, NT, MAXR, P + 1, PEND>(s, tw, tt);
     }
 }
 template <typename T, int L, int NT, int MAXR, int P>
-__device__ __forceinline__ void ct_dit(C2<T>* s, const C2<T>* tw) {
+__device__ __forceinline__ void ct_dit(C2<T>* s, const C2<T>* tw, const C2<T>* tt = nullptr) {
     constexpr CtPlan pl = make_ct_plan(L, MAXR);
     if constexpr (P >= 0) {
-        ct_pass<T, pl.r[P], pl.s[P], L, NT, true>(s, tw);
+        if (tt && table_twiddles<T>(P)) ct_pass<T, pl.r[P], pl.s[P], L, NT, true, true>(s, tw, tt + pl.toff[P]);
+        else ct_pass<T, pl.r[P], pl.s[P], L, NT, true>(s, tw);
         __syncthreads();
-        ct_dit<T, L, NT, MAXR, P - 1>(s, tw);
+        ct_dit<T, L, NT, MAXR, P - 1>(s, tw, tt);
     }
 }
 
@@ -994,6 +1024,69 @@ __device__ __forceinline__ void half_scatter_t(const FilterArgs& a, const Seg& S
     }
 }
 
+// Last forward pass, paired real-spectrum step and first inverse pass in
+// registers.  The last pass (radix R, R consecutive positions per butterfly,
+// no twiddles) leaves butterfly c with the frequencies kc + (M/R) q; the
+// mirror images M - k of those sit in the partner butterfly c' at outputs
+// R - 1 - q (for kc = 0 at outputs (R - q) mod R, in c itself; kc = M/(2R)
+// is its own partner too).  The item table lists the pairs {c, c'} by the
+// position of c (bit 31: the kc = 0 item).  A thread takes one pair: DFT_R of both,
+// the spectrum step of every pair (k, M - k), written conjugated, and the
+// first conjugate-domain pass (DFT_R, no twiddles), so the spectrum step
+// costs no shared-memory round trip and no barrier of its own.
+template <typename T, int M, int NT, int R>
+__device__ __forceinline__ void ct_fused_spectrum(C2<T>* s, const uint32_t* __restrict__ items, const void* Hi,
+                                                  int64_t cb) {
+    constexpr int NB = M / R;
+    constexpr int NI = NB / 2 + 1;
+    static_assert(NB % 2 == 0 && 16 % R == 0, "fused spectrum pass: butterfly pairs inside padding groups");
+#pragma unroll 1
+    for (int i = threadIdx.x; i < NI; i += NT) {
+        const uint32_t pr = __ldg(items + i);
+        const int c = (int)(pr & 0xffffu), c2 = (int)((pr >> 16) & 0x7fffu);
+        T aa[R], ab[R], be[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) ld_coef(Hi, cb + (int64_t)i * R + q, aa[q], ab[q], be[q]);
+        // positions c R .. c R + R - 1 stay inside one 16-point padding group
+        const int b0 = sidx(c * R), b1 = sidx(c2 * R);
+        C2<T> x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = s[b0 + q];
+        Dft<T, R>::run(x);
+        if (c != c2) {
+            C2<T> y[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) y[q] = s[b1 + q];
+            Dft<T, R>::run(y);
+            C2<T> xo[R], yo[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const C2<T> A = x[q], B = y[R - 1 - q];
+                xo[q] = C2<T>{aa[q] * A.x + be[q] * B.y, -(aa[q] * A.y + be[q] * B.x)};
+                yo[R - 1 - q] = C2<T>{ab[q] * B.x + be[q] * A.y, -(ab[q] * B.y + be[q] * A.x)};
+            }
+            Dft<T, R>::run(xo);
+            Dft<T, R>::run(yo);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                s[b0 + q] = xo[q];
+                s[b1 + q] = yo[q];
+            }
+        } else {
+            const bool zero = (pr >> 31) != 0u;
+            C2<T> xo[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const C2<T> A = x[q], B = zero ? x[(R - q) % R] : x[R - 1 - q];
+                xo[q] = C2<T>{aa[q] * A.x + be[q] * B.y, -(aa[q] * A.y + be[q] * B.x)};
+            }
+            Dft<T, R>::run(xo);
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[b0 + q] = xo[q];
+        }
+    }
+}
+
 template <typename T> struct HalfMinBlocks { static constexpr int value = 1; };
 template <> struct HalfMinBlocks<float> { static constexpr int value = 2; };
 
@@ -1008,6 +1101,20 @@ __global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(con
     if constexpr (std::is_same<T, float>::value) half_gather_f32<FROM_TOD, NT>(a, S, s, M);
     else half_gather_t<T, FROM_TOD, NT>(a, S, s, M);
     __syncthreads();
+    if constexpr (MCT > 0) {
+        constexpr CtPlan pl = make_ct_plan(MCT, MaxRadix<T>::value);
+        constexpr int R = pl.r[pl.np - 1];
+        if constexpr ((MCT / R) % 2 == 0 && 16 % R == 0) {
+            const C2<T>* tt = reinterpret_cast<const C2<T>*>(a.twp);
+            ct_dif<T, MCT, NT, MaxRadix<T>::value, 0, pl.np - 1>(s, tw, tt);
+            ct_fused_spectrum<T, MCT, NT, R>(s, a.items, a.Hi, (int64_t)S.band * ((MCT / R) / 2 + 1) * R);
+            __syncthreads();
+            if constexpr (pl.np >= 2) ct_dit<T, MCT, NT, MaxRadix<T>::value, pl.np - 2>(s, tw, tt);
+            if constexpr (std::is_same<T, float>::value) half_scatter_f32<NT>(a, S, s, M);
+            else half_scatter_t<T, NT>(a, S, s);
+            return;
+        }
+    }
     if constexpr (MCT > 0) ct_dif<T, MCT, NT, MaxRadix<T>::value, 0>(s, tw);
     else fft_dif<T>(s, tw, a.fp);
     // paired real-spectrum filter, written conjugated for the inverse; the
@@ -1306,6 +1413,7 @@ inline void launch_half_t(const FilterArgs& a, cudaStream_t s) {
         return launch_half_nt<T, FROM_TOD, 256, 0>(a, sm, s);
     } else if constexpr (std::is_same<T, df>::value) {
         if (a.L == 9216) return launch_half_nt<T, FROM_TOD, 512, 9216>(a, sm, s);
+        if (a.L == 12288) return launch_half_nt<T, FROM_TOD, 512, 12288>(a, sm, s);
         return launch_half_nt<T, FROM_TOD, 512, 0>(a, sm, s);
     } else {
         if (a.L == 9216) return launch_half_nt<T, FROM_TOD, 256, 9216>(a, sm, s);

@@ -127,6 +127,7 @@ struct mm_ctx {
     int max_iter = 0;
     bool use_lens = false;
     std::vector<int64_t> lens;
+    const void* tod_dev = nullptr;   // device timeline of the current solve (mixed precision), in s_tod
     DevBuf s_tod, s_b, s_x, s_r, s_z, s_p, s_src, s_q, s_st, s_hist, s_u, s_xtot, s_rtrue, s_q64, s_mask;
     Plan* plan_op = nullptr;
     Plan* plan_64 = nullptr;
@@ -676,7 +677,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
 }
 
 mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, void* dst, const RhsState* st,
-                     int tod_is_float);
+                     int tod_is_float, const void* xmap = nullptr);
 
 // Process-wide record of tuned choices, keyed by problem shape.
 struct TuneKey {
@@ -827,8 +828,9 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
 
 // dst (V4<T>[nrhs][n_pix], zeroed by the caller) += P^T W (P src | d).
 mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, void* dst, const RhsState* st,
-                     int tod_is_float) {
+                     int tod_is_float, const void* xmap) {
     FilterArgs a{};
+    a.xmap = xmap;
     a.segs = plan->segs.as<Seg>();
     a.n_work = plan->n_work;
     a.pix = ctx->d_pix.as<int32_t>();
@@ -1024,12 +1026,30 @@ mm_status read_state(mm_ctx* ctx) {
 }
 
 // float64 residual b - A x per right-hand side (x in s_xtot or s_x), written to
-// s_rtrue; norms to host.
+// s_rtrue; norms to host.  With the float32 operator (mixed precision) it is
+// formed in one float64-accurate pass from the timeline, P^T W (d - P x), so b
+// itself is needed only to float32 accuracy; otherwise as b - A x.
 mm_status true_residual(mm_ctx* ctx, const V4<double>* x, std::vector<double>& rr) {
-    TRY(apply_A_dev(ctx, ctx->p64, x, ctx->s_q64.as<V4<double>>(), ctx->nrhs, ctx->plan_64));
-    launch_residual(ctx->s_b.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), ctx->s_rtrue.as<V4<double>>(),
-                    ctx->w_norms.as<double>(), ctx->n_pix, ctx->nrhs, ctx->w_partial.as<double>(),
-                    ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+    if (is_f32(ctx) && ctx->tod_dev) {
+        TRY(ensure_work(ctx, ctx->nrhs, ctx->k));
+        const int64_t nv = (int64_t)ctx->n_pix * ctx->nrhs;
+        const void* xm = x;
+        if (ctx->p64 == 2) {
+            launch_map_to_df(x, ctx->w_src.p, nv, ctx->stream);
+            xm = ctx->w_src.p;
+        }
+        CK(cudaMemsetAsync(ctx->s_rtrue.p, 0, nv * sizeof(V4<double>), ctx->stream));
+        TRY(run_filter(ctx, ctx->plan_64, true, ctx->tod_dev, ctx->s_rtrue.p, nullptr, 1, xm));
+        CK(cudaMemsetAsync(ctx->s_q64.p, 0, nv * sizeof(V4<double>), ctx->stream));
+        launch_residual(ctx->s_rtrue.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), nullptr, ctx->w_norms.as<double>(),
+                        ctx->n_pix, ctx->nrhs, ctx->w_partial.as<double>(), ctx->w_counter.as<unsigned>(),
+                        ctx->grid_x, ctx->stream);
+    } else {
+        TRY(apply_A_dev(ctx, ctx->p64, x, ctx->s_q64.as<V4<double>>(), ctx->nrhs, ctx->plan_64));
+        launch_residual(ctx->s_b.as<V4<double>>(), ctx->s_q64.as<V4<double>>(), ctx->s_rtrue.as<V4<double>>(),
+                        ctx->w_norms.as<double>(), ctx->n_pix, ctx->nrhs, ctx->w_partial.as<double>(),
+                        ctx->w_counter.as<unsigned>(), ctx->grid_x, ctx->stream);
+    }
     CKL();
     rr.resize(ctx->nrhs);
     CK(cudaMemcpyAsync(rr.data(), ctx->w_norms.p, ctx->nrhs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1804,14 +1824,30 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     const size_t esz = f32 ? 4 : 8;
     const void* src = tod;
-    if (mem == MM_HOST) {
+    ctx->tod_dev = nullptr;
+    if (mem == MM_HOST || f32) {
+        // the mixed-precision refinement reads the timeline again (residuals
+        // P^T W (d - P x)), so it keeps its own device copy
         CK(ctx->s_tod.ensure((size_t)nrhs * ctx->n_samples * esz));
-        CK(cudaMemcpyAsync(ctx->s_tod.p, tod, (size_t)nrhs * ctx->n_samples * esz, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->s_tod.p, tod, (size_t)nrhs * ctx->n_samples * esz,
+                           mem == MM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
         src = ctx->s_tod.p;
+        ctx->tod_dev = ctx->s_tod.p;
     }
-    // b = P^T W d in float64
     CK(cudaMemsetAsync(ctx->s_b.p, 0, v4, ctx->stream));
-    TRY(run_filter(ctx, ctx->plan_64, true, src, ctx->s_b.p, nullptr, f32 ? 1 : 0));
+    if (f32) {
+        // b = P^T W d with the float32 operator: the inner solve stops at
+        // float32 accuracy anyway, and every refinement residual comes from d
+        TRY(ensure_work(ctx, nrhs, ctx->k));
+        V4<float>* q = ctx->w_q.as<V4<float>>();
+        CK(cudaMemsetAsync(q, 0, (size_t)ctx->n_pix * nrhs * sizeof(V4<float>), ctx->stream));
+        TRY(run_filter(ctx, ctx->plan_op, true, src, q, nullptr, 1));
+        launch_from_f32(q, ctx->s_b.as<V4<double>>(), (int64_t)ctx->n_pix * nrhs, ctx->stream);
+        CKL();
+    } else {
+        // b = P^T W d in float64
+        TRY(run_filter(ctx, ctx->plan_64, true, src, ctx->s_b.p, nullptr, 0));
+    }
     CK(ctx->d_lastb.ensure((size_t)ctx->n_pix * sizeof(V4<double>)));
     CK(cudaMemcpyAsync(ctx->d_lastb.p, ctx->s_b.p, (size_t)ctx->n_pix * sizeof(V4<double>), cudaMemcpyDeviceToDevice,
                        ctx->stream));
@@ -2155,6 +2191,7 @@ int64_t mm_estimate_bytes(int64_t n_samples, int32_t n_pix, int32_t n_bands, int
                           int32_t m_max, int32_t k, mm_precision prec) {
     const int64_t esz = prec == MM_FP32_MIXED ? 4 : 8;
     int64_t b = n_samples * (4 + 4 + 16);              // pix, psi, float64 weights
+    if (prec == MM_FP32_MIXED) b += n_samples * 16;    // double-float weights
     b += (int64_t)nrhs * n_samples * esz;              // timelines
     b += (int64_t)n_pix * 32 * (12 + 2 * (int64_t)nrhs * 6);  // maps and PCG state
     b += (int64_t)(m_max + 1) * n_pix * 32;            // Arnoldi basis

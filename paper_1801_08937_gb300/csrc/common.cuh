@@ -88,6 +88,8 @@ struct FilterArgs {
     FftPasses fp;
     const RhsState* state; // may be null: all right-hand sides active
     int tod_is_float;      // src TOD element type when from_tod (1: float, 0: double)
+    const void* xmap;      // from_tod, float64 / double-float only: map x (V4<T>) whose P x is subtracted
+                           // from the timeline, giving the residual P^T W (d - P x) = b - A x; may be null
 };
 
 // T = float or double; from_tod selects b = P^T W d (src is a TOD).

@@ -454,12 +454,27 @@ __device__ __forceinline__ V4<df> ldmap(const V4<df>* m) {
     return {df(a.x, a.y), df(a.z, a.w), df(b.x, b.y), df(b.z, b.w)};
 }
 
-// y_t of right-hand side `rhs`: (P x)_t, or d_t when FROM_TOD.
+// (P x)_t for the map a.xmap: the timeline residual d_t - (P x)_t, whose
+// filtered transpose is b - A x = P^T W (d - P x) (Sect. 3, Eq. linearsystem).
+template <typename T>
+__device__ __forceinline__ T xmap_value(const FilterArgs& a, int64_t t, int rhs) {
+    const int p = __ldg(a.pix + t);
+    if (p < 0) return T(0);
+    T c, s;
+    weights(a, t, c, s);
+    const V4<T> m = ldmap<T>(reinterpret_cast<const V4<T>*>(a.xmap) + (int64_t)rhs * a.n_pix + p);
+    return m.x + c * m.y + s * m.z;
+}
+
+// y_t of right-hand side `rhs`: (P x)_t, or d_t when FROM_TOD (d_t - (P x)_t
+// when a residual map is given).
 template <typename T, bool FROM_TOD>
 __device__ __forceinline__ T sample_value(const FilterArgs& a, int64_t t, int rhs) {
     if (FROM_TOD) {
-        if (a.tod_is_float) return T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t));
-        return T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t));
+        T v = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t))
+                             : T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t));
+        if (sizeof(T) > 4 && a.xmap) v = v - xmap_value<T>(a, t, rhs);
+        return v;
     } else {
         const int p = __ldg(a.pix + t);
         if (p < 0) return T(0);
@@ -493,10 +508,8 @@ __device__ __forceinline__ void gather_pair(const FilterArgs& a, const Seg& A, c
             ya[g] = T(0);
             yb[g] = T(0);
             if (FROM_TOD) {
-                if (va) ya[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + A.rhs * a.n_samples + ta))
-                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + A.rhs * a.n_samples + ta));
-                if (vb) yb[g] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + B.rhs * a.n_samples + tb))
-                                               : T(__ldg(reinterpret_cast<const double*>(a.src) + B.rhs * a.n_samples + tb));
+                if (va) ya[g] = sample_value<T, true>(a, ta, A.rhs);
+                if (vb) yb[g] = sample_value<T, true>(a, tb, B.rhs);
             } else {
                 if (va) {
                     pa[g] = __ldg(a.pix + ta);

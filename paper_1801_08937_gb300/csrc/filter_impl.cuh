@@ -575,7 +575,8 @@ __device__ __forceinline__ void atomic_add3(V4<double>* q, df a, df b, df c) {
 
 // Warp-cooperative P^T: every lane holds one sample (p < 0: nothing).
 // Consecutive lanes with equal p form a run; a suffix sum inside each run
-// leaves the run total on its first lane, which issues one atomic.
+// leaves the run total on its first lane, which issues one atomic.  The sum
+// takes only as many doubling steps as the longest run in the warp needs.
 template <typename T>
 __device__ __forceinline__ void scatter_vals(int p, T v0, T v1, T v2, V4<typename AccT<T>::type>* q) {
     const unsigned FULL = 0xffffffffu;
@@ -585,8 +586,9 @@ __device__ __forceinline__ void scatter_vals(int p, T v0, T v1, T v2, V4<typenam
     const unsigned heads = __ballot_sync(FULL, head);
     const unsigned above = heads & ~((2u << lane) - 1u);
     const int end = above ? (__ffs(above) - 1) : 32;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    const int need = (int)__reduce_max_sync(FULL, head ? (unsigned)(end - (int)lane) : 0u);
+#pragma unroll 1
+    for (int d = 1; d < need; d <<= 1) {
         const T o0 = shfl_down_t(v0, d);
         const T o1 = shfl_down_t(v1, d);
         const T o2 = shfl_down_t(v2, d);
@@ -1422,6 +1424,8 @@ inline void launch_half_t(const FilterArgs& a, cudaStream_t s) {
                 case 2304: return launch_half_nt<T, FROM_TOD, 256, 2304>(a, sm, s);
                 default: break;
             }
+        } else {
+            if (a.L == 9216) return launch_half_nt<T, FROM_TOD, 512, 9216>(a, sm, s);
         }
         return launch_half_nt<T, FROM_TOD, 256, 0>(a, sm, s);
     } else if constexpr (std::is_same<T, df>::value) {

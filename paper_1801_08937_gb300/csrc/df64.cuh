@@ -1,10 +1,15 @@
 // Double-float arithmetic: a value is an unevaluated sum hi + lo of two
-// float32 numbers (|lo| of the order of ulp(hi)), giving about 44 bits of precision
-// from float32 units.  Addition uses the error-free two-sum of Knuth and
-// Moller; multiplication uses the error-free product through a fused
-// multiply-add (Dekker's product with FMA).  Sums renormalise with the
-// fast two-sum of Dekker; products leave that to the next sum.  GB300 issues float32 at 64 times its float64
-// rate, so float64-accurate products run several times faster this way.
+// float32 numbers, giving about 44 bits of precision from float32 units.
+// Addition uses the error-free two-sum of Knuth and Moller on the hi parts;
+// multiplication uses the error-free product through a fused multiply-add
+// (Dekker's product with FMA).  Neither renormalises: the lo part carries
+// only rounding errors of the order of eps_32 times the magnitudes of the
+// operands that produced it, and is itself rounded in float32, so every
+// result is exact to about eps_32^2 of those magnitudes, which is the
+// absolute accuracy a transform or band sum needs (after a cancellation lo
+// may exceed ulp(hi); the represented value hi + lo stays as accurate).
+// GB300 issues float32 at 64 times its float64 rate, so float64-accurate
+// products run several times faster this way.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -34,12 +39,12 @@ __device__ __forceinline__ df df_fast_two_sum(float a, float b) {
 __device__ __forceinline__ df operator+(df a, df b) {
     df s = df_two_sum(a.hi, b.hi);
     s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-    return df_fast_two_sum(s.hi, s.lo);
+    return s;
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
-// The product is returned as (p, e) without renormalising: a product cannot
-// cancel, so |e| stays within a few ulp of p, and the next sum renormalises.
+// The product is returned as (p, e) without renormalising; the dropped term
+// a.lo b.lo is of the order of eps_32^2 |a| |b|.
 __device__ __forceinline__ df operator*(df a, df b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);

@@ -241,6 +241,48 @@ def test_solve_bd_matches_oracle(prec):
     assert rel(x[0], xo) < 1e-6
 
 
+@pytest.mark.parametrize("products", [1, 2])
+def test_mixed_true_residual_matches_oracle(products):
+    """The mixed-precision solve forms its refinement residual as P^T W (d - P x) in one
+    float64-accurate pass (native float64 or double-float); the residual it reports for the
+    returned map equals the oracle's ||b - A x|| / ||b|| on that map."""
+    scan, d, _ = scan_and_tod(SMALL, seed=23, flag_frac=0.01)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan, MM.MM_FP32_MIXED)
+    c.set_option("fp64_products", products)
+    c.build_bd()
+    tod = d.astype(c.tod_dtype)
+    for tol in (1e-6, 1e-9):
+        x, info = c.solve(tod, MM.MM_PRECOND_BD, tol=tol, max_iter=2000)
+        assert info[0]["status"] == "MM_OK"
+        b = O.rhs(prob, tod.astype(np.float64))
+        r = b - O.apply_A(prob, x[0])
+        ref = np.linalg.norm(r) / np.linalg.norm(b)
+        assert ref <= tol
+        # double-float / float64 rounding of the pass: ~1e-13 of ||b||, far below the residual
+        assert abs(info[0]["true_rel_res"] - ref) <= 1e-3 * ref + 1e-11
+
+
+def test_mixed_true_residual_uneven_batch():
+    """The same for a batch of right-hand sides of uneven length (one pass for all of them)."""
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=8192, n_int=8, half_bw=32, f_knee=1.0)
+    scan = synth.make_scan(seed=24, **cfg)
+    lens = np.array([8192, 5001, 6400], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 200 + i), synth.make_noise(scan, 200 + i))
+                     for i in range(len(lens))]).astype(np.float32)
+    c = ctx_for(scan, MM.MM_FP32_MIXED)
+    c.build_bd()
+    x, info = c.solve(tods, MM.MM_PRECOND_BD, tol=1e-9, max_iter=3000, rhs_len=lens)
+    _, _, good = oracle_problem(scan)
+    for i, L in enumerate(lens):
+        assert info[i]["status"] == "MM_OK"
+        prob, mbd, idx = truncated_problem(scan, int(L), good=good)
+        b = O.rhs(prob, tods[i][idx].astype(np.float64))
+        ref = np.linalg.norm(b - O.apply_A(prob, x[i])) / np.linalg.norm(b)
+        assert ref <= 1e-9
+        assert abs(info[i]["true_rel_res"] - ref) <= 1e-3 * ref + 1e-11
+
+
 def test_signal_only_recovers_sky():
     scan, d, s = scan_and_tod(SMALL, seed=9, noise=False)
     prob, mbd, good = oracle_problem(scan)

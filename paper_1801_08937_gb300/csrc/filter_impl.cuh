@@ -606,18 +606,19 @@ __device__ __forceinline__ void scatter_warp(int p, T c, T s, T z, V4<typename A
     scatter_vals<T>(p, z, z * c, z * s, q);
 }
 
-// float32 scatter of four consecutive outputs per lane: runs of equal pixels
-// are summed in registers first, a lane's leading run joins the previous
-// lane's trailing run when they share a pixel, runs strictly inside a lane's
-// four samples go out directly, and the trailing runs go through the
+// Scatter of four consecutive outputs per lane: runs of equal pixels are
+// summed in registers first, a lane's leading run joins the previous lane's
+// trailing run when they share a pixel, runs strictly inside a lane's four
+// samples go out directly, and the trailing runs go through the
 // warp-segmented reduction.  Every output is counted once.
-__device__ __forceinline__ void scatter4_vals(const int (&p)[4], const float (&v0)[4], const float (&v1)[4],
-                                              const float (&v2)[4], V4<float>* q) {
+template <typename T>
+__device__ __forceinline__ void scatter4_vals(const int (&p)[4], const T (&v0)[4], const T (&v1)[4],
+                                              const T (&v2)[4], V4<typename AccT<T>::type>* q) {
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     int kf = p[0], cur = p[0];
-    float f0 = v0[0], f1 = v1[0], f2 = v2[0];
-    float c0 = v0[0], c1 = v1[0], c2 = v2[0];
+    T f0 = v0[0], f1 = v1[0], f2 = v2[0];
+    T c0 = v0[0], c1 = v1[0], c2 = v2[0];
     bool first_done = false;
 #pragma unroll
     for (int j = 1; j < 4; ++j) {
@@ -644,9 +645,9 @@ __device__ __forceinline__ void scatter4_vals(const int (&p)[4], const float (&v
     const bool multi = first_done;
     const int prev_last = __shfl_up_sync(FULL, cur, 1);
     const bool give = multi && lane > 0 && kf == prev_last;
-    const float r0 = __shfl_down_sync(FULL, f0, 1);
-    const float r1 = __shfl_down_sync(FULL, f1, 1);
-    const float r2 = __shfl_down_sync(FULL, f2, 1);
+    const T r0 = shfl_down_t(f0, 1);
+    const T r1 = shfl_down_t(f1, 1);
+    const T r2 = shfl_down_t(f2, 1);
     const int rgive = __shfl_down_sync(FULL, (int)give, 1);
     if (lane < 31 && rgive) {
         c0 += r0;
@@ -654,7 +655,22 @@ __device__ __forceinline__ void scatter4_vals(const int (&p)[4], const float (&v
         c2 += r2;
     }
     if (multi && !give && kf >= 0) atomic_add3(q + kf, f0, f1, f2);
-    scatter_vals<float>(cur, c0, c1, c2, q);
+    scatter_vals<T>(cur, c0, c1, c2, q);
+}
+
+// Pixel indices of four consecutive samples t0..t0+3 (a vector load past L1
+// when aligned); samples at or beyond the segment end come back flagged.
+__device__ __forceinline__ void load4_pix(const FilterArgs& a, int64_t t0, bool act, int count, int (&p)[4]) {
+    if (act && count >= 4 && (t0 & 3) == 0) {
+        int4 pv;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(pv.x), "=r"(pv.y), "=r"(pv.z), "=r"(pv.w)
+                     : "l"(a.pix + t0));
+        p[0] = pv.x; p[1] = pv.y; p[2] = pv.z; p[3] = pv.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = (act && j < count) ? __ldg(a.pix + t0 + j) : -1;
+    }
 }
 
 // Pixel and angle of four consecutive samples t0..t0+3 (vector loads when
@@ -1016,26 +1032,35 @@ __device__ __forceinline__ void half_scatter_f32(const FilterArgs& a, const Seg&
     }
 }
 
+// float64 / double-float scatter, four consecutive samples per lane as in
+// the float32 one (in-lane run sums, then the warp-segmented reduction).
 template <typename T, int NT>
-__device__ __forceinline__ void half_scatter_t(const FilterArgs& a, const Seg& S, const C2<T>* s) {
+__device__ __forceinline__ void half_scatter_t(const FilterArgs& a, const Seg& S, const C2<T>* s, int M) {
     constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     using Acc = typename AccT<T>::type;
     V4<Acc>* q = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
-    for (int base = warp * 32; base < S.n_out; base += NW * 32) {
-        const int i = base + lane;
-        int p = -1;
-        T c = T(0), sn = T(0), z = T(0);
-        if (i < S.n_out) {
-            const int64_t t = S.out0 + i;
-            p = __ldg(a.pix + t);
-            if (p >= 0) {
-                weights(a, t, c, sn);
-                const C2<T> e = s[sidx(i >> 1)];
-                z = (i & 1) ? -e.y : e.x;
+    for (int base = warp * 128; base < S.n_out; base += NW * 128) {
+        const int i0 = base + 4 * lane;
+        const int64_t t0 = S.out0 + i0;
+        int p[4];
+        load4_pix(a, t0, i0 < S.n_out, S.n_out - i0, p);
+        const int m0 = min(i0 >> 1, M - 2);
+        const C2<T> e0 = s[sidx(m0)], e1 = s[sidx(m0 + 1)];
+        const T z[4] = {e0.x, -e0.y, e1.x, -e1.y};
+        T v0[4], v1[4], v2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T zz = T(0), c = T(0), sn = T(0);
+            if (p[j] >= 0) {
+                zz = z[j];
+                weights(a, t0 + j, c, sn);
             }
+            v0[j] = zz;
+            v1[j] = zz * c;
+            v2[j] = zz * sn;
         }
-        scatter_warp<T>(p, c, sn, z, q);
+        scatter4_vals<T>(p, v0, v1, v2, q);
     }
 }
 
@@ -1126,7 +1151,7 @@ __global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(con
             __syncthreads();
             if constexpr (pl.np >= 2) ct_dit<T, MCT, NT, MaxRadix<T>::value, pl.np - 2>(s, tw, tt);
             if constexpr (std::is_same<T, float>::value) half_scatter_f32<NT>(a, S, s, M);
-            else half_scatter_t<T, NT>(a, S, s);
+            else half_scatter_t<T, NT>(a, S, s, M);
             return;
         }
     }
@@ -1163,7 +1188,7 @@ __global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(con
         ct_dit<T, MCT, NT, MaxRadix<T>::value, make_ct_plan(MCT > 0 ? MCT : 64, MaxRadix<T>::value).np - 1>(s, tw);
     else fft_dit_conj<T>(s, tw, a.fp);
     if constexpr (std::is_same<T, float>::value) half_scatter_f32<NT>(a, S, s, M);
-    else half_scatter_t<T, NT>(a, S, s);
+    else half_scatter_t<T, NT>(a, S, s, M);
 }
 
 // ---------------- direct band variant, float32, four samples per thread ----------------

@@ -199,9 +199,11 @@ int64_t max_block_len(const mm_ctx* c) {
 }
 
 // Mixed-radix pass plan for L = 2^a 3^b (b <= 2): a radix-3 or radix-9 pass
-// first, then radix 16 while it divides, then one radix 2, 4 or 8 pass.
-// maxr: largest power-of-two radix (8 for double-float plans, 16 otherwise),
-// the same rule as the kernels' compile-time plans.
+// first, then radix 16 while it divides, then one radix 2, 4 or 8 pass
+// (radix 8 plans end in 4, 4 instead of 8, 2, so the last pass -- fused with
+// the spectrum step -- is never a radix-2 one).  maxr: largest power-of-two
+// radix (8 for double-float plans, 16 otherwise), the same rule as the
+// kernels' compile-time plans.
 bool fft_passes(int L, FftPasses* fp, int maxr = 16) {
     int rest = L, np = 0, span = L;
     fp->L = L;
@@ -215,7 +217,15 @@ bool fft_passes(int L, FftPasses* fp, int maxr = 16) {
     if (rest % 9 == 0) add(9);
     else if (rest % 3 == 0) add(3);
     while (rest % maxr == 0 && np < 8) add(maxr);
-    if (rest > 1 && rest < maxr && (rest == 8 || rest == 4 || rest == 2)) add(rest);
+    if (maxr == 8 && rest == 2 && np > 0 && fp->radix[np - 1] == 8 && np < 8) {
+        --np;
+        span *= 8;
+        rest *= 8;
+        add(4);
+        add(4);
+    } else if (rest > 1 && rest < maxr && (rest == 8 || rest == 4 || rest == 2)) {
+        add(rest);
+    }
     fp->npass = np;
     return rest == 1 && np <= 8;
 }

@@ -291,7 +291,13 @@ __host__ __device__ constexpr CtPlan make_ct_plan(int L, int MAXR = 16) {
     while (rest % MAXR == 0 && p.np < 8) {
         p.r[p.np] = MAXR; p.s[p.np] = span; span /= MAXR; rest /= MAXR; ++p.np;
     }
-    if (rest > 1 && rest < MAXR && (rest == 8 || rest == 4 || rest == 2)) {
+    if (MAXR == 8 && rest == 2 && p.np > 0 && p.r[p.np - 1] == 8 && p.np < 8) {
+        // end in 4, 4 rather than 8, 2 (the host planner's rule)
+        --p.np;
+        span *= 8;
+        p.r[p.np] = 4; p.s[p.np] = span; span /= 4; ++p.np;
+        p.r[p.np] = 4; p.s[p.np] = span; ++p.np;
+    } else if (rest > 1 && rest < MAXR && (rest == 8 || rest == 4 || rest == 2)) {
         p.r[p.np] = rest; p.s[p.np] = span; ++p.np;
     }
     int off = 0;
@@ -970,13 +976,49 @@ __device__ __forceinline__ void half_gather_f32(const FilterArgs& a, const Seg& 
     }
 }
 
+// float64 / double-float gather: four consecutive samples (two complex
+// points) per thread, pixel indices as one vector load, the weight and map
+// loads of all four issued before the arithmetic.  From a timeline, d_t (or
+// d_t - (P x)_t when a residual map is given).
 template <typename T, bool FROM_TOD, int NT>
 __device__ __forceinline__ void half_gather_t(const FilterArgs& a, const Seg& S, C2<T>* s, int M) {
-    for (int m = threadIdx.x; m < M; m += NT) {
-        const int i = 2 * m;
-        const T y0 = i < S.n_out ? sample_value<T, FROM_TOD>(a, S.out0 + i, S.rhs) : T(0);
-        const T y1 = i + 1 < S.n_out ? sample_value<T, FROM_TOD>(a, S.out0 + i + 1, S.rhs) : T(0);
-        s[sidx(m)] = C2<T>{y0, y1};
+    const int ng = M >> 1;
+    const bool with_map = !FROM_TOD || a.xmap != nullptr;
+    const V4<T>* map =
+        with_map ? reinterpret_cast<const V4<T>*>(FROM_TOD ? a.xmap : a.src) + (int64_t)S.rhs * a.n_pix : nullptr;
+    for (int u = threadIdx.x; u < ng; u += NT) {
+        const int i0 = 4 * u;
+        const int64_t t0 = S.out0 + i0;
+        const bool act = i0 < S.n_out;
+        T y[4] = {T(0), T(0), T(0), T(0)};
+        if (FROM_TOD) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (act && j < S.n_out - i0)
+                    y[j] = a.tod_is_float
+                               ? T(__ldg(reinterpret_cast<const float*>(a.src) + S.rhs * a.n_samples + t0 + j))
+                               : T(__ldg(reinterpret_cast<const double*>(a.src) + S.rhs * a.n_samples + t0 + j));
+        }
+        if (with_map) {
+            int p[4];
+            load4_pix(a, t0, act, S.n_out - i0, p);
+            T c[4], sn[4];
+            V4<T> m[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (p[j] >= 0) {
+                    weights(a, t0 + j, c[j], sn[j]);
+                    m[j] = ldmap<T>(map + p[j]);
+                }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (p[j] >= 0) {
+                    const T px = m[j].x + c[j] * m[j].y + sn[j] * m[j].z;
+                    y[j] = FROM_TOD ? y[j] - px : px;
+                }
+        }
+        s[sidx(2 * u)] = C2<T>{y[0], y[1]};
+        s[sidx(2 * u + 1)] = C2<T>{y[2], y[3]};
     }
 }
 

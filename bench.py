@@ -39,6 +39,8 @@ METRIC = "time-to-1e-8 residual per map (2-level vs M_BD), A·x samples/s, p99 l
 UNIT = "s/map"
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 CUDA-core rate (nominal)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# ncu: k_filter_half<float, 0, 512, 9216> moved 140.3 MB read + 3.0 MB written for 1.68e7 samples
+NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (140.259328e6 + 3.013888e6) / 16777216
 
 
 def parse():
@@ -364,8 +366,15 @@ def main():
     achieved_gbs = bytes_per_launch / (ax_ms * 1e-3) / 1e9 if ax_ms > 0 else 0.0
     alu_peak = FP32_PEAK_TFLOPS if prec == M.MM_FP32_MIXED else FP64_PEAK_TFLOPS
     achieved_tf = flops_per_launch / (ax_ms * 1e-3) / 1e12 if ax_ms > 0 else 0.0
+    # DRAM bytes (read + write) per sample of this kernel, from an ncu capture of the same kernel on
+    # 16 of the 128 detectors (1.68e7 samples, inputs larger than L2); traffic scales with samples
+    traffic = None
+    if prec == M.MM_FP32_MIXED and whole == 2 and L == 18432:
+        traffic = NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 * scan.n_samples
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak if alu_peak else None, "traffic": None,
+                "frac": achieved_tf / alu_peak if alu_peak else None, "traffic": traffic,
+                "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum per sample from one ncu capture "
+                                 "(16-detector cut), scaled by samples to this launch") if traffic else None,
                 "kernel": "%s<%s> (gather + FFT Toeplitz + scatter)"
                           % ("k_filter_half" if whole == 2 else "k_filter_fft",
                              "float" if prec == M.MM_FP32_MIXED else "double"),

@@ -493,14 +493,23 @@ def run_scale(args, world, rank, local):
         ctx.apply_A(out, out=torch.empty_like(out))
         if name == "mixed":
             ctx.set_option("inner_tol", args.inner_tol)
-            ctx.set_option("harvest", args.m_max)
             t_bd, (_, ibd) = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter,
                                                      out=out))
+            # coarse space, once per scan: k = 64 Ritz vectors need a Lanczos sequence longer than 64, so
+            # the harvested M_BD run is carried to a tighter inner tolerance than the timed one
+            m_h = max(args.m_max, 160)
+            ctx.set_option("inner_tol", 1e-13)
+            ctx.set_option("harvest", m_h)
+            t_h, _ = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=out))
             ctx.set_option("harvest", 0)
+            ctx.set_option("inner_tol", args.inner_tol)
             t_c, k = timed(lambda: ctx.build_coarse_from_solve(k=64))
+            harvested = int(ctx.get_option("harvested"))
+            t_c += t_h
             t_2l, (_, i2l) = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.max_iter,
                                                      out=out))
             res[name] = {"m_bd_s": t_bd, "m_bd_iters": ibd[0]["iters"], "coarse_s": t_c, "k": k,
+                         "coarse_from": f"Lanczos vectors of an M_BD run ({harvested} kept)",
                          "two_level_s": t_2l, "two_level_iters": i2l[0]["iters"],
                          "true_rel_res": i2l[0]["true_rel_res"]}
         else:

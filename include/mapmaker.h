@@ -222,8 +222,12 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * PCG run between float64-accurate refinements (default 2e-6);
  * "half_transform": 1 (default) lets a whole block of N real samples run as
  * one N/2-point complex transform per CTA (paired real-spectrum step), 0
- * keeps two blocks per N-point transform.  Errors: MM_ERR_ARG for an
- * unknown name or value. */
+ * keeps two blocks per N-point transform; "coarse_prefix": 1 (default) forms
+ * the per-RHS coarse products A_i Z of an uneven-length two-level batch from
+ * products over whole blocks computed once per coarse space (block-diagonal
+ * W; needs the same block boundaries in every detector) plus the one partly
+ * covered block per detector, 0 forms every A_i Z directly.  Errors:
+ * MM_ERR_ARG for an unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
 /* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"

@@ -62,6 +62,7 @@ struct Plan {
     int f64 = 0;
     int nrhs = 0;
     std::vector<int64_t> lens;
+    std::vector<int64_t> starts;   // per right-hand side: samples before it (per detector) are inactive
     DevBuf segs;
     int n_work = 0;
 };
@@ -84,6 +85,7 @@ struct mm_ctx {
     int opt_autotune = 1;
     int opt_half = 1;              // allow whole blocks as half-length complex transforms
     int opt_harvest = 0;           // Lanczos vectors kept from an M_BD solve (0: off)
+    int opt_coarse_prefix = 1;     // uneven-length batches: A_i Z from block-prefix products (0: directly)
     int opt_apply_prec = 0;        // mm_apply_A precision: 0 context, 1 float64, 2 double-float
     double opt_inner_tol = 2e-6;   // floor of the float32-operator PCG tolerance between refinements
     double last_apply_ms = 0.0;
@@ -146,6 +148,10 @@ struct mm_ctx {
     // per right-hand-side coarse operators for batches of uneven length
     bool coarse_per_rhs = false;
     DevBuf d_AZr, d_Einvr;
+    // block-prefix coarse products T[m] = A_(first m blocks of every detector) Z,
+    // [(blocks per detector + 1)][k][n_pix][4], for uneven-length batches
+    DevBuf d_Tpref;
+    bool tpref_valid = false;
     // asynchronous stepping
     RhsState* h_st_pinned = nullptr;
     int h_st_pinned_n = 0;
@@ -605,8 +611,11 @@ mm_status build_half_tables(mm_ctx* ctx, FftTables& ft, const FftPasses& fpM, in
 
 // Segment list: for every block, chunk and right-hand side, pairs of segments
 // that share a band (and halo).
+// starts (optional, per right-hand side): the first starts[r] samples of every
+// detector are inactive; each start must fall on a block boundary (whole
+// blocks are skipped), as the block-prefix coarse products use it.
 mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, int variant, int L,
-                    int whole, int V, Plan** out) {
+                    int whole, int V, Plan** out, const std::vector<int64_t>& starts = {}) {
     FftPasses fp{};
     int logL = 0;
     if (variant == 2) {
@@ -615,7 +624,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     }
     for (auto& p : ctx->plans)
         if (p->variant == variant && p->L == L && p->V == V && p->whole == whole && p->f64 == f64 &&
-            p->nrhs == nrhs && p->lens == lens) {
+            p->nrhs == nrhs && p->lens == lens && p->starts == starts) {
             *out = p.get();
             return MM_OK;
         }
@@ -640,6 +649,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
                 int64_t hi = o1;
                 if (!lens.empty()) hi = std::min(hi, det0 + lens[r]);
                 if (c0 >= hi) continue;
+                if (!starts.empty() && o0 < det0 + starts[r]) continue;
                 Seg s{};
                 s.out0 = c0;
                 s.lo = o0;
@@ -668,6 +678,7 @@ mm_status make_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& 
     p->f64 = f64;
     p->nrhs = nrhs;
     p->lens = lens;
+    p->starts = starts;
     p->n_work = (int)(single ? segs.size() : segs.size() / 2);
     CK(p->segs.ensure(std::max<size_t>(1, segs.size()) * sizeof(Seg)));
     if (!segs.empty())
@@ -802,7 +813,8 @@ mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_
     return MM_OK;
 }
 
-mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, Plan** out) {
+mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& lens, Plan** out,
+                   const std::vector<int64_t>& starts = {}) {
     int variant = ctx->opt_filter;
     int L = 0, V = 0, whole = 0;
     if (variant == 0 && ctx->opt_fft_len == 0 && ctx->opt_fft_log2 == 0 && ctx->opt_autotune && !ctx->capturing) {
@@ -811,11 +823,11 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
         TuneKey key{f64, ctx->lam, ctx->n_blocks, 1, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
         for (auto& kv : tune_cache())
             if (kv.first == key && (ctx->opt_half || kv.second.whole != 2)) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
-                                                  kv.second.whole, kv.second.V, out);
+                                                  kv.second.whole, kv.second.V, out, starts);
         TuneVal best{};
         TRY(autotune_plan(ctx, f64, 1, {}, &best));
         tune_record(key, best);
-        return make_plan(ctx, f64, nrhs, lens, best.variant, best.L, best.whole, best.V, out);
+        return make_plan(ctx, f64, nrhs, lens, best.variant, best.L, best.whole, best.V, out, starts);
     }
     if (variant == 0) variant = (ctx->lam <= 32) ? 1 : 2;
     if (variant == 2) {
@@ -833,7 +845,7 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
         const size_t sm = direct_smem_bytes(V, ctx->lam, f64 != 0);
         if (sm > 200 * 1024) return fail(ctx, MM_ERR_ARG, "direct filter tile plus halo exceeds shared memory");
     }
-    return make_plan(ctx, f64, nrhs, lens, variant, L, whole, V, out);
+    return make_plan(ctx, f64, nrhs, lens, variant, L, whole, V, out, starts);
 }
 
 // dst (V4<T>[nrhs][n_pix], zeroed by the caller) += P^T W (P src | d).
@@ -1162,6 +1174,7 @@ mm_status orthonormalise(mm_ctx* ctx, DevBuf& X, int kin, int* kout) {
 
 // Given Z (ctx->d_Z, k columns), form AZ, E = Z^T A Z and E^-1.
 mm_status finish_coarse(mm_ctx* ctx) {
+    ctx->tpref_valid = false;
     const int k = ctx->k;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     CK(ctx->d_AZ.ensure((size_t)k * n * 8));
@@ -1180,6 +1193,7 @@ mm_status finish_coarse(mm_ctx* ctx) {
     std::vector<double> L = E, Einv;
     if (!host_cholesky(L, k)) {
         ctx->k = 0;
+    ctx->tpref_valid = false;
         return fail(ctx, MM_ERR_SINGULAR, "coarse operator E = Z^T A Z is not positive definite");
     }
     host_spd_inverse_from_chol(L, k, Einv);
@@ -1196,13 +1210,77 @@ namespace {
 // basis Z is shared, AZ_i = A_i Z and E_i = Z^T A_i Z use each right-hand
 // side's own A_i (its first rhs_len[i] samples per detector), so that
 // M_2l,i A_i Z = Z holds for every i (Sect. 3.2, Eq. ident).
-mm_status coarse_for_lens(mm_ctx* ctx) {
+// Block boundaries relative to the detector start when every detector has the
+// same ones (then the first L samples of each detector cover the same blocks).
+static bool uniform_block_bounds(const mm_ctx* ctx, std::vector<int64_t>* rel) {
+    rel->clear();
+    if (ctx->n_t <= 0 || ctx->n_samples % ctx->n_t != 0) return false;
+    const int64_t n_det = ctx->n_samples / ctx->n_t;
+    std::vector<std::vector<int64_t>> per(n_det);
+    for (int b = 0; b < ctx->n_blocks; ++b) {
+        const int64_t o0 = ctx->block_off[b], d = o0 / ctx->n_t;
+        if (d < 0 || d >= n_det || ctx->block_off[b + 1] > (d + 1) * ctx->n_t) return false;
+        per[d].push_back(o0 - d * ctx->n_t);
+    }
+    for (int64_t d = 0; d < n_det; ++d)
+        if (per[d] != per[0]) return false;
+    *rel = per[0];
+    if (rel->empty() || (*rel)[0] != 0) return false;
+    rel->push_back(ctx->n_t);
+    return true;
+}
+
+// A_i Z for right-hand sides of uneven length.  W is block diagonal, so with
+// the same block boundaries in every detector A_i Z is the product over the
+// blocks that lie wholly inside the first L_i samples, T[m_i] (computed once
+// per coarse space: one product per block column, then prefix sums), plus the
+// product over the one partly covered block of each detector.  Otherwise the
+// products are formed directly for every right-hand side.
+mm_status coarse_products_for_lens(mm_ctx* ctx, bool f64) {
     const int k = ctx->k, R = ctx->nrhs;
     const int64_t n = (int64_t)ctx->n_pix * 4;
-    const bool f64 = !is_f32(ctx);
-    std::vector<int64_t> lens_rep;
-    for (int r = 0; r < R; ++r)
-        for (int c = 0; c < k; ++c) lens_rep.push_back(ctx->lens[r]);
+    std::vector<int64_t> rel;
+    const bool prefix = ctx->opt_coarse_prefix && uniform_block_bounds(ctx, &rel) &&
+                        (double)(rel.size() + 1) * k * n * 8 * 3 <= 6.0e9;   // D, T and a replicated Z
+    std::vector<int64_t> lens_rep, starts_rep;
+    std::vector<int> full(R, 0);
+    for (int r = 0; r < R; ++r) {
+        if (prefix)
+            while (full[r] + 1 < (int)rel.size() && rel[full[r] + 1] <= ctx->lens[r]) ++full[r];
+        for (int c = 0; c < k; ++c) {
+            lens_rep.push_back(ctx->lens[r]);
+            starts_rep.push_back(prefix ? rel[full[r]] : 0);
+        }
+    }
+    if (prefix && !ctx->tpref_valid) {
+        const int nbd = (int)rel.size() - 1;
+        std::vector<int64_t> lc, sc;
+        for (int m = 0; m < nbd; ++m)
+            for (int c = 0; c < k; ++c) {
+                lc.push_back(rel[m + 1]);
+                sc.push_back(rel[m]);
+            }
+        DevBuf zcol, D;
+        CK(zcol.ensure((size_t)nbd * k * n * 8));
+        for (int m = 0; m < nbd; ++m)
+            CK(cudaMemcpyAsync(zcol.as<double>() + (size_t)m * k * n, ctx->d_Z.p, (size_t)k * n * 8,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(D.ensure((size_t)nbd * k * n * 8));
+        Plan* pcol = nullptr;
+        TRY(get_plan(ctx, f64, nbd * k, lc, &pcol, sc));
+        TRY(apply_A_dev(ctx, f64, zcol.as<V4<double>>(), D.as<V4<double>>(), nbd * k, pcol));
+        // T[0] = 0, T[m + 1] = T[m] + D[m]
+        CK(ctx->d_Tpref.ensure((size_t)(nbd + 1) * k * n * 8));
+        CK(cudaMemsetAsync(ctx->d_Tpref.p, 0, (size_t)k * n * 8, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_Tpref.as<double>() + (size_t)k * n, D.p, (size_t)nbd * k * n * 8,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int m = 1; m < nbd; ++m)
+            launch_axpy_masked(ctx->d_Tpref.as<double>() + (size_t)(m + 1) * k * n,
+                               ctx->d_Tpref.as<double>() + (size_t)m * k * n, (int64_t)k * n, 1, nullptr, ctx->stream);
+        CKL();
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->tpref_valid = true;
+    }
     DevBuf zrep;
     CK(zrep.ensure((size_t)R * k * n * 8));
     for (int r = 0; r < R; ++r)
@@ -1210,8 +1288,24 @@ mm_status coarse_for_lens(mm_ctx* ctx) {
                            cudaMemcpyDeviceToDevice, ctx->stream));
     CK(ctx->d_AZr.ensure((size_t)R * k * n * 8));
     Plan* plan = nullptr;
-    TRY(get_plan(ctx, f64, R * k, lens_rep, &plan));
+    TRY(get_plan(ctx, f64, R * k, lens_rep, &plan, prefix ? starts_rep : std::vector<int64_t>{}));
     TRY(apply_A_dev(ctx, f64, zrep.as<V4<double>>(), ctx->d_AZr.as<V4<double>>(), R * k, plan));
+    if (prefix) {
+        for (int r = 0; r < R; ++r)
+            if (full[r] > 0)
+                launch_axpy_masked(ctx->d_AZr.as<double>() + (size_t)r * k * n,
+                                   ctx->d_Tpref.as<double>() + (size_t)full[r] * k * n, (int64_t)k * n, 1, nullptr,
+                                   ctx->stream);
+        CKL();
+    }
+    return MM_OK;
+}
+
+mm_status coarse_for_lens(mm_ctx* ctx) {
+    const int k = ctx->k, R = ctx->nrhs;
+    const int64_t n = (int64_t)ctx->n_pix * 4;
+    const bool f64 = !is_f32(ctx);
+    TRY(coarse_products_for_lens(ctx, f64));
     DevBuf dG;
     CK(dG.ensure((size_t)R * k * k * 8));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(k, 2) * sizeof(double) + 64));
@@ -1331,6 +1425,7 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     destroy_graph(ctx);
     ctx->have_pointing = ctx->have_bd = false;
     ctx->k = 0;
+    ctx->tpref_valid = false;
     ctx->have_lastb = false;
     ctx->plans.clear();
     ctx->n_samples = n_samples;
@@ -1404,6 +1499,7 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
     if (n_dropped_out) *n_dropped_out = dropped;
     ctx->have_bd = true;
     ctx->k = 0;
+    ctx->tpref_valid = false;
     return MM_OK;
 }
 
@@ -1553,6 +1649,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     const int n_pix = ctx->n_pix;
     const int64_t n = (int64_t)n_pix * 4;
     ctx->k = 0;
+    ctx->tpref_valid = false;
     TRY(ensure_work(ctx, 1, 128));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * (m_max + 2) * 8 + 64));
     CK(ctx->d_W.ensure((size_t)(m_max + 1) * n * 8));
@@ -1720,6 +1817,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     CK(dC.ensure(C.size() * 8));
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     ctx->k = 0;
+    ctx->tpref_valid = false;
     TRY(ensure_work(ctx, 1, 128));
     CK(ctx->d_Z.ensure((size_t)ksel * n * 8));
     launch_combo(ctx->d_harv.as<double>(), n, m, dC.as<double>(), ksel, ctx->d_Z.as<double>(), n, n, ctx->stream);
@@ -1741,6 +1839,7 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     CK(cudaSetDevice(ctx->device));
     const int64_t n = (int64_t)ctx->n_pix * 4;
     ctx->k = 0;
+    ctx->tpref_valid = false;
     DevBuf in3;
     const double* src = Z;
     if (mem == MM_HOST) {
@@ -2127,6 +2226,8 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_autotune = v ? 1 : 0;
     } else if (n == "half_transform") {
         ctx->opt_half = v ? 1 : 0;
+    } else if (n == "coarse_prefix") {
+        ctx->opt_coarse_prefix = v ? 1 : 0;
     } else if (n == "inner_tol") {
         if (!(value > 0.0) || value > 1e-2) return fail(ctx, MM_ERR_ARG, "inner_tol must lie in (0, 1e-2]");
         ctx->opt_inner_tol = value;
@@ -2162,6 +2263,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "time_filter") *value = ctx->opt_time_filter;
     else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "half_transform") *value = ctx->opt_half;
+    else if (n == "coarse_prefix") *value = ctx->opt_coarse_prefix;
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;
     else if (n == "apply_precision") *value = ctx->opt_apply_prec;

@@ -500,7 +500,8 @@ def run_scale(args, world, rank, local):
             m_h = max(args.m_max, 160)
             ctx.set_option("inner_tol", 1e-13)
             ctx.set_option("harvest", m_h)
-            t_h, _ = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=out))
+            t_h, _ = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=min(args.tol, 1e-12), max_iter=args.max_iter,
+                                             out=out))
             ctx.set_option("harvest", 0)
             ctx.set_option("inner_tol", args.inner_tol)
             t_c, k = timed(lambda: ctx.build_coarse_from_solve(k=64))

@@ -13,4 +13,8 @@ Parity unpinned: none of the functions here; the paper's own iteration counts
 (Sect. 7) are qualitative and are not used as pins.
 """
 from .mapmaking import *  # noqa: F401,F403
-from .mapmaking import __all__  # noqa: F401
+from .mapmaking import __all__ as _all_mm
+from .templates import *  # noqa: F401,F403
+from .templates import __all__ as _all_t
+
+__all__ = list(_all_mm) + list(_all_t)

@@ -12,7 +12,7 @@ elevation scans at 0.4 deg/s over a small patch, polarisation-sensitive
 detectors behind a rotating half-wave plate) at the sizes named in ``CONFIGS``.
 """
 from .scan import (Scan, CONFIGS, make_scan, make_sky, make_noise, make_tod,
-                   toeplitz_band, scan_from_config, mc_lengths)
+                   toeplitz_band, scan_from_config, mc_lengths, make_templates, AZ_BIN_PX)
 
 __all__ = ["Scan", "CONFIGS", "make_scan", "make_sky", "make_noise", "make_tod",
-           "toeplitz_band", "scan_from_config", "mc_lengths"]
+           "toeplitz_band", "scan_from_config", "mc_lengths", "make_templates", "AZ_BIN_PX"]

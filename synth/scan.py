@@ -102,13 +102,17 @@ def toeplitz_band(half_bw: int, f_knee: float, alpha: float = 1.0,
 def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
               f_knee=1.0, alpha: float = 1.0, sigma: float = 1.0, seed: int = 0,
               speed: float = SCAN_SPEED_PX, flag_frac: float = 0.0,
-              fs: float = FS_HZ) -> Scan:
+              fs: float = FS_HZ, hwp: bool = True) -> Scan:
     """Back-and-forth raster scan of an nx x ny patch by ``n_det`` detectors.
 
     Azimuth: a triangle wave over [0, nx) at ``speed`` pixels per sample with
     a random phase per detector.  Elevation: a slow drift that crosses the
     patch once per detector timeline, with detector offsets spread over a
-    quarter of the patch height.  HWP angle psi ~ U[0, pi) i.i.d. per sample.
+    quarter of the patch height.  HWP angle psi ~ U[0, pi) i.i.d. per sample;
+    with ``hwp=False`` there is no half-wave plate: detector d keeps the
+    polarisation angle (d mod 4) pi/4 of its place in the focal plane, turned
+    slowly by the sky rotation (pi/4 over the timeline), so the polarised
+    signal varies on scan time scales as in the paper's scans.
     ``f_knee`` is a scalar or a (lo, hi) range drawn uniformly per detector.
     A fraction ``flag_frac`` of samples is flagged (pixel -1).
     """
@@ -133,6 +137,10 @@ def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
         np.add(iy, ix, out=pix[d * n_t:(d + 1) * n_t])
     psi = rng.random(N, dtype=np.float32)
     psi *= np.float32(np.pi)
+    if not hwp:
+        rot = (np.pi / 4.0) * t / n_t
+        for d in range(n_det):
+            psi[d * n_t:(d + 1) * n_t] = np.mod((d % 4) * (np.pi / 4.0) + rot, np.pi).astype(np.float32)
     np.minimum(psi, np.nextafter(np.float32(np.pi), np.float32(0)), out=psi)
     if flag_frac > 0:
         pix[rng.random(N, dtype=np.float32) < flag_frac] = -1
@@ -148,7 +156,39 @@ def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
     return Scan(nx=nx, ny=ny, n_det=n_det, n_t=n_t, n_int=n_int, half_bw=half_bw,
                 pix=pix, psi=psi, block_off=block_off, block_band=block_band,
                 band=band, f_knee=fk, seed=seed,
-                meta=dict(alpha=alpha, sigma=sigma, fs=fs, speed=speed, flag_frac=flag_frac))
+                meta=dict(alpha=alpha, sigma=sigma, fs=fs, speed=speed, flag_frac=flag_frac, x0=x0, hwp=hwp))
+
+
+# Ground-pickup bins of 0.08 deg (Sect. 5) with ~1.7' pixels: 2.8 pixels of azimuth per bin.
+AZ_BIN_PX = 0.08 * 60.0 / 1.7
+
+
+def make_templates(scan: Scan, bin_px: float = AZ_BIN_PX):
+    """Scan geometry of the template filters: subscans and azimuth bins.
+
+    A subscan is one azimuth sweep of the back-and-forth raster (the samples
+    between two turnarounds), cut at block edges so every subscan lies in
+    one stationary block.  The azimuth bin of a sample is floor(az / bin_px)
+    over the sweep range [0, nx).  Returns (sub_off int64 [n_sub + 1],
+    az_bin int32 [N], n_az_bins).
+    """
+    x0 = np.asarray(scan.meta["x0"], dtype=np.float64)
+    speed = float(scan.meta.get("speed", SCAN_SPEED_PX))
+    nx, n_t = scan.nx, scan.n_t
+    t = np.arange(n_t, dtype=np.float64)
+    n_bins = int(np.ceil(nx / bin_px))
+    az_bin = np.empty(scan.n_samples, dtype=np.int32)
+    cuts = [np.asarray(scan.block_off, dtype=np.int64)]
+    for d in range(scan.n_det):
+        raw = x0[d] + speed * t
+        sweep = np.floor(raw / nx).astype(np.int64)
+        pos = np.mod(raw, 2.0 * nx)
+        np.subtract(2.0 * nx, pos, out=pos, where=pos >= nx)
+        az_bin[d * n_t:(d + 1) * n_t] = np.minimum((pos / bin_px).astype(np.int32), n_bins - 1)
+        turns = np.nonzero(np.diff(sweep))[0] + 1
+        cuts.append(turns.astype(np.int64) + d * n_t)
+    sub_off = np.unique(np.concatenate(cuts))
+    return sub_off, az_bin, n_bins
 
 
 def make_sky(n_pix: int, seed: int = 0, sigma_i: float = 1.0, sigma_qu: float = 0.1) -> np.ndarray:

@@ -23,7 +23,8 @@ Readings where the paper is silent (each also listed in the design notes):
   * W is diagonal with one weight w_b per stationary block (the block's c_0);
   * B holds the Legendre polynomials P_0..P_K of u = 2 (i + 1/2) / m - 1,
     i = 0..m-1 the sample index inside a subscan of m samples; every subscan
-    lies inside one block;
+    lies inside one block; a subscan of m <= K samples takes order m - 1
+    (its polynomials then span every timeline on it, and F_B removes it);
   * G has one column per azimuth bin and per block (one constant-elevation
     scan = one block); samples with bin -1 are in no column;
   * the filters act on every sample of the timeline, flagged ones included
@@ -85,7 +86,7 @@ def filter_poly(y, wv, sub_off, order) -> np.ndarray:
         a, b = int(sub_off[s]), int(sub_off[s + 1])
         if b <= a:
             continue
-        B = legendre_basis(b - a, order)
+        B = legendre_basis(b - a, min(order, b - a - 1))
         w = wv[a:b]
         WB = w[:, None] * B
         coef = np.linalg.solve(B.T @ WB, WB.T @ y[a:b])

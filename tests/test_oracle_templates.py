@@ -56,6 +56,15 @@ def test_polynomial_filter_annihilates_its_templates(order):
     assert np.abs(O.filter_poly(z, tp.sample_weight(), tp.sub_off, order)).max() > 1e-3
 
 
+def test_subscans_shorter_than_the_order_are_removed_entirely():
+    """m <= K samples: the fit space (order m - 1) spans every timeline on the subscan, so F_B gives 0."""
+    y = np.arange(1.0, 8.0)
+    sub_off = np.array([0, 1, 3, 7])
+    out = O.filter_poly(y, np.ones(7), sub_off, 3)
+    assert np.abs(out[:3]).max() < 1e-12
+    assert np.abs(out[3:]).max() < 1e-12          # 4 samples, cubic fit: exact as well
+
+
 def test_polynomial_filter_keeps_the_orthogonal_complement():
     """A timeline orthogonal to every subscan's polynomials passes as W y (F_B = W - W B (...) B^T W)."""
     scan, tp = tproblem(order=2, ground=False)

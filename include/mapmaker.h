@@ -265,6 +265,39 @@ mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int me
 mm_status mm_solve_launch(mm_ctx* ctx, int32_t n_iter);
 mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done);
 
+/* Template filters of ground-based scans (Sect. 2.1, Eq. filt, Eq.
+ * filtnoise, Eq. unb; Sect. 4; Sect. 5.1).  After this call the context's
+ * operator is A = P^T F P and b = P^T F d with the symmetric simplified filter
+ * F = F_B W^-1 F_G W^-1 F_B, F_X = W - W X (X^T W X)^-1 X^T W, W = w_b I on
+ * block b (w_b = c_0 of the block's band: the pointing must have been set up
+ * with half_bw = 0, white weights).
+ *  poly_order      K in -1..3: X = B holds the Legendre polynomials P_0..P_K
+ *                  of u = 2 (i + 1/2)/m - 1 over each subscan of m samples
+ *                  (order min(K, m - 1) on subscans of m <= K samples);
+ *                  -1: no polynomial filter.
+ *  subscan_off     [n_subscans + 1] HOST array of sample offsets, 0 ..
+ *                  n_samples, strictly increasing, every subscan inside one
+ *                  block (block boundaries are subscan boundaries).  May be
+ *                  NULL when poly_order < 0.
+ *  az_bin          [n_samples] azimuth bin of every sample (-1: none), host
+ *                  or device per `mem`; X = G holds one indicator column per
+ *                  bin and per block (a block is one constant-elevation
+ *                  scan).  NULL: no ground filter.  1 <= n_az_bins <= 8192.
+ *  qu_only         1: pointing rows (0, cos 2psi, sin 2psi) -- the
+ *                  differenced timeline d^- of Sect. 5.1 (Eq. d-); I is not
+ *                  solved for (M_BD inverts the 2x2 (Q, U) block, a pixel
+ *                  needs 2 hits and rcond >= rcond_min of that block).
+ * The filters act on every sample, flagged ones included.  Calling with
+ * poly_order = -1, az_bin = NULL and qu_only = 0 restores the band weight.
+ * Clears M_BD and the coarse space (rebuild them), sets "fp64_products" to 1
+ * (native float64; double-float products are not available here).
+ * Right-hand sides of uneven length (rhs_len) are not supported with
+ * templates (MM_ERR_ARG at solve time).  The longest block and the bins must
+ * fit shared memory: 8 bytes per sample + 12 bytes per bin <= 220 KB.
+ * Errors: MM_ERR_ARG, MM_ERR_STATE (no pointing), MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, const int64_t* subscan_off,
+                           const int32_t* az_bin, int32_t n_az_bins, int32_t qu_only, int mem);
+
 /* M_2l applied without allocating device memory during the call (the paper
  * has no counterpart; this is a deployment variant of mm_apply_precond).
  * For callers that must not call cudaMalloc/cudaFree while they run: latency-

@@ -10,6 +10,8 @@
 #include <memory>
 #include <string>
 #include <vector>
+#include <map>
+#include <array>
 
 #include "../../include/mapmaker.h"
 #include "common.cuh"
@@ -148,6 +150,11 @@ struct mm_ctx {
     // per right-hand-side coarse operators for batches of uneven length
     bool coarse_per_rhs = false;
     DevBuf d_AZr, d_Einvr;
+    // template filters (mm_set_templates): F = F_B W^-1 F_G W^-1 F_B
+    bool tmpl_on = false;
+    int tmpl_order = -1, tmpl_bins = 0, tmpl_qu = 0;
+    int64_t tmpl_max_block = 0;
+    DevBuf d_tsub, d_tblk, d_tginv, d_taz, d_twb;
     // block-prefix coarse products T[m] = A_(first m blocks of every detector) Z,
     // [(blocks per detector + 1)][k][n_pix][4], for uneven-length batches
     DevBuf d_Tpref;
@@ -882,7 +889,25 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         e1 = pr.second;
     }
     a.csdf = ctx->d_csdf.as<float4>();
-    if (plan->variant == 2) {
+    if (ctx->tmpl_on) {
+        if (!plan->lens.empty() || !plan->starts.empty())
+            return fail(ctx, MM_ERR_ARG, "template filters: right-hand sides of uneven length are not supported");
+        if (plan->f64 == 2)
+            return fail(ctx, MM_ERR_ARG, "template filters: double-float products are not available (float64 is)");
+        TmplArgs t{};
+        t.block_off = ctx->d_block_off.as<int64_t>();
+        t.n_blocks = ctx->n_blocks;
+        t.max_block = ctx->tmpl_max_block;
+        t.w_block = ctx->d_twb.as<double>();
+        t.sub_off = ctx->d_tsub.as<int64_t>();
+        t.blk_sub = ctx->d_tblk.as<int32_t>();
+        t.ginv = ctx->d_tginv.as<double>();
+        t.order = ctx->tmpl_order;
+        t.az = ctx->tmpl_bins > 0 ? ctx->d_taz.as<int32_t>() : nullptr;
+        t.n_bins = ctx->tmpl_bins;
+        t.qu_only = ctx->tmpl_qu;
+        launch_filter_tmpl(a, t, plan->nrhs, plan->f64 == 1, from_tod, ctx->stream);
+    } else if (plan->variant == 2) {
         FftTables& ft = plan->ft;
         a.H = ft.H.p;
         a.tw = ft.tw.p;
@@ -1104,7 +1129,7 @@ mm_status bd_for_lens(mm_ctx* ctx) {
                          ctx->n_t, d_sorted.as<int64_t>(), R, sums.as<double>(), ctx->n_pix, ctx->stream);
     CK(bdsorted.ensure((size_t)R * ctx->n_pix * 6 * sizeof(double)));
     launch_bd_invert(sums.as<double>(), bdsorted.as<double>(), ctx->d_good.as<uint8_t>(), nullptr, ctx->n_pix, R, 0.0, 0,
-                     ctx->stream);
+                     ctx->stream, ctx->tmpl_on ? ctx->tmpl_qu : 0);
     CKL();
     CK(ctx->d_bd_rhs.ensure((size_t)R * ctx->n_pix * 6 * sizeof(double)));
     const size_t per = (size_t)ctx->n_pix * 6 * sizeof(double);
@@ -1465,8 +1490,112 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     CK(ctx->d_banddf.ensure(bdf.size() * 4));
     CK(cudaMemcpyAsync(ctx->d_banddf.p, bdf.data(), bdf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     ctx->have_csdf = false;
+    ctx->tmpl_on = false;
+    ctx->tmpl_qu = 0;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_pointing = true;
+    return MM_OK;
+}
+
+// Template filters of ground-based scans (Sect. 2.1, Eq. filtnoise; Sect. 4;
+// Sect. 5.1): subscan polynomials and azimuth-bin ground templates, white
+// block weights, optionally the differenced timeline's (0, cos, sin) rows.
+mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, const int64_t* subscan_off,
+                           const int32_t* az_bin, int32_t n_az_bins, int32_t qu_only, int mem) {
+    if (!ctx) return MM_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_set_templates: set the pointing first");
+    if (mem != MM_HOST && mem != MM_DEVICE) return fail(ctx, MM_ERR_ARG, "mem must be MM_HOST or MM_DEVICE");
+    ctx->have_bd = false;   // M_BD and any coarse space belong to the previous operator
+    ctx->k = 0;
+    ctx->tpref_valid = false;
+    if (poly_order < 0 && !az_bin && !qu_only) {
+        ctx->tmpl_on = false;
+        ctx->tmpl_qu = 0;
+        return MM_OK;
+    }
+    if (ctx->lam != 0)
+        return fail(ctx, MM_ERR_ARG, "template filters need white block weights: set the pointing with half_bw = 0");
+    if (poly_order < -1 || poly_order > 3) return fail(ctx, MM_ERR_ARG, "poly_order must be -1..3");
+    if (az_bin && (n_az_bins <= 0 || n_az_bins > 8192)) return fail(ctx, MM_ERR_ARG, "n_az_bins must be 1..8192");
+    const int64_t N = ctx->n_samples;
+    std::vector<int64_t> so;
+    if (poly_order >= 0) {
+        if (n_subscans <= 0 || !subscan_off) return fail(ctx, MM_ERR_ARG, "subscan offsets needed for poly_order >= 0");
+        so.assign(subscan_off, subscan_off + n_subscans + 1);
+    } else {
+        so = ctx->block_off;   // unused without polynomials
+    }
+    const int ns = (int)so.size() - 1;
+    if (so[0] != 0 || so[ns] != N) return fail(ctx, MM_ERR_ARG, "subscan_off must start at 0 and end at n_samples");
+    std::vector<int32_t> blk_sub(ctx->n_blocks + 1, 0);
+    {
+        int b = 0;
+        for (int s = 0; s < ns; ++s) {
+            if (so[s + 1] <= so[s]) return fail(ctx, MM_ERR_ARG, "subscan_off must be strictly increasing");
+            while (ctx->block_off[b + 1] <= so[s]) blk_sub[++b] = s;
+            if (so[s] < ctx->block_off[b] || so[s + 1] > ctx->block_off[b + 1])
+                return fail(ctx, MM_ERR_ARG, "every subscan must lie inside one block");
+        }
+        while (b < ctx->n_blocks) blk_sub[++b] = ns;
+        for (int bb = 0; bb < ctx->n_blocks; ++bb)
+            if (so[blk_sub[bb]] != ctx->block_off[bb])
+                return fail(ctx, MM_ERR_ARG, "block boundaries must be subscan boundaries");
+    }
+    // inverse Gram matrices of the Legendre columns P_0..P_Ks, Ks = min(K, m - 1), per subscan
+    std::vector<double> ginv((size_t)ns * 16, 0.0);
+    if (poly_order >= 0) {
+        std::map<int64_t, std::array<double, 16>> cache;
+        for (int s = 0; s < ns; ++s) {
+            const int64_t m = so[s + 1] - so[s];
+            auto it = cache.find(m);
+            if (it == cache.end()) {
+                const int K = (int)std::min<int64_t>(poly_order, m - 1), n = K + 1;
+                std::vector<double> G((size_t)n * n, 0.0), Ginv;
+                for (int64_t i = 0; i < m; ++i) {
+                    const double u = 2.0 * ((double)i + 0.5) / (double)m - 1.0;
+                    const double p[4] = {1.0, u, 1.5 * u * u - 0.5, (2.5 * u * u - 1.5) * u};
+                    for (int j = 0; j < n; ++j)
+                        for (int l = 0; l < n; ++l) G[(size_t)j * n + l] += p[j] * p[l];
+                }
+                if (!host_cholesky(G, n)) return fail(ctx, MM_ERR_ARG, "singular subscan Gram matrix");
+                host_spd_inverse_from_chol(G, n, Ginv);
+                std::array<double, 16> g{};
+                for (int j = 0; j < n; ++j)
+                    for (int l = 0; l < n; ++l) g[j * 4 + l] = Ginv[(size_t)j * n + l];
+                it = cache.emplace(m, g).first;
+            }
+            std::copy(it->second.begin(), it->second.end(), ginv.begin() + (size_t)s * 16);
+        }
+    }
+    std::vector<double> wb(ctx->n_blocks);
+    int64_t maxb = 0;
+    for (int b = 0; b < ctx->n_blocks; ++b) {
+        wb[b] = ctx->band[(size_t)ctx->block_band[b] * (ctx->lam + 1)];
+        maxb = std::max(maxb, ctx->block_off[b + 1] - ctx->block_off[b]);
+    }
+    const int nbins = az_bin ? n_az_bins : 0;
+    if (tmpl_smem_bytes(maxb, nbins, true) > smem_limit_bytes())
+        return fail(ctx, MM_ERR_ARG, "template filters: longest block plus azimuth bins exceed shared memory");
+    CK(ctx->d_tsub.ensure(so.size() * 8));
+    CK(ctx->d_tblk.ensure(blk_sub.size() * 4));
+    CK(ctx->d_tginv.ensure(ginv.size() * 8));
+    CK(ctx->d_twb.ensure(wb.size() * 8));
+    CK(cudaMemcpyAsync(ctx->d_tsub.p, so.data(), so.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_tblk.p, blk_sub.data(), blk_sub.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_tginv.p, ginv.data(), ginv.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_twb.p, wb.data(), wb.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (az_bin) {
+        CK(ctx->d_taz.ensure((size_t)N * 4));
+        CK(copy_in(ctx->d_taz.p, az_bin, (size_t)N * 4, mem, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tmpl_on = true;
+    ctx->tmpl_order = poly_order;
+    ctx->tmpl_bins = nbins;
+    ctx->tmpl_qu = qu_only ? 1 : 0;
+    ctx->tmpl_max_block = maxb;
+    ctx->p64 = 1;   // float64-accurate products of the template filter run in native float64
     return MM_OK;
 }
 
@@ -1490,7 +1619,7 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
                          ctx->d_block_band.as<int32_t>(), ctx->d_band64.as<double>(), ctx->lam + 1, ctx->n_blocks, 0,
                          ctx->n_t, d_len.as<int64_t>(), 1, ctx->d_sums.as<double>(), n_pix, ctx->stream);
     launch_bd_invert(ctx->d_sums.as<double>(), ctx->d_bd.as<double>(), ctx->d_good.as<uint8_t>(),
-                     ctx->d_dropped.as<int>(), n_pix, 1, rcond_min, 1, ctx->stream);
+                     ctx->d_dropped.as<int>(), n_pix, 1, rcond_min, 1, ctx->stream, ctx->tmpl_on ? ctx->tmpl_qu : 0);
     launch_flag_samples(ctx->d_pix.as<int32_t>(), ctx->d_good.as<uint8_t>(), ctx->n_samples, ctx->stream);
     CKL();
     int dropped = 0;
@@ -1559,7 +1688,8 @@ mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int 
     launch_map_in(xsrc, in4.as<V4<double>>(), nv, ctx->stream);
     CKL();
     Plan* plan = nullptr;
-    const int aprec = ctx->opt_apply_prec ? ctx->opt_apply_prec : (is_f32(ctx) ? 0 : 1);
+    int aprec = ctx->opt_apply_prec ? ctx->opt_apply_prec : (is_f32(ctx) ? 0 : 1);
+    if (ctx->tmpl_on && aprec == 2) aprec = 1;
     TRY(get_plan(ctx, aprec, nrhs, {}, &plan));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     TRY(apply_A_dev(ctx, aprec, in4.as<V4<double>>(), out4.as<V4<double>>(), nrhs, plan));

@@ -92,6 +92,24 @@ struct FilterArgs {
                            // from the timeline, giving the residual P^T W (d - P x) = b - A x; may be null
 };
 
+// Template filter F = F_B W^-1 F_G W^-1 F_B (white W = w_b I per block):
+// Legendre polynomials of each subscan and azimuth bins of each block.
+struct TmplArgs {
+    const int64_t* block_off;  // [n_blocks + 1]
+    int n_blocks;
+    int64_t max_block;         // longest block (shared memory size)
+    const double* w_block;     // [n_blocks] white weight of each block
+    const int64_t* sub_off;    // [n_sub + 1] subscans, each inside one block
+    const int32_t* blk_sub;    // [n_blocks + 1] first subscan of each block
+    const double* ginv;        // [n_sub][4][4] inverse Gram matrix of the subscan's Legendre columns
+    int order;                 // polynomial order K (-1: no polynomial filter)
+    const int32_t* az;         // [N] azimuth bin of each sample (-1: none); null: no ground filter
+    int n_bins;
+    int qu_only;               // 1: pointing rows (0, cos 2psi, sin 2psi) (differenced timeline)
+};
+void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s);
+size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64);
+
 // T = float or double; from_tod selects b = P^T W d (src is a TOD).
 void launch_filter_fft_f32(const FilterArgs& a, bool from_tod, cudaStream_t s);
 void launch_filter_fft_f64(const FilterArgs& a, bool from_tod, cudaStream_t s);
@@ -123,7 +141,7 @@ void launch_bd_accumulate(const int32_t* pix, const float* psi, const int64_t* b
                           double* sums /*[nrhs][n_pix][7]*/, int n_pix, cudaStream_t s);
 void launch_bd_invert(const double* sums, double* bd /*[nrhs][n_pix][6]*/, uint8_t* good,
                       int* n_dropped, int n_pix, int nrhs, double rcond_min, int set_good,
-                      cudaStream_t s);
+                      cudaStream_t s, int qu_only = 0);
 void launch_flag_samples(int32_t* pix, const uint8_t* good, int64_t n, cudaStream_t s);
 void launch_bd_apply(const double* bd, int bd_per_rhs, const V4<double>* x, V4<double>* y,
                      int n_pix, int nrhs, cudaStream_t s);

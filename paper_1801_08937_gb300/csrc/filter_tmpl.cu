@@ -1,0 +1,230 @@
+// Template-filtered product A x = P^T F P x (and P^T F d, P^T F (d - P x)) for
+// ground-based scans: F = F_B W^-1 F_G W^-1 F_B (Sect. 5.1) with the weighted
+// template filter F_X = W - W X (X^T W X)^-1 X^T W of Sect. 2.1 (Eq.
+// filtnoise), X = B the Legendre polynomials P_0..P_K of each azimuth sweep
+// (subscan) and X = G the azimuth-bin indicators of each constant-elevation
+// scan (Sect. 4), and W = w_b I on stationary block b (white noise, Sect.
+// 4.1).  With W constant on a block both filters are w_b times orthogonal
+// projections, so F = w_b (1 - Pi_B)(1 - Pi_G)(1 - Pi_B) on the block.
+//
+// One CTA per (block, right-hand side); the block's timeline lives in shared
+// memory through
+//   1. gather y = P x (rows (1, cos 2psi, sin 2psi), or (0, cos, sin) for the
+//      differenced timeline d^- of Sect. 5.1), or the timeline d, or d - P x;
+//   2. y -= B (B^T B)^-1 B^T y per subscan: one warp per subscan sums the
+//      moments sum_i y_i P_j(u_i), u_i = 2 (i + 1/2)/m - 1, and multiplies by
+//      the subscan's inverse Gram matrix (float64, precomputed on the host);
+//   3. y -= bin means of y over the block's azimuth bins (runs of equal bins
+//      in a warp are summed before one shared-memory atomic per run);
+//   4. step 2 again;
+//   5. z = w_b y scattered into the map (P^T), runs of equal pixels summed in
+//      the warp first.
+#include "filter_impl.cuh"
+
+namespace mm {
+
+constexpr int TMPL_NT = 512;
+
+__device__ __forceinline__ int shfl_down_t(int v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+// Sum of v over the run of lanes with equal key that starts at this lane
+// (valid on the run's first lane, `head`); runs are consecutive lanes.
+template <typename T>
+__device__ __forceinline__ T warp_run_sum(int key, T v, bool& head) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const int kprev = __shfl_up_sync(FULL, key, 1);
+    head = (lane == 0) || (key != kprev);
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const int end = above ? (__ffs(above) - 1) : 32;
+    const int need = (int)__reduce_max_sync(FULL, head ? (unsigned)(end - (int)lane) : 0u);
+#pragma unroll 1
+    for (int d = 1; d < need; d <<= 1) {
+        const T o = shfl_down_t(v, d);
+        if ((int)lane + d < end) v += o;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_all(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Legendre polynomials P_0..P_3 at u.
+template <typename T>
+__device__ __forceinline__ void legendre4(T u, T (&p)[4]) {
+    p[0] = T(1);
+    p[1] = u;
+    p[2] = T(1.5) * u * u - T(0.5);
+    p[3] = (T(2.5) * u * u - T(1.5)) * u;
+}
+
+// y -= B (B^T B)^-1 B^T y on every subscan of the block (one warp per subscan).
+template <typename T>
+__device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0) {
+    if (t.order < 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = TMPL_NT / 32;
+    const int K = t.order;
+    for (int s = t.blk_sub[blk] + warp; s < t.blk_sub[blk + 1]; s += nw) {
+        const int64_t s0 = t.sub_off[s];
+        const int m = (int)(t.sub_off[s + 1] - s0);
+        const int o = (int)(s0 - b0);
+        const T inv_m = T(2) / T(m);
+        T mom[4] = {T(0), T(0), T(0), T(0)};
+        for (int i = lane; i < m; i += 32) {
+            T p[4];
+            legendre4<T>(T(i) * inv_m + (inv_m * T(0.5) - T(1)), p);
+            const T v = y[o + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j <= K) mom[j] += v * p[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mom[j] = warp_sum_all(mom[j]);
+        // coefficients c = G^-1 mom (every lane holds the moments)
+        const double* gi = t.ginv + (int64_t)s * 16;
+        T c[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (j <= K && l <= K) acc += T(gi[j * 4 + l]) * mom[l];
+            c[j] = acc;
+        }
+        for (int i = lane; i < m; i += 32) {
+            T p[4];
+            legendre4<T>(T(i) * inv_m + (inv_m * T(0.5) - T(1)), p);
+            T fit = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j <= K) fit += c[j] * p[j];
+            y[o + i] -= fit;
+        }
+    }
+}
+
+template <typename T, bool FROM_TOD>
+__global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, const TmplArgs t) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int blk = blockIdx.x, rhs = blockIdx.y;
+    if (a.state && !a.state[rhs].active) return;
+    const int64_t b0 = t.block_off[blk];
+    const int nb = (int)(t.block_off[blk + 1] - b0);
+    T* y = reinterpret_cast<T*>(smraw);
+    T* gsum = y + ((nb + 1) & ~1);
+    int* gcnt = reinterpret_cast<int*>(gsum + t.n_bins);
+    const T iw = t.qu_only ? T(0) : T(1);
+    const V4<T>* xm = nullptr;
+    if (!FROM_TOD) xm = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix;
+    else if (a.xmap) xm = reinterpret_cast<const V4<T>*>(a.xmap) + (int64_t)rhs * a.n_pix;
+    // 1. gather
+    for (int i = threadIdx.x; i < nb; i += TMPL_NT) {
+        const int64_t ts = b0 + i;
+        T v = T(0);
+        if (FROM_TOD)
+            v = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + ts))
+                               : T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + ts));
+        if (xm) {
+            const int p = __ldg(a.pix + ts);
+            if (p >= 0) {
+                T c, s;
+                weights(a, ts, c, s);
+                const V4<T> m = ldmap<T>(xm + p);
+                const T px = iw * m.x + c * m.y + s * m.z;
+                v = FROM_TOD ? v - px : px;
+            }
+        }
+        y[i] = v;
+    }
+    for (int i = threadIdx.x; i < t.n_bins; i += TMPL_NT) {
+        gsum[i] = T(0);
+        gcnt[i] = 0;
+    }
+    __syncthreads();
+    // 2. polynomial templates
+    project_poly<T>(y, t, blk, b0);
+    __syncthreads();
+    // 3. ground template: bin means over the block
+    if (t.az && t.n_bins > 0) {
+        for (int base = 0; base < nb; base += TMPL_NT) {
+            const int i = base + threadIdx.x;
+            int g = -1;
+            T v = T(0);
+            if (i < nb) {
+                g = __ldg(t.az + b0 + i);
+                if (g >= t.n_bins) g = -1;   // out-of-range bins belong to no column
+                v = y[i];
+            }
+            bool head;
+            const T sv = warp_run_sum<T>(g, v, head);
+            const int cn = warp_run_sum<int>(g, (g >= 0) ? 1 : 0, head);
+            if (head && g >= 0) {
+                atomicAdd(gsum + g, sv);
+                atomicAdd(gcnt + g, cn);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += TMPL_NT) {
+            const int g = __ldg(t.az + b0 + i);
+            if (g >= 0 && g < t.n_bins) y[i] -= gsum[g] / T(gcnt[g]);
+        }
+        __syncthreads();
+        // 4. polynomial templates again
+        project_poly<T>(y, t, blk, b0);
+        __syncthreads();
+    }
+    // without a ground template F_B W^-1 F_B = w_b (1 - Pi_B)^2 = w_b (1 - Pi_B): one projection
+    // 5. weight and scatter
+    using Acc = typename AccT<T>::type;
+    V4<Acc>* q = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)rhs * a.n_pix;
+    const T wb = T(t.w_block[blk]);
+    for (int base = 0; base < nb; base += TMPL_NT) {
+        const int i = base + threadIdx.x;
+        int p = -1;
+        T z = T(0), c = T(0), s = T(0);
+        if (i < nb) {
+            const int64_t ts = b0 + i;
+            p = __ldg(a.pix + ts);
+            if (p >= 0) {
+                weights(a, ts, c, s);
+                z = wb * y[i];
+            }
+        }
+        scatter_vals<T>(p, iw * z, z * c, z * s, q);
+    }
+}
+
+size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64) {
+    const size_t e = f64 ? 8 : 4;
+    return (size_t)((max_block + 1) & ~1LL) * e + (size_t)n_bins * (e + 4);
+}
+
+template <typename T, bool FROM_TOD>
+static void launch_tmpl_t(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
+    const size_t sm = tmpl_smem_bytes(t.max_block, t.n_bins, sizeof(T) == 8);
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        configured = sm;
+    }
+    k_filter_tmpl<T, FROM_TOD><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
+    count_launches(1);
+}
+
+void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s) {
+    if (t.n_blocks <= 0 || nrhs <= 0) return;
+    if (f64) {
+        if (from_tod) launch_tmpl_t<double, true>(a, t, nrhs, s);
+        else launch_tmpl_t<double, false>(a, t, nrhs, s);
+    } else {
+        if (from_tod) launch_tmpl_t<float, true>(a, t, nrhs, s);
+        else launch_tmpl_t<float, false>(a, t, nrhs, s);
+    }
+}
+
+}  // namespace mm

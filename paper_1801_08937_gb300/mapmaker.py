@@ -57,6 +57,7 @@ SIGNATURES = [
     ("mm_solve_launch", C.c_int, [_VP, _I32]),
     ("mm_build_coarse_from_solve", C.c_int, [_VP, _I32, _D, C.POINTER(_I32)]),
     ("mm_solve_poll", C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32)]),
+    ("mm_set_templates", C.c_int, [_VP, _I32, _I32, _VP, _VP, _I32, _I32, C.c_int]),
 ]
 
 _lib = None
@@ -172,6 +173,14 @@ class Context:
         """Pointing and weight of a synthetic scan object (pix, psi, blocks, bands)."""
         self.setup_pointing(scan.pix, scan.psi, scan.block_off, scan.block_band, scan.band,
                             scan.n_pix, n_det=scan.n_det)
+
+    def set_templates(self, poly_order=-1, subscan_off=None, az_bin=None, n_az_bins=0, qu_only=False):
+        """Template filters F = F_B W^-1 F_G W^-1 F_B (mm_set_templates); subscan_off is host memory."""
+        so = None if subscan_off is None else np.ascontiguousarray(subscan_off, dtype=np.int64)
+        pa, m1, k1 = _arg(az_bin, np.int32)
+        self._check(self.lib.mm_set_templates(
+            self.h, int(poly_order), 0 if so is None else int(so.shape[0] - 1),
+            None if so is None else C.c_void_p(so.ctypes.data), pa, int(n_az_bins), int(bool(qu_only)), _mem(m1)))
 
     def build_bd(self, rcond_min: float = 1e-3) -> int:
         n = C.c_int32(0)

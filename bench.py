@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=2e-6)
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale"],
+    ap.add_argument("--poly-order", type=int, default=1, help="templates mode: subscan polynomial order")
+    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
                          "apply: A x alone (profiling)")
     ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
@@ -233,6 +234,8 @@ def main():
         return run_apply(args, world, rank, local)
     if args.mode == "scale":
         return run_scale(args, world, rank, local)
+    if args.mode == "templates":
+        return run_templates(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -447,6 +450,112 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------- template filters (the paper's ground-based filtering) ----------------
+def run_templates(args, world, rank, local):
+    """The paper's filters (Sect. 4, 5.1) on the config's scan geometry without a half-wave plate: white
+    noise, polarisation maps from the differenced timeline, subscan Legendre polynomials of order
+    --poly-order and the azimuth-bin ground template in F = F_B W^-1 F_G W^-1 F_B.  Per map: M_2l (k Ritz
+    vectors from the Lanczos sequence of a first M_BD run) against M_BD; the filtered A x alone against
+    the HBM roofline (pix, psi and azimuth bin: 12 B/sample)."""
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    # the filters leave a near-null space of slowly varying Q/U patterns (hundreds of modes at c1): the
+    # coarse space needs the largest k and well converged Ritz vectors; untouched defaults become those
+    if args.k == 32:
+        args.k = 128
+    if args.coarse == "lanczos" and args.m_max == 120:
+        args.coarse, args.m_max = "arnoldi", 400
+    if args.eps_arn == 1e-6:
+        args.eps_arn = 1e-12
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t_gen = time.time()
+    over = {"n_det": args.n_det} if args.n_det else {}
+    scan = synth.scan_from_config(args.config, seed=rank, half_bw=0, f_knee=0.0, hwp=False, **over)
+    sub_off, az, n_bins = synth.make_templates(scan)
+    sky = synth.make_sky(scan.n_pix, rank)
+    sky[:, 0] = 0.0
+    tod = torch.from_numpy(synth.make_tod(scan, sky, synth.make_noise(scan, rank)).astype(np.float32)).to(dev)
+    az_d = torch.from_numpy(az).to(dev)
+    t_gen = time.time() - t_gen
+    out = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
+    prec = M.MM_FP32_MIXED if args.precision == "mixed" else M.MM_FP64
+    if prec == M.MM_FP64:
+        tod = tod.double()
+    ctx = M.Context(local, stream.cuda_stream, prec)
+    ctx.set_option("inner_tol", args.inner_tol)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r = fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / 1e3, r
+
+    def setup():
+        ctx.setup_scan(scan)
+        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, True)
+        dropped = ctx.build_bd(1e-3)
+        if args.coarse == "arnoldi":
+            return dropped, ctx.build_coarse(ctx.rhs(tod)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
+        ctx.set_option("harvest", args.m_max)
+        ctx.solve(tod, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=out)
+        ctx.set_option("harvest", 0)
+        return dropped, ctx.build_coarse_from_solve(k=args.k)
+
+    res = {}
+    if args.steps > 0:
+        t_setup, (dropped, k) = timed(setup)
+    else:   # A x alone
+        ctx.setup_scan(scan)
+        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, True)
+        t_setup, dropped, k = 0.0, ctx.build_bd(1e-3), 0
+    for name, pc in ((("two_level", M.MM_PRECOND_2L), ("m_bd", M.MM_PRECOND_BD)) if args.steps > 0 else ()):
+        ctx.solve(tod, pc, tol=args.tol, max_iter=args.max_iter, out=out)
+        tot, info = 0.0, None
+        for _ in range(args.steps):
+            t, (_, info) = timed(lambda: ctx.solve(tod, pc, tol=args.tol, max_iter=args.max_iter, out=out))
+            tot += t
+        res[name] = {"time_per_map_s": tot / args.steps, "iters": info[0]["iters"], "status": info[0]["status"],
+                     "true_rel_res": info[0]["true_rel_res"], "refinements": info[0]["refinements"]}
+    x = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        ctx.apply_A(x, out=y)
+    ctx.set_option("time_filter", 1)
+    ctx.get_option("filter_ms")
+    reps = 20
+    for _ in range(reps):
+        ctx.apply_A(x, out=y)
+    ax_ms = ctx.get_option("filter_ms") / reps
+    ctx.set_option("time_filter", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = 12.0 * scan.n_samples / (ax_ms * 1e-3) / 1e9
+    line = {"mode": "templates", "config": f"{args.config} geometry, no half-wave plate, white noise, d^- (Q/U) maps, "
+                                            f"polynomial order {args.poly_order} per subscan, {n_bins} azimuth bins",
+            "precision": args.precision, "coarse_from": args.coarse, "m_max": args.m_max,
+            "samples": scan.n_samples, "subscans": int(len(sub_off) - 1), "pixels_dropped": dropped, "k": k,
+            "setup_once_s": t_setup, "two_level": res.get("two_level"), "m_bd": res.get("m_bd"),
+            "apply_A": {"kernel": "k_filter_tmpl<%s>" % ("double" if prec == M.MM_FP64 else "float"), "ms": ax_ms, "samples_per_s": scan.n_samples / (ax_ms * 1e-3),
+                        "hbm_gbs_12B_per_sample": gbs, "hbm_frac_of_measured": gbs / hbm},
+            "gen_s": t_gen}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 # ---------------- mixed precision at scale (c4) ----------------

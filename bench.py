@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
     ap.add_argument("--poly-order", type=int, default=1, help="templates mode: subscan polynomial order")
+    ap.add_argument("--stokes", type=int, default=1, choices=[0, 1, 2],
+                    help="templates mode: 1 Q/U maps from d^-, 2 I maps from d^+, 0 I/Q/U")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
                          "apply: A x alone (profiling)")
@@ -480,7 +482,10 @@ def run_templates(args, world, rank, local):
     scan = synth.scan_from_config(args.config, seed=rank, half_bw=0, f_knee=0.0, hwp=False, **over)
     sub_off, az, n_bins = synth.make_templates(scan)
     sky = synth.make_sky(scan.n_pix, rank)
-    sky[:, 0] = 0.0
+    if args.stokes == 1:
+        sky[:, 0] = 0.0
+    elif args.stokes == 2:
+        sky[:, 1:] = 0.0
     tod = torch.from_numpy(synth.make_tod(scan, sky, synth.make_noise(scan, rank)).astype(np.float32)).to(dev)
     az_d = torch.from_numpy(az).to(dev)
     t_gen = time.time() - t_gen
@@ -503,7 +508,7 @@ def run_templates(args, world, rank, local):
 
     def setup():
         ctx.setup_scan(scan)
-        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, True)
+        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
         dropped = ctx.build_bd(1e-3)
         if args.coarse == "arnoldi":
             return dropped, ctx.build_coarse(ctx.rhs(tod)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
@@ -517,7 +522,7 @@ def run_templates(args, world, rank, local):
         t_setup, (dropped, k) = timed(setup)
     else:   # A x alone
         ctx.setup_scan(scan)
-        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, True)
+        ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
         t_setup, dropped, k = 0.0, ctx.build_bd(1e-3), 0
     for name, pc in ((("two_level", M.MM_PRECOND_2L), ("m_bd", M.MM_PRECOND_BD)) if args.steps > 0 else ()):
         ctx.solve(tod, pc, tol=args.tol, max_iter=args.max_iter, out=out)
@@ -545,7 +550,8 @@ def run_templates(args, world, rank, local):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     gbs = 12.0 * scan.n_samples / (ax_ms * 1e-3) / 1e9
-    line = {"mode": "templates", "config": f"{args.config} geometry, no half-wave plate, white noise, d^- (Q/U) maps, "
+    line = {"mode": "templates", "config": f"{args.config} geometry, no half-wave plate, white noise, "
+                                            f"{['I/Q/U', 'd^- (Q/U)', 'd^+ (I)'][args.stokes]} maps, "
                                             f"polynomial order {args.poly_order} per subscan, {n_bins} azimuth bins",
             "precision": args.precision, "coarse_from": args.coarse, "m_max": args.m_max,
             "samples": scan.n_samples, "subscans": int(len(sub_off) - 1), "pixels_dropped": dropped, "k": k,

@@ -283,12 +283,18 @@ mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done);
  *                  or device per `mem`; X = G holds one indicator column per
  *                  bin and per block (a block is one constant-elevation
  *                  scan).  NULL: no ground filter.  1 <= n_az_bins <= 8192.
- *  qu_only         1: pointing rows (0, cos 2psi, sin 2psi) -- the
- *                  differenced timeline d^- of Sect. 5.1 (Eq. d-); I is not
- *                  solved for (M_BD inverts the 2x2 (Q, U) block, a pixel
- *                  needs 2 hits and rcond >= rcond_min of that block).
+ *  stokes          0: pointing rows (1, cos 2psi, sin 2psi) (I, Q, U);
+ *                  1: rows (0, cos 2psi, sin 2psi) -- the differenced
+ *                  timeline d^- of Sect. 5.1 (Eq. d-); I is not solved for
+ *                  (M_BD inverts the 2x2 (Q, U) block, a pixel needs 2 hits
+ *                  and rcond >= rcond_min of that block);
+ *                  2: rows (1, 0, 0) -- the summed timeline d^+ (Eq. d+,
+ *                  intensity maps of App. B); Q, U are not solved for (1x1
+ *                  M_BD, 1 hit).  With polynomial templates a constant I map
+ *                  is then an exact null vector of A: the solve converges in
+ *                  the range of A and leaves that component at 0.
  * The filters act on every sample, flagged ones included.  Calling with
- * poly_order = -1, az_bin = NULL and qu_only = 0 restores the band weight.
+ * poly_order = -1, az_bin = NULL and stokes = 0 restores the band weight.
  * Clears M_BD and the coarse space (rebuild them), sets "fp64_products" to 1
  * (native float64; double-float products are not available here).
  * Right-hand sides of uneven length (rhs_len) are not supported with
@@ -296,7 +302,7 @@ mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done);
  * fit shared memory: 8 bytes per sample + 12 bytes per bin <= 220 KB.
  * Errors: MM_ERR_ARG, MM_ERR_STATE (no pointing), MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, const int64_t* subscan_off,
-                           const int32_t* az_bin, int32_t n_az_bins, int32_t qu_only, int mem);
+                           const int32_t* az_bin, int32_t n_az_bins, int32_t stokes, int mem);
 
 /* M_2l applied without allocating device memory during the call (the paper
  * has no counterpart; this is a deployment variant of mm_apply_precond).

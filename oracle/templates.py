@@ -29,9 +29,11 @@ Readings where the paper is silent (each also listed in the design notes):
     scan = one block); samples with bin -1 are in no column;
   * the filters act on every sample of the timeline, flagged ones included
     (they carry y_t = 0 from P and are not scattered back);
-  * in the polarisation-only mode the I column of P is zero; M_BD inverts
-    the 2x2 (Q, U) block, I stays 0, and a pixel needs at least 2 hits and
-    lambda_min / lambda_max >= rcond_min of that block.
+  * in the polarisation-only mode (stokes 1) the I column of P is zero; M_BD
+    inverts the 2x2 (Q, U) block, I stays 0, and a pixel needs at least 2
+    hits and lambda_min / lambda_max >= rcond_min of that block; in the
+    intensity-only mode (stokes 2, the summed timeline d^+) the Q, U columns
+    are zero, M_BD is 1 / (P^T W P)_II and a pixel needs 1 hit.
 
 Parity unpinned: none of the functions here (pins in
 tests/test_oracle_templates.py).
@@ -49,7 +51,7 @@ class TemplateProblem:
     """Pointing, block weights and templates of one template-filtered problem."""
 
     def __init__(self, pix, psi, block_off, w_block, n_pix, sub_off, poly_order, az_bin, n_az_bins,
-                 qu_only=True):
+                 stokes=1):
         self.pix = np.asarray(pix, dtype=np.int64)
         self.psi = np.asarray(psi, dtype=np.float32)
         self.block_off = np.asarray(block_off, dtype=np.int64)
@@ -59,11 +61,12 @@ class TemplateProblem:
         self.poly_order = int(poly_order)
         self.az_bin = None if az_bin is None else np.asarray(az_bin, dtype=np.int64)
         self.n_az_bins = int(n_az_bins)
-        self.qu_only = bool(qu_only)
+        self.stokes = int(stokes)   # 0: I, Q, U; 1: Q, U (d^-); 2: I (d^+)
+        self.qu_only = self.stokes == 1
 
     def with_pix(self, pix):
         return TemplateProblem(pix, self.psi, self.block_off, self.w_block, self.n_pix, self.sub_off,
-                               self.poly_order, self.az_bin, self.n_az_bins, self.qu_only)
+                               self.poly_order, self.az_bin, self.n_az_bins, self.stokes)
 
     def sample_weight(self) -> np.ndarray:
         """Diagonal of W: w_b on every sample of block b."""
@@ -126,10 +129,12 @@ def apply_F(tp: TemplateProblem, y) -> np.ndarray:
 
 
 def pointing_rows(tp: TemplateProblem) -> np.ndarray:
-    """Rows of P: (1, cos 2psi, sin 2psi), or (0, cos 2psi, sin 2psi) for d^- (Sect. 5.1, Eq. d-)."""
+    """Rows of P: (1, cos 2psi, sin 2psi); (0, cos 2psi, sin 2psi) for d^- (Sect. 5.1, Eq. d-);
+    (1, 0, 0) for d^+ (Eq. d+)."""
     ang = 2.0 * tp.psi.astype(np.float64)
-    first = np.zeros_like(ang) if tp.qu_only else np.ones_like(ang)
-    return np.stack([first, np.cos(ang), np.sin(ang)], axis=1)
+    first = np.zeros_like(ang) if tp.stokes == 1 else np.ones_like(ang)
+    pol = 0.0 if tp.stokes == 2 else 1.0
+    return np.stack([first, pol * np.cos(ang), pol * np.sin(ang)], axis=1)
 
 
 def _P(tp, x):
@@ -169,20 +174,26 @@ def bd_blocks_T(tp: TemplateProblem):
     return blocks, hits
 
 
-def select_pixels_T(blocks, hits, qu_only, rcond_min: float = 1e-3) -> np.ndarray:
+def select_pixels_T(blocks, hits, stokes, rcond_min: float = 1e-3) -> np.ndarray:
     """Enough redundancy (Sect. 5): hits >= number of unknowns and a conditioned block."""
-    sub = blocks[:, 1:, 1:] if qu_only else blocks
+    stokes = int(stokes)
+    if stokes == 2:
+        return (hits >= 1) & (blocks[:, 0, 0] > 0)
+    sub = blocks[:, 1:, 1:] if stokes == 1 else blocks
     ev = np.linalg.eigvalsh(sub)
     with np.errstate(divide="ignore", invalid="ignore"):
         rc = np.where(ev[:, -1] > 0, ev[:, 0] / ev[:, -1], 0.0)
-    return (hits >= (2 if qu_only else 3)) & (rc >= rcond_min)
+    return (hits >= (2 if stokes == 1 else 3)) & (rc >= rcond_min)
 
 
-def bd_inverse_T(blocks, good, qu_only) -> np.ndarray:
-    """M_BD: inverse of each kept block (its (Q, U) part in the polarisation-only mode)."""
+def bd_inverse_T(blocks, good, stokes) -> np.ndarray:
+    """M_BD: inverse of each kept block (its (Q, U) part for d^-, its I entry for d^+)."""
     inv = np.zeros_like(blocks)
+    stokes = int(stokes)
     if good.any():
-        if qu_only:
+        if stokes == 2:
+            inv[good, 0, 0] = 1.0 / blocks[good, 0, 0]
+        elif stokes == 1:
             inv[good, 1:, 1:] = np.linalg.inv(blocks[good, 1:, 1:])
         else:
             inv[good] = np.linalg.inv(blocks[good])

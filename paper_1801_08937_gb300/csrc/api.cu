@@ -905,7 +905,7 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         t.order = ctx->tmpl_order;
         t.az = ctx->tmpl_bins > 0 ? ctx->d_taz.as<int32_t>() : nullptr;
         t.n_bins = ctx->tmpl_bins;
-        t.qu_only = ctx->tmpl_qu;
+        t.stokes = ctx->tmpl_qu;
         launch_filter_tmpl(a, t, plan->nrhs, plan->f64 == 1, from_tod, ctx->stream);
     } else if (plan->variant == 2) {
         FftTables& ft = plan->ft;
@@ -1501,7 +1501,7 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
 // Sect. 5.1): subscan polynomials and azimuth-bin ground templates, white
 // block weights, optionally the differenced timeline's (0, cos, sin) rows.
 mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, const int64_t* subscan_off,
-                           const int32_t* az_bin, int32_t n_az_bins, int32_t qu_only, int mem) {
+                           const int32_t* az_bin, int32_t n_az_bins, int32_t stokes, int mem) {
     if (!ctx) return MM_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_set_templates: set the pointing first");
@@ -1509,7 +1509,8 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     ctx->have_bd = false;   // M_BD and any coarse space belong to the previous operator
     ctx->k = 0;
     ctx->tpref_valid = false;
-    if (poly_order < 0 && !az_bin && !qu_only) {
+    if (stokes < 0 || stokes > 2) return fail(ctx, MM_ERR_ARG, "stokes must be 0 (I, Q, U), 1 (Q, U) or 2 (I)");
+    if (poly_order < 0 && !az_bin && stokes == 0) {
         ctx->tmpl_on = false;
         ctx->tmpl_qu = 0;
         return MM_OK;
@@ -1593,7 +1594,7 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     ctx->tmpl_on = true;
     ctx->tmpl_order = poly_order;
     ctx->tmpl_bins = nbins;
-    ctx->tmpl_qu = qu_only ? 1 : 0;
+    ctx->tmpl_qu = stokes;
     ctx->tmpl_max_block = maxb;
     ctx->p64 = 1;   // float64-accurate products of the template filter run in native float64
     return MM_OK;

@@ -105,7 +105,7 @@ struct TmplArgs {
     int order;                 // polynomial order K (-1: no polynomial filter)
     const int32_t* az;         // [N] azimuth bin of each sample (-1: none); null: no ground filter
     int n_bins;
-    int qu_only;               // 1: pointing rows (0, cos 2psi, sin 2psi) (differenced timeline)
+    int stokes;                // 0: rows (1, cos 2psi, sin 2psi); 1: (0, cos, sin), d^-; 2: (1, 0, 0), d^+
 };
 void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s);
 size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64);
@@ -141,7 +141,7 @@ void launch_bd_accumulate(const int32_t* pix, const float* psi, const int64_t* b
                           double* sums /*[nrhs][n_pix][7]*/, int n_pix, cudaStream_t s);
 void launch_bd_invert(const double* sums, double* bd /*[nrhs][n_pix][6]*/, uint8_t* good,
                       int* n_dropped, int n_pix, int nrhs, double rcond_min, int set_good,
-                      cudaStream_t s, int qu_only = 0);
+                      cudaStream_t s, int stokes = 0);
 void launch_flag_samples(int32_t* pix, const uint8_t* good, int64_t n, cudaStream_t s);
 void launch_bd_apply(const double* bd, int bd_per_rhs, const V4<double>* x, V4<double>* y,
                      int n_pix, int nrhs, cudaStream_t s);

@@ -9,8 +9,9 @@
 //
 // One CTA per (block, right-hand side); the block's timeline lives in shared
 // memory through
-//   1. gather y = P x (rows (1, cos 2psi, sin 2psi), or (0, cos, sin) for the
-//      differenced timeline d^- of Sect. 5.1), or the timeline d, or d - P x;
+//   1. gather y = P x (rows (1, cos 2psi, sin 2psi); (0, cos, sin) for the
+//      differenced timeline d^- and (1, 0, 0) for the summed timeline d^+ of
+//      Sect. 5.1), or the timeline d, or d - P x;
 //   2. y -= B (B^T B)^-1 B^T y per subscan: one warp per subscan sums the
 //      moments sum_i y_i P_j(u_i), u_i = 2 (i + 1/2)/m - 1, and multiplies by
 //      the subscan's inverse Gram matrix (float64, precomputed on the host);
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     T* y = reinterpret_cast<T*>(smraw);
     T* gsum = y + ((nb + 1) & ~1);
     int* gcnt = reinterpret_cast<int*>(gsum + t.n_bins);
-    const T iw = t.qu_only ? T(0) : T(1);
+    const T iw = t.stokes == 1 ? T(0) : T(1);   // I column of P
+    const T pw = t.stokes == 2 ? T(0) : T(1);   // Q, U columns
     const V4<T>* xm = nullptr;
     if (!FROM_TOD) xm = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix;
     else if (a.xmap) xm = reinterpret_cast<const V4<T>*>(a.xmap) + (int64_t)rhs * a.n_pix;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
                     if (p[j] >= 0) {
                         float c, s;
                         weights_from(a, t0 + j, ps[j], c, s);
-                        const float px = iw * m[j].x + c * m[j].y + s * m[j].z;
+                        const float px = iw * m[j].x + pw * (c * m[j].y + s * m[j].z);
                         v[j] = FROM_TOD ? v[j] - px : px;
                     }
             }
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
                 T c, s;
                 weights(a, ts, c, s);
                 const V4<T> m = ldmap<T>(xm + p);
-                const T px = iw * m.x + c * m.y + s * m.z;
+                const T px = iw * m.x + pw * (c * m.y + s * m.z);
                 v = FROM_TOD ? v - px : px;
             }
         }
@@ -236,8 +238,8 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
                     weights_from(a, t0 + j, ps[j], c, sn);
                 }
                 v0[j] = iw * z;
-                v1[j] = z * c;
-                v2[j] = z * sn;
+                v1[j] = pw * z * c;
+                v2[j] = pw * z * sn;
             }
             scatter4_vals(p, v0, v1, v2, q);
         }
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
                 z = wb * y[i];
             }
         }
-        scatter_vals<T>(p, iw * z, z * c, z * s, q);
+        scatter_vals<T>(p, iw * z, pw * z * c, pw * z * s, q);
     }
 }
 

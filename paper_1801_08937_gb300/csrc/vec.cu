@@ -269,17 +269,32 @@ __device__ void sym3_eig(double a[3][3], double& lmin, double& lmax) {
 // (hits >= 3 and rcond >= rcond_min); otherwise `good` is read and a kept
 // pixel whose block is numerically singular for this right-hand side gets a
 // zero block.
-// qu_only: only the (Q, U) block counts (pointing rows (0, cos, sin) of the
+// stokes 1: only the (Q, U) block counts (pointing rows (0, cos, sin) of the
 // differenced timeline): at least 2 hits and a conditioned 2x2 block; the I
-// entries of the inverse are zero.
+// entries of the inverse are zero.  stokes 2: only I (rows (1, 0, 0) of the
+// summed timeline): at least 1 hit, the 1x1 inverse, Q and U entries zero.
 __global__ void k_bd_invert(const double* sums, double* bd, uint8_t* good, int* n_dropped, int n_pix, int nrhs,
-                            double rcond_min, int set_good, int qu_only) {
+                            double rcond_min, int set_good, int stokes) {
     const int64_t total = (int64_t)n_pix * nrhs;
     for (int64_t idx = blockIdx.x * (int64_t)VT + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * VT) {
         const int p = (int)(idx % n_pix);
         const double* S = sums + idx * 7;
         const double s00 = S[0], s01 = S[1], s02 = S[2], s11 = S[3], s12 = S[4], s22 = S[5], hits = S[6];
-        if (qu_only) {
+        if (stokes == 2) {
+            bool keep1;
+            if (set_good) {
+                keep1 = hits >= 1.0 && s00 > 0.0;
+                good[p] = keep1 ? 1 : 0;
+                if (!keep1) atomicAdd(n_dropped, 1);
+            } else {
+                keep1 = good[p] != 0 && s00 > 0.0;
+            }
+            double* o = bd + idx * 6;
+            for (int e = 0; e < 6; ++e) o[e] = 0.0;
+            if (keep1) o[0] = 1.0 / s00;
+            continue;
+        }
+        if (stokes == 1) {
             const double tr = s11 + s22, det2 = s11 * s22 - s12 * s12;
             const double disc = sqrt(fmax(0.25 * (s11 - s22) * (s11 - s22) + s12 * s12, 0.0));
             const double lmax2 = 0.5 * tr + disc, lmin2 = 0.5 * tr - disc;
@@ -336,9 +351,9 @@ __global__ void k_bd_invert(const double* sums, double* bd, uint8_t* good, int* 
     }
 }
 void launch_bd_invert(const double* sums, double* bd, uint8_t* good, int* n_dropped, int n_pix, int nrhs,
-                      double rcond_min, int set_good, cudaStream_t s, int qu_only) {
+                      double rcond_min, int set_good, cudaStream_t s, int stokes) {
     k_bd_invert<<<grid_for((int64_t)n_pix * nrhs), VT, 0, s>>>(sums, bd, good, n_dropped, n_pix, nrhs, rcond_min,
-                                                              set_good, qu_only);
+                                                              set_good, stokes);
     count_launches(1);
 }
 

@@ -174,13 +174,14 @@ class Context:
         self.setup_pointing(scan.pix, scan.psi, scan.block_off, scan.block_band, scan.band,
                             scan.n_pix, n_det=scan.n_det)
 
-    def set_templates(self, poly_order=-1, subscan_off=None, az_bin=None, n_az_bins=0, qu_only=False):
-        """Template filters F = F_B W^-1 F_G W^-1 F_B (mm_set_templates); subscan_off is host memory."""
+    def set_templates(self, poly_order=-1, subscan_off=None, az_bin=None, n_az_bins=0, stokes=0):
+        """Template filters F = F_B W^-1 F_G W^-1 F_B (mm_set_templates); subscan_off is host memory.
+        stokes: 0 I, Q, U; 1 (or True) Q, U from d^-; 2 I from d^+."""
         so = None if subscan_off is None else np.ascontiguousarray(subscan_off, dtype=np.int64)
         pa, m1, k1 = _arg(az_bin, np.int32)
         self._check(self.lib.mm_set_templates(
             self.h, int(poly_order), 0 if so is None else int(so.shape[0] - 1),
-            None if so is None else C.c_void_p(so.ctypes.data), pa, int(n_az_bins), int(bool(qu_only)), _mem(m1)))
+            None if so is None else C.c_void_p(so.ctypes.data), pa, int(n_az_bins), int(stokes), _mem(m1)))
 
     def build_bd(self, rcond_min: float = 1e-3) -> int:
         n = C.c_int32(0)

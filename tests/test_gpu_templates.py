@@ -45,14 +45,14 @@ def ctx_tmpl(scan, sub_off, az, nb, order, ground, qu_only, prec=MM.MM_FP64):
 
 def kept(tp, rcond_min=1e-3):
     blocks, hits = O.bd_blocks_T(tp)
-    good = O.select_pixels_T(blocks, hits, tp.qu_only, rcond_min)
+    good = O.select_pixels_T(blocks, hits, tp.stokes, rcond_min)
     tp = tp.with_pix(O.flag_samples(tp.pix, good))
     blocks, _ = O.bd_blocks_T(tp)
-    return tp, good, O.bd_inverse_T(blocks, good, tp.qu_only)
+    return tp, good, O.bd_inverse_T(blocks, good, tp.stokes)
 
 
-@pytest.mark.parametrize("order,ground,qu_only", [(0, True, True), (1, True, True), (3, True, True),
-                                                  (2, False, True), (-1, True, True), (1, True, False)])
+@pytest.mark.parametrize("order,ground,qu_only", [(0, True, 1), (1, True, 1), (3, True, 1), (2, False, 1),
+                                                  (-1, True, 1), (1, True, 0), (3, True, 2), (0, False, 2)])
 @pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
 def test_apply_A_matches_oracle(order, ground, qu_only, prec):
     scan, so, az, nb = scan_tmpl(seed=1)
@@ -160,6 +160,32 @@ def test_short_subscans_and_unbinned_samples():
     c.close()
 
 
+def test_intensity_only_d_plus():
+    """Summed timeline d^+ (Eq. d+, intensity maps of App. B, Legendre up to order 3): M_BD is the 1x1
+    inverse; a constant I map is an exact null vector of A, so the solve is checked through the
+    oracle's residual of the returned map and the null component left at 0."""
+    scan, so, az, nb = scan_tmpl(seed=11, flag_frac=0.0)
+    tp = oracle_tp(scan, so, az, nb, 3, True, 2)
+    c = ctx_tmpl(scan, so, az, nb, 3, True, 2)
+    dropped = c.build_bd(1e-3)
+    tpk, good, mbd = kept(tp)
+    assert dropped == int((~good).sum())
+    r = np.random.default_rng(11).standard_normal((scan.n_pix, 3))
+    assert rel(c.apply_precond(MM.MM_PRECOND_BD, r)[0], O.bd_apply(mbd, r)) < 1e-12
+    ones = np.zeros((scan.n_pix, 3))
+    ones[good, 0] = 1.0
+    assert np.abs(c.apply_A(ones)[0]).max() < 1e-9 * np.abs(c.apply_A(r)[0]).max()
+    sky = synth.make_sky(scan.n_pix, 11)
+    sky[:, 1:] = 0.0
+    d = synth.make_tod(scan, sky, synth.make_noise(scan, 11))
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=5000)
+    assert info[0]["status"] == "MM_OK"
+    b = O.rhs_T(tpk, d)
+    assert np.linalg.norm(b - O.apply_A_T(tpk, x[0])) <= 2e-10 * np.linalg.norm(b)
+    assert np.abs(x[0][:, 1:]).max() == 0.0
+    c.close()
+
+
 def test_template_argument_errors():
     scan, so, az, nb = scan_tmpl(seed=10)
     c = MM.Context(0, None, MM.MM_FP64)
@@ -175,6 +201,9 @@ def test_template_argument_errors():
     bad = so[so != scan.block_off[1]]                   # one subscan across a block edge
     with pytest.raises(MM.MapMakerError) as e:
         c.set_templates(1, bad, az, nb, True)
+    assert e.value.status == MM.MM_ERR_ARG
+    with pytest.raises(MM.MapMakerError) as e:
+        c.set_templates(1, so, az, nb, 3)               # no such Stokes selection
     assert e.value.status == MM.MM_ERR_ARG
     with pytest.raises(MM.MapMakerError) as e:
         c.set_templates(4, so, az, nb, True)            # order above 3

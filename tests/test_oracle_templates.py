@@ -125,12 +125,29 @@ def test_dense_assembly_matches_matrix_free():
     assert np.abs(A[0::3]).max() == 0.0 and np.abs(A[:, 0::3]).max() == 0.0
 
 
+def test_constant_intensity_is_a_null_vector_of_the_filtered_d_plus_system():
+    """d^+ rows (1, 0, 0): a constant I map gives a constant timeline, which every subscan's P_0
+    template removes (Eq. filt), so A 1 = 0 exactly; Q and U rows and columns vanish."""
+    scan, tp = tproblem(order=0, ground=False, qu_only=2)
+    ones = np.zeros((scan.n_pix, 3))
+    ones[:, 0] = 1.0
+    assert np.abs(O.apply_A_T(tp, ones)).max() < 1e-12
+    x = np.random.default_rng(12).standard_normal((scan.n_pix, 3))
+    Ax = O.apply_A_T(tp, x)
+    assert np.abs(Ax[:, 1:]).max() == 0.0 and np.abs(Ax[:, 0]).max() > 1e-3
+    blocks, hits = O.bd_blocks_T(tp)
+    good = O.select_pixels_T(blocks, hits, 2)
+    inv = O.bd_inverse_T(blocks, good, 2)
+    np.testing.assert_allclose(inv[good, 0, 0] * blocks[good, 0, 0], 1.0)
+    assert np.abs(inv[:, 1:, :]).max() == 0.0
+
+
 def _kept(tp):
     blocks, hits = O.bd_blocks_T(tp)
-    good = O.select_pixels_T(blocks, hits, tp.qu_only)
+    good = O.select_pixels_T(blocks, hits, tp.stokes)
     tp = tp.with_pix(O.flag_samples(tp.pix, good))
     blocks, _ = O.bd_blocks_T(tp)
-    return tp, good, O.bd_inverse_T(blocks, good, tp.qu_only)
+    return tp, good, O.bd_inverse_T(blocks, good, tp.stokes)
 
 
 def test_filtered_estimator_is_unbiased_under_polynomial_contamination():

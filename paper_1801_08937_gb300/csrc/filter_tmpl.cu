@@ -13,10 +13,13 @@
 //      differenced timeline d^- and (1, 0, 0) for the summed timeline d^+ of
 //      Sect. 5.1), or the timeline d, or d - P x;
 //   2. y -= B (B^T B)^-1 B^T y per subscan: one warp per subscan sums the
-//      moments sum_i y_i P_j(u_i), u_i = 2 (i + 1/2)/m - 1, and multiplies by
-//      the subscan's inverse Gram matrix (float64, precomputed on the host);
-//   3. y -= bin means of y over the block's azimuth bins (runs of equal bins
-//      in a warp are summed before one shared-memory atomic per run);
+//      moments sum_i y_i P_j(u_i), u_i = 2 (i + 1/2)/m - 1, multiplies by the
+//      subscan's inverse Gram matrix (float64, precomputed on the host) and
+//      subtracts the fit (the order K is a compile-time parameter);
+//   3. y -= bin means of y over the block's azimuth bins, all warps over the
+//      whole block (runs of equal bins in a warp are summed before one
+//      shared-memory atomic per run; folding this into the per-subscan
+//      passes, which keep only one warp per subscan busy, was slower);
 //   4. step 2 again;
 //   5. z = w_b y scattered into the map (P^T), runs of equal pixels summed in
 //      the warp first.
@@ -64,52 +67,86 @@ __device__ __forceinline__ void legendre4(T u, T (&p)[4]) {
     p[3] = (T(2.5) * u * u - T(1.5)) * u;
 }
 
-// y -= B (B^T B)^-1 B^T y on every subscan of the block (one warp per subscan).
-template <typename T>
-__device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0) {
-    if (t.order < 0) return;
+// Coefficients c = G^-1 m of the subscan's Legendre fit from the moments m
+// (every lane holds them after the warp sum).
+template <typename T, int K>
+__device__ __forceinline__ void fit_coef(const double* __restrict__ gi, const T (&mom)[4], T (&c)[4]) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l <= K; ++l) acc += T(gi[j * 4 + l]) * mom[l];
+        c[j] = acc;
+    }
+}
+
+// One pass of (1 - Pi_B) over every subscan of the block, one warp per subscan
+// (warp-uniform sample loop, lanes on consecutive samples):
+//   moments of y' = y - ground_mean (GSUB: the ground fit of the previous
+//   step is removed on the fly and written back), then y' -= B c, and (GACC)
+//   the azimuth-bin sums of the result accumulated for the next ground fit.
+template <typename T, int K, bool GSUB, bool GACC>
+__device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0, T* gsum, int* gcnt) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = TMPL_NT / 32;
-    const int K = t.order;
     for (int s = t.blk_sub[blk] + warp; s < t.blk_sub[blk + 1]; s += nw) {
         const int64_t s0 = t.sub_off[s];
         const int m = (int)(t.sub_off[s + 1] - s0);
         const int o = (int)(s0 - b0);
         const T inv_m = T(2) / T(m);
+        const T u0 = inv_m * T(0.5) - T(1);
         T mom[4] = {T(0), T(0), T(0), T(0)};
-        for (int i = lane; i < m; i += 32) {
-            T p[4];
-            legendre4<T>(T(i) * inv_m + (inv_m * T(0.5) - T(1)), p);
-            const T v = y[o + i];
+        for (int base = 0; base < m; base += 32) {
+            const int i = base + lane;
+            if (i < m) {
+                T v = y[o + i];
+                if (GSUB) {
+                    const int g = __ldg(t.az + s0 + i);
+                    if (g >= 0 && g < t.n_bins) {
+                        v -= gsum[g] / T(gcnt[g]);
+                        y[o + i] = v;
+                    }
+                }
+                T p[4];
+                legendre4<T>(T(i) * inv_m + u0, p);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j <= K) mom[j] += v * p[j];
+                for (int j = 0; j <= K; ++j) mom[j] += v * p[j];
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) mom[j] = warp_sum_all(mom[j]);
-        // coefficients c = G^-1 mom (every lane holds the moments)
-        const double* gi = t.ginv + (int64_t)s * 16;
+        for (int j = 0; j <= K; ++j) mom[j] = warp_sum_all(mom[j]);
         T c[4];
+        fit_coef<T, K>(t.ginv + (int64_t)s * 16, mom, c);
+        for (int base = 0; base < m; base += 32) {
+            const int i = base + lane;
+            T v = T(0);
+            int g = -1;
+            if (i < m) {
+                T p[4];
+                legendre4<T>(T(i) * inv_m + u0, p);
+                T fit = T(0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            T acc = T(0);
-#pragma unroll
-            for (int l = 0; l < 4; ++l)
-                if (j <= K && l <= K) acc += T(gi[j * 4 + l]) * mom[l];
-            c[j] = acc;
-        }
-        for (int i = lane; i < m; i += 32) {
-            T p[4];
-            legendre4<T>(T(i) * inv_m + (inv_m * T(0.5) - T(1)), p);
-            T fit = T(0);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j <= K) fit += c[j] * p[j];
-            y[o + i] -= fit;
+                for (int j = 0; j <= K; ++j) fit += c[j] * p[j];
+                v = y[o + i] - fit;
+                y[o + i] = v;
+                if (GACC) {
+                    g = __ldg(t.az + s0 + i);
+                    if (g >= t.n_bins) g = -1;
+                }
+            }
+            if (GACC) {
+                bool head;
+                const T sv = warp_run_sum<T>(g, v, head);
+                const int cn = warp_run_sum<int>(g, (g >= 0) ? 1 : 0, head);
+                if (head && g >= 0) {
+                    atomicAdd(gsum + g, sv);
+                    atomicAdd(gcnt + g, cn);
+                }
+            }
         }
     }
 }
 
-template <typename T, bool FROM_TOD>
+template <typename T, bool FROM_TOD, int K>
 __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, const TmplArgs t) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int blk = blockIdx.x, rhs = blockIdx.y;
@@ -182,11 +219,14 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
         gcnt[i] = 0;
     }
     __syncthreads();
-    // 2. polynomial templates
-    project_poly<T>(y, t, blk, b0);
-    __syncthreads();
-    // 3. ground template: bin means over the block
-    if (t.az && t.n_bins > 0) {
+    const bool ground = t.az && t.n_bins > 0;
+    // 2. (1 - Pi_B) y (one warp per subscan)
+    if constexpr (K >= 0) {
+        project_poly<T, K, false, false>(y, t, blk, b0, gsum, gcnt);
+        __syncthreads();
+    }
+    if (ground) {
+        // 3. y - azimuth-bin means over the block (all warps: runs of equal bins summed in the warp)
         for (int base = 0; base < nb; base += TMPL_NT) {
             const int i = base + threadIdx.x;
             int g = -1;
@@ -210,9 +250,11 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
             if (g >= 0 && g < t.n_bins) y[i] -= gsum[g] / T(gcnt[g]);
         }
         __syncthreads();
-        // 4. polynomial templates again
-        project_poly<T>(y, t, blk, b0);
-        __syncthreads();
+        // 4. (1 - Pi_B) again
+        if constexpr (K >= 0) {
+            project_poly<T, K, false, false>(y, t, blk, b0, gsum, gcnt);
+            __syncthreads();
+        }
     }
     // without a ground template F_B W^-1 F_B = w_b (1 - Pi_B)^2 = w_b (1 - Pi_B): one projection
     // 5. weight and scatter
@@ -266,16 +308,27 @@ size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64) {
     return (size_t)((max_block + 1) & ~1LL) * e + (size_t)n_bins * (e + 4);
 }
 
-template <typename T, bool FROM_TOD>
-static void launch_tmpl_t(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
+template <typename T, bool FROM_TOD, int K>
+static void launch_tmpl_k(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
     const size_t sm = tmpl_smem_bytes(t.max_block, t.n_bins, sizeof(T) == 8);
     static size_t configured = 0;
     if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         configured = sm;
     }
-    k_filter_tmpl<T, FROM_TOD><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
+    k_filter_tmpl<T, FROM_TOD, K><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
     count_launches(1);
+}
+
+template <typename T, bool FROM_TOD>
+static void launch_tmpl_t(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
+    switch (t.order) {
+        case 0: return launch_tmpl_k<T, FROM_TOD, 0>(a, t, nrhs, s);
+        case 1: return launch_tmpl_k<T, FROM_TOD, 1>(a, t, nrhs, s);
+        case 2: return launch_tmpl_k<T, FROM_TOD, 2>(a, t, nrhs, s);
+        case 3: return launch_tmpl_k<T, FROM_TOD, 3>(a, t, nrhs, s);
+        default: return launch_tmpl_k<T, FROM_TOD, -1>(a, t, nrhs, s);
+    }
 }
 
 void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s) {

@@ -205,6 +205,16 @@ def cpu_oracle_sample(cfg_name, seed, n_products, budget_s=20.0):
     return est, desc, 1
 
 
+def workload_config(args, world):
+    """The `config` object of the default bench line (both arms)."""
+    return {"workload": f"{args.config}: 256x256 patch, 128 det x 2^20 samples, lambda 2048, "
+                        f"64 intervals, k={args.k}; one step = one map (b = P^T W d + two-level PCG "
+                        f"to {args.tol:g}) on a resident scan whose pointing, M_BD and coarse space "
+                        f"were built once",
+            "precision": args.precision, "l2": "inputs (1.1 GB pointing + timeline) exceed L2",
+            "replicas": world}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -214,7 +224,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": est, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.config + "-oracle-sample"},
+            "data": "synthetic", "config": workload_config(args, world),
             "cpu_baseline": {"value": est, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": est, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.time() - t0}
@@ -427,12 +437,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == M.MM_FP32_MIXED else "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.config}: 256x256 patch, 128 det x 2^20 samples, lambda 2048, "
-                                   f"64 intervals, k={args.k}; one step = one map (b = P^T W d + two-level PCG "
-                                   f"to {args.tol:g}) on a resident scan whose pointing, M_BD and coarse space "
-                                   f"were built once",
-                       "precision": args.precision, "l2": "inputs (1.1 GB pointing + timeline) exceed L2",
-                       "replicas": world},
+            "config": workload_config(args, world),
             "two_level": {"iters": info2l["iters"], "true_rel_res": info2l["true_rel_res"],
                           "refinements": info2l["refinements"], "k": k_used, "status": info2l["status"],
                           "setup_once_s": setup_ms / 1e3, "coarse_from": args.coarse, "m_max": args.m_max,

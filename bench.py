@@ -617,7 +617,9 @@ def run_scale(args, world, rank, local):
                                                      out=out))
             # coarse space, once per scan: k = 64 Ritz vectors need a Lanczos sequence longer than 64, so
             # the harvested M_BD run is carried to a tighter inner tolerance than the timed one
-            m_h = max(args.m_max, 160)
+            # (all Ritz pairs of a 64-step sequence: longer float32 Lanczos sequences lose orthogonality
+            # and their k = 64 smallest Ritz vectors deflate less)
+            m_h = 64
             ctx.set_option("inner_tol", 1e-13)
             ctx.set_option("harvest", m_h)
             t_h, _ = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=min(args.tol, 1e-12), max_iter=args.max_iter,

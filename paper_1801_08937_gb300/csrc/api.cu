@@ -1855,9 +1855,16 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     std::vector<std::vector<double>> cols;
     std::vector<double> vals;
     const int kwant = k > 0 ? std::min(k, m) : m;
+    // Ritz values at the round-off level of the largest belong to null directions
+    // of A (e.g. a constant intensity map under polynomial templates): A Z has no
+    // component there, E = Z^T A Z would be singular, so they are not deflated
+    double wmax = 0.0;
+    for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
+    const double wnull = 1e-10 * wmax;
     for (int idx : order) {
         if ((int)cols.size() >= kwant) break;
         if (used[idx]) continue;
+        if (std::fabs(wr[idx]) <= wnull) continue;
         if (k <= 0 && !(wr[idx] < eps_lambda)) break;
         used[idx] = 1;
         std::vector<double> c(m);
@@ -1933,8 +1940,11 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     const int kwant = k > 0 ? std::min(k, m) : m;
     std::vector<int> sel;
     std::vector<double> vals;
+    double wmax = 0.0;
+    for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
     for (int idx : order) {
         if ((int)sel.size() >= kwant) break;
+        if (std::fabs(wr[idx]) <= 1e-10 * wmax) continue;   // null directions of A (see mm_build_coarse)
         if (k <= 0 && !(wr[idx] < eps_lambda)) break;
         sel.push_back(idx);
         vals.push_back(wr[idx]);
@@ -2175,6 +2185,9 @@ static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
         if (ctx->final_status[i] != 0) continue;
         const double target = is_f32(ctx) ? ctx->true_res[i] : ctx->rec_res[i];
         if (!(target <= ctx->tol)) ctx->final_status[i] = MM_ERR_NOT_CONVERGED;
+        // float64 products: the recurrence stops the solve, but a true residual far above it means the
+        // recurrence drifted (an inconsistent preconditioner): not converged either
+        if (!is_f32(ctx) && !(ctx->true_res[i] <= 100.0 * ctx->tol)) ctx->final_status[i] = MM_ERR_NOT_CONVERGED;
     }
     ctx->phase = PH_DONE;
     *done = 1;

@@ -183,6 +183,13 @@ def test_intensity_only_d_plus():
     b = O.rhs_T(tpk, d)
     assert np.linalg.norm(b - O.apply_A_T(tpk, x[0])) <= 2e-10 * np.linalg.norm(b)
     assert np.abs(x[0][:, 1:]).max() == 0.0
+    # two-level: the null direction's zero Ritz value is not deflated, E stays SPD
+    k = c.build_coarse(c.rhs(d)[0], m_max=120, eps_arn=1e-12, k=24)
+    assert k >= 8
+    x2, i2 = c.solve(d, MM.MM_PRECOND_2L, tol=1e-10, max_iter=5000)
+    assert i2[0]["status"] == "MM_OK" and i2[0]["true_rel_res"] <= 1e-9
+    assert np.linalg.norm(b - O.apply_A_T(tpk, x2[0])) <= 2e-10 * np.linalg.norm(b)
+    assert i2[0]["iters"] < info[0]["iters"]
     c.close()
 
 

@@ -34,6 +34,37 @@ __device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
 
 template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
+
+// float32 complex sums as one packed two-lane instruction (add/sub/fma .f32x2,
+// sm_100 and later): the same round-to-nearest result per lane as two scalar
+// operations, half the issue slots in the butterflies.
+__device__ __forceinline__ unsigned long long pk2(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ C2<float> upk2(unsigned long long r) {
+    C2<float> c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(r));
+    return c;
+}
+template <> __device__ __forceinline__ C2<float> cadd(C2<float> a, C2<float> b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    return upk2(r);
+}
+template <> __device__ __forceinline__ C2<float> csub(C2<float> a, C2<float> b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    return upk2(r);
+}
+// d -/+ i e = (d.x + s e.y, d.y - s e.x): one fma.f32x2 of the swapped pair
+// (e.y, e.x) with multipliers (s, -s), s = +-1 (exact multiplies, one rounding)
+__device__ __forceinline__ C2<float> c_minus_i(C2<float> d, C2<float> e, float sgn) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(e.y, e.x)), "l"(pk2(sgn, -sgn)), "l"(pk2(d.x, d.y)));
+    return upk2(r);
+}
 template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
@@ -72,6 +103,13 @@ template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1,
     a2 = csub(s02, s13);
     a1 = {d02.x + d13.y, d02.y - d13.x};   // d02 - i d13
     a3 = {d02.x - d13.y, d02.y + d13.x};   // d02 + i d13
+}
+template <> __device__ __forceinline__ void dft4(C2<float>& a0, C2<float>& a1, C2<float>& a2, C2<float>& a3) {
+    const C2<float> s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = c_minus_i(d02, d13, 1.0f);    // d02 - i d13
+    a3 = c_minus_i(d02, d13, -1.0f);   // d02 + i d13
 }
 
 template <typename T, int R> struct Dft;

@@ -80,13 +80,10 @@ __device__ __forceinline__ void fit_coef(const double* __restrict__ gi, const T 
     }
 }
 
-// One pass of (1 - Pi_B) over every subscan of the block, one warp per subscan
-// (warp-uniform sample loop, lanes on consecutive samples):
-//   moments of y' = y - ground_mean (GSUB: the ground fit of the previous
-//   step is removed on the fly and written back), then y' -= B c, and (GACC)
-//   the azimuth-bin sums of the result accumulated for the next ground fit.
-template <typename T, int K, bool GSUB, bool GACC>
-__device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0, T* gsum, int* gcnt) {
+// y -= B (B^T B)^-1 B^T y on every subscan of the block, one warp per
+// subscan (warp-uniform sample loops, lanes on consecutive samples).
+template <typename T, int K>
+__device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = TMPL_NT / 32;
     for (int s = t.blk_sub[blk] + warp; s < t.blk_sub[blk + 1]; s += nw) {
         const int64_t s0 = t.sub_off[s];
@@ -95,53 +92,24 @@ __device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0, T* gs
         const T inv_m = T(2) / T(m);
         const T u0 = inv_m * T(0.5) - T(1);
         T mom[4] = {T(0), T(0), T(0), T(0)};
-        for (int base = 0; base < m; base += 32) {
-            const int i = base + lane;
-            if (i < m) {
-                T v = y[o + i];
-                if (GSUB) {
-                    const int g = __ldg(t.az + s0 + i);
-                    if (g >= 0 && g < t.n_bins) {
-                        v -= gsum[g] / T(gcnt[g]);
-                        y[o + i] = v;
-                    }
-                }
-                T p[4];
-                legendre4<T>(T(i) * inv_m + u0, p);
+        for (int i = lane; i < m; i += 32) {
+            T p[4];
+            legendre4<T>(T(i) * inv_m + u0, p);
+            const T v = y[o + i];
 #pragma unroll
-                for (int j = 0; j <= K; ++j) mom[j] += v * p[j];
-            }
+            for (int j = 0; j <= K; ++j) mom[j] += v * p[j];
         }
 #pragma unroll
         for (int j = 0; j <= K; ++j) mom[j] = warp_sum_all(mom[j]);
         T c[4];
         fit_coef<T, K>(t.ginv + (int64_t)s * 16, mom, c);
-        for (int base = 0; base < m; base += 32) {
-            const int i = base + lane;
-            T v = T(0);
-            int g = -1;
-            if (i < m) {
-                T p[4];
-                legendre4<T>(T(i) * inv_m + u0, p);
-                T fit = T(0);
+        for (int i = lane; i < m; i += 32) {
+            T p[4];
+            legendre4<T>(T(i) * inv_m + u0, p);
+            T fit = T(0);
 #pragma unroll
-                for (int j = 0; j <= K; ++j) fit += c[j] * p[j];
-                v = y[o + i] - fit;
-                y[o + i] = v;
-                if (GACC) {
-                    g = __ldg(t.az + s0 + i);
-                    if (g >= t.n_bins) g = -1;
-                }
-            }
-            if (GACC) {
-                bool head;
-                const T sv = warp_run_sum<T>(g, v, head);
-                const int cn = warp_run_sum<int>(g, (g >= 0) ? 1 : 0, head);
-                if (head && g >= 0) {
-                    atomicAdd(gsum + g, sv);
-                    atomicAdd(gcnt + g, cn);
-                }
-            }
+            for (int j = 0; j <= K; ++j) fit += c[j] * p[j];
+            y[o + i] -= fit;
         }
     }
 }
@@ -222,7 +190,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     const bool ground = t.az && t.n_bins > 0;
     // 2. (1 - Pi_B) y (one warp per subscan)
     if constexpr (K >= 0) {
-        project_poly<T, K, false, false>(y, t, blk, b0, gsum, gcnt);
+        project_poly<T, K>(y, t, blk, b0);
         __syncthreads();
     }
     if (ground) {
@@ -252,7 +220,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
         __syncthreads();
         // 4. (1 - Pi_B) again
         if constexpr (K >= 0) {
-            project_poly<T, K, false, false>(y, t, blk, b0, gsum, gcnt);
+            project_poly<T, K>(y, t, blk, b0);
             __syncthreads();
         }
     }

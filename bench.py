@@ -39,8 +39,8 @@ METRIC = "time-to-1e-8 residual per map (2-level vs M_BD), A·x samples/s, p99 l
 UNIT = "s/map"
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 CUDA-core rate (nominal)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-# ncu: k_filter_half<float, 0, 512, 9216> moved 140.3 MB read + 3.0 MB written for 1.68e7 samples
-NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (140.259328e6 + 3.013888e6) / 16777216
+# ncu: k_filter_half<float, 0, 512, 9216> moved 140.1 MB read + 2.8 MB written for 1.68e7 samples
+NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (140.050432e6 + 2.814976e6) / 16777216
 
 
 def parse():

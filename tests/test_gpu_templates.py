@@ -193,6 +193,22 @@ def test_intensity_only_d_plus():
     c.close()
 
 
+def test_device_azimuth_bins_match_host():
+    """mm_set_templates with the azimuth bins in device memory gives the same operator as from host memory."""
+    torch = pytest.importorskip("torch")
+    scan, so, az, nb = scan_tmpl(seed=12)
+    x = np.random.default_rng(12).standard_normal((scan.n_pix, 3))
+    c1 = ctx_tmpl(scan, so, az, nb, 1, True, 1)
+    y1 = c1.apply_A(x)[0]
+    c1.close()
+    c2 = MM.Context(0, None, MM.MM_FP64)
+    c2.setup_scan(scan)
+    c2.set_templates(1, so, torch.from_numpy(az).cuda(), nb, 1)
+    y2 = c2.apply_A(x)[0]
+    c2.close()
+    assert rel(y2, y1) < 1e-13
+
+
 def test_template_argument_errors():
     scan, so, az, nb = scan_tmpl(seed=10)
     c = MM.Context(0, None, MM.MM_FP64)

@@ -474,9 +474,9 @@ def run_templates(args, world, rank, local):
     # the filters leave a near-null space of slowly varying Q/U patterns (hundreds of modes at c1): the
     # coarse space needs the largest k and well converged Ritz vectors; untouched defaults become those
     if args.k == 32:
-        args.k = 128
+        args.k = 256
     if args.coarse == "lanczos" and args.m_max == 120:
-        args.coarse, args.m_max = "arnoldi", 400
+        args.coarse, args.m_max = "arnoldi", 1000
     if args.eps_arn == 1e-6:
         args.eps_arn = 1e-12
     torch.cuda.set_device(local)

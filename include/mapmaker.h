@@ -153,6 +153,8 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
  * the k smallest (or, if k <= 0, all with real part below eps_lambda) form Z,
  * a complex pair adding its real and imaginary parts.  Z is orthonormalised,
  * AZ = A Z and E = Z^T A Z are formed, and E is factored (float64).
+ * Ritz values at the round-off level of the largest (null directions of A)
+ * are not used.  1 <= m_max <= 1024, k <= 512.
  * *k_out (may be NULL) receives dim Z.  Needs mm_build_bd.
  * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_SINGULAR, MM_ERR_CUDA. */
 mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, double eps_arn,
@@ -168,14 +170,15 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
  * Ritz pairs of T_m (Appendix A, Eq. ritz, in its symmetric form) give the
  * deflation basis: the k smallest (or, if k <= 0, those below eps_lambda)
  * form Z = V S, then Z is orthonormalised and AZ, E = Z^T A Z formed as in
- * mm_build_coarse.  *k_out (may be NULL) receives dim Z.
+ * mm_build_coarse (k <= 512).  *k_out (may be NULL) receives dim Z.
  * Errors: MM_ERR_STATE (no harvested solve), MM_ERR_ARG, MM_ERR_SINGULAR,
  * MM_ERR_CUDA. */
 mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, int32_t* k_out);
 
 /* Install a deflation basis Z [k][n_pix][3] float64 (`mem`) instead of
  * building one: the paper's "simplified" reuse of a basis computed on another
- * data subset (Sect. 7).  AZ and E = Z^T A Z are formed with this context's A.
+ * data subset (Sect. 7).  AZ and E = Z^T A Z are formed with this context's A;
+ * 1 <= k <= 512.
  * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_SINGULAR, MM_ERR_CUDA. */
 mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem);
 

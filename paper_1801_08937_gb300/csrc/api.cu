@@ -1774,14 +1774,14 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
     if (m_max <= 0 || m_max > 1024) return fail(ctx, MM_ERR_ARG, "m_max must lie in [1, 1024]");
-    if (k > 128) return fail(ctx, MM_ERR_ARG, "k must be at most 128");
+    if (k > MM_K_MAX) return fail(ctx, MM_ERR_ARG, "k must be at most 512");
     if (!b_or_null && !ctx->have_lastb) return fail(ctx, MM_ERR_STATE, "no right-hand side: pass b or call mm_rhs");
     CK(cudaSetDevice(ctx->device));
     const int n_pix = ctx->n_pix;
     const int64_t n = (int64_t)n_pix * 4;
     ctx->k = 0;
     ctx->tpref_valid = false;
-    TRY(ensure_work(ctx, 1, 128));
+    TRY(ensure_work(ctx, 1, MM_K_MAX));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * (m_max + 2) * 8 + 64));
     CK(ctx->d_W.ensure((size_t)(m_max + 1) * n * 8));
     CK(ctx->d_h.ensure((size_t)(m_max + 2) * 8 * 2));
@@ -1916,7 +1916,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
     if (ctx->harvest_count < 2) return fail(ctx, MM_ERR_STATE, "no harvested M_BD solve (set option harvest > 1)");
-    if (k > 128) return fail(ctx, MM_ERR_ARG, "k must be at most 128");
+    if (k > MM_K_MAX) return fail(ctx, MM_ERR_ARG, "k must be at most 512");
     CK(cudaSetDevice(ctx->device));
     const int m = ctx->harvest_count;
     const int64_t n = (int64_t)ctx->n_pix * 4;
@@ -1959,7 +1959,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     ctx->k = 0;
     ctx->tpref_valid = false;
-    TRY(ensure_work(ctx, 1, 128));
+    TRY(ensure_work(ctx, 1, MM_K_MAX));
     CK(ctx->d_Z.ensure((size_t)ksel * n * 8));
     launch_combo(ctx->d_harv.as<double>(), n, m, dC.as<double>(), ksel, ctx->d_Z.as<double>(), n, n, ctx->stream);
     CKL();
@@ -1976,7 +1976,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
 mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
-    if (k <= 0 || k > 128 || !Z) return fail(ctx, MM_ERR_ARG, "k must lie in [1, 128] and Z non-null");
+    if (k <= 0 || k > MM_K_MAX || !Z) return fail(ctx, MM_ERR_ARG, "k must lie in [1, 512] and Z non-null");
     CK(cudaSetDevice(ctx->device));
     const int64_t n = (int64_t)ctx->n_pix * 4;
     ctx->k = 0;

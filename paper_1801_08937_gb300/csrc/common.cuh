@@ -18,6 +18,9 @@
 
 namespace mm {
 
+// Largest coarse space (number of deflation vectors k) the M_2l kernels hold.
+constexpr int MM_K_MAX = 512;
+
 // Kernels launched by this library since load (every launcher adds its count).
 long long launches_total();
 void count_launches(int n);

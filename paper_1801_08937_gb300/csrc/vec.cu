@@ -573,7 +573,7 @@ __global__ void k_m2l_ztr(const PcgArgs a, const V4<double>* v) {
         if (lane == 0) a.partial[((int64_t)blockIdx.x * a.nrhs + rhs) * k + c] = s;
     }
     if (last_block(a.counter, rhs)) {
-        __shared__ double t[128];
+        __shared__ double t[MM_K_MAX];
         for (int c = warp; c < k; c += nw) {
             const double s = warp_gather(a.partial, gridDim.x, (int64_t)a.nrhs * k, (int64_t)rhs * k + c);
             if (lane == 0) t[c] = s;
@@ -595,7 +595,7 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
     const int rhs = blockIdx.y;
     if (a.st && !a.st[rhs].active) return;
     const int64_t off = (int64_t)rhs * a.n_pix;
-    __shared__ double u[128];
+    __shared__ double u[MM_K_MAX];
     for (int c = threadIdx.x; c < a.k; c += VT) u[c] = a.u[(int64_t)rhs * a.k + c];
     __syncthreads();
     double acc[1] = {0.0};

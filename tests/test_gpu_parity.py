@@ -555,7 +555,7 @@ def test_argument_and_state_errors():
         c.solve(np.zeros(scan.n_samples), MM.MM_PRECOND_2L)   # no coarse space yet
     assert e.value.status == MM.MM_ERR_STATE
     with pytest.raises(MM.MapMakerError) as e:
-        c.build_coarse(None, m_max=10, k=200)
+        c.build_coarse(None, m_max=10, k=600)   # above the 512 limit
     assert e.value.status == MM.MM_ERR_ARG
     # an all-zero timeline solves to the zero map at once
     x, info = c.solve(np.zeros(scan.n_samples), MM.MM_PRECOND_BD, tol=1e-8)

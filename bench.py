@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
     ap.add_argument("--poly-order", type=int, default=1, help="templates mode: subscan polynomial order")
+    ap.add_argument("--fp64-products", type=int, default=1, choices=[1, 2],
+                    help="templates mode, fp64: operator products in native float64 (1) or double-float (2)")
     ap.add_argument("--stokes", type=int, default=1, choices=[0, 1, 2],
                     help="templates mode: 1 Q/U maps from d^-, 2 I maps from d^+, 0 I/Q/U")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates"],
@@ -514,6 +516,7 @@ def run_templates(args, world, rank, local):
     def setup():
         ctx.setup_scan(scan)
         ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
+        ctx.set_option("fp64_products", args.fp64_products)
         dropped = ctx.build_bd(1e-3)
         if args.coarse == "arnoldi":
             return dropped, ctx.build_coarse(ctx.rhs(tod)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
@@ -528,6 +531,7 @@ def run_templates(args, world, rank, local):
     else:   # A x alone
         ctx.setup_scan(scan)
         ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
+        ctx.set_option("fp64_products", args.fp64_products)
         t_setup, dropped, k = 0.0, ctx.build_bd(1e-3), 0
     for name, pc in ((("two_level", M.MM_PRECOND_2L), ("m_bd", M.MM_PRECOND_BD)) if args.steps > 0 else ()):
         ctx.solve(tod, pc, tol=args.tol, max_iter=args.max_iter, out=out)
@@ -561,7 +565,9 @@ def run_templates(args, world, rank, local):
             "precision": args.precision, "coarse_from": args.coarse, "m_max": args.m_max,
             "samples": scan.n_samples, "subscans": int(len(sub_off) - 1), "pixels_dropped": dropped, "k": k,
             "setup_once_s": t_setup, "two_level": res.get("two_level"), "m_bd": res.get("m_bd"),
-            "apply_A": {"kernel": "k_filter_tmpl<%s>" % ("double" if prec == M.MM_FP64 else "float"), "ms": ax_ms, "samples_per_s": scan.n_samples / (ax_ms * 1e-3),
+            "fp64_products": ["float64", "double-float"][args.fp64_products - 1] if prec == M.MM_FP64 else None,
+            "apply_A": {"kernel": "k_filter_tmpl<%s>" % (("double", "df")[args.fp64_products - 1] if prec == M.MM_FP64
+                                                         else "float"), "ms": ax_ms, "samples_per_s": scan.n_samples / (ax_ms * 1e-3),
                         "hbm_gbs_12B_per_sample": gbs, "hbm_frac_of_measured": gbs / hbm},
             "gen_s": t_gen}
     if rank == 0:

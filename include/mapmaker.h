@@ -219,8 +219,11 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * mm_build_coarse_from_solve); "time_filter": 1 records CUDA events around
  * every filter launch; "fp64_products": 1 native float64 or 2 (default for
  * MM_FP32_MIXED) double-float arithmetic (float32 pairs, about 44 bits) for
- * b and the refinement residuals; "apply_precision": precision of
- * mm_apply_A (0 context, 1 float64, 2 double-float); "inner_tol": in
+ * b and the refinement residuals, and in MM_FP64 for every operator product
+ * as well (PCG, Arnoldi, A Z, mm_apply_A; vectors, dot products and the
+ * coarse space stay float64); MM_ERR_STATE while a solve is in progress;
+ * "apply_precision": precision of mm_apply_A (0 context, 1 float64,
+ * 2 double-float); "inner_tol": in
  * MM_FP32_MIXED, the smallest relative tolerance asked of a float32-operator
  * PCG run between float64-accurate refinements (default 2e-6);
  * "half_transform": 1 (default) lets a whole block of N real samples run as
@@ -298,8 +301,8 @@ mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done);
  *                  the range of A and leaves that component at 0.
  * The filters act on every sample, flagged ones included.  Calling with
  * poly_order = -1, az_bin = NULL and stokes = 0 restores the band weight.
- * Clears M_BD and the coarse space (rebuild them), sets "fp64_products" to 1
- * (native float64; double-float products are not available here).
+ * Clears M_BD and the coarse space (rebuild them) and sets "fp64_products"
+ * to 1 (native float64); set it to 2 afterwards for double-float products.
  * Right-hand sides of uneven length (rhs_len) are not supported with
  * templates (MM_ERR_ARG at solve time).  The longest block and the bins must
  * fit shared memory: 8 bytes per sample + 12 bytes per bin <= 220 KB.

@@ -194,6 +194,10 @@ mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
     } while (0)
 
 bool is_f32(const mm_ctx* c) { return c->prec == MM_FP32_MIXED; }
+// Precision of the solver's operator products (PCG, Arnoldi, A Z): float32 in
+// MM_FP32_MIXED; in MM_FP64 the float64-accurate kind of "fp64_products"
+// (1 native float64, 2 double-float).
+int op_prec(const mm_ctx* c) { return is_f32(c) ? 0 : c->p64; }
 
 cudaError_t copy_in(void* dst, const void* src, size_t bytes, int mem, cudaStream_t s) {
     return cudaMemcpyAsync(dst, src, bytes, mem == MM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
@@ -892,8 +896,6 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
     if (ctx->tmpl_on) {
         if (!plan->lens.empty() || !plan->starts.empty())
             return fail(ctx, MM_ERR_ARG, "template filters: right-hand sides of uneven length are not supported");
-        if (plan->f64 == 2)
-            return fail(ctx, MM_ERR_ARG, "template filters: double-float products are not available (float64 is)");
         TmplArgs t{};
         t.block_off = ctx->d_block_off.as<int64_t>();
         t.n_blocks = ctx->n_blocks;
@@ -906,7 +908,7 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
         t.az = ctx->tmpl_bins > 0 ? ctx->d_taz.as<int32_t>() : nullptr;
         t.n_bins = ctx->tmpl_bins;
         t.stokes = ctx->tmpl_qu;
-        launch_filter_tmpl(a, t, plan->nrhs, plan->f64 == 1, from_tod, ctx->stream);
+        launch_filter_tmpl(a, t, plan->nrhs, plan->f64, from_tod, ctx->stream);
     } else if (plan->variant == 2) {
         FftTables& ft = plan->ft;
         a.H = ft.H.p;
@@ -990,7 +992,7 @@ PcgArgs pcg_args(mm_ctx* ctx) {
         a.src_f32 = 1;
     } else {
         a.q64 = ctx->s_q.as<V4<double>>();
-        a.src_f32 = 0;
+        a.src_f32 = op_prec(ctx) == 2 ? 2 : 0;   // 2: double-float operator input
     }
     a.src = ctx->s_src.p;
     a.qacc = ctx->s_q.p;
@@ -1203,7 +1205,7 @@ mm_status finish_coarse(mm_ctx* ctx) {
     const int k = ctx->k;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     CK(ctx->d_AZ.ensure((size_t)k * n * 8));
-    TRY(apply_A_dev(ctx, !is_f32(ctx), ctx->d_Z.as<V4<double>>(), ctx->d_AZ.as<V4<double>>(), k));
+    TRY(apply_A_dev(ctx, op_prec(ctx), ctx->d_Z.as<V4<double>>(), ctx->d_AZ.as<V4<double>>(), k));
     DevBuf dG;
     CK(dG.ensure((size_t)k * k * 8));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(k, 2) * sizeof(double) + 64));
@@ -1261,7 +1263,7 @@ static bool uniform_block_bounds(const mm_ctx* ctx, std::vector<int64_t>* rel) {
 // per coarse space: one product per block column, then prefix sums), plus the
 // product over the one partly covered block of each detector.  Otherwise the
 // products are formed directly for every right-hand side.
-mm_status coarse_products_for_lens(mm_ctx* ctx, bool f64) {
+mm_status coarse_products_for_lens(mm_ctx* ctx, int f64) {
     const int k = ctx->k, R = ctx->nrhs;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     std::vector<int64_t> rel;
@@ -1329,8 +1331,7 @@ mm_status coarse_products_for_lens(mm_ctx* ctx, bool f64) {
 mm_status coarse_for_lens(mm_ctx* ctx) {
     const int k = ctx->k, R = ctx->nrhs;
     const int64_t n = (int64_t)ctx->n_pix * 4;
-    const bool f64 = !is_f32(ctx);
-    TRY(coarse_products_for_lens(ctx, f64));
+    TRY(coarse_products_for_lens(ctx, op_prec(ctx)));
     DevBuf dG;
     CK(dG.ensure((size_t)R * k * k * 8));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * std::max(k, 2) * sizeof(double) + 64));
@@ -1596,7 +1597,7 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     ctx->tmpl_bins = nbins;
     ctx->tmpl_qu = stokes;
     ctx->tmpl_max_block = maxb;
-    ctx->p64 = 1;   // float64-accurate products of the template filter run in native float64
+    ctx->p64 = 1;   // native float64 by default; "fp64_products" = 2 selects double-float afterwards
     return MM_OK;
 }
 
@@ -1689,8 +1690,7 @@ mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int 
     launch_map_in(xsrc, in4.as<V4<double>>(), nv, ctx->stream);
     CKL();
     Plan* plan = nullptr;
-    int aprec = ctx->opt_apply_prec ? ctx->opt_apply_prec : (is_f32(ctx) ? 0 : 1);
-    if (ctx->tmpl_on && aprec == 2) aprec = 1;
+    const int aprec = ctx->opt_apply_prec ? ctx->opt_apply_prec : op_prec(ctx);
     TRY(get_plan(ctx, aprec, nrhs, {}, &plan));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     TRY(apply_A_dev(ctx, aprec, in4.as<V4<double>>(), out4.as<V4<double>>(), nrhs, plan));
@@ -1811,7 +1811,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     launch_scale_host(W, n, 1.0 / std::sqrt(nrm2), ctx->stream);
     std::vector<double> H((size_t)(m_max + 1) * m_max, 0.0);   // row-major (m_max+1) x m_max
     Plan* plan = nullptr;
-    const bool f64 = !is_f32(ctx);
+    const int f64 = op_prec(ctx);
     TRY(get_plan(ctx, f64, 1, {}, &plan));
     V4<double>* q = ctx->w_b.as<V4<double>>();
     int m = m_max;
@@ -2069,7 +2069,7 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     }
     ctx->coarse_per_rhs = false;
     if (ctx->use_lens && precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx));
-    TRY(get_plan(ctx, !f32, nrhs, ctx->lens, &ctx->plan_op));
+    TRY(get_plan(ctx, op_prec(ctx), nrhs, ctx->lens, &ctx->plan_op));
     TRY(get_plan(ctx, ctx->p64, nrhs, ctx->lens, &ctx->plan_64));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     const size_t esz = f32 ? 4 : 8;
@@ -2380,6 +2380,7 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_apply_prec = v;
     } else if (n == "fp64_products") {
         if (v != 1 && v != 2) return fail(ctx, MM_ERR_ARG, "fp64_products must be 1 (float64) or 2 (double-float)");
+        if (ctx->phase != PH_IDLE) return fail(ctx, MM_ERR_STATE, "fp64_products cannot change during a solve");
         ctx->p64 = v;
     } else if (n == "harvest") {
         if (v < 0 || v > 4096) return fail(ctx, MM_ERR_ARG, "harvest must lie in [0, 4096]");
@@ -2428,12 +2429,12 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "plan_fft_log2") {
         Plan* p = nullptr;
         if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");
-        TRY(get_plan(ctx, !is_f32(ctx), 1, {}, &p));
+        TRY(get_plan(ctx, op_prec(ctx), 1, {}, &p));
         *value = p->variant == 2 ? p->logL : 0;
     } else if (n == "plan_fft_len" || n == "plan_whole") {
         Plan* p = nullptr;
         if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "no pointing");
-        TRY(get_plan(ctx, !is_f32(ctx), 1, {}, &p));
+        TRY(get_plan(ctx, op_prec(ctx), 1, {}, &p));
         *value = n == "plan_whole" ? p->whole : (p->variant == 2 ? p->L : 0);
     } else if (n == "device_bytes") {
         size_t f = 0, t = 0;

@@ -110,7 +110,8 @@ struct TmplArgs {
     int n_bins;
     int stokes;                // 0: rows (1, cos 2psi, sin 2psi); 1: (0, cos, sin), d^-; 2: (1, 0, 0), d^+
 };
-void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s);
+// prec: 0 float32, 1 float64, 2 double-float
+void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, int prec, bool from_tod, cudaStream_t s);
 size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64);
 
 // T = float or double; from_tod selects b = P^T W d (src is a TOD).
@@ -157,7 +158,7 @@ struct PcgArgs {
     const V4<double>* q64;   // A p in float64 (FP64 operator)
     const V4<float>* q32;    // A p in float32 (FP32 operator)
     void* src;               // gather source for the next product (V4<T>)
-    int src_f32;
+    int src_f32;             // operator input: 0 float64, 1 float32, 2 double-float
     void* qacc;              // accumulator to clear (V4<T>)
     const double* bd; int bd_per_rhs;
     // two-level

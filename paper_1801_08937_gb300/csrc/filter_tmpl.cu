@@ -23,6 +23,10 @@
 //   4. step 2 again;
 //   5. z = w_b y scattered into the map (P^T), runs of equal pixels summed in
 //      the warp first.
+// The arithmetic type is float32, float64, or double-float (float32 pairs,
+// float64 atomics for the bin sums and the map); the double-float kernel gives
+// float64-accurate products from the float32 units, which GB300 issues at 64
+// times its float64 rate.
 #include "filter_impl.cuh"
 
 namespace mm {
@@ -30,6 +34,20 @@ namespace mm {
 constexpr int TMPL_NT = 512;
 
 __device__ __forceinline__ int shfl_down_t(int v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float shfl_xor_t(float v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_xor_t(double v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ df shfl_xor_t(df v, int d) {
+    return df(__shfl_xor_sync(0xffffffffu, v.hi, d), __shfl_xor_sync(0xffffffffu, v.lo, d));
+}
+
+// 2 / m in the arithmetic type (double-float: from the float64 quotient).
+template <typename T> __device__ __forceinline__ T two_over(int m) { return T(2) / T(m); }
+template <> __device__ __forceinline__ df two_over<df>(int m) { return df(2.0 / (double)m); }
+
+// A value in the accumulator type of the bin sums and the map.
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ double to_acc(df v) { return (double)v; }
 
 // Sum of v over the run of lanes with equal key that starts at this lane
 // (valid on the run's first lane, `head`); runs are consecutive lanes.
@@ -54,7 +72,7 @@ __device__ __forceinline__ T warp_run_sum(int key, T v, bool& head) {
 template <typename T>
 __device__ __forceinline__ T warp_sum_all(T v) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    for (int d = 16; d > 0; d >>= 1) v += shfl_xor_t(v, d);
     return v;
 }
 
@@ -89,7 +107,7 @@ __device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0) {
         const int64_t s0 = t.sub_off[s];
         const int m = (int)(t.sub_off[s + 1] - s0);
         const int o = (int)(s0 - b0);
-        const T inv_m = T(2) / T(m);
+        const T inv_m = two_over<T>(m);
         const T u0 = inv_m * T(0.5) - T(1);
         T mom[4] = {T(0), T(0), T(0), T(0)};
         for (int i = lane; i < m; i += 32) {
@@ -121,8 +139,10 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     if (a.state && !a.state[rhs].active) return;
     const int64_t b0 = t.block_off[blk];
     const int nb = (int)(t.block_off[blk + 1] - b0);
+    using Acc = typename AccT<T>::type;
+    static_assert(sizeof(Acc) == sizeof(T), "bin means overwrite the bin sums in place");
     T* y = reinterpret_cast<T*>(smraw);
-    T* gsum = y + ((nb + 1) & ~1);
+    Acc* gsum = reinterpret_cast<Acc*>(y + ((nb + 1) & ~1));
     int* gcnt = reinterpret_cast<int*>(gsum + t.n_bins);
     const T iw = t.stokes == 1 ? T(0) : T(1);   // I column of P
     const T pw = t.stokes == 2 ? T(0) : T(1);   // Q, U columns
@@ -183,7 +203,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
         y[i] = v;
     }
     for (int i = threadIdx.x; i < t.n_bins; i += TMPL_NT) {
-        gsum[i] = T(0);
+        gsum[i] = Acc(0);
         gcnt[i] = 0;
     }
     __syncthreads();
@@ -208,14 +228,22 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
             const T sv = warp_run_sum<T>(g, v, head);
             const int cn = warp_run_sum<int>(g, (g >= 0) ? 1 : 0, head);
             if (head && g >= 0) {
-                atomicAdd(gsum + g, sv);
+                atomicAdd(gsum + g, to_acc(sv));
                 atomicAdd(gcnt + g, cn);
             }
         }
         __syncthreads();
+        // bin means, in place of the sums (one division per bin, not per sample)
+        T* gmean = reinterpret_cast<T*>(gsum);
+        for (int i = threadIdx.x; i < t.n_bins; i += TMPL_NT) {
+            const Acc sm = gsum[i];
+            const int n = gcnt[i];
+            gmean[i] = n > 0 ? T(sm / Acc(n)) : T(0);
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < nb; i += TMPL_NT) {
             const int g = __ldg(t.az + b0 + i);
-            if (g >= 0 && g < t.n_bins) y[i] -= gsum[g] / T(gcnt[g]);
+            if (g >= 0 && g < t.n_bins) y[i] -= gmean[g];
         }
         __syncthreads();
         // 4. (1 - Pi_B) again
@@ -226,7 +254,6 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     }
     // without a ground template F_B W^-1 F_B = w_b (1 - Pi_B)^2 = w_b (1 - Pi_B): one projection
     // 5. weight and scatter
-    using Acc = typename AccT<T>::type;
     V4<Acc>* q = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)rhs * a.n_pix;
     const T wb = T(t.w_block[blk]);
     if constexpr (std::is_same<T, float>::value) {
@@ -299,9 +326,12 @@ static void launch_tmpl_t(const FilterArgs& a, const TmplArgs& t, int nrhs, cuda
     }
 }
 
-void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, bool f64, bool from_tod, cudaStream_t s) {
+void launch_filter_tmpl(const FilterArgs& a, const TmplArgs& t, int nrhs, int prec, bool from_tod, cudaStream_t s) {
     if (t.n_blocks <= 0 || nrhs <= 0) return;
-    if (f64) {
+    if (prec == 2) {
+        if (from_tod) launch_tmpl_t<df, true>(a, t, nrhs, s);
+        else launch_tmpl_t<df, false>(a, t, nrhs, s);
+    } else if (prec == 1) {
         if (from_tod) launch_tmpl_t<double, true>(a, t, nrhs, s);
         else launch_tmpl_t<double, false>(a, t, nrhs, s);
     } else {

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace mm {
 
@@ -456,9 +457,13 @@ __global__ void k_pcg_src(const PcgArgs a, int first) {
         V4<double> pv = a.p[off + i];
         pv = first ? zv : V4<double>{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, 0.0};
         a.p[off + i] = pv;
-        if (a.src_f32) {
+        if (a.src_f32 == 1) {
             reinterpret_cast<V4<float>*>(a.src)[off + i] = V4<float>{(float)pv.x, (float)pv.y, (float)pv.z, 0.0f};
             reinterpret_cast<V4<float>*>(a.qacc)[off + i] = V4<float>{0.f, 0.f, 0.f, 0.f};
+        } else if (a.src_f32 == 2) {
+            // double-float operator input, float64 accumulators
+            reinterpret_cast<V4<df>*>(a.src)[off + i] = V4<df>{df(pv.x), df(pv.y), df(pv.z), df(0.0)};
+            reinterpret_cast<V4<double>*>(a.qacc)[off + i] = V4<double>{0, 0, 0, 0};
         } else {
             reinterpret_cast<V4<double>*>(a.src)[off + i] = pv;
             reinterpret_cast<V4<double>*>(a.qacc)[off + i] = V4<double>{0, 0, 0, 0};

@@ -241,6 +241,30 @@ def test_solve_bd_matches_oracle(prec):
     assert rel(x[0], xo) < 1e-6
 
 
+@pytest.mark.parametrize("filt,fft_len", [(1, 0), (2, 4608), (2, 8192)])
+def test_fp64_solve_with_double_float_products(filt, fft_len):
+    """MM_FP64 with "fp64_products" = 2: every operator product of the solve (b, PCG, Arnoldi, A Z,
+    the true residual) and mm_apply_A run in double-float arithmetic; A x matches the oracle to
+    1e-11 and the M_BD and M_2l maps match the oracle map."""
+    scan, d, _ = scan_and_tod(SMALL, seed=25, flag_frac=0.01)
+    prob, mbd, good = oracle_problem(scan)
+    c = ctx_for(scan, MM.MM_FP64, filt, fft_len=fft_len)
+    c.set_option("fp64_products", 2)
+    c.build_bd()
+    xr = np.random.default_rng(25).standard_normal((scan.n_pix, 3))
+    assert rel(c.apply_A(xr)[0], O.apply_A(prob, xr)) < TOL64
+    x, info = c.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=2000)
+    assert info[0]["status"] == "MM_OK" and info[0]["true_rel_res"] < 1e-9
+    xo = _oracle_solution(prob, mbd, O.rhs(prob, d))
+    assert rel(x[0], xo) < 1e-6
+    k = c.build_coarse(None, m_max=60, eps_arn=1e-8, k=16)
+    assert k >= 4
+    x2, i2 = c.solve(d, MM.MM_PRECOND_2L, tol=1e-10, max_iter=2000)
+    assert i2[0]["status"] == "MM_OK" and rel(x2[0], xo) < 1e-6
+    assert i2[0]["iters"] <= info[0]["iters"]
+    c.close()
+
+
 @pytest.mark.parametrize("products", [1, 2])
 def test_mixed_true_residual_matches_oracle(products):
     """The mixed-precision solve forms its refinement residual as P^T W (d - P x) in one

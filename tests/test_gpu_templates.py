@@ -3,8 +3,9 @@
 A = P^T F P with F = F_B W^-1 F_G W^-1 F_B (Sect. 2.1 Eq. filtnoise, Sect. 4,
 Sect. 5.1): Legendre subscan polynomials, azimuth-bin ground templates, white
 block weights, and the differenced timeline d^- (pointing rows (0, cos, sin)).
-Tolerances as for the band operator: float64 1e-11, float32 1e-5 relative on
-A x; solved maps 1e-6 against an oracle solution converged to 1e-13.
+Tolerances as for the band operator: float64 and double-float (option
+"fp64_products" = 2) 1e-11, float32 1e-5 relative on A x; solved maps 1e-6
+against an oracle solution converged to 1e-13.
 """
 import numpy as np
 import pytest
@@ -53,15 +54,17 @@ def kept(tp, rcond_min=1e-3):
 
 @pytest.mark.parametrize("order,ground,qu_only", [(0, True, 1), (1, True, 1), (3, True, 1), (2, False, 1),
                                                   (-1, True, 1), (1, True, 0), (3, True, 2), (0, False, 2)])
-@pytest.mark.parametrize("prec", [MM.MM_FP64, MM.MM_FP32_MIXED])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df"])
 def test_apply_A_matches_oracle(order, ground, qu_only, prec):
     scan, so, az, nb = scan_tmpl(seed=1)
     tp = oracle_tp(scan, so, az, nb, order, ground, qu_only)
-    c = ctx_tmpl(scan, so, az, nb, order, ground, qu_only, prec)
+    c = ctx_tmpl(scan, so, az, nb, order, ground, qu_only, MM.MM_FP32_MIXED if prec == "f32" else MM.MM_FP64)
+    if prec == "df":
+        c.set_option("fp64_products", 2)
     x = np.random.default_rng(2).standard_normal((2, scan.n_pix, 3))
     y = c.apply_A(x)
     for r in range(2):
-        assert rel(y[r], O.apply_A_T(tp, x[r])) < (TOL64 if prec == MM.MM_FP64 else TOL32)
+        assert rel(y[r], O.apply_A_T(tp, x[r])) < (TOL32 if prec == "f32" else TOL64)
     c.close()
 
 
@@ -129,6 +132,44 @@ def test_solve_bd_and_two_level_match_oracle(prec):
     assert i2[0]["status"] == "MM_OK"
     assert rel(x2[0], xo) < 1e-6
     assert i2[0]["iters"] < ib[0]["iters"]
+    c.close()
+
+
+@pytest.mark.parametrize("stokes", [1, 2])
+def test_double_float_products_rhs_and_two_level_solve(stokes):
+    """MM_FP64 with "fp64_products" = 2: b, the PCG and Arnoldi products and the true residual run in
+    double-float arithmetic; b matches the oracle to 1e-11, and the M_BD and M_2l maps match the oracle
+    map (d^-) or satisfy the oracle's normal equations (d^+, which has a null vector)."""
+    scan, so, az, nb = scan_tmpl(seed=13, flag_frac=0.0 if stokes == 2 else 0.01)
+    order = 1 if stokes == 1 else 3
+    tp = oracle_tp(scan, so, az, nb, order, True, stokes)
+    sky = synth.make_sky(scan.n_pix, 13)
+    if stokes == 1:
+        sky[:, 0] = 0.0
+    else:
+        sky[:, 1:] = 0.0
+    d = synth.make_tod(scan, sky, synth.make_noise(scan, 13))
+    c = ctx_tmpl(scan, so, az, nb, order, True, stokes)
+    c.set_option("fp64_products", 2)
+    assert c.get_option("fp64_products") == 2
+    c.build_bd(1e-3)
+    tpk, good, mbd = kept(tp)
+    b = c.rhs(d)[0]
+    bo = O.rhs_T(tpk, d)
+    assert rel(b, bo) < TOL64
+    xb, ib = c.solve(d, MM.MM_PRECOND_BD, tol=1e-10, max_iter=5000)
+    assert ib[0]["status"] == "MM_OK" and ib[0]["true_rel_res"] <= 1e-9
+    k = c.build_coarse(b, m_max=120, eps_arn=1e-12, k=24)
+    assert k >= 8
+    x2, i2 = c.solve(d, MM.MM_PRECOND_2L, tol=1e-10, max_iter=5000)
+    assert i2[0]["status"] == "MM_OK" and i2[0]["true_rel_res"] <= 1e-9
+    assert i2[0]["iters"] < ib[0]["iters"]
+    if stokes == 1:
+        xo = _oracle_map(tpk, mbd, d)
+        assert rel(xb[0], xo) < 1e-6 and rel(x2[0], xo) < 1e-6
+    else:
+        for x in (xb[0], x2[0]):
+            assert np.linalg.norm(bo - O.apply_A_T(tpk, x)) <= 2e-10 * np.linalg.norm(bo)
     c.close()
 
 

@@ -149,33 +149,33 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     const V4<T>* xm = nullptr;
     if (!FROM_TOD) xm = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix;
     else if (a.xmap) xm = reinterpret_cast<const V4<T>*>(a.xmap) + (int64_t)rhs * a.n_pix;
-    // 1. gather (float32: four consecutive samples per thread, vector pointing loads)
-    if constexpr (std::is_same<T, float>::value) {
+    // 1. gather (float32 and double-float: four consecutive samples per thread, vector pointing loads)
+    if constexpr (!std::is_same<T, double>::value) {
         for (int u = threadIdx.x; 4 * u < nb; u += TMPL_NT) {
             const int i0 = 4 * u;
             const int64_t t0 = b0 + i0;
             int p[4];
             float ps[4];
             load4(a, t0, true, nb - i0, p, ps);
-            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            T v[4] = {T(0), T(0), T(0), T(0)};
             if (FROM_TOD) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (i0 + j < nb)
-                        v[j] = a.tod_is_float ? __ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t0 + j)
-                                              : (float)__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t0 + j);
+                        v[j] = a.tod_is_float ? T(__ldg(reinterpret_cast<const float*>(a.src) + rhs * a.n_samples + t0 + j))
+                                              : T(__ldg(reinterpret_cast<const double*>(a.src) + rhs * a.n_samples + t0 + j));
             }
             if (xm) {
-                V4<float> m[4];
+                V4<T> m[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (p[j] >= 0) m[j] = ldmap<float>(xm + p[j]);
+                    if (p[j] >= 0) m[j] = ldmap<T>(xm + p[j]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (p[j] >= 0) {
-                        float c, s;
+                        T c, s;
                         weights_from(a, t0 + j, ps[j], c, s);
-                        const float px = iw * m[j].x + pw * (c * m[j].y + s * m[j].z);
+                        const T px = iw * m[j].x + pw * (c * m[j].y + s * m[j].z);
                         v[j] = FROM_TOD ? v[j] - px : px;
                     }
             }
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     // 5. weight and scatter
     V4<Acc>* q = reinterpret_cast<V4<Acc>*>(a.dst) + (int64_t)rhs * a.n_pix;
     const T wb = T(t.w_block[blk]);
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (!std::is_same<T, double>::value) {
         // four consecutive samples per lane, in-lane run sums, then the warp-segmented sums
         constexpr int NW = TMPL_NT / 32;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
             int p[4];
             float ps[4];
             load4(a, t0, i0 < nb, nb - i0, p, ps);
-            float v0[4], v1[4], v2[4];
+            T v0[4], v1[4], v2[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float z = 0.0f, c = 0.0f, sn = 0.0f;
+                T z = T(0), c = T(0), sn = T(0);
                 if (p[j] >= 0) {
                     z = wb * y[i0 + j];
                     weights_from(a, t0 + j, ps[j], c, sn);

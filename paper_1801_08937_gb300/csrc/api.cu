@@ -1846,8 +1846,9 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     std::vector<double> Hm((size_t)m * m);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m_max + j];
-    std::vector<double> wr, wi, vr, vi;
-    if (!host_eig(Hm, m, wr, wi, vr, vi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m did not converge");
+    // Ritz values first; Ritz vectors (inverse iteration) only for the selected ones
+    std::vector<double> wr, wi, er, ei;
+    if (!host_hess_eigvals(Hm, m, wr, wi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m did not converge");
     std::vector<int> order(m);
     for (int i = 0; i < m; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
@@ -1867,9 +1868,9 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
         if (std::fabs(wr[idx]) <= wnull) continue;
         if (k <= 0 && !(wr[idx] < eps_lambda)) break;
         used[idx] = 1;
-        std::vector<double> c(m);
-        for (int i = 0; i < m; ++i) c[i] = vr[(size_t)i * m + idx];
-        cols.push_back(c);
+        if (!host_hess_eigvec(Hm, m, wr[idx], wi[idx], er, ei))
+            return fail(ctx, MM_ERR_SINGULAR, "inverse iteration for a Ritz vector failed");
+        cols.push_back(er);
         vals.push_back(wr[idx]);
         if (wi[idx] != 0.0) {
             int partner = -1;
@@ -1884,9 +1885,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
             }
             if (partner >= 0) used[partner] = 1;
             if ((int)cols.size() < kwant) {
-                std::vector<double> ci(m);
-                for (int i = 0; i < m; ++i) ci[i] = vi[(size_t)i * m + idx];
-                cols.push_back(ci);
+                cols.push_back(ei);
                 vals.push_back(wr[idx]);
             }
         }
@@ -1932,8 +1931,8 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
             T[(size_t)(j + 1) * m + j] = off;
         }
     }
-    std::vector<double> wr, wi, vr, vi;
-    if (!host_eig(T, m, wr, wi, vr, vi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
+    std::vector<double> wr, wi, er, ei;
+    if (!host_hess_eigvals(T, m, wr, wi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
     std::vector<int> order(m);
     for (int i = 0; i < m; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
@@ -1952,8 +1951,11 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     const int ksel = (int)sel.size();
     if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
     std::vector<double> C((size_t)m * ksel);
-    for (int r = 0; r < m; ++r)
-        for (int c = 0; c < ksel; ++c) C[(size_t)r * ksel + c] = vr[(size_t)r * m + sel[c]];
+    for (int c = 0; c < ksel; ++c) {
+        if (!host_hess_eigvec(T, m, wr[sel[c]], wi[sel[c]], er, ei))
+            return fail(ctx, MM_ERR_SINGULAR, "inverse iteration for a Ritz vector failed");
+        for (int r = 0; r < m; ++r) C[(size_t)r * ksel + c] = er[r];
+    }
     DevBuf dC;
     CK(dC.ensure(C.size() * 8));
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));

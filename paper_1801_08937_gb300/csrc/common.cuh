@@ -221,10 +221,13 @@ struct CoarseView {
 };
 
 // ---------------- host linear algebra ----------------
-// Eigenvalues and right eigenvectors of a real m x m matrix (row-major),
-// via complex shifted QR and inverse iteration.  Returns false on failure.
-bool host_eig(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi,
-              std::vector<double>& vr, std::vector<double>& vi);
+// Eigenvalues of a real upper Hessenberg m x m matrix (row-major) by
+// double-shift QR; near-real values come back real.  False on failure.
+bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
+// Right eigenvector (unit norm, largest component real positive) of the
+// Hessenberg H for the eigenvalue wr + i wi, by inverse iteration.
+bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
+                      std::vector<double>& vi);
 // Lower Cholesky factor in place (row-major n x n); false if not SPD.
 bool host_cholesky(std::vector<double>& A, int n);
 // Inverse of an SPD matrix from its Cholesky factor.

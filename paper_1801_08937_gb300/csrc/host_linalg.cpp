@@ -1,12 +1,17 @@
 // Small dense float64 linear algebra on the host: the eigen-solve of the
-// Arnoldi Hessenberg matrix H_m (Appendix A, Eq. ritz; m <= a few hundred),
-// the Cholesky factor of the coarse operator E = Z^T A Z (Sect. 3.2) and the
-// triangular inverses used to orthonormalise Z.
+// Arnoldi Hessenberg matrix H_m (Appendix A, Eq. ritz; m up to about a
+// thousand) and of the Lanczos tridiagonal matrix, the Cholesky factor of the
+// coarse operator E = Z^T A Z (Sect. 3.2) and the triangular inverses used to
+// orthonormalise Z.
 //
-// Eigenvalues: single-shift QR iteration on the complex upper Hessenberg
-// matrix with Wilkinson shifts and Givens rotations (deflating from the
-// bottom).  Eigenvectors: inverse iteration with the Hessenberg LU of
-// (H - lambda I), three sweeps from a fixed start vector.
+// Eigenvalues: Francis double-shift QR iteration in real arithmetic on the
+// active window of the upper Hessenberg matrix (3-element Householder
+// reflectors chase the bulge; 1x1 and 2x2 blocks deflate from the bottom; an
+// exceptional shift every tenth iteration without deflation).  Only the
+// window is updated, which is all the eigenvalues need.  Eigenvectors, for
+// the wanted eigenvalues only: inverse iteration with one Hessenberg LU of
+// (H - sigma I) (pivoting between adjacent rows) and three solves from a
+// fixed start vector; real arithmetic for a real eigenvalue.
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -17,160 +22,234 @@ namespace mm {
 
 using cd = std::complex<double>;
 
-static bool hess_eigenvalues(std::vector<cd> a, int n, std::vector<cd>& ev) {
-    auto A = [&](int i, int j) -> cd& { return a[(size_t)i * n + j]; };
-    ev.assign(n, cd(0, 0));
-    const double eps = 2.220446049250313e-16;
-    int hi = n - 1;
-    int iter = 0, total = 0;
-    while (hi >= 0) {
-        if (hi == 0) {
-            ev[0] = A(0, 0);
-            break;
+namespace {
+
+double max_abs(const std::vector<double>& H, int n) {
+    double h = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) h = std::max(h, std::fabs(H[i]));
+    return h;
+}
+
+// Eigenvalues of the 2x2 block [[a, b], [c, d]].
+void eig2(double a, double b, double c, double d, double& r1, double& i1, double& r2, double& i2) {
+    const double mid = 0.5 * (a + d), p = 0.5 * (a - d);
+    const double disc = p * p + b * c;
+    if (disc >= 0.0) {
+        const double sq = std::sqrt(disc);
+        r1 = mid + sq;
+        r2 = mid - sq;
+        i1 = i2 = 0.0;
+    } else {
+        const double sq = std::sqrt(-disc);
+        r1 = r2 = mid;
+        i1 = sq;
+        i2 = -sq;
+    }
+}
+
+// Unit 2-norm, largest component real and positive.
+bool normalise(std::vector<double>& y) {
+    double nrm = 0.0;
+    int imax = 0;
+    for (size_t i = 0; i < y.size(); ++i) {
+        nrm += y[i] * y[i];
+        if (std::fabs(y[i]) > std::fabs(y[imax])) imax = (int)i;
+    }
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0) || !std::isfinite(nrm)) return false;
+    const double f = (y[imax] < 0 ? -1.0 : 1.0) / nrm;
+    for (double& v : y) v *= f;
+    return true;
+}
+bool normalise(std::vector<cd>& y) {
+    double nrm = 0.0;
+    int imax = 0;
+    for (size_t i = 0; i < y.size(); ++i) {
+        nrm += std::norm(y[i]);
+        if (std::abs(y[i]) > std::abs(y[imax])) imax = (int)i;
+    }
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0) || !std::isfinite(nrm)) return false;
+    const cd ph = std::abs(y[imax]) > 0 ? std::conj(y[imax]) / std::abs(y[imax]) : cd(1, 0);
+    for (cd& v : y) v *= ph / nrm;
+    return true;
+}
+
+// sum_j a[j] b[j] with four independent partial sums (the back-substitution
+// is otherwise one serial chain of dependent additions).
+template <typename S>
+S dot4(const S* a, const S* b, int len) {
+    S s0 = S(0), s1 = S(0), s2 = S(0), s3 = S(0);
+    int j = 0;
+    for (; j + 4 <= len; j += 4) {
+        s0 += a[j] * b[j];
+        s1 += a[j + 1] * b[j + 1];
+        s2 += a[j + 2] * b[j + 2];
+        s3 += a[j + 3] * b[j + 3];
+    }
+    for (; j < len; ++j) s0 += a[j] * b[j];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Inverse iteration for the eigenvector of the upper Hessenberg H (n x n,
+// row-major) closest to sigma; S is double or complex.  The LU of
+// (H - sigma I) is formed in one pass over H (the pivot row is carried in a
+// buffer; rows of U are stored packed from their diagonal).  Tiny pivots are
+// replaced by a perturbation of the order of 1e-14 ||H||.
+template <typename S>
+bool inverse_iteration(const std::vector<double>& H, int n, S sigma, double hnorm, std::vector<S>& y) {
+    const double tiny = 1e-14 * (hnorm > 0 ? hnorm : 1.0);
+    std::vector<size_t> off(n + 1);
+    off[0] = 0;
+    for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(n - i);
+    std::vector<S> u(off[n]);
+    std::vector<char> swp(n, 0);
+    std::vector<S> mult(n, S(0));
+    std::vector<S> bufa(n), bufb(n);
+    S* cur = bufa.data();
+    S* nxt = bufb.data();
+    for (int j = 0; j < n; ++j) cur[j] = H[j];
+    cur[0] -= sigma;
+    for (int k = 0; k + 1 < n; ++k) {
+        const double* hr = &H[(size_t)(k + 1) * n];
+        for (int j = k; j < n; ++j) nxt[j] = hr[j];
+        nxt[k + 1] -= sigma;
+        if (std::abs(nxt[k]) > std::abs(cur[k])) {
+            swp[k] = 1;
+            std::swap(cur, nxt);
         }
-        int l = hi;
-        while (l > 0) {
-            const double s = std::abs(A(l - 1, l - 1)) + std::abs(A(l, l));
-            if (std::abs(A(l, l - 1)) <= eps * (s > 0 ? s : 1.0)) {
-                A(l, l - 1) = 0.0;
-                break;
-            }
-            --l;
+        if (std::abs(cur[k]) < tiny) cur[k] = tiny;
+        const S f = nxt[k] / cur[k];
+        mult[k] = f;
+        S* ur = &u[off[k]];
+        for (int j = k; j < n; ++j) ur[j - k] = cur[j];
+        for (int j = k + 1; j < n; ++j) nxt[j] -= f * cur[j];
+        std::swap(cur, nxt);
+    }
+    if (std::abs(cur[n - 1]) < tiny) cur[n - 1] = tiny;
+    u[off[n - 1]] = cur[n - 1];
+    y.resize(n);
+    for (int i = 0; i < n; ++i) y[i] = S(1.0 + 0.01 * ((i * 7919) % 101));
+    for (int sweep = 0; sweep < 3; ++sweep) {
+        for (int k = 0; k + 1 < n; ++k) {
+            if (swp[k]) std::swap(y[k], y[k + 1]);
+            y[k + 1] -= mult[k] * y[k];
         }
-        if (l == hi) {
-            ev[hi] = A(hi, hi);
-            --hi;
-            iter = 0;
-            continue;
+        for (int i = n - 1; i >= 0; --i) {
+            const S* ur = &u[off[i]];
+            y[i] = (y[i] - dot4(ur + 1, &y[i + 1], n - i - 1)) / ur[0];
         }
-        if (++total > 60 * n + 200) return false;
-        ++iter;
-        // Wilkinson shift from the trailing 2x2 block
-        cd mu;
-        const cd p = A(hi - 1, hi - 1), q = A(hi - 1, hi), r = A(hi, hi - 1), d = A(hi, hi);
-        if (iter % 11 == 10) {
-            mu = d + std::abs(r) * 0.75;   // exceptional shift
-        } else {
-            const cd half = 0.5 * (p - d);
-            const cd disc = std::sqrt(half * half + q * r);
-            const cd m1 = d - q * r / (half + disc), m2 = d - q * r / (half - disc);
-            const bool use1 = std::abs(half + disc) >= std::abs(half - disc);
-            mu = use1 ? m1 : m2;
-            if (!std::isfinite(mu.real()) || !std::isfinite(mu.imag())) mu = d;
-        }
-        // QR step on the active block [l, hi]
-        const int m = hi - l + 1;
-        std::vector<double> cs(m);
-        std::vector<cd> sn(m);
-        for (int k = l; k <= hi; ++k) A(k, k) -= mu;
-        for (int k = l; k < hi; ++k) {
-            const cd x = A(k, k), y = A(k + 1, k);
-            const double ax = std::abs(x), ay = std::abs(y);
-            const double rr = std::hypot(ax, ay);
-            double c;
-            cd s;
-            if (rr == 0.0) {
-                c = 1.0;
-                s = 0.0;
-            } else if (ax == 0.0) {
-                c = 0.0;
-                s = std::conj(y) / ay;
-            } else {
-                c = ax / rr;
-                s = (x / ax) * std::conj(y) / rr;
-            }
-            cs[k - l] = c;
-            sn[k - l] = s;
-            for (int j = k; j <= hi; ++j) {
-                const cd u = A(k, j), v = A(k + 1, j);
-                A(k, j) = c * u + s * v;
-                A(k + 1, j) = -std::conj(s) * u + c * v;
-            }
-        }
-        for (int k = l; k < hi; ++k) {
-            const double c = cs[k - l];
-            const cd s = sn[k - l];
-            const int iend = (k + 2 < hi) ? k + 2 : hi;
-            for (int i = l; i <= iend; ++i) {
-                const cd u = A(i, k), v = A(i, k + 1);
-                A(i, k) = u * c + v * std::conj(s);
-                A(i, k + 1) = -u * s + v * c;
-            }
-        }
-        for (int k = l; k <= hi; ++k) A(k, k) += mu;
+        if (!normalise(y)) return false;
     }
     return true;
 }
 
-// Solve (H - sigma I) y = b for upper Hessenberg H with partial pivoting
-// between adjacent rows; tiny pivots are replaced by a perturbation.
-static void hess_shifted_solve(const std::vector<double>& H, int n, cd sigma, std::vector<cd>& b, double hnorm) {
-    std::vector<cd> a((size_t)n * n);
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = H[(size_t)i * n + j] - (i == j ? sigma : cd(0));
-    auto A = [&](int i, int j) -> cd& { return a[(size_t)i * n + j]; };
-    const double tiny = 1e-14 * (hnorm > 0 ? hnorm : 1.0);
-    for (int k = 0; k < n - 1; ++k) {
-        if (std::abs(A(k + 1, k)) > std::abs(A(k, k))) {
-            for (int j = k; j < n; ++j) std::swap(A(k, j), A(k + 1, j));
-            std::swap(b[k], b[k + 1]);
+}  // namespace
+
+bool host_hess_eigvals(const std::vector<double>& H, int n, std::vector<double>& wr, std::vector<double>& wi) {
+    std::vector<double> a(H.begin(), H.begin() + (size_t)n * n);
+    auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+    wr.assign(n, 0.0);
+    wi.assign(n, 0.0);
+    const double hnorm = max_abs(H, n);
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, its = 0, total = 0;
+    while (hi >= 0) {
+        int l = hi;
+        for (; l > 0; --l) {
+            double s = std::fabs(A(l - 1, l - 1)) + std::fabs(A(l, l));
+            if (s == 0.0) s = hnorm;
+            if (std::fabs(A(l, l - 1)) <= eps * s) {
+                A(l, l - 1) = 0.0;
+                break;
+            }
         }
-        if (std::abs(A(k, k)) < tiny) A(k, k) = tiny;
-        const cd f = A(k + 1, k) / A(k, k);
-        if (f != cd(0)) {
-            for (int j = k; j < n; ++j) A(k + 1, j) -= f * A(k, j);
-            b[k + 1] -= f * b[k];
+        if (l == hi) {
+            wr[hi] = A(hi, hi);
+            --hi;
+            its = 0;
+            continue;
+        }
+        if (l == hi - 1) {
+            eig2(A(hi - 1, hi - 1), A(hi - 1, hi), A(hi, hi - 1), A(hi, hi), wr[hi - 1], wi[hi - 1], wr[hi], wi[hi]);
+            hi -= 2;
+            its = 0;
+            continue;
+        }
+        if (++total > 40 * n + 100) return false;
+        ++its;
+        // shifts: the eigenvalues of the trailing 2x2 block (sum s, product t)
+        double s, t;
+        if (its % 10 == 0) {
+            const double ex = std::fabs(A(hi, hi - 1)) + std::fabs(A(hi - 1, hi - 2));
+            const double s1 = A(hi, hi) + 0.75 * ex, s2 = A(hi, hi) - 0.4375 * ex;
+            s = s1 + s2;
+            t = s1 * s2;
+        } else {
+            s = A(hi - 1, hi - 1) + A(hi, hi);
+            t = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);
+        }
+        // first column of (H - s1 I)(H - s2 I) = H^2 - s H + t I on the window
+        double x = A(l, l) * A(l, l) + A(l, l + 1) * A(l + 1, l) - s * A(l, l) + t;
+        double y = A(l + 1, l) * (A(l, l) + A(l + 1, l + 1) - s);
+        double z = A(l + 1, l) * A(l + 2, l + 1);
+        for (int k = l; k < hi; ++k) {
+            const bool three = k + 2 <= hi;
+            if (k > l) {
+                x = A(k, k - 1);
+                y = A(k + 1, k - 1);
+                z = three ? A(k + 2, k - 1) : 0.0;
+            }
+            const double nrm = std::sqrt(x * x + y * y + z * z);
+            if (nrm == 0.0) continue;
+            const double alpha = x >= 0.0 ? -nrm : nrm;
+            const double v0 = x - alpha, v1 = y, v2 = z;
+            const double beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+            // rows k..k+2 from the left
+            for (int j = std::max(l, k - 1); j <= hi; ++j) {
+                const double w = beta * (v0 * A(k, j) + v1 * A(k + 1, j) + (three ? v2 * A(k + 2, j) : 0.0));
+                A(k, j) -= w * v0;
+                A(k + 1, j) -= w * v1;
+                if (three) A(k + 2, j) -= w * v2;
+            }
+            if (k > l) {
+                A(k, k - 1) = alpha;
+                A(k + 1, k - 1) = 0.0;
+                if (three) A(k + 2, k - 1) = 0.0;
+            }
+            // columns k..k+2 from the right
+            const int iend = std::min(k + 3, hi);
+            for (int i = l; i <= iend; ++i) {
+                const double w = beta * (A(i, k) * v0 + A(i, k + 1) * v1 + (three ? A(i, k + 2) * v2 : 0.0));
+                A(i, k) -= w * v0;
+                A(i, k + 1) -= w * v1;
+                if (three) A(i, k + 2) -= w * v2;
+            }
         }
     }
-    if (std::abs(A(n - 1, n - 1)) < tiny) A(n - 1, n - 1) = tiny;
-    for (int i = n - 1; i >= 0; --i) {
-        cd s = b[i];
-        for (int j = i + 1; j < n; ++j) s -= A(i, j) * b[j];
-        b[i] = s / A(i, i);
-    }
+    // near-real values are made real, so conjugate pairs and real values are unambiguous
+    for (int j = 0; j < n; ++j)
+        if (std::fabs(wi[j]) <= 1e-12 * (std::hypot(wr[j], wi[j]) + hnorm * 1e-3)) wi[j] = 0.0;
+    return true;
 }
 
-bool host_eig(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi,
-              std::vector<double>& vr, std::vector<double>& vi) {
-    std::vector<cd> a((size_t)m * m);
-    double hnorm = 0.0;
-    for (size_t i = 0; i < a.size(); ++i) {
-        a[i] = H[i];
-        hnorm = std::max(hnorm, std::abs(H[i]));
+bool host_hess_eigvec(const std::vector<double>& H, int n, double wr, double wi, std::vector<double>& vr,
+                      std::vector<double>& vi) {
+    const double hnorm = max_abs(H, n);
+    const double pert = 1e-13 * (hnorm > 0 ? hnorm : 1.0);
+    vr.assign(n, 0.0);
+    vi.assign(n, 0.0);
+    if (wi == 0.0) {
+        std::vector<double> y;
+        if (!inverse_iteration<double>(H, n, wr + pert, hnorm, y)) return false;
+        vr = y;
+        return true;
     }
-    std::vector<cd> ev;
-    if (!hess_eigenvalues(a, m, ev)) return false;
-    wr.resize(m);
-    wi.resize(m);
-    vr.assign((size_t)m * m, 0.0);
-    vi.assign((size_t)m * m, 0.0);
-    for (int j = 0; j < m; ++j) {
-        // clean near-real values so conjugate pairs and real values are unambiguous
-        cd lam = ev[j];
-        if (std::abs(lam.imag()) <= 1e-12 * (std::abs(lam) + hnorm * 1e-3)) lam = cd(lam.real(), 0.0);
-        wr[j] = lam.real();
-        wi[j] = lam.imag();
-        std::vector<cd> y(m);
-        for (int i = 0; i < m; ++i) y[i] = cd(1.0 + 0.01 * ((i * 7919) % 101), 0.0);
-        const cd sigma = lam + cd(1e-13 * (hnorm > 0 ? hnorm : 1.0), 0.0);
-        for (int sweep = 0; sweep < 3; ++sweep) {
-            hess_shifted_solve(H, m, sigma, y, hnorm);
-            double nrm = 0.0;
-            int imax = 0;
-            for (int i = 0; i < m; ++i) {
-                nrm += std::norm(y[i]);
-                if (std::abs(y[i]) > std::abs(y[imax])) imax = i;
-            }
-            nrm = std::sqrt(nrm);
-            if (!(nrm > 0) || !std::isfinite(nrm)) return false;
-            // unit norm, largest component real and positive
-            const cd ph = std::abs(y[imax]) > 0 ? std::conj(y[imax]) / std::abs(y[imax]) : cd(1, 0);
-            for (int i = 0; i < m; ++i) y[i] *= ph / nrm;
-        }
-        for (int i = 0; i < m; ++i) {
-            vr[(size_t)i * m + j] = y[i].real();
-            vi[(size_t)i * m + j] = (wi[j] == 0.0) ? 0.0 : y[i].imag();
-        }
+    std::vector<cd> y;
+    if (!inverse_iteration<cd>(H, n, cd(wr + pert, wi), hnorm, y)) return false;
+    for (int i = 0; i < n; ++i) {
+        vr[i] = y[i].real();
+        vi[i] = y[i].imag();
     }
     return true;
 }

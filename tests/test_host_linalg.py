@@ -1,0 +1,193 @@
+"""Host eigen-solver of the coarse-space build (CPU): the Ritz values of the Arnoldi Hessenberg matrix
+H_m and of the Lanczos tridiagonal matrix (Appendix A, Eq. ritz) and their eigenvectors, against
+numpy's LAPACK eigen-solvers and the eigen-equation itself.
+
+The library's host source is compiled here with g++ together with a two-function extern "C" shim,
+so no GPU is needed.
+"""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1801_08937_gb300", "csrc")
+
+SHIM = r"""
+#include <vector>
+namespace mm {
+bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
+bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
+                      std::vector<double>& vi);
+}
+extern "C" int t_eigvals(const double* H, int m, double* wr, double* wi) {
+    std::vector<double> h(H, H + (size_t)m * m), r, i;
+    if (!mm::host_hess_eigvals(h, m, r, i)) return 0;
+    for (int j = 0; j < m; ++j) { wr[j] = r[j]; wi[j] = i[j]; }
+    return 1;
+}
+extern "C" int t_eigvec(const double* H, int m, double wr, double wi, double* vr, double* vi) {
+    std::vector<double> h(H, H + (size_t)m * m), r, i;
+    if (!mm::host_hess_eigvec(h, m, wr, wi, r, i)) return 0;
+    for (int j = 0; j < m; ++j) { vr[j] = r[j]; vi[j] = i[j]; }
+    return 1;
+}
+"""
+
+
+def _cuda_include():
+    for nvcc in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if nvcc and os.path.exists(nvcc):
+            inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+            if os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+                return inc
+    return None
+
+
+@pytest.fixture(scope="module")
+def eig(tmp_path_factory):
+    inc = _cuda_include()
+    if inc is None or shutil.which("g++") is None:
+        pytest.skip("g++ or the CUDA headers are missing")
+    d = tmp_path_factory.mktemp("host_linalg")
+    shim = d / "shim.cpp"
+    shim.write_text(SHIM)
+    so = d / "libhostlinalg.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", inc, "-I", CSRC, "-x", "c++",
+                    os.path.join(CSRC, "host_linalg.cpp"), "-x", "none", str(shim), "-o", str(so)], check=True)
+    lib = C.CDLL(str(so))
+    P = C.POINTER(C.c_double)
+    lib.t_eigvals.argtypes = [P, C.c_int, P, P]
+    lib.t_eigvec.argtypes = [P, C.c_int, C.c_double, C.c_double, P, P]
+
+    def p(a):
+        return a.ctypes.data_as(P)
+
+    def vals(H):
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        m = H.shape[0]
+        wr, wi = np.zeros(m), np.zeros(m)
+        assert lib.t_eigvals(p(H), m, p(wr), p(wi)) == 1
+        return wr + 1j * wi
+
+    def vec(H, lam):
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        m = H.shape[0]
+        vr, vi = np.zeros(m), np.zeros(m)
+        assert lib.t_eigvec(p(H), m, lam.real, lam.imag, p(vr), p(vi)) == 1
+        return vr + 1j * vi
+
+    return vals, vec
+
+
+def _arnoldi(B, m, seed):
+    n = B.shape[0]
+    rng = np.random.default_rng(seed)
+    W = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    w = rng.standard_normal(n)
+    W[:, 0] = w / np.linalg.norm(w)
+    for j in range(m):
+        v = B @ W[:, j]
+        for _ in range(2):
+            h = W[:, :j + 1].T @ v
+            v -= W[:, :j + 1] @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(v)
+        W[:, j + 1] = v / H[j + 1, j]
+    return H[:m, :m]
+
+
+def _match(a, b):
+    """Largest distance from each value of a to the nearest unused value of b."""
+    b = list(b)
+    worst = 0.0
+    for x in sorted(a, key=lambda z: (z.real, z.imag)):
+        i = int(np.argmin([abs(x - y) for y in b]))
+        worst = max(worst, abs(x - b.pop(i)))
+    return worst
+
+
+def test_ritz_values_of_a_preconditioned_spd_operator(eig):
+    """H_m of Arnoldi on B = D A (D, A SPD, so B is similar to an SPD matrix): the eigenvalues equal
+    LAPACK's, are real and positive, and the smallest ones' eigenvectors satisfy H v = lambda v."""
+    vals, vec = eig
+    rng = np.random.default_rng(0)
+    n, m = 400, 150
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    ev = np.concatenate([np.geomspace(1e-4, 0.3, 40), 1.0 + 0.5 * rng.random(n - 40)])
+    A = (Q * ev) @ Q.T
+    B = (0.5 + rng.random(n))[:, None] * A
+    H = _arnoldi(B, m, 1)
+    lam = vals(H)
+    ref = np.linalg.eigvals(H)
+    hn = np.abs(H).max()
+    assert _match(lam, ref) <= 1e-12 * hn
+    assert np.abs(lam.imag).max() <= 1e-6 * hn and lam.real.min() > 0
+    for x in sorted(lam, key=lambda z: z.real)[:12]:
+        v = vec(H, x)
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        assert np.linalg.norm(H @ v - x * v) <= 1e-11 * hn
+
+
+def test_complex_pairs_of_a_random_hessenberg_matrix(eig):
+    """A random upper Hessenberg matrix has complex conjugate pairs: values match LAPACK, pairs come out
+    exactly conjugate, and the complex eigenvectors satisfy the eigen-equation."""
+    vals, vec = eig
+    rng = np.random.default_rng(2)
+    m = 60
+    H = np.triu(rng.standard_normal((m, m)), -1)
+    lam = vals(H)
+    ref = np.linalg.eigvals(H)
+    hn = np.abs(H).max()
+    assert _match(lam, ref) <= 1e-10 * hn
+    cplx = lam[lam.imag != 0]
+    assert len(cplx) >= 4
+    assert _match(cplx, np.conj(cplx)) == 0.0
+    for x in cplx[:6]:
+        v = vec(H, x)
+        assert np.linalg.norm(H @ v - x * v) <= 1e-10 * hn * max(1.0, abs(x))
+
+
+def test_symmetric_tridiagonal_lanczos_matrix(eig):
+    """The Lanczos matrix T (symmetric tridiagonal, positive definite): real values equal eigvalsh."""
+    vals, vec = eig
+    rng = np.random.default_rng(3)
+    m = 80
+    d = 1.0 + rng.random(m)
+    e = 0.4 * rng.random(m - 1)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    lam = vals(T)
+    assert np.abs(lam.imag).max() == 0.0
+    np.testing.assert_allclose(np.sort(lam.real), np.linalg.eigvalsh(T), atol=1e-13)
+    lo = np.sort(lam.real)[0]
+    v = vec(T, lo + 0j)
+    assert np.linalg.norm(T @ v - lo * v) <= 1e-12
+
+
+@pytest.mark.parametrize("case", ["one", "rotation", "triangular", "zero", "identity", "jordan"])
+def test_degenerate_matrices(eig, case):
+    vals, vec = eig
+    if case == "one":
+        H, ref = np.array([[2.5]]), [2.5]
+    elif case == "rotation":
+        H, ref = np.array([[0.0, 1.0], [-1.0, 0.0]]), [1j, -1j]
+    elif case == "triangular":
+        H = np.triu(np.arange(1.0, 17.0).reshape(4, 4))
+        ref = np.diag(H)
+    elif case == "zero":
+        H, ref = np.zeros((5, 5)), np.zeros(5)
+    elif case == "identity":
+        H, ref = np.eye(6), np.ones(6)
+    else:   # a 3x3 Jordan block: one defective eigenvalue
+        H, ref = np.eye(3) * 2.0 + np.diag([1.0, 1.0], 1), [2.0, 2.0, 2.0]
+    lam = vals(H)
+    assert _match(lam, np.asarray(ref, dtype=complex)) <= (1e-5 if case == "jordan" else 1e-14)
+    if case != "zero":
+        x = lam[0]
+        v = vec(H, x)
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        assert np.linalg.norm(H @ v - x * v) <= 1e-8 * max(1.0, np.abs(H).max())

@@ -272,31 +272,50 @@ bool host_cholesky(std::vector<double>& A, int n) {
 }
 
 void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv) {
-    // inv = L^-T L^-1, column by column
-    inv.assign((size_t)n * n, 0.0);
-    std::vector<double> y(n);
-    for (int c = 0; c < n; ++c) {
-        for (int i = 0; i < n; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * y[k];
-            y[i] = s / L[(size_t)i * n + i];
+    // M = L^-1 row by row (row i = (e_i - sum_{k<i} L_ik M_k) / L_ii), then
+    // inv = M^T M as a sum of outer products of the rows of M; row-major
+    // throughout
+    std::vector<double> M((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double* mi = &M[(size_t)i * n];
+        mi[i] = 1.0;
+        for (int k = 0; k < i; ++k) {
+            const double f = L[(size_t)i * n + k];
+            if (f == 0.0) continue;
+            const double* mk = &M[(size_t)k * n];
+            for (int c = 0; c <= k; ++c) mi[c] -= f * mk[c];
         }
-        for (int i = n - 1; i >= 0; --i) {
-            double s = y[i];
-            for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * inv[(size_t)k * n + c];
-            inv[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        const double d = 1.0 / L[(size_t)i * n + i];
+        for (int c = 0; c <= i; ++c) mi[c] *= d;
+    }
+    inv.assign((size_t)n * n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const double* mk = &M[(size_t)k * n];
+        for (int a = 0; a <= k; ++a) {
+            const double f = mk[a];
+            if (f == 0.0) continue;
+            double* ra = &inv[(size_t)a * n];
+            for (int b = 0; b <= a; ++b) ra[b] += f * mk[b];
         }
     }
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < a; ++b) inv[(size_t)b * n + a] = inv[(size_t)a * n + b];
 }
 
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv) {
+    // row i of R^-1 = (e_i - sum_{k>i} R_ik row k of R^-1) / R_ii, from the last row up
     Rinv.assign((size_t)n * n, 0.0);
-    for (int c = 0; c < n; ++c) {
-        for (int i = n - 1; i >= 0; --i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = i + 1; k < n; ++k) s -= R[(size_t)i * n + k] * Rinv[(size_t)k * n + c];
-            Rinv[(size_t)i * n + c] = s / R[(size_t)i * n + i];
+    for (int i = n - 1; i >= 0; --i) {
+        double* ri = &Rinv[(size_t)i * n];
+        ri[i] = 1.0;
+        for (int k = i + 1; k < n; ++k) {
+            const double f = R[(size_t)i * n + k];
+            if (f == 0.0) continue;
+            const double* rk = &Rinv[(size_t)k * n];
+            for (int c = k; c < n; ++c) ri[c] -= f * rk[c];
         }
+        const double d = 1.0 / R[(size_t)i * n + i];
+        for (int c = i; c < n; ++c) ri[c] *= d;
     }
 }
 

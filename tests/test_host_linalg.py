@@ -1,9 +1,10 @@
-"""Host eigen-solver of the coarse-space build (CPU): the Ritz values of the Arnoldi Hessenberg matrix
-H_m and of the Lanczos tridiagonal matrix (Appendix A, Eq. ritz) and their eigenvectors, against
-numpy's LAPACK eigen-solvers and the eigen-equation itself.
+"""Host linear algebra of the coarse-space build (CPU): the Ritz values of the Arnoldi Hessenberg
+matrix H_m and of the Lanczos tridiagonal matrix (Appendix A, Eq. ritz) and their eigenvectors,
+against numpy's LAPACK eigen-solvers and the eigen-equation itself; the Cholesky factor of
+E = Z^T A Z and its inverse (Sect. 3.2), and the triangular inverse that orthonormalises Z.
 
-The library's host source is compiled here with g++ together with a two-function extern "C" shim,
-so no GPU is needed.
+The library's host source is compiled here with g++ together with a small extern "C" shim, so no
+GPU is needed.
 """
 import ctypes as C
 import os
@@ -22,6 +23,21 @@ namespace mm {
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
                       std::vector<double>& vi);
+bool host_cholesky(std::vector<double>& A, int n);
+void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
+void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
+}
+extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
+    std::vector<double> a(A, A + (size_t)n * n), v;
+    if (!mm::host_cholesky(a, n)) return 0;
+    mm::host_spd_inverse_from_chol(a, n, v);
+    for (size_t i = 0; i < (size_t)n * n; ++i) { L[i] = a[i]; inv[i] = v[i]; }
+    return 1;
+}
+extern "C" void t_upper_inv(const double* R, int n, double* Ri) {
+    std::vector<double> r(R, R + (size_t)n * n), v;
+    mm::host_upper_inverse(r, n, v);
+    for (size_t i = 0; i < (size_t)n * n; ++i) Ri[i] = v[i];
 }
 extern "C" int t_eigvals(const double* H, int m, double* wr, double* wi) {
     std::vector<double> h(H, H + (size_t)m * m), r, i;
@@ -62,6 +78,8 @@ def eig(tmp_path_factory):
     P = C.POINTER(C.c_double)
     lib.t_eigvals.argtypes = [P, C.c_int, P, P]
     lib.t_eigvec.argtypes = [P, C.c_int, C.c_double, C.c_double, P, P]
+    lib.t_chol_inv.argtypes = [P, C.c_int, P, P]
+    lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
     def p(a):
         return a.ctypes.data_as(P)
@@ -80,6 +98,21 @@ def eig(tmp_path_factory):
         assert lib.t_eigvec(p(H), m, lam.real, lam.imag, p(vr), p(vi)) == 1
         return vr + 1j * vi
 
+    def chol_inv(A):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        n = A.shape[0]
+        L, inv = np.zeros((n, n)), np.zeros((n, n))
+        ok = lib.t_chol_inv(p(A), n, p(L), p(inv))
+        return (L, inv) if ok == 1 else None
+
+    def upper_inv(R):
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        Ri = np.zeros_like(R)
+        lib.t_upper_inv(p(R), R.shape[0], p(Ri))
+        return Ri
+
+    vals.chol_inv = chol_inv
+    vals.upper_inv = upper_inv
     return vals, vec
 
 
@@ -191,3 +224,31 @@ def test_degenerate_matrices(eig, case):
         v = vec(H, x)
         assert abs(np.linalg.norm(v) - 1.0) < 1e-12
         assert np.linalg.norm(H @ v - x * v) <= 1e-8 * max(1.0, np.abs(H).max())
+
+
+@pytest.mark.parametrize("n", [1, 7, 96])
+def test_cholesky_and_spd_inverse(eig, n):
+    """E = L L^T with L lower triangular (LAPACK's factor), E^-1 equal to numpy's inverse; a matrix
+    that is not positive definite is refused."""
+    vals, _ = eig
+    rng = np.random.default_rng(n)
+    B = rng.standard_normal((n, n))
+    E = B @ B.T + n * np.eye(n)
+    L, inv = vals.chol_inv(E)
+    np.testing.assert_allclose(np.triu(L, 1), 0.0)
+    np.testing.assert_allclose(L, np.linalg.cholesky(E), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(inv, np.linalg.inv(E), rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(inv, inv.T, rtol=0, atol=0)
+    if n > 1:
+        E[0, 0] = -1.0
+        assert vals.chol_inv(E) is None
+
+
+@pytest.mark.parametrize("n", [1, 5, 80])
+def test_upper_triangular_inverse(eig, n):
+    vals, _ = eig
+    rng = np.random.default_rng(10 + n)
+    R = np.triu(rng.standard_normal((n, n))) + 3.0 * np.eye(n)
+    Ri = vals.upper_inv(R)
+    np.testing.assert_allclose(np.tril(Ri, -1), 0.0)
+    np.testing.assert_allclose(R @ Ri, np.eye(n), atol=1e-12)

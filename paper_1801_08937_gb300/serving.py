@@ -222,7 +222,9 @@ class MapServer:
             pending = list(self._pending)
         keep = []
         for req, fut in pending:
-            if len(self._active) >= self.max_active:
+            # requests waiting for their scan's set-up start solving when it ends: they count too
+            in_flight = len(self._active) + sum(len(w) for w in self._setting_up.values())
+            if in_flight >= self.max_active:
                 keep.append((req, fut))
                 continue
             e = self._scans.get(req.scan_id)

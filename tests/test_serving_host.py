@@ -1,0 +1,213 @@
+"""The map server's scheduling logic on the host (CPU): admission by device memory, resident
+per-scan state with LRU eviction, the harvest mode of the coarse space, per-scan set-up errors and
+the cap on concurrent solves.  The library context and the CUDA calls are replaced by fakes that
+record what the scheduler asks of them; the arithmetic itself is covered by the GPU tests.
+"""
+import contextlib
+import threading
+
+import numpy as np
+import pytest
+
+pytest.importorskip("torch")
+from paper_1801_08937_gb300 import serving as S  # noqa: E402
+
+M = S.M
+
+
+class FakeStream:
+    cuda_stream = 0
+
+    def synchronize(self):
+        pass
+
+
+class FakeCuda:
+    def __init__(self, free):
+        self.free = free
+
+    def Stream(self, device=None):
+        return FakeStream()
+
+    def stream(self, s):
+        return contextlib.nullcontext()
+
+    def mem_get_info(self, device):
+        return self.free, self.free
+
+    def set_device(self, device):
+        pass
+
+    def synchronize(self, device=None):
+        pass
+
+
+class FakeTorch:
+    def __init__(self, free=1 << 40):
+        self.cuda = FakeCuda(free)
+
+
+class FakeContext:
+    """Records calls; a solve finishes after three polls with the map filled by sum(tod)."""
+    lock = threading.Lock()
+    log = []
+    fail_npix = set()
+    live = 0
+    max_live = 0
+
+    def __init__(self, device, stream, precision):
+        self.opts = {}
+        self.harvested = 0
+        self.n_pix = None
+        with FakeContext.lock:
+            FakeContext.live += 1
+            FakeContext.max_live = max(FakeContext.max_live, FakeContext.live)
+
+    def _rec(self, *what):
+        with FakeContext.lock:
+            FakeContext.log.append(what)
+
+    def setup_pointing(self, pix, psi, block_off, block_band, band, n_pix, n_det=1):
+        self.n_pix = n_pix
+        self._rec("setup", n_pix)
+        if n_pix in FakeContext.fail_npix:
+            raise RuntimeError(f"bad scan {n_pix}")
+
+    def build_bd(self, rcond):
+        return 0
+
+    def rhs(self, tod):
+        return np.zeros((1, self.n_pix, 3))
+
+    def build_coarse(self, b, m_max, eps_arn, k):
+        self._rec("coarse", self.n_pix)
+        return k
+
+    def build_coarse_from_solve(self, k):
+        self._rec("coarse_from_solve", self.n_pix)
+        return k
+
+    def set_option(self, name, value):
+        self.opts[name] = value
+
+    def get_option(self, name):
+        return self.harvested if name == "harvested" else self.opts.get(name, 0)
+
+    def solve_begin(self, tod, precond, tol=1e-8, max_iter=500):
+        self.tod, self.precond, self.polls = np.asarray(tod), precond, 0
+        if self.opts.get("harvest", 0) > 0:
+            self.harvested = self.opts["harvest"]
+        self._rec("begin", self.n_pix, precond)
+
+    def solve_launch(self, n_iter):
+        pass
+
+    def solve_poll(self):
+        self.polls += 1
+        return True, self.polls >= 3
+
+    def solve_end(self, out=None, like=None):
+        x = np.full((1, self.n_pix, 3), float(self.tod.sum()))
+        return x, [{"iters": self.polls, "status": "MM_OK", "precond": self.precond}]
+
+    def close(self):
+        self._rec("close", self.n_pix)
+        with FakeContext.lock:
+            FakeContext.live -= 1
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    FakeContext.log = []
+    FakeContext.fail_npix = set()
+    FakeContext.live = 0
+    FakeContext.max_live = 0
+    monkeypatch.setattr(M, "Context", FakeContext)
+    monkeypatch.setattr(M, "estimate_bytes", lambda *a, **k: 1000)
+    return FakeContext
+
+
+def spec(n_pix, n_samples=64):
+    return S.ScanSpec(np.zeros(n_samples, np.int32), np.zeros(n_samples, np.float32),
+                      np.array([0, n_samples]), np.zeros(1, np.int32), np.ones((1, 2)), n_pix)
+
+
+def server(**kw):
+    free = kw.pop("free", 1 << 40)
+    srv = S.MapServer(device=0, precision=M.MM_FP64, reserve_bytes=0, **kw)
+    srv.torch = FakeTorch(free)
+    return srv.start()
+
+
+def request(n_pix, value, **kw):
+    return S.MapRequest(f"scan{n_pix}", spec(n_pix), np.full(64, value, np.float64), **kw)
+
+
+def test_repeated_scans_hit_the_resident_state_and_results_route_to_their_requests(fake):
+    srv = server()
+    order = [(10, 1.0), (20, 2.0), (10, 3.0), (20, 4.0), (10, 5.0)]
+    futs = []
+    for n, v in order:
+        futs.append(srv.submit(request(n, v)))
+    res = [f.result(timeout=20) for f in futs]
+    srv.stop()
+    for (n, v), r in zip(order, res):
+        assert r.map.shape == (n, 3) and np.all(r.map == 64 * v)
+        assert r.info["precond"] == M.MM_PRECOND_2L
+    st = srv.stats()
+    assert st["completed"] == 5 and st["cache_hits"] == 3
+    assert sum(1 for e in fake.log if e[0] == "setup") == 2
+    assert sum(1 for e in fake.log if e[0] == "coarse") == 2     # one Arnoldi basis per scan
+    assert [r.scan_cached for r in res] == [False, False, True, True, True]
+
+
+def test_memory_budget_evicts_the_least_recently_used_idle_scan(fake):
+    # a scan holds 1000 B; a solve needs 8 B per sample + 512 B per pixel (64 samples, 3-5 pixels):
+    # the budget fits one resident scan and its solve, never two scans
+    srv = server(budget_bytes=4100)
+    futs = [srv.submit(request(n, 1.0)) for n in (3, 4, 5)]
+    for f in futs:
+        f.result(timeout=20)
+    srv.stop()
+    assert srv.stats()["evictions"] == 2
+    closes = [e[1] for e in fake.log if e[0] == "close"]
+    assert closes[:2] == [3, 4]                                  # evicted in arrival (LRU) order
+    assert fake.max_live == 1
+
+
+def test_harvest_mode_solves_a_new_scan_with_m_bd_then_deflates_later_requests(fake):
+    srv = server(coarse="harvest", m_max=40)
+    r1 = srv.submit(request(7, 1.0)).result(timeout=20)
+    assert r1.info["precond"] == M.MM_PRECOND_BD
+    for _ in range(2000):                                         # the basis is built off the critical path
+        if any(e[0] == "coarse_from_solve" for e in fake.log):
+            break
+        threading.Event().wait(0.005)
+    r2 = srv.submit(request(7, 2.0)).result(timeout=20)
+    srv.stop()
+    assert r2.info["precond"] == M.MM_PRECOND_2L
+    assert not any(e[0] == "coarse" for e in fake.log)            # no separate Arnoldi run
+    begins = [e for e in fake.log if e[0] == "begin"]
+    assert [b[2] for b in begins] == [M.MM_PRECOND_BD, M.MM_PRECOND_2L]
+
+
+def test_a_failing_scan_set_up_fails_its_requests_only(fake):
+    fake.fail_npix = {30}
+    srv = server()
+    bad = [srv.submit(request(30, 1.0)) for _ in range(2)]
+    good = srv.submit(request(31, 2.0))
+    for f in bad:
+        with pytest.raises(RuntimeError, match="bad scan 30"):
+            f.result(timeout=20)
+    assert np.all(good.result(timeout=20).map == 128.0)
+    srv.stop()
+    assert srv.error is None
+
+
+def test_concurrent_solves_are_capped(fake):
+    srv = server(max_active=1)
+    futs = [srv.submit(request(n, float(n))) for n in (40, 41, 42, 43)]
+    for n, f in zip((40, 41, 42, 43), futs):
+        assert np.all(f.result(timeout=20).map == 64.0 * n)
+    srv.stop()
+    assert srv.stats()["max_concurrent"] == 1

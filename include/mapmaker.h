@@ -332,7 +332,9 @@ mm_status mm_apply_precond_2l_noalloc(mm_ctx* ctx, const double* x, double* y, i
 
 /* Device bytes a context needs for a problem of this shape (pointing, maps,
  * PCG state, Arnoldi basis of m_max vectors and k coarse vectors), for
- * admission control.  Pure host arithmetic. */
+ * admission control, with the default options ("fp64_products" = 2 in
+ * MM_FP64 adds 16 bytes per sample of double-float weights).  Pure host
+ * arithmetic; needs no device. */
 int64_t mm_estimate_bytes(int64_t n_samples, int32_t n_pix, int32_t n_bands, int32_t half_bw,
                           int32_t nrhs, int32_t m_max, int32_t k, mm_precision prec);
 

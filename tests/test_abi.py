@@ -61,3 +61,35 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_create_without_a_device_fails_cleanly(lib):
+    """No usable GPU: mm_create returns an error status and no context; the NULL-context calls are safe."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+    from paper_1801_08937_gb300 import mapmaker as M
+    h = C.c_void_p()
+    assert lib.mm_create(C.byref(h), 0, None, M.MM_FP64) == M.MM_ERR_CUDA
+    assert h.value is None
+    assert lib.mm_destroy(None) == M.MM_OK
+    assert lib.mm_last_error(None) == b"null context"
+
+
+def test_estimate_bytes_is_host_arithmetic_and_grows_with_the_problem(lib):
+    from paper_1801_08937_gb300 import mapmaker as M
+    base = dict(n_samples=1 << 20, n_pix=4096, n_bands=8, half_bw=512, nrhs=1, m_max=100, k=32)
+
+    def est(prec=M.MM_FP64, **over):
+        a = dict(base)
+        a.update(over)
+        return M.estimate_bytes(a["n_samples"], a["n_pix"], a["n_bands"], a["half_bw"], a["nrhs"], a["m_max"],
+                                a["k"], prec)
+
+    b0 = est()
+    assert b0 > (1 << 20) * 8                              # at least the pointing
+    for key, val in (("n_samples", 1 << 21), ("n_pix", 8192), ("nrhs", 4), ("m_max", 200), ("k", 64)):
+        assert est(**{key: val}) > b0, key
+    # float32 timelines, plus double-float weights for the refinement residuals
+    assert est(M.MM_FP32_MIXED) == b0 - (1 << 20) * 4 + (1 << 20) * 16

@@ -1920,19 +1920,15 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     const int m = ctx->harvest_count;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     // T: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal -sqrt(beta_j)/alpha_j
-    std::vector<double> T((size_t)m * m, 0.0);
+    std::vector<double> td(m), te(std::max(1, m - 1), 0.0);
     const auto& al = ctx->harv_alpha;
     const auto& be = ctx->harv_beta;
     for (int j = 0; j < m; ++j) {
-        T[(size_t)j * m + j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-        if (j + 1 < m) {
-            const double off = -std::sqrt(std::max(0.0, be[j])) / al[j];
-            T[(size_t)j * m + j + 1] = off;
-            T[(size_t)(j + 1) * m + j] = off;
-        }
+        td[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+        if (j + 1 < m) te[j] = -std::sqrt(std::max(0.0, be[j])) / al[j];
     }
-    std::vector<double> wr, wi, er, ei;
-    if (!host_hess_eigvals(T, m, wr, wi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
+    std::vector<double> wr, er;
+    if (!host_tridiag_eigvals(td, te, m, wr)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
     std::vector<int> order(m);
     for (int i = 0; i < m; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
@@ -1952,7 +1948,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
     std::vector<double> C((size_t)m * ksel);
     for (int c = 0; c < ksel; ++c) {
-        if (!host_hess_eigvec(T, m, wr[sel[c]], wi[sel[c]], er, ei))
+        if (!host_tridiag_eigvec(td, te, m, wr[sel[c]], er))
             return fail(ctx, MM_ERR_SINGULAR, "inverse iteration for a Ritz vector failed");
         for (int r = 0; r < m; ++r) C[(size_t)r * ksel + c] = er[r];
     }

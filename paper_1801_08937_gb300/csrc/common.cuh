@@ -228,6 +228,13 @@ bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>&
 // Hessenberg H for the eigenvalue wr + i wi, by inverse iteration.
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
                       std::vector<double>& vi);
+// Eigenvalues (ascending order not guaranteed) of the symmetric tridiagonal
+// matrix with diagonal d[n] and off-diagonal e[n-1]; false on failure.
+bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double>& e, int n,
+                          std::vector<double>& w);
+// Unit eigenvector (largest component positive) of that matrix for the eigenvalue lam.
+bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
+                         std::vector<double>& v);
 // Lower Cholesky factor in place (row-major n x n); false if not SPD.
 bool host_cholesky(std::vector<double>& A, int n);
 // Inverse of an SPD matrix from its Cholesky factor.

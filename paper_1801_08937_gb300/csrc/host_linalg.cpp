@@ -11,7 +11,10 @@
 // window is updated, which is all the eigenvalues need.  Eigenvectors, for
 // the wanted eigenvalues only: inverse iteration with one Hessenberg LU of
 // (H - sigma I) (pivoting between adjacent rows) and three solves from a
-// fixed start vector; real arithmetic for a real eigenvalue.
+// fixed start vector; real arithmetic for a real eigenvalue.  The symmetric
+// tridiagonal Lanczos matrix has its own solver: implicit QR steps with the
+// Wilkinson shift (O(m) per step) and inverse iteration with a tridiagonal
+// LU (O(m) per solve).
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -250,6 +253,102 @@ bool host_hess_eigvec(const std::vector<double>& H, int n, double wr, double wi,
     for (int i = 0; i < n; ++i) {
         vr[i] = y[i].real();
         vi[i] = y[i].imag();
+    }
+    return true;
+}
+
+bool host_tridiag_eigvals(const std::vector<double>& d_in, const std::vector<double>& e_in, int n,
+                          std::vector<double>& w) {
+    // implicit symmetric QR steps with the Wilkinson shift on the unreduced
+    // window [l, hi]; a Givens rotation on (k, k+1) chases the bulge, which
+    // sits at (k+1, k-1) before step k
+    w.assign(d_in.begin(), d_in.begin() + n);
+    std::vector<double>& d = w;
+    std::vector<double> e(e_in.begin(), e_in.begin() + std::max(0, n - 1));
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, total = 0;
+    while (hi > 0) {
+        if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
+            e[hi - 1] = 0.0;
+            --hi;
+            continue;
+        }
+        int l = hi - 1;
+        while (l > 0 && std::fabs(e[l - 1]) > eps * (std::fabs(d[l - 1]) + std::fabs(d[l]))) --l;
+        if (l > 0) e[l - 1] = 0.0;
+        if (++total > 30 * n + 100) return false;
+        const double delta = 0.5 * (d[hi - 1] - d[hi]);
+        const double eh = e[hi - 1];
+        const double den = delta + (delta >= 0.0 ? 1.0 : -1.0) * std::hypot(delta, eh);
+        const double mu = den != 0.0 ? d[hi] - eh * eh / den : d[hi];
+        double x = d[l] - mu, z = e[l], bulge = 0.0;
+        for (int k = l; k < hi; ++k) {
+            if (k > l) {
+                x = e[k - 1];
+                z = bulge;
+            }
+            const double r = std::hypot(x, z);
+            const double c = r != 0.0 ? x / r : 1.0, sn = r != 0.0 ? z / r : 0.0;
+            if (k > l) e[k - 1] = r;
+            const double a = d[k], b = e[k], f = d[k + 1];
+            d[k] = c * c * a + 2.0 * c * sn * b + sn * sn * f;
+            d[k + 1] = sn * sn * a - 2.0 * c * sn * b + c * c * f;
+            e[k] = c * sn * (f - a) + (c * c - sn * sn) * b;
+            if (k + 1 < hi) {
+                bulge = sn * e[k + 1];
+                e[k + 1] = c * e[k + 1];
+            }
+        }
+    }
+    return true;
+}
+
+bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
+                         std::vector<double>& v) {
+    // inverse iteration with the LU of T - sigma I (row interchanges between
+    // neighbours; U has two superdiagonals), three solves from a fixed start
+    double tnorm = 0.0;
+    for (int i = 0; i < n; ++i) tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) +
+                                                         (i + 1 < n ? std::fabs(e[i]) : 0.0));
+    const double scale = tnorm > 0 ? tnorm : 1.0;
+    const double sigma = lam + 1e-13 * scale, tiny = 1e-14 * scale;
+    std::vector<double> u0(n), u1(n, 0.0), u2(n, 0.0), mult(n, 0.0);
+    std::vector<char> swp(n, 0);
+    double c0 = d[0] - sigma, c1 = n > 1 ? e[0] : 0.0, c2 = 0.0;   // pivot row at columns k, k+1, k+2
+    for (int k = 0; k + 1 < n; ++k) {
+        double n0 = e[k], n1 = d[k + 1] - sigma, n2 = k + 2 < n ? e[k + 1] : 0.0;
+        if (std::fabs(n0) > std::fabs(c0)) {
+            swp[k] = 1;
+            std::swap(c0, n0);
+            std::swap(c1, n1);
+            std::swap(c2, n2);
+        }
+        if (std::fabs(c0) < tiny) c0 = tiny;
+        const double f = n0 / c0;
+        mult[k] = f;
+        u0[k] = c0;
+        u1[k] = c1;
+        u2[k] = c2;
+        c0 = n1 - f * c1;
+        c1 = n2 - f * c2;
+        c2 = 0.0;
+    }
+    if (std::fabs(c0) < tiny) c0 = tiny;
+    u0[n - 1] = c0;
+    v.resize(n);
+    for (int i = 0; i < n; ++i) v[i] = 1.0 + 0.01 * ((i * 7919) % 101);
+    for (int sweep = 0; sweep < 3; ++sweep) {
+        for (int k = 0; k + 1 < n; ++k) {
+            if (swp[k]) std::swap(v[k], v[k + 1]);
+            v[k + 1] -= mult[k] * v[k];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = v[i];
+            if (i + 1 < n) s -= u1[i] * v[i + 1];
+            if (i + 2 < n) s -= u2[i] * v[i + 2];
+            v[i] = s / u0[i];
+        }
+        if (!normalise(v)) return false;
     }
     return true;
 }

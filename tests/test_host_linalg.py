@@ -23,9 +23,25 @@ namespace mm {
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
                       std::vector<double>& vi);
+bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double>& e, int n,
+                          std::vector<double>& w);
+bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
+                         std::vector<double>& v);
 bool host_cholesky(std::vector<double>& A, int n);
 void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
+}
+extern "C" int t_tri_eigvals(const double* d, const double* e, int n, double* w) {
+    std::vector<double> dd(d, d + n), ee(e, e + (n > 1 ? n - 1 : 0)), ww;
+    if (!mm::host_tridiag_eigvals(dd, ee, n, ww)) return 0;
+    for (int i = 0; i < n; ++i) w[i] = ww[i];
+    return 1;
+}
+extern "C" int t_tri_eigvec(const double* d, const double* e, int n, double lam, double* v) {
+    std::vector<double> dd(d, d + n), ee(e, e + (n > 1 ? n - 1 : 0)), vv;
+    if (!mm::host_tridiag_eigvec(dd, ee, n, lam, vv)) return 0;
+    for (int i = 0; i < n; ++i) v[i] = vv[i];
+    return 1;
 }
 extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     std::vector<double> a(A, A + (size_t)n * n), v;
@@ -79,6 +95,8 @@ def eig(tmp_path_factory):
     lib.t_eigvals.argtypes = [P, C.c_int, P, P]
     lib.t_eigvec.argtypes = [P, C.c_int, C.c_double, C.c_double, P, P]
     lib.t_chol_inv.argtypes = [P, C.c_int, P, P]
+    lib.t_tri_eigvals.argtypes = [P, P, C.c_int, P]
+    lib.t_tri_eigvec.argtypes = [P, P, C.c_int, C.c_double, P]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
     def p(a):
@@ -111,7 +129,23 @@ def eig(tmp_path_factory):
         lib.t_upper_inv(p(R), R.shape[0], p(Ri))
         return Ri
 
+    def tri(d, e):
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        e = np.ascontiguousarray(e if len(e) else np.zeros(1), dtype=np.float64)
+        w = np.zeros(len(d))
+        assert lib.t_tri_eigvals(p(d), p(e), len(d), p(w)) == 1
+        return w
+
+    def tri_vec(d, e, lam):
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        e = np.ascontiguousarray(e if len(e) else np.zeros(1), dtype=np.float64)
+        v = np.zeros(len(d))
+        assert lib.t_tri_eigvec(p(d), p(e), len(d), float(lam), p(v)) == 1
+        return v
+
     vals.chol_inv = chol_inv
+    vals.tri = tri
+    vals.tri_vec = tri_vec
     vals.upper_inv = upper_inv
     return vals, vec
 
@@ -252,3 +286,52 @@ def test_upper_triangular_inverse(eig, n):
     Ri = vals.upper_inv(R)
     np.testing.assert_allclose(np.tril(Ri, -1), 0.0)
     np.testing.assert_allclose(R @ Ri, np.eye(n), atol=1e-12)
+
+
+def _tridiag(d, e):
+    return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+
+
+@pytest.mark.parametrize("case", ["lanczos", "large", "diagonal", "wilkinson", "split", "tiny_offdiag", "one",
+                                  "two"])
+def test_symmetric_tridiagonal_solver(eig, case):
+    """The dedicated solver of the Lanczos matrix: values equal LAPACK's eigvalsh to round-off of ||T||,
+    eigenvectors satisfy T v = lambda v and are orthogonal for separated values."""
+    vals, _ = eig
+    rng = np.random.default_rng(sum(map(ord, case)))
+    if case == "lanczos":       # the Lanczos matrix of a PCG run: 1/alpha_j + beta_{j-1}/alpha_{j-1}, -sqrt(beta_j)/alpha_j
+        al = 0.5 + rng.random(120)
+        be = 0.8 * rng.random(119)
+        d = 1.0 / al + np.concatenate([[0.0], be / al[:-1]])
+        e = -np.sqrt(be) / al[:-1]
+    elif case == "large":
+        d, e = rng.standard_normal(700), rng.standard_normal(699)
+    elif case == "diagonal":
+        d, e = rng.standard_normal(9), np.zeros(8)
+    elif case == "wilkinson":   # W21+: pairs of nearly equal eigenvalues
+        d, e = np.abs(np.arange(-10.0, 11.0)), np.ones(20)
+    elif case == "split":       # two unreduced blocks
+        d, e = rng.standard_normal(12), rng.standard_normal(11)
+        e[5] = 0.0
+    elif case == "tiny_offdiag":
+        d, e = np.arange(1.0, 11.0), 1e-17 * np.ones(9)
+    elif case == "one":
+        d, e = np.array([3.25]), np.zeros(0)
+    else:
+        d, e = np.array([1.0, 1.0]), np.array([2.0])
+    T = _tridiag(d, e)
+    w = np.sort(vals.tri(d, e))
+    ref = np.linalg.eigvalsh(T)
+    tn = max(1.0, np.abs(T).sum(axis=1).max())
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-13 * tn)
+    gaps = np.diff(ref)
+    pick = [i for i in range(len(ref)) if (i == 0 or gaps[i - 1] > 1e-6 * tn) and (i == len(ref) - 1 or gaps[i] > 1e-6 * tn)]
+    V = []
+    for i in pick[:10]:
+        v = vals.tri_vec(d, e, w[i])
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        assert np.linalg.norm(T @ v - w[i] * v) <= 1e-12 * tn
+        V.append(v)
+    if len(V) > 1:
+        G = np.array(V) @ np.array(V).T
+        assert np.abs(G - np.eye(len(V))).max() < 1e-8

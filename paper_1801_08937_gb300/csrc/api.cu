@@ -1847,54 +1847,11 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m_max + j];
     // Ritz values first; Ritz vectors (inverse iteration) only for the selected ones
-    std::vector<double> wr, wi, er, ei;
-    if (!host_hess_eigvals(Hm, m, wr, wi)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m did not converge");
-    std::vector<int> order(m);
-    for (int i = 0; i < m; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
-    std::vector<char> used(m, 0);
-    std::vector<std::vector<double>> cols;
-    std::vector<double> vals;
-    const int kwant = k > 0 ? std::min(k, m) : m;
-    // Ritz values at the round-off level of the largest belong to null directions
-    // of A (e.g. a constant intensity map under polynomial templates): A Z has no
-    // component there, E = Z^T A Z would be singular, so they are not deflated
-    double wmax = 0.0;
-    for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
-    const double wnull = 1e-10 * wmax;
-    for (int idx : order) {
-        if ((int)cols.size() >= kwant) break;
-        if (used[idx]) continue;
-        if (std::fabs(wr[idx]) <= wnull) continue;
-        if (k <= 0 && !(wr[idx] < eps_lambda)) break;
-        used[idx] = 1;
-        if (!host_hess_eigvec(Hm, m, wr[idx], wi[idx], er, ei))
-            return fail(ctx, MM_ERR_SINGULAR, "inverse iteration for a Ritz vector failed");
-        cols.push_back(er);
-        vals.push_back(wr[idx]);
-        if (wi[idx] != 0.0) {
-            int partner = -1;
-            double best = 1e300;
-            for (int j2 = 0; j2 < m; ++j2) {
-                if (used[j2]) continue;
-                const double d = std::fabs(wr[j2] - wr[idx]) + std::fabs(wi[j2] + wi[idx]);
-                if (d < best) {
-                    best = d;
-                    partner = j2;
-                }
-            }
-            if (partner >= 0) used[partner] = 1;
-            if ((int)cols.size() < kwant) {
-                cols.push_back(ei);
-                vals.push_back(wr[idx]);
-            }
-        }
-    }
-    const int ksel = (int)cols.size();
-    if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
-    std::vector<double> C((size_t)m * ksel);
-    for (int r = 0; r < m; ++r)
-        for (int c = 0; c < ksel; ++c) C[(size_t)r * ksel + c] = cols[c][r];
+    std::vector<double> C, vals;
+    const int rs = host_ritz_hess(Hm, m, k, eps_lambda, C, vals);
+    if (rs == 1) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m failed");
+    if (rs == 2) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
+    const int ksel = (int)vals.size();
     DevBuf dC;
     CK(dC.ensure(C.size() * 8));
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
@@ -1927,31 +1884,11 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
         td[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
         if (j + 1 < m) te[j] = -std::sqrt(std::max(0.0, be[j])) / al[j];
     }
-    std::vector<double> wr, er;
-    if (!host_tridiag_eigvals(td, te, m, wr)) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
-    std::vector<int> order(m);
-    for (int i = 0; i < m; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
-    const int kwant = k > 0 ? std::min(k, m) : m;
-    std::vector<int> sel;
-    std::vector<double> vals;
-    double wmax = 0.0;
-    for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
-    for (int idx : order) {
-        if ((int)sel.size() >= kwant) break;
-        if (std::fabs(wr[idx]) <= 1e-10 * wmax) continue;   // null directions of A (see mm_build_coarse)
-        if (k <= 0 && !(wr[idx] < eps_lambda)) break;
-        sel.push_back(idx);
-        vals.push_back(wr[idx]);
-    }
-    const int ksel = (int)sel.size();
-    if (ksel == 0) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
-    std::vector<double> C((size_t)m * ksel);
-    for (int c = 0; c < ksel; ++c) {
-        if (!host_tridiag_eigvec(td, te, m, wr[sel[c]], er))
-            return fail(ctx, MM_ERR_SINGULAR, "inverse iteration for a Ritz vector failed");
-        for (int r = 0; r < m; ++r) C[(size_t)r * ksel + c] = er[r];
-    }
+    std::vector<double> C, vals;
+    const int rs = host_ritz_tridiag(td, te, m, k, eps_lambda, C, vals);
+    if (rs == 1) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
+    if (rs == 2) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
+    const int ksel = (int)vals.size();
     DevBuf dC;
     CK(dC.ensure(C.size() * 8));
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));

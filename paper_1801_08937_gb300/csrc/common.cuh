@@ -235,6 +235,16 @@ bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double
 // Unit eigenvector (largest component positive) of that matrix for the eigenvalue lam.
 bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
                          std::vector<double>& v);
+// Ritz selection (Appendix A, Eq. ritz) from the Arnoldi H_m or the
+// symmetric tridiagonal Lanczos T_m: the k smallest Ritz pairs by real part
+// (k <= 0: those below eps_lambda), complex pairs as real and imaginary
+// parts, null values (|theta| <= 1e-10 max |theta|) skipped.  C [m][ksel]
+// row-major holds the Ritz vectors in the Krylov basis, vals their values.
+// Returns 0, 1 if an eigen-solve failed, 2 if nothing was selected.
+int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+                   std::vector<double>& vals);
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
+                      std::vector<double>& C, std::vector<double>& vals);
 // Lower Cholesky factor in place (row-major n x n); false if not SPD.
 bool host_cholesky(std::vector<double>& A, int n);
 // Inverse of an SPD matrix from its Cholesky factor.

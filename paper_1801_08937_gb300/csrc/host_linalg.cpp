@@ -15,6 +15,7 @@
 // tridiagonal Lanczos matrix has its own solver: implicit QR steps with the
 // Wilkinson shift (O(m) per step) and inverse iteration with a tridiagonal
 // LU (O(m) per solve).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -351,6 +352,89 @@ bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>
         if (!normalise(v)) return false;
     }
     return true;
+}
+
+namespace {
+
+// The selection of the Ritz pairs (Appendix A, Eq. ritz) from the values
+// wr + i wi; vec(idx, er, ei) computes the vector of value idx.  Sorted by
+// real part, the k smallest are kept (k <= 0: those below eps_lambda); a
+// complex pair gives its real and imaginary parts (its partner is not taken
+// again); values at the round-off level of the largest are skipped: they
+// belong to null directions of A (e.g. a constant intensity map under
+// polynomial templates), which A Z cannot deflate and which would make
+// E = Z^T A Z singular.
+template <typename VecFn>
+int select_ritz(int m, int k, double eps_lambda, const std::vector<double>& wr, const std::vector<double>& wi,
+                VecFn vec, std::vector<double>& C, std::vector<double>& vals) {
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
+    std::vector<char> used(m, 0);
+    std::vector<std::vector<double>> cols;
+    vals.clear();
+    const int kwant = k > 0 ? std::min(k, m) : m;
+    double wmax = 0.0;
+    for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
+    const double wnull = 1e-10 * wmax;
+    std::vector<double> er, ei;
+    for (int idx : order) {
+        if ((int)cols.size() >= kwant) break;
+        if (used[idx]) continue;
+        if (std::fabs(wr[idx]) <= wnull) continue;
+        if (k <= 0 && !(wr[idx] < eps_lambda)) break;
+        used[idx] = 1;
+        if (!vec(idx, er, ei)) return 1;
+        cols.push_back(er);
+        vals.push_back(wr[idx]);
+        if (wi[idx] != 0.0) {
+            int partner = -1;
+            double best = 1e300;
+            for (int j2 = 0; j2 < m; ++j2) {
+                if (used[j2]) continue;
+                const double dd = std::fabs(wr[j2] - wr[idx]) + std::fabs(wi[j2] + wi[idx]);
+                if (dd < best) {
+                    best = dd;
+                    partner = j2;
+                }
+            }
+            if (partner >= 0) used[partner] = 1;
+            if ((int)cols.size() < kwant) {
+                cols.push_back(ei);
+                vals.push_back(wr[idx]);
+            }
+        }
+    }
+    const int ksel = (int)cols.size();
+    if (ksel == 0) return 2;
+    C.assign((size_t)m * ksel, 0.0);
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < ksel; ++c) C[(size_t)r * ksel + c] = cols[c][r];
+    return 0;
+}
+
+}  // namespace
+
+int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+                   std::vector<double>& vals) {
+    std::vector<double> wr, wi;
+    if (!host_hess_eigvals(H, m, wr, wi)) return 1;
+    auto vec = [&](int idx, std::vector<double>& er, std::vector<double>& ei) {
+        return host_hess_eigvec(H, m, wr[idx], wi[idx], er, ei);
+    };
+    return select_ritz(m, k, eps_lambda, wr, wi, vec, C, vals);
+}
+
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
+                      std::vector<double>& C, std::vector<double>& vals) {
+    std::vector<double> wr;
+    if (!host_tridiag_eigvals(d, e, m, wr)) return 1;
+    const std::vector<double> wi(m, 0.0);
+    auto vec = [&](int idx, std::vector<double>& er, std::vector<double>& ei) {
+        ei.assign(m, 0.0);
+        return host_tridiag_eigvec(d, e, m, wr[idx], er);
+    };
+    return select_ritz(m, k, eps_lambda, wr, wi, vec, C, vals);
 }
 
 bool host_cholesky(std::vector<double>& A, int n) {

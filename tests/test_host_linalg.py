@@ -27,6 +27,10 @@ bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double
                           std::vector<double>& w);
 bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
                          std::vector<double>& v);
+int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+                   std::vector<double>& vals);
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
+                      std::vector<double>& C, std::vector<double>& vals);
 bool host_cholesky(std::vector<double>& A, int n);
 void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
@@ -42,6 +46,24 @@ extern "C" int t_tri_eigvec(const double* d, const double* e, int n, double lam,
     if (!mm::host_tridiag_eigvec(dd, ee, n, lam, vv)) return 0;
     for (int i = 0; i < n; ++i) v[i] = vv[i];
     return 1;
+}
+extern "C" int t_ritz(const double* H, const double* d, const double* e, int m, int k, double eps, double* C,
+                      double* vals, int* ksel) {
+    std::vector<double> c, v;
+    int rs;
+    if (H) {
+        std::vector<double> h(H, H + (size_t)m * m);
+        rs = mm::host_ritz_hess(h, m, k, eps, c, v);
+    } else {
+        std::vector<double> dd(d, d + m), ee(e, e + (m > 1 ? m - 1 : 1));
+        rs = mm::host_ritz_tridiag(dd, ee, m, k, eps, c, v);
+    }
+    *ksel = (int)v.size();
+    if (rs == 0) {
+        for (size_t i = 0; i < c.size(); ++i) C[i] = c[i];
+        for (size_t i = 0; i < v.size(); ++i) vals[i] = v[i];
+    }
+    return rs;
 }
 extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     std::vector<double> a(A, A + (size_t)n * n), v;
@@ -97,6 +119,7 @@ def eig(tmp_path_factory):
     lib.t_chol_inv.argtypes = [P, C.c_int, P, P]
     lib.t_tri_eigvals.argtypes = [P, P, C.c_int, P]
     lib.t_tri_eigvec.argtypes = [P, P, C.c_int, C.c_double, P]
+    lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
     def p(a):
@@ -143,7 +166,19 @@ def eig(tmp_path_factory):
         assert lib.t_tri_eigvec(p(d), p(e), len(d), float(lam), p(v)) == 1
         return v
 
+    def ritz(H=None, d=None, e=None, k=0, eps=0.0):
+        m = H.shape[0] if H is not None else len(d)
+        Cm, v, ks = np.zeros(m * m), np.zeros(m), C.c_int(0)
+        args = [p(np.ascontiguousarray(H, dtype=np.float64)) if H is not None else None,
+                p(np.ascontiguousarray(d, dtype=np.float64)) if d is not None else None,
+                p(np.ascontiguousarray(e if len(e) else np.zeros(1), dtype=np.float64)) if e is not None else None]
+        rs = lib.t_ritz(*args, m, k, eps, p(Cm), p(v), C.byref(ks))
+        if rs != 0:
+            return rs, None, None
+        return 0, Cm[:m * ks.value].reshape(m, ks.value), v[:ks.value]
+
     vals.chol_inv = chol_inv
+    vals.ritz = ritz
     vals.tri = tri
     vals.tri_vec = tri_vec
     vals.upper_inv = upper_inv
@@ -335,3 +370,59 @@ def test_symmetric_tridiagonal_solver(eig, case):
     if len(V) > 1:
         G = np.array(V) @ np.array(V).T
         assert np.abs(G - np.eye(len(V))).max() < 1e-8
+
+
+def test_ritz_selection_smallest_real_pairs(eig):
+    """The k smallest Ritz pairs of H_m by real part, in ascending order, with H C = C diag(theta)."""
+    vals, _ = eig
+    rng = np.random.default_rng(20)
+    n, m = 300, 80
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = (Q * np.concatenate([np.geomspace(1e-3, 0.2, 20), 1.0 + rng.random(n - 20)])) @ Q.T
+    H = _arnoldi((0.5 + rng.random(n))[:, None] * A, m, 21)
+    rs, Cm, th = vals.ritz(H=H, k=10)
+    assert rs == 0 and Cm.shape == (m, 10)
+    full = np.sort(np.linalg.eigvals(H).real)
+    ref = full[:10]
+    np.testing.assert_allclose(th, ref, rtol=1e-10)
+    assert np.all(np.diff(th) >= 0)
+    np.testing.assert_allclose(H @ Cm, Cm * th, atol=1e-10 * np.abs(H).max())
+    # k <= 0: every value below eps_lambda
+    rs, Cm, th = vals.ritz(H=H, k=0, eps=0.1)
+    assert rs == 0 and np.all(th < 0.1) and len(th) == int((full < 0.1).sum())
+    assert vals.ritz(H=H, k=0, eps=1e-9)[0] == 2              # nothing below: no Ritz value selected
+
+
+def test_ritz_selection_splits_complex_pairs_and_skips_null_values(eig):
+    vals, _ = eig
+    # block diagonal: a rotation-scaling block (values 1 +- 2i), then 3 and 5, and an exact 0 (null direction)
+    H = np.zeros((5, 5))
+    H[0:2, 0:2] = [[1.0, 2.0], [-2.0, 1.0]]
+    H[2, 2], H[3, 3], H[4, 4] = 3.0, 5.0, 0.0
+    H[1, 2] = 0.3
+    H[3, 4] = 0.2
+    rs, Cm, th = vals.ritz(H=H, k=3)
+    assert rs == 0 and Cm.shape == (5, 3)
+    np.testing.assert_allclose(th, [1.0, 1.0, 3.0], atol=1e-13)      # the 0 is skipped, the pair gives 2 columns
+    P = Cm[:, :2]                                                    # real and imaginary parts span an invariant plane
+    R = H @ P - P @ np.linalg.lstsq(P, H @ P, rcond=None)[0]
+    assert np.abs(R).max() < 1e-12
+    np.testing.assert_allclose(H @ Cm[:, 2], 3.0 * Cm[:, 2], atol=1e-12)
+    # k = 1 stops inside the pair: one column only
+    rs, Cm, th = vals.ritz(H=H, k=1)
+    assert rs == 0 and Cm.shape == (5, 1)
+
+
+def test_ritz_selection_of_the_lanczos_tridiagonal(eig):
+    vals, _ = eig
+    rng = np.random.default_rng(22)
+    al = 0.5 + rng.random(60)
+    be = 0.8 * rng.random(59)
+    d = 1.0 / al + np.concatenate([[0.0], be / al[:-1]])
+    e = -np.sqrt(be) / al[:-1]
+    T = _tridiag(d, e)
+    rs, Cm, th = vals.ritz(d=d, e=e, k=8)
+    assert rs == 0 and Cm.shape == (60, 8)
+    np.testing.assert_allclose(th, np.linalg.eigvalsh(T)[:8], atol=1e-13 * np.abs(T).sum(axis=1).max())
+    np.testing.assert_allclose(Cm.T @ Cm, np.eye(8), atol=1e-10)
+    np.testing.assert_allclose(T @ Cm, Cm * th, atol=1e-11)

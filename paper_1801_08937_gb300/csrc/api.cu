@@ -1530,46 +1530,10 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     }
     const int ns = (int)so.size() - 1;
     if (so[0] != 0 || so[ns] != N) return fail(ctx, MM_ERR_ARG, "subscan_off must start at 0 and end at n_samples");
-    std::vector<int32_t> blk_sub(ctx->n_blocks + 1, 0);
-    {
-        int b = 0;
-        for (int s = 0; s < ns; ++s) {
-            if (so[s + 1] <= so[s]) return fail(ctx, MM_ERR_ARG, "subscan_off must be strictly increasing");
-            while (ctx->block_off[b + 1] <= so[s]) blk_sub[++b] = s;
-            if (so[s] < ctx->block_off[b] || so[s + 1] > ctx->block_off[b + 1])
-                return fail(ctx, MM_ERR_ARG, "every subscan must lie inside one block");
-        }
-        while (b < ctx->n_blocks) blk_sub[++b] = ns;
-        for (int bb = 0; bb < ctx->n_blocks; ++bb)
-            if (so[blk_sub[bb]] != ctx->block_off[bb])
-                return fail(ctx, MM_ERR_ARG, "block boundaries must be subscan boundaries");
-    }
-    // inverse Gram matrices of the Legendre columns P_0..P_Ks, Ks = min(K, m - 1), per subscan
-    std::vector<double> ginv((size_t)ns * 16, 0.0);
-    if (poly_order >= 0) {
-        std::map<int64_t, std::array<double, 16>> cache;
-        for (int s = 0; s < ns; ++s) {
-            const int64_t m = so[s + 1] - so[s];
-            auto it = cache.find(m);
-            if (it == cache.end()) {
-                const int K = (int)std::min<int64_t>(poly_order, m - 1), n = K + 1;
-                std::vector<double> G((size_t)n * n, 0.0), Ginv;
-                for (int64_t i = 0; i < m; ++i) {
-                    const double u = 2.0 * ((double)i + 0.5) / (double)m - 1.0;
-                    const double p[4] = {1.0, u, 1.5 * u * u - 0.5, (2.5 * u * u - 1.5) * u};
-                    for (int j = 0; j < n; ++j)
-                        for (int l = 0; l < n; ++l) G[(size_t)j * n + l] += p[j] * p[l];
-                }
-                if (!host_cholesky(G, n)) return fail(ctx, MM_ERR_ARG, "singular subscan Gram matrix");
-                host_spd_inverse_from_chol(G, n, Ginv);
-                std::array<double, 16> g{};
-                for (int j = 0; j < n; ++j)
-                    for (int l = 0; l < n; ++l) g[j * 4 + l] = Ginv[(size_t)j * n + l];
-                it = cache.emplace(m, g).first;
-            }
-            std::copy(it->second.begin(), it->second.end(), ginv.begin() + (size_t)s * 16);
-        }
-    }
+    std::vector<int32_t> blk_sub;
+    std::vector<double> ginv;
+    std::string lerr;
+    if (!host_template_layout(ctx->block_off, so, poly_order, blk_sub, ginv, lerr)) return fail(ctx, MM_ERR_ARG, lerr);
     std::vector<double> wb(ctx->n_blocks);
     int64_t maxb = 0;
     for (int b = 0; b < ctx->n_blocks; ++b) {

@@ -245,6 +245,14 @@ int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda
                    std::vector<double>& vals);
 int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
                       std::vector<double>& C, std::vector<double>& vals);
+// Layout of the polynomial templates (Sect. 4.1): checks that subscan
+// offsets so[0..ns] increase, that every subscan lies inside one block and
+// that block boundaries are subscan boundaries; blk_sub[b] = first subscan of
+// block b (blk_sub[n_blocks] = ns); ginv[s][4][4] = (B^T B)^-1 of subscan s's
+// Legendre columns P_0..P_min(K, m-1) (poly_order K < 0: zeros).  False with
+// err set on a bad layout.
+bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
+                          std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err);
 // Lower Cholesky factor in place (row-major n x n); false if not SPD.
 bool host_cholesky(std::vector<double>& A, int n);
 // Inverse of an SPD matrix from its Cholesky factor.

@@ -16,8 +16,12 @@
 // Wilkinson shift (O(m) per step) and inverse iteration with a tridiagonal
 // LU (O(m) per solve).
 #include <algorithm>
+#include <array>
+#include <cstdint>
 #include <cmath>
 #include <complex>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -500,6 +504,60 @@ void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>
         const double d = 1.0 / R[(size_t)i * n + i];
         for (int c = i; c < n; ++c) ri[c] *= d;
     }
+}
+
+bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
+                          std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err) {
+    const int nb = (int)block_off.size() - 1, ns = (int)so.size() - 1;
+    blk_sub.assign(nb + 1, 0);
+    int b = 0;
+    for (int s = 0; s < ns; ++s) {
+        if (so[s + 1] <= so[s]) {
+            err = "subscan_off must be strictly increasing";
+            return false;
+        }
+        while (block_off[b + 1] <= so[s]) blk_sub[++b] = s;
+        if (so[s] < block_off[b] || so[s + 1] > block_off[b + 1]) {
+            err = "every subscan must lie inside one block";
+            return false;
+        }
+    }
+    while (b < nb) blk_sub[++b] = ns;
+    for (int bb = 0; bb < nb; ++bb)
+        if (so[blk_sub[bb]] != block_off[bb]) {
+            err = "block boundaries must be subscan boundaries";
+            return false;
+        }
+    // G = B^T B of the Legendre columns P_0..P_Ks at u_i = 2 (i + 1/2) / m - 1,
+    // Ks = min(K, m - 1), inverted once per distinct subscan length
+    ginv.assign((size_t)ns * 16, 0.0);
+    if (poly_order < 0) return true;
+    std::map<int64_t, std::array<double, 16>> cache;
+    for (int s = 0; s < ns; ++s) {
+        const int64_t m = so[s + 1] - so[s];
+        auto it = cache.find(m);
+        if (it == cache.end()) {
+            const int K = (int)std::min<int64_t>(poly_order, m - 1), n = K + 1;
+            std::vector<double> G((size_t)n * n, 0.0), Gi;
+            for (int64_t i = 0; i < m; ++i) {
+                const double u = 2.0 * ((double)i + 0.5) / (double)m - 1.0;
+                const double p[4] = {1.0, u, 1.5 * u * u - 0.5, (2.5 * u * u - 1.5) * u};
+                for (int j = 0; j < n; ++j)
+                    for (int l = 0; l < n; ++l) G[(size_t)j * n + l] += p[j] * p[l];
+            }
+            if (!host_cholesky(G, n)) {
+                err = "singular subscan Gram matrix";
+                return false;
+            }
+            host_spd_inverse_from_chol(G, n, Gi);
+            std::array<double, 16> g{};
+            for (int j = 0; j < n; ++j)
+                for (int l = 0; l < n; ++l) g[j * 4 + l] = Gi[(size_t)j * n + l];
+            it = cache.emplace(m, g).first;
+        }
+        std::copy(it->second.begin(), it->second.end(), ginv.begin() + (size_t)s * 16);
+    }
+    return true;
 }
 
 }  // namespace mm

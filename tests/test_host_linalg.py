@@ -18,8 +18,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1801_08937_gb300", "csrc")
 
 SHIM = r"""
+#include <cstdint>
+#include <cstring>
+#include <string>
 #include <vector>
 namespace mm {
+bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
+                          std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err);
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
                       std::vector<double>& vi);
@@ -64,6 +69,20 @@ extern "C" int t_ritz(const double* H, const double* d, const double* e, int m, 
         for (size_t i = 0; i < v.size(); ++i) vals[i] = v[i];
     }
     return rs;
+}
+extern "C" int t_layout(const int64_t* bo, int nb, const int64_t* so, int ns, int order, int32_t* blk_sub,
+                        double* ginv, char* err) {
+    std::vector<int64_t> b(bo, bo + nb + 1), s(so, so + ns + 1);
+    std::vector<int32_t> bs;
+    std::vector<double> g;
+    std::string e;
+    if (!mm::host_template_layout(b, s, order, bs, g, e)) {
+        std::strncpy(err, e.c_str(), 255);
+        return 0;
+    }
+    for (size_t i = 0; i < bs.size(); ++i) blk_sub[i] = bs[i];
+    for (size_t i = 0; i < g.size(); ++i) ginv[i] = g[i];
+    return 1;
 }
 extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     std::vector<double> a(A, A + (size_t)n * n), v;
@@ -119,6 +138,8 @@ def eig(tmp_path_factory):
     lib.t_chol_inv.argtypes = [P, C.c_int, P, P]
     lib.t_tri_eigvals.argtypes = [P, P, C.c_int, P]
     lib.t_tri_eigvec.argtypes = [P, P, C.c_int, C.c_double, P]
+    I64 = C.POINTER(C.c_int64)
+    lib.t_layout.argtypes = [I64, C.c_int, I64, C.c_int, C.c_int, C.POINTER(C.c_int32), P, C.c_char_p]
     lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
@@ -177,7 +198,20 @@ def eig(tmp_path_factory):
             return rs, None, None
         return 0, Cm[:m * ks.value].reshape(m, ks.value), v[:ks.value]
 
+    def layout(block_off, so, order):
+        bo = np.ascontiguousarray(block_off, dtype=np.int64)
+        sv = np.ascontiguousarray(so, dtype=np.int64)
+        bs = np.zeros(len(bo), np.int32)
+        g = np.zeros(16 * (len(sv) - 1))
+        err = C.create_string_buffer(256)
+        ok = lib.t_layout(bo.ctypes.data_as(I64), len(bo) - 1, sv.ctypes.data_as(I64), len(sv) - 1, order,
+                          bs.ctypes.data_as(C.POINTER(C.c_int32)), p(g), err)
+        if not ok:
+            return err.value.decode()
+        return bs, g.reshape(-1, 4, 4)
+
     vals.chol_inv = chol_inv
+    vals.layout = layout
     vals.ritz = ritz
     vals.tri = tri
     vals.tri_vec = tri_vec
@@ -426,3 +460,33 @@ def test_ritz_selection_of_the_lanczos_tridiagonal(eig):
     np.testing.assert_allclose(th, np.linalg.eigvalsh(T)[:8], atol=1e-13 * np.abs(T).sum(axis=1).max())
     np.testing.assert_allclose(Cm.T @ Cm, np.eye(8), atol=1e-10)
     np.testing.assert_allclose(T @ Cm, Cm * th, atol=1e-11)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_template_layout_gram_inverses_and_block_map(eig, order):
+    """Per subscan, (B^T B)^-1 of the Legendre columns P_0..P_min(K, m-1) at u = 2 (i + 1/2) / m - 1
+    equals numpy's inverse of legvander's Gram matrix (short subscans take order m - 1); every block
+    maps to its first subscan."""
+    from numpy.polynomial import legendre
+    vals, _ = eig
+    block_off = np.array([0, 100, 100, 230, 300])         # one empty block
+    so = np.array([0, 1, 3, 40, 100, 101, 150, 230, 300])   # subscans of 1, 2, 37, 60, 1, 49, 80, 70 samples
+    bs, g = vals.layout(block_off, so, order)
+    assert list(bs) == [0, 4, 4, 7, 8]
+    for s in range(len(so) - 1):
+        m = so[s + 1] - so[s]
+        K = min(order, m - 1)
+        u = 2.0 * (np.arange(m) + 0.5) / m - 1.0
+        B = legendre.legvander(u, K)
+        ref = np.linalg.inv(B.T @ B)
+        np.testing.assert_allclose(g[s, :K + 1, :K + 1], ref, rtol=1e-11, atol=1e-13)
+        assert np.all(g[s, K + 1:, :] == 0.0) and np.all(g[s, :, K + 1:] == 0.0)
+
+
+def test_template_layout_rejects_bad_subscans(eig):
+    vals, _ = eig
+    bo = np.array([0, 100, 200])
+    assert vals.layout(bo, [0, 50, 150, 200], 1) == "every subscan must lie inside one block"
+    assert vals.layout(bo, [0, 50, 50, 100, 200], 1) == "subscan_off must be strictly increasing"
+    bs, g = vals.layout(bo, [0, 100, 200], -1)               # no polynomials: blocks as subscans, no Gram data
+    assert list(bs) == [0, 1, 2] and np.all(g == 0.0)

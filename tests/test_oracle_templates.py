@@ -8,6 +8,8 @@ against the subspaces it must annihilate or preserve, the ground fit
 against a brute-force loop, the estimator against exact recovery.
 """
 import copy
+import json
+import os
 
 import numpy as np
 import pytest
@@ -190,3 +192,14 @@ def test_filters_create_small_eigenvalues_that_two_level_removes():
     it_2l = O.pcg(lambda v: A @ v, lambda v: O.m2l_apply(v, lambda r: M @ r, Z, AZ, L), b,
                   tol=1e-10, max_iter=2000)[1]["iters"]
     assert it_2l < it_bd
+
+
+def test_hand_worked_template_filters():
+    """Four samples worked by hand (fixture tests/golden/hand_template_filters.json): order-0 and
+    order-1 subscan fits, the ground bins alone, and order 1 around the ground bins."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_template_filters.json")))
+    for case in g["cases"]:
+        az = None if case["az_bin"] is None else np.array(case["az_bin"])
+        tp = O.TemplateProblem(g["pix"], g["psi"], g["block_off"], g["w_block"], g["n_pix"], g["subscan_off"],
+                               case["poly_order"], az, case["n_az_bins"], g["stokes"])
+        np.testing.assert_allclose(O.apply_A_T(tp, np.array(g["x"])), np.array(case["Ax"]), atol=1e-14)

@@ -150,7 +150,7 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
  * first right-hand side of the last mm_rhs/mm_solve call), with two classical
  * Gram-Schmidt passes per step in float64, stopping when h_{j+1,j} <= eps_arn
  * or after m_max steps.  Ritz pairs of H_m (Eq. ritz) are sorted by real part;
- * the k smallest (or, if k <= 0, all with real part below eps_lambda) form Z,
+ * the k smallest (or, if k <= 0, all with real part below eps_lambda, at most 512) form Z,
  * a complex pair adding its real and imaginary parts.  Z is orthonormalised,
  * AZ = A Z and E = Z^T A Z are formed, and E is factored (float64).
  * Ritz values at the round-off level of the largest (null directions of A)
@@ -168,7 +168,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
  * B V = V T_m + (rank one) with T_m tridiagonal, diagonal
  * 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j.
  * Ritz pairs of T_m (Appendix A, Eq. ritz, in its symmetric form) give the
- * deflation basis: the k smallest (or, if k <= 0, those below eps_lambda)
+ * deflation basis: the k smallest (or, if k <= 0, those below eps_lambda, at most 512)
  * form Z = V S, then Z is orthonormalised and AZ, E = Z^T A Z formed as in
  * mm_build_coarse (k <= 512).  *k_out (may be NULL) receives dim Z.
  * Errors: MM_ERR_STATE (no harvested solve), MM_ERR_ARG, MM_ERR_SINGULAR,

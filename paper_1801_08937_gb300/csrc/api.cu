@@ -1812,7 +1812,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
         for (int j = 0; j < m; ++j) Hm[(size_t)i * m + j] = H[(size_t)i * m_max + j];
     // Ritz values first; Ritz vectors (inverse iteration) only for the selected ones
     std::vector<double> C, vals;
-    const int rs = host_ritz_hess(Hm, m, k, eps_lambda, C, vals);
+    const int rs = host_ritz_hess(Hm, m, k, MM_K_MAX, eps_lambda, C, vals);
     if (rs == 1) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of H_m failed");
     if (rs == 2) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
     const int ksel = (int)vals.size();
@@ -1849,7 +1849,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
         if (j + 1 < m) te[j] = -std::sqrt(std::max(0.0, be[j])) / al[j];
     }
     std::vector<double> C, vals;
-    const int rs = host_ritz_tridiag(td, te, m, k, eps_lambda, C, vals);
+    const int rs = host_ritz_tridiag(td, te, m, k, MM_K_MAX, eps_lambda, C, vals);
     if (rs == 1) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");
     if (rs == 2) return fail(ctx, MM_ERR_ARG, "no Ritz value selected");
     const int ksel = (int)vals.size();

@@ -237,14 +237,14 @@ bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>
                          std::vector<double>& v);
 // Ritz selection (Appendix A, Eq. ritz) from the Arnoldi H_m or the
 // symmetric tridiagonal Lanczos T_m: the k smallest Ritz pairs by real part
-// (k <= 0: those below eps_lambda), complex pairs as real and imaginary
+// (k <= 0: those below eps_lambda, at most kmax), complex pairs as real and imaginary
 // parts, null values (|theta| <= 1e-10 max |theta|) skipped.  C [m][ksel]
 // row-major holds the Ritz vectors in the Krylov basis, vals their values.
 // Returns 0, 1 if an eigen-solve failed, 2 if nothing was selected.
-int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double eps_lambda, std::vector<double>& C,
                    std::vector<double>& vals);
-int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
-                      std::vector<double>& C, std::vector<double>& vals);
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, int kmax,
+                      double eps_lambda, std::vector<double>& C, std::vector<double>& vals);
 // Layout of the polynomial templates (Sect. 4.1): checks that subscan
 // offsets so[0..ns] increase, that every subscan lies inside one block and
 // that block boundaries are subscan boundaries; blk_sub[b] = first subscan of

@@ -362,22 +362,23 @@ namespace {
 
 // The selection of the Ritz pairs (Appendix A, Eq. ritz) from the values
 // wr + i wi; vec(idx, er, ei) computes the vector of value idx.  Sorted by
-// real part, the k smallest are kept (k <= 0: those below eps_lambda); a
+// real part, the k smallest are kept (k <= 0: those below eps_lambda, at
+// most kmax of them, the size the coarse-space kernels hold); a
 // complex pair gives its real and imaginary parts (its partner is not taken
 // again); values at the round-off level of the largest are skipped: they
 // belong to null directions of A (e.g. a constant intensity map under
 // polynomial templates), which A Z cannot deflate and which would make
 // E = Z^T A Z singular.
 template <typename VecFn>
-int select_ritz(int m, int k, double eps_lambda, const std::vector<double>& wr, const std::vector<double>& wi,
-                VecFn vec, std::vector<double>& C, std::vector<double>& vals) {
+int select_ritz(int m, int k, int kmax, double eps_lambda, const std::vector<double>& wr,
+                const std::vector<double>& wi, VecFn vec, std::vector<double>& C, std::vector<double>& vals) {
     std::vector<int> order(m);
     for (int i = 0; i < m; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wr[a] < wr[b]; });
     std::vector<char> used(m, 0);
     std::vector<std::vector<double>> cols;
     vals.clear();
-    const int kwant = k > 0 ? std::min(k, m) : m;
+    const int kwant = std::min(k > 0 ? k : kmax, m);
     double wmax = 0.0;
     for (int i = 0; i < m; ++i) wmax = std::max(wmax, std::fabs(wr[i]));
     const double wnull = 1e-10 * wmax;
@@ -419,18 +420,18 @@ int select_ritz(int m, int k, double eps_lambda, const std::vector<double>& wr, 
 
 }  // namespace
 
-int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double eps_lambda, std::vector<double>& C,
                    std::vector<double>& vals) {
     std::vector<double> wr, wi;
     if (!host_hess_eigvals(H, m, wr, wi)) return 1;
     auto vec = [&](int idx, std::vector<double>& er, std::vector<double>& ei) {
         return host_hess_eigvec(H, m, wr[idx], wi[idx], er, ei);
     };
-    return select_ritz(m, k, eps_lambda, wr, wi, vec, C, vals);
+    return select_ritz(m, k, kmax, eps_lambda, wr, wi, vec, C, vals);
 }
 
-int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
-                      std::vector<double>& C, std::vector<double>& vals) {
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, int kmax,
+                      double eps_lambda, std::vector<double>& C, std::vector<double>& vals) {
     std::vector<double> wr;
     if (!host_tridiag_eigvals(d, e, m, wr)) return 1;
     const std::vector<double> wi(m, 0.0);
@@ -438,7 +439,7 @@ int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e
         ei.assign(m, 0.0);
         return host_tridiag_eigvec(d, e, m, wr[idx], er);
     };
-    return select_ritz(m, k, eps_lambda, wr, wi, vec, C, vals);
+    return select_ritz(m, k, kmax, eps_lambda, wr, wi, vec, C, vals);
 }
 
 bool host_cholesky(std::vector<double>& A, int n) {

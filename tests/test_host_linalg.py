@@ -32,10 +32,10 @@ bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double
                           std::vector<double>& w);
 bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
                          std::vector<double>& v);
-int host_ritz_hess(const std::vector<double>& H, int m, int k, double eps_lambda, std::vector<double>& C,
+int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double eps_lambda, std::vector<double>& C,
                    std::vector<double>& vals);
-int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, double eps_lambda,
-                      std::vector<double>& C, std::vector<double>& vals);
+int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, int kmax,
+                      double eps_lambda, std::vector<double>& C, std::vector<double>& vals);
 bool host_cholesky(std::vector<double>& A, int n);
 void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
@@ -52,16 +52,16 @@ extern "C" int t_tri_eigvec(const double* d, const double* e, int n, double lam,
     for (int i = 0; i < n; ++i) v[i] = vv[i];
     return 1;
 }
-extern "C" int t_ritz(const double* H, const double* d, const double* e, int m, int k, double eps, double* C,
-                      double* vals, int* ksel) {
+extern "C" int t_ritz(const double* H, const double* d, const double* e, int m, int k, int kmax, double eps,
+                      double* C, double* vals, int* ksel) {
     std::vector<double> c, v;
     int rs;
     if (H) {
         std::vector<double> h(H, H + (size_t)m * m);
-        rs = mm::host_ritz_hess(h, m, k, eps, c, v);
+        rs = mm::host_ritz_hess(h, m, k, kmax, eps, c, v);
     } else {
         std::vector<double> dd(d, d + m), ee(e, e + (m > 1 ? m - 1 : 1));
-        rs = mm::host_ritz_tridiag(dd, ee, m, k, eps, c, v);
+        rs = mm::host_ritz_tridiag(dd, ee, m, k, kmax, eps, c, v);
     }
     *ksel = (int)v.size();
     if (rs == 0) {
@@ -140,7 +140,7 @@ def eig(tmp_path_factory):
     lib.t_tri_eigvec.argtypes = [P, P, C.c_int, C.c_double, P]
     I64 = C.POINTER(C.c_int64)
     lib.t_layout.argtypes = [I64, C.c_int, I64, C.c_int, C.c_int, C.POINTER(C.c_int32), P, C.c_char_p]
-    lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
+    lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
     def p(a):
@@ -187,13 +187,13 @@ def eig(tmp_path_factory):
         assert lib.t_tri_eigvec(p(d), p(e), len(d), float(lam), p(v)) == 1
         return v
 
-    def ritz(H=None, d=None, e=None, k=0, eps=0.0):
+    def ritz(H=None, d=None, e=None, k=0, eps=0.0, kmax=512):
         m = H.shape[0] if H is not None else len(d)
         Cm, v, ks = np.zeros(m * m), np.zeros(m), C.c_int(0)
         args = [p(np.ascontiguousarray(H, dtype=np.float64)) if H is not None else None,
                 p(np.ascontiguousarray(d, dtype=np.float64)) if d is not None else None,
                 p(np.ascontiguousarray(e if len(e) else np.zeros(1), dtype=np.float64)) if e is not None else None]
-        rs = lib.t_ritz(*args, m, k, eps, p(Cm), p(v), C.byref(ks))
+        rs = lib.t_ritz(*args, m, k, kmax, eps, p(Cm), p(v), C.byref(ks))
         if rs != 0:
             return rs, None, None
         return 0, Cm[:m * ks.value].reshape(m, ks.value), v[:ks.value]
@@ -425,6 +425,10 @@ def test_ritz_selection_smallest_real_pairs(eig):
     rs, Cm, th = vals.ritz(H=H, k=0, eps=0.1)
     assert rs == 0 and np.all(th < 0.1) and len(th) == int((full < 0.1).sum())
     assert vals.ritz(H=H, k=0, eps=1e-9)[0] == 2              # nothing below: no Ritz value selected
+    # k <= 0 keeps at most kmax vectors (the coarse-space kernels' capacity)
+    rs, Cm, th = vals.ritz(H=H, k=0, eps=10.0, kmax=7)
+    assert rs == 0 and Cm.shape == (m, 7)
+    np.testing.assert_allclose(th, full[:7], rtol=1e-10)
 
 
 def test_ritz_selection_splits_complex_pairs_and_skips_null_values(eig):

@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
     ap.add_argument("--poly-order", type=int, default=1, help="templates mode: subscan polynomial order")
-    ap.add_argument("--fp64-products", type=int, default=1, choices=[1, 2],
-                    help="templates mode, fp64: operator products in native float64 (1) or double-float (2)")
+    ap.add_argument("--fp64-products", type=int, default=2, choices=[1, 2],
+                    help="templates mode, fp64: operator products in native float64 (1) or double-float (2, default)")
     ap.add_argument("--stokes", type=int, default=1, choices=[0, 1, 2],
                     help="templates mode: 1 Q/U maps from d^-, 2 I maps from d^+, 0 I/Q/U")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates"],

@@ -1840,14 +1840,8 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     CK(cudaSetDevice(ctx->device));
     const int m = ctx->harvest_count;
     const int64_t n = (int64_t)ctx->n_pix * 4;
-    // T: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal -sqrt(beta_j)/alpha_j
-    std::vector<double> td(m), te(std::max(1, m - 1), 0.0);
-    const auto& al = ctx->harv_alpha;
-    const auto& be = ctx->harv_beta;
-    for (int j = 0; j < m; ++j) {
-        td[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-        if (j + 1 < m) te[j] = -std::sqrt(std::max(0.0, be[j])) / al[j];
-    }
+    std::vector<double> td, te;
+    host_lanczos_tridiag(ctx->harv_alpha, ctx->harv_beta, m, td, te);
     std::vector<double> C, vals;
     const int rs = host_ritz_tridiag(td, te, m, k, MM_K_MAX, eps_lambda, C, vals);
     if (rs == 1) return fail(ctx, MM_ERR_SINGULAR, "eigen-solve of the Lanczos matrix failed");

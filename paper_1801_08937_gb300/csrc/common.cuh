@@ -245,6 +245,10 @@ int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double 
                    std::vector<double>& vals);
 int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, int kmax,
                       double eps_lambda, std::vector<double>& C, std::vector<double>& vals);
+// The Lanczos matrix T_m of a PCG run with M_BD from its coefficients
+// alpha_j, beta_j (j < m): diagonal d[m], off-diagonal e[m-1].
+void host_lanczos_tridiag(const std::vector<double>& alpha, const std::vector<double>& beta, int m,
+                          std::vector<double>& d, std::vector<double>& e);
 // Layout of the polynomial templates (Sect. 4.1): checks that subscan
 // offsets so[0..ns] increase, that every subscan lies inside one block and
 // that block boundaries are subscan boundaries; blk_sub[b] = first subscan of

@@ -507,6 +507,19 @@ void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>
     }
 }
 
+void host_lanczos_tridiag(const std::vector<double>& alpha, const std::vector<double>& beta, int m,
+                          std::vector<double>& d, std::vector<double>& e) {
+    // PCG with M_BD is the Lanczos process of B = M_BD A in the M_BD^-1 inner
+    // product; its coefficients give T_m with diagonal
+    // 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j
+    d.assign(m, 0.0);
+    e.assign(std::max(1, m - 1), 0.0);
+    for (int j = 0; j < m; ++j) {
+        d[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < m) e[j] = -std::sqrt(std::max(0.0, beta[j])) / alpha[j];
+    }
+}
+
 bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
                           std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err) {
     const int nb = (int)block_off.size() - 1, ns = (int)so.size() - 1;

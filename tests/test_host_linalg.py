@@ -23,6 +23,8 @@ SHIM = r"""
 #include <string>
 #include <vector>
 namespace mm {
+void host_lanczos_tridiag(const std::vector<double>& alpha, const std::vector<double>& beta, int m,
+                          std::vector<double>& d, std::vector<double>& e);
 bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
                           std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err);
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
@@ -84,6 +86,12 @@ extern "C" int t_layout(const int64_t* bo, int nb, const int64_t* so, int ns, in
     for (size_t i = 0; i < g.size(); ++i) ginv[i] = g[i];
     return 1;
 }
+extern "C" void t_lanczos(const double* al, const double* be, int m, double* d, double* e) {
+    std::vector<double> a(al, al + m), b(be, be + m), dd, ee;
+    mm::host_lanczos_tridiag(a, b, m, dd, ee);
+    for (int i = 0; i < m; ++i) d[i] = dd[i];
+    for (int i = 0; i + 1 < m; ++i) e[i] = ee[i];
+}
 extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     std::vector<double> a(A, A + (size_t)n * n), v;
     if (!mm::host_cholesky(a, n)) return 0;
@@ -140,6 +148,7 @@ def eig(tmp_path_factory):
     lib.t_tri_eigvec.argtypes = [P, P, C.c_int, C.c_double, P]
     I64 = C.POINTER(C.c_int64)
     lib.t_layout.argtypes = [I64, C.c_int, I64, C.c_int, C.c_int, C.POINTER(C.c_int32), P, C.c_char_p]
+    lib.t_lanczos.argtypes = [P, P, C.c_int, P, P]
     lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
@@ -210,7 +219,16 @@ def eig(tmp_path_factory):
             return err.value.decode()
         return bs, g.reshape(-1, 4, 4)
 
+    def lanczos(al, be):
+        al = np.ascontiguousarray(al, dtype=np.float64)
+        be = np.ascontiguousarray(be, dtype=np.float64)
+        m = len(al)
+        d, e = np.zeros(m), np.zeros(max(1, m - 1))
+        lib.t_lanczos(p(al), p(be), m, p(d), p(e))
+        return d, e[:m - 1]
+
     vals.chol_inv = chol_inv
+    vals.lanczos = lanczos
     vals.layout = layout
     vals.ritz = ritz
     vals.tri = tri
@@ -494,3 +512,57 @@ def test_template_layout_rejects_bad_subscans(eig):
     assert vals.layout(bo, [0, 50, 50, 100, 200], 1) == "subscan_off must be strictly increasing"
     bs, g = vals.layout(bo, [0, 100, 200], -1)               # no polynomials: blocks as subscans, no Gram data
     assert list(bs) == [0, 1, 2] and np.all(g == 0.0)
+
+
+def _angle(A, B):
+    """Sine of the largest principal angle between the column spans of A and B (equal dimensions)."""
+    qa, _ = np.linalg.qr(A)
+    qb, _ = np.linalg.qr(B)
+    return float(np.linalg.norm(qa - qb @ (qb.T @ qa), 2))
+
+
+def _tiny_problem():
+    import synth
+    from helpers import oracle_problem
+    scan = synth.make_scan(seed=3, **synth.CONFIGS["small"])
+    prob, mbd, good = oracle_problem(scan)
+    d = synth.make_tod(scan, synth.make_sky(scan.n_pix, 3), synth.make_noise(scan, 3))
+    return prob, mbd, d
+
+
+def test_coarse_space_from_a_harvested_solve_matches_the_oracle(eig):
+    """Host side of mm_build_coarse_from_solve against the oracle: T_m from the PCG coefficients of an
+    M_BD run equals the oracle's Lanczos matrix, its k smallest Ritz values match, and V_m C spans the
+    oracle's deflation basis."""
+    import oracle as O
+    vals, _ = eig
+    prob, mbd, d = _tiny_problem()
+    A = lambda v: O.apply_A(prob, v).reshape(-1)
+    M = lambda v: O.bd_apply(mbd, v).reshape(-1)
+    b = O.rhs(prob, d).reshape(-1)
+    al, be, V = O.pcg_lanczos(A, M, b, 40)
+    lam, Q, T = O.lanczos_ritz(al, be, V, 8)
+    dd, ee = vals.lanczos(al, be)
+    np.testing.assert_allclose(dd, np.diag(T), rtol=1e-15)
+    np.testing.assert_allclose(ee, np.diag(T, 1), rtol=1e-15)
+    rs, Cm, th = vals.ritz(d=dd, e=ee, k=8)
+    assert rs == 0
+    np.testing.assert_allclose(th, lam, rtol=1e-10)
+    assert _angle(V @ Cm, Q) < 1e-8
+
+
+def test_coarse_space_from_arnoldi_matches_the_oracle(eig):
+    """Host side of mm_build_coarse: the Ritz selection from the Arnoldi H_m of B = M_BD A gives the
+    oracle's Ritz values and spans the oracle's deflation basis W_m Y."""
+    import oracle as O
+    vals, _ = eig
+    prob, mbd, d = _tiny_problem()
+    A = lambda v: O.apply_A(prob, v).reshape(-1)
+    M = lambda v: O.bd_apply(mbd, v).reshape(-1)
+    r0 = M(O.rhs(prob, d).reshape(-1))
+    W, H, m = O.arnoldi(lambda v: M(A(v)), r0, 40, 1e-12)
+    Q, ref = O.ritz_basis(W, H, m, 8)
+    rs, Cm, th = vals.ritz(H=H[:m, :m], k=8)
+    assert rs == 0 and Cm.shape[1] == len(ref)
+    np.testing.assert_allclose(th, ref, rtol=1e-9)
+    assert _angle(W[:, :m] @ Cm, Q) < 1e-7

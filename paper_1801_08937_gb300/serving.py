@@ -121,6 +121,7 @@ class MapServer:
         self.evictions = 0
         self.admitted = 0
         self.rejected = 0
+        self.failed = 0
         self.max_concurrent = 0
         self.t0 = None
         self.error = None
@@ -154,7 +155,7 @@ class MapServer:
                 "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                 "maps_per_s": self.completed / wall if wall > 0 else 0.0, "cache_hits": self.cache_hits,
                 "evictions": self.evictions, "admitted": self.admitted, "max_concurrent": self.max_concurrent,
-                "resident_scans": len(self._scans)}
+                "resident_scans": len(self._scans), "failed": self.failed}
 
     # ---------------- memory accounting ----------------
     def _free_bytes(self) -> int:
@@ -284,20 +285,47 @@ class MapServer:
                 else:
                     self._start_solve(req, fut, e, cached=False)
 
+    def _drop_failed(self, a, ex):
+        """A solve that raised fails its own request; its scan's context is closed and forgotten (its
+        state is unknown), so a later request on the scan sets it up again."""
+        if not a.fut.done():
+            a.fut.set_exception(ex)
+        sid = a.req.scan_id
+        if self._scans.get(sid) is a.entry:
+            del self._scans[sid]
+            try:
+                a.entry.ctx.close()
+            except Exception:
+                pass
+        self.failed += 1
+
     def _tick(self) -> bool:
         progressed = False
+        failed = set()
         for a in self._active:
             if not a.launched:
-                a.entry.ctx.solve_launch(self.iters_per_tick)
+                try:
+                    a.entry.ctx.solve_launch(self.iters_per_tick)
+                except Exception as ex:
+                    self._drop_failed(a, ex)
+                    failed.add(id(a))
+                    continue
                 a.launched = True
         still = []
         for a in self._active:
-            ready, done = a.entry.ctx.solve_poll()
+            if id(a) in failed:
+                continue
+            try:
+                ready, done = a.entry.ctx.solve_poll()
+                x, info = a.entry.ctx.solve_end() if done else (None, None)
+            except Exception as ex:
+                self._drop_failed(a, ex)
+                progressed = True
+                continue
             if ready:
                 a.launched = False
                 progressed = True
             if done:
-                x, info = a.entry.ctx.solve_end()
                 now = time.perf_counter()
                 if a.entry.harvesting:
                     # deflation basis from this M_BD run's Lanczos vectors, off the critical path

@@ -52,6 +52,7 @@ class FakeContext:
     lock = threading.Lock()
     log = []
     fail_npix = set()
+    fail_poll = set()
     live = 0
     max_live = 0
 
@@ -104,6 +105,9 @@ class FakeContext:
 
     def solve_poll(self):
         self.polls += 1
+        if self.n_pix in FakeContext.fail_poll:
+            FakeContext.fail_poll.discard(self.n_pix)       # fails once
+            raise RuntimeError(f"breakdown on {self.n_pix}")
         return True, self.polls >= 3
 
     def solve_end(self, out=None, like=None):
@@ -120,6 +124,7 @@ class FakeContext:
 def fake(monkeypatch):
     FakeContext.log = []
     FakeContext.fail_npix = set()
+    FakeContext.fail_poll = set()
     FakeContext.live = 0
     FakeContext.max_live = 0
     monkeypatch.setattr(M, "Context", FakeContext)
@@ -211,3 +216,19 @@ def test_concurrent_solves_are_capped(fake):
         assert np.all(f.result(timeout=20).map == 64.0 * n)
     srv.stop()
     assert srv.stats()["max_concurrent"] == 1
+
+
+def test_a_failing_solve_fails_its_request_only_and_its_scan_is_set_up_again(fake):
+    fake.fail_poll = {50}
+    srv = server()
+    bad = srv.submit(request(50, 1.0))
+    good = srv.submit(request(51, 2.0))
+    with pytest.raises(RuntimeError, match="breakdown on 50"):
+        bad.result(timeout=20)
+    assert np.all(good.result(timeout=20).map == 128.0)
+    again = srv.submit(request(50, 3.0)).result(timeout=20)        # the scan's context was dropped: fresh set-up
+    srv.stop()
+    assert np.all(again.map == 192.0) and not again.scan_cached
+    assert srv.error is None and srv.stats()["failed"] == 1
+    assert sum(1 for e in fake.log if e[:2] == ("setup", 50)) == 2
+    assert ("close", 50) in fake.log

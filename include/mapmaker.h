@@ -50,8 +50,10 @@ typedef enum {
     MM_ERR_STATE = 4,          /* call out of order (e.g. solve before setup)     */
     MM_ERR_NOT_CONVERGED = 5,  /* PCG hit max_iter; the map is still written     */
     MM_ERR_BREAKDOWN = 6,      /* p^T A p <= 0 or a NaN appeared                  */
-    MM_ERR_SINGULAR = 7,       /* coarse operator E is not SPD                    */
-    MM_ERR_TIMEOUT = 8         /* a bounded device wait gave up                   */
+    MM_ERR_SINGULAR = 7,       /* coarse operator E is not SPD, or an eigen-solve */
+                               /* of H_m / T_m did not converge                   */
+    MM_ERR_TIMEOUT = 8         /* reserved for a bounded device wait that gives   */
+                               /* up; no kernel of this library waits on another  */
 } mm_status;
 
 typedef enum {

@@ -93,3 +93,36 @@ def test_estimate_bytes_is_host_arithmetic_and_grows_with_the_problem(lib):
         assert est(**{key: val}) > b0, key
     # float32 timelines, plus double-float weights for the refinement residuals
     assert est(M.MM_FP32_MIXED) == b0 - (1 << 20) * 4 + (1 << 20) * 16
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No libmapmaker.so: loading raises instead of falling back to anything else."""
+    from paper_1801_08937_gb300 import mapmaker as M
+    monkeypatch.setattr(M, "_lib", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        M.load_library(str(tmp_path / "libmapmaker.so"))
+
+
+def test_binding_marshals_arrays_without_copying_what_it_can_pass():
+    import numpy as np
+    from paper_1801_08937_gb300 import mapmaker as M
+    a = np.arange(6, dtype=np.float64)
+    p, mem, keep = M._arg(a, np.float64)
+    assert p.value == a.ctypes.data and mem == M.MM_HOST and keep is a
+    p, mem, keep = M._arg(a.astype(np.float32), np.float64)          # converted copy for an input
+    assert keep.dtype == np.float64 and np.array_equal(keep, a)
+    with pytest.raises(TypeError):
+        M._arg(a.astype(np.float32), np.float64, writable=True)      # an output is never silently copied
+    with pytest.raises(TypeError):
+        M._arg(a[::2], np.float64, writable=True)
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(4, dtype=torch.float64)
+    p, mem, keep = M._arg(t, np.float64)
+    assert p.value == t.data_ptr() and mem == M.MM_HOST
+    with pytest.raises(TypeError):
+        M._arg(t.float(), np.float64)
+    with pytest.raises(ValueError):
+        M._arg(torch.zeros((4, 4), dtype=torch.float64).t(), np.float64)
+    assert M._mem(M.MM_HOST, None) == M.MM_HOST
+    with pytest.raises(ValueError):
+        M._mem(M.MM_HOST, M.MM_DEVICE)

@@ -98,9 +98,8 @@ const char* mm_last_error(const mm_ctx* ctx);
  *                   count samples per detector.  Use 1 for a single timeline.
  *  n_pix            pixels; unknowns are (I, Q, U) per pixel.
  *  pix [n_samples]  pixel of each sample, -1 marks a flagged sample (zero row
- *                   of P); values must lie in [-1, n_pix).  Host arrays are
- *                   checked (MM_ERR_ARG); with mem = MM_DEVICE the caller
- *                   guarantees the range (the kernels index the map by it).
+ *                   of P); values must lie in [-1, n_pix), checked
+ *                   (MM_ERR_ARG) for host and device arrays alike.
  *  psi [n_samples]  HWP angle in radians; the row of P is (1, cos 2psi, sin 2psi).
  *  n_blocks, block_off [n_blocks+1]  stationary blocks [off_b, off_{b+1}),
  *                   contiguous, increasing, block_off[0] = 0,

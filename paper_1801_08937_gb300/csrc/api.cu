@@ -1444,9 +1444,29 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     if (n_pix > (1 << 26)) return fail(ctx, MM_ERR_ARG, "n_pix too large");
     for (size_t i = 0; i < (size_t)n_bands * (half_bw + 1); ++i)
         if (!std::isfinite(band[i])) return fail(ctx, MM_ERR_ARG, "band holds a non-finite value");
-    if (mem == MM_HOST) {
-        for (int64_t t = 0; t < n_samples; ++t)
-            if (pix[t] < -1 || pix[t] >= n_pix) return fail(ctx, MM_ERR_ARG, "pix out of range [-1, n_pix)");
+    {
+        // the kernels index the map by pix: its range is checked for host and device arrays (a device
+        // array through a bounded host buffer, once per pointing set-up)
+        auto in_range = [n_pix](const int32_t* p, int64_t c) {
+            int32_t lo = 0, hi = -1;
+            for (int64_t i = 0; i < c; ++i) {
+                lo = std::min(lo, p[i]);
+                hi = std::max(hi, p[i]);
+            }
+            return lo >= -1 && hi < n_pix;
+        };
+        if (mem == MM_HOST) {
+            if (!in_range(pix, n_samples)) return fail(ctx, MM_ERR_ARG, "pix out of range [-1, n_pix)");
+        } else {
+            const int64_t chunk = (int64_t)1 << 22;
+            std::vector<int32_t> hb((size_t)std::min<int64_t>(chunk, n_samples));
+            for (int64_t t0 = 0; t0 < n_samples; t0 += chunk) {
+                const int64_t c = std::min<int64_t>(chunk, n_samples - t0);
+                CK(cudaMemcpyAsync(hb.data(), pix + t0, (size_t)c * 4, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                if (!in_range(hb.data(), c)) return fail(ctx, MM_ERR_ARG, "pix out of range [-1, n_pix)");
+            }
+        }
     }
     destroy_graph(ctx);
     ctx->have_pointing = ctx->have_bd = false;

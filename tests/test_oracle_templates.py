@@ -203,3 +203,34 @@ def test_hand_worked_template_filters():
         tp = O.TemplateProblem(g["pix"], g["psi"], g["block_off"], g["w_block"], g["n_pix"], g["subscan_off"],
                                case["poly_order"], az, case["n_az_bins"], g["stokes"])
         np.testing.assert_allclose(O.apply_A_T(tp, np.array(g["x"])), np.array(case["Ax"]), atol=1e-14)
+
+
+def _subset(seed):
+    scan, tp = tproblem(order=1, ground=True, n_det=4, n_t=1024, ny=4, nx=8, seed=seed)
+    tp, good, mbd = _kept(tp)
+    sky = synth.make_sky(scan.n_pix, seed)
+    sky[:, 0] = 0.0
+    d = synth.make_tod(scan, sky, synth.make_noise(scan, seed))
+    A = lambda v: O.apply_A_T(tp, v.reshape(-1, 3)).reshape(-1)  # noqa: E731
+    M = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+    return A, M, O.rhs_T(tp, d).reshape(-1)
+
+
+def test_simplified_reuse_of_a_deflation_basis_across_data_subsets():
+    """Sect. 7 (divide and conquer): Ritz vectors computed on one data subset (another raster of the same
+    patch) deflate the filtered system of a different subset; M_2l with that basis and the subset's own
+    A Z and E needs fewer PCG iterations than M_BD (the "simplified" approach), and a basis from the
+    subset itself (the "active" approach) fewer still."""
+    A0, M0, b0 = _subset(11)
+    W, H, m = O.arnoldi(lambda v: M0(A0(v)), M0(b0), 80, 1e-12)
+    Z0, _ = O.ritz_basis(W, H, m, 16)
+    for seed in (12, 13):
+        A, M, b = _subset(seed)
+        it_bd = O.pcg(A, M, b, tol=1e-8, max_iter=3000)[1]["iters"]
+        AZ, _, L = O.coarse_space(A, Z0)
+        it_simplified = O.pcg(A, lambda v: O.m2l_apply(v, M, Z0, AZ, L), b, tol=1e-8, max_iter=3000)[1]["iters"]
+        W1, H1, m1 = O.arnoldi(lambda v: M(A(v)), M(b), 80, 1e-12)
+        Z1, _ = O.ritz_basis(W1, H1, m1, 16)
+        AZ1, _, L1 = O.coarse_space(A, Z1)
+        it_active = O.pcg(A, lambda v: O.m2l_apply(v, M, Z1, AZ1, L1), b, tol=1e-8, max_iter=3000)[1]["iters"]
+        assert it_active <= it_simplified < it_bd

@@ -516,7 +516,8 @@ def run_templates(args, world, rank, local):
     def setup():
         ctx.setup_scan(scan)
         ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
-        ctx.set_option("fp64_products", args.fp64_products)
+        if prec == M.MM_FP64:
+            ctx.set_option("fp64_products", args.fp64_products)
         dropped = ctx.build_bd(1e-3)
         if args.coarse == "arnoldi":
             return dropped, ctx.build_coarse(ctx.rhs(tod)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
@@ -531,7 +532,8 @@ def run_templates(args, world, rank, local):
     else:   # A x alone
         ctx.setup_scan(scan)
         ctx.set_templates(args.poly_order, sub_off, az_d, n_bins, args.stokes)
-        ctx.set_option("fp64_products", args.fp64_products)
+        if prec == M.MM_FP64:
+            ctx.set_option("fp64_products", args.fp64_products)
         t_setup, dropped, k = 0.0, ctx.build_bd(1e-3), 0
     for name, pc in ((("two_level", M.MM_PRECOND_2L), ("m_bd", M.MM_PRECOND_BD)) if args.steps > 0 else ()):
         ctx.solve(tod, pc, tol=args.tol, max_iter=args.max_iter, out=out)

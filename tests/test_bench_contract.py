@@ -27,3 +27,17 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_under_two_ranks_prints_on_rank_zero_only():
+    outs = {}
+    for rank in (0, 1):
+        env = dict(os.environ, WORLD_SIZE="2", RANK=str(rank), LOCAL_RANK=str(rank))
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                              "--steps", "1", "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, env=env,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        outs[rank] = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert outs[1] == [] and len(outs[0]) == 1
+    d = json.loads(outs[0][0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2

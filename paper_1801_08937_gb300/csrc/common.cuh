@@ -225,9 +225,10 @@ struct CoarseView {
 // double-shift QR; near-real values come back real.  False on failure.
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
 // Right eigenvector (unit norm, largest component real positive) of the
-// Hessenberg H for the eigenvalue wr + i wi, by inverse iteration.
+// Hessenberg H for the eigenvalue wr + i wi, by inverse iteration; hnorm =
+// max |H_ij| when the caller has it (negative: computed here).
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
-                      std::vector<double>& vi);
+                      std::vector<double>& vi, double hnorm = -1.0);
 // Eigenvalues (ascending order not guaranteed) of the symmetric tridiagonal
 // matrix with diagonal d[n] and off-diagonal e[n-1]; false on failure.
 bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double>& e, int n,

@@ -242,8 +242,8 @@ bool host_hess_eigvals(const std::vector<double>& H, int n, std::vector<double>&
 }
 
 bool host_hess_eigvec(const std::vector<double>& H, int n, double wr, double wi, std::vector<double>& vr,
-                      std::vector<double>& vi) {
-    const double hnorm = max_abs(H, n);
+                      std::vector<double>& vi, double hnorm) {
+    if (hnorm < 0.0) hnorm = max_abs(H, n);
     const double pert = 1e-13 * (hnorm > 0 ? hnorm : 1.0);
     vr.assign(n, 0.0);
     vi.assign(n, 0.0);
@@ -424,8 +424,9 @@ int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double 
                    std::vector<double>& vals) {
     std::vector<double> wr, wi;
     if (!host_hess_eigvals(H, m, wr, wi)) return 1;
+    const double hnorm = max_abs(H, m);
     auto vec = [&](int idx, std::vector<double>& er, std::vector<double>& ei) {
-        return host_hess_eigvec(H, m, wr[idx], wi[idx], er, ei);
+        return host_hess_eigvec(H, m, wr[idx], wi[idx], er, ei, hnorm);
     };
     return select_ritz(m, k, kmax, eps_lambda, wr, wi, vec, C, vals);
 }

@@ -29,7 +29,7 @@ bool host_template_layout(const std::vector<int64_t>& block_off, const std::vect
                           std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err);
 bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
 bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
-                      std::vector<double>& vi);
+                      std::vector<double>& vi, double hnorm = -1.0);
 bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double>& e, int n,
                           std::vector<double>& w);
 bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,

@@ -16,6 +16,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import os
+
 import numpy as np
 
 FS_HZ = 100.0          # sampling rate of every configured workload
@@ -99,6 +101,20 @@ def toeplitz_band(half_bw: int, f_knee: float, alpha: float = 1.0,
     return band
 
 
+def _each(fn, items, n_samples):
+    """fn(i) for every item; on several host threads for large inputs (numpy releases the GIL in the
+    element-wise and FFT work, and every item writes its own slice, so the values do not depend on
+    the order)."""
+    items = list(items)
+    if n_samples < (1 << 22) or len(items) < 2:
+        for i in items:
+            fn(i)
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1, len(items))) as ex:
+        list(ex.map(fn, items))
+
+
 def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
               f_knee=1.0, alpha: float = 1.0, sigma: float = 1.0, seed: int = 0,
               speed: float = SCAN_SPEED_PX, flag_frac: float = 0.0,
@@ -126,7 +142,8 @@ def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
     y0 = rng.uniform(0.0, ny)
     st = speed * t
     ty = t * (ny / n_t)
-    for d in range(n_det):
+
+    def raster(d):
         pos = np.mod(x0[d] + st, 2.0 * nx)
         np.subtract(2.0 * nx, pos, out=pos, where=pos >= nx)
         ix = np.minimum(pos.astype(np.int32), nx - 1)
@@ -135,6 +152,8 @@ def make_scan(nx: int, ny: int, n_det: int, n_t: int, n_int: int, half_bw: int,
         iy = np.minimum(y.astype(np.int32), ny - 1)
         np.multiply(iy, nx, out=iy)
         np.add(iy, ix, out=pix[d * n_t:(d + 1) * n_t])
+
+    _each(raster, range(n_det), N)
     psi = rng.random(N, dtype=np.float32)
     psi *= np.float32(np.pi)
     if not hwp:
@@ -215,12 +234,17 @@ def make_noise(scan: Scan, seed: int = 0) -> np.ndarray:
     blen = scan.n_t // scan.n_int
     f = np.fft.rfftfreq(blen, 1.0 / fs)
     fpos = np.where(f > 0, f, f[1] if f.shape[0] > 1 else 1.0)
-    for d in range(scan.n_det):
+    def shape_block(d):
         fk = float(scan.f_knee[d])
         shape = np.sqrt(1.0 + (fk / fpos) ** alpha) if fk > 0 else np.ones_like(f)
-        w = rng.standard_normal((scan.n_int, blen))
-        seg = np.fft.irfft(np.fft.rfft(w, axis=1) * shape, n=blen, axis=1) * sigma
-        n[d * scan.n_t:(d + 1) * scan.n_t] = seg.reshape(-1)
+        w = n[d * scan.n_t:(d + 1) * scan.n_t].reshape(scan.n_int, blen)
+        w[...] = np.fft.irfft(np.fft.rfft(w, axis=1) * shape, n=blen, axis=1) * sigma
+
+    # the white samples are drawn in detector order first, so the stream is the same however the
+    # Fourier shaping below is spread over host cores
+    for d in range(scan.n_det):
+        n[d * scan.n_t:(d + 1) * scan.n_t] = rng.standard_normal((scan.n_int, blen)).reshape(-1)
+    _each(shape_block, range(scan.n_det), scan.n_samples)
     return n
 
 
@@ -234,7 +258,8 @@ def make_tod(scan: Scan, sky: np.ndarray | None, noise: np.ndarray | None) -> np
     d = np.zeros(N, dtype=np.float64)
     if sky is not None:
         chunk = 1 << 20
-        for a in range(0, N, chunk):
+
+        def fill(a):
             b = min(N, a + chunk)
             pix = scan.pix[a:b]
             ok = pix >= 0
@@ -242,6 +267,10 @@ def make_tod(scan: Scan, sky: np.ndarray | None, noise: np.ndarray | None) -> np
             ang = 2.0 * scan.psi[a:b][ok].astype(np.float64)
             seg = d[a:b]
             seg[ok] = sky[p, 0] + sky[p, 1] * np.cos(ang) + sky[p, 2] * np.sin(ang)
+
+        # chunks are independent (numpy releases the GIL in the element-wise work): the same values
+        # as a serial loop, on several host cores
+        _each(fill, range(0, N, chunk), N)
     if noise is not None:
         d += noise
     return d

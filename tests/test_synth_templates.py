@@ -46,3 +46,20 @@ def test_generator_is_seeded():
     a1 = synth.make_templates(s1)
     a2 = synth.make_templates(s2)
     assert np.array_equal(a1[0], a2[0]) and np.array_equal(a1[1], a2[1])
+
+
+def test_threaded_generation_gives_the_serial_values(monkeypatch):
+    """Large inputs are generated on several host threads; the values equal a one-thread run."""
+    import synth.scan as SC
+    cfg = dict(nx=32, ny=32, n_det=4, n_t=1 << 20, n_int=4, half_bw=16, f_knee=1.0, seed=9, flag_frac=0.01)
+
+    def run():
+        scan = synth.make_scan(**cfg)
+        n = synth.make_noise(scan, 9)
+        return scan.pix, n, synth.make_tod(scan, synth.make_sky(scan.n_pix, 9), n)
+
+    threaded = run()
+    monkeypatch.setattr(SC.os, "cpu_count", lambda: 1)
+    serial = run()
+    for a, b in zip(threaded, serial):
+        assert np.array_equal(a, b)

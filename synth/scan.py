@@ -197,15 +197,18 @@ def make_templates(scan: Scan, bin_px: float = AZ_BIN_PX):
     t = np.arange(n_t, dtype=np.float64)
     n_bins = int(np.ceil(nx / bin_px))
     az_bin = np.empty(scan.n_samples, dtype=np.int32)
-    cuts = [np.asarray(scan.block_off, dtype=np.int64)]
-    for d in range(scan.n_det):
+    cuts = [np.asarray(scan.block_off, dtype=np.int64)] + [None] * scan.n_det
+
+    def sweeps(d):
         raw = x0[d] + speed * t
         sweep = np.floor(raw / nx).astype(np.int64)
         pos = np.mod(raw, 2.0 * nx)
         np.subtract(2.0 * nx, pos, out=pos, where=pos >= nx)
         az_bin[d * n_t:(d + 1) * n_t] = np.minimum((pos / bin_px).astype(np.int32), n_bins - 1)
         turns = np.nonzero(np.diff(sweep))[0] + 1
-        cuts.append(turns.astype(np.int64) + d * n_t)
+        cuts[d + 1] = turns.astype(np.int64) + d * n_t
+
+    _each(sweeps, range(scan.n_det), scan.n_samples)
     sub_off = np.unique(np.concatenate(cuts))
     return sub_off, az_bin, n_bins
 

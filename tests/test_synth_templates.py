@@ -56,7 +56,8 @@ def test_threaded_generation_gives_the_serial_values(monkeypatch):
     def run():
         scan = synth.make_scan(**cfg)
         n = synth.make_noise(scan, 9)
-        return scan.pix, n, synth.make_tod(scan, synth.make_sky(scan.n_pix, 9), n)
+        so, az, _ = synth.make_templates(scan)
+        return scan.pix, n, synth.make_tod(scan, synth.make_sky(scan.n_pix, 9), n), so, az
 
     threaded = run()
     monkeypatch.setattr(SC.os, "cpu_count", lambda: 1)

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 #include <map>
@@ -729,6 +730,14 @@ struct TuneVal {
 // read from it at first use and appended to it as JSON lines.
 const char* tune_file() { return std::getenv("MM_TUNE_CACHE"); }
 
+// The plan cache is shared by every context of the process (contexts may be
+// set up on several host threads): it is read and extended under this lock.
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+// Callers hold tune_mutex().
 std::vector<std::pair<TuneKey, TuneVal>>& tune_cache() {
     static std::vector<std::pair<TuneKey, TuneVal>> c;
     static bool loaded = false;
@@ -760,7 +769,18 @@ std::vector<std::pair<TuneKey, TuneVal>>& tune_cache() {
     return c;
 }
 
+bool tune_lookup(const TuneKey& k, bool allow_half, TuneVal* v) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    for (auto& kv : tune_cache())
+        if (kv.first == k && (allow_half || kv.second.whole != 2)) {
+            *v = kv.second;
+            return true;
+        }
+    return false;
+}
+
 void tune_record(const TuneKey& k, const TuneVal& v) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
     tune_cache().push_back({k, v});
     if (const char* path = tune_file()) {
         if (FILE* f = std::fopen(path, "a")) {
@@ -832,9 +852,9 @@ mm_status get_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_t>& l
         // tuned once per precision and geometry on a single right-hand side: the
         // per-CTA work of a plan does not depend on how many right-hand sides share it
         TuneKey key{f64, ctx->lam, ctx->n_blocks, 1, ctx->n_samples, max_block_len(ctx), 0, ctx->n_pix};
-        for (auto& kv : tune_cache())
-            if (kv.first == key && (ctx->opt_half || kv.second.whole != 2)) return make_plan(ctx, f64, nrhs, lens, kv.second.variant, kv.second.L,
-                                                  kv.second.whole, kv.second.V, out, starts);
+        TuneVal hit{};
+        if (tune_lookup(key, ctx->opt_half != 0, &hit))
+            return make_plan(ctx, f64, nrhs, lens, hit.variant, hit.L, hit.whole, hit.V, out, starts);
         TuneVal best{};
         TRY(autotune_plan(ctx, f64, 1, {}, &best));
         tune_record(key, best);

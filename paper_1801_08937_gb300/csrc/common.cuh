@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,6 +26,20 @@ constexpr int MM_K_MAX = 512;
 // Kernels launched by this library since load (every launcher adds its count).
 long long launches_total();
 void count_launches(int n);
+
+// Raises a kernel's dynamic shared-memory configuration to at least sm bytes,
+// never lowering it: set(sm) runs once per larger size, under a lock, so
+// contexts set up on several host threads cannot leave a kernel configured
+// below a size another thread already launches with.
+std::mutex& smem_config_mutex();
+template <typename F>
+inline void raise_smem_once(std::atomic<size_t>& configured, size_t sm, F&& set) {
+    if (sm <= configured.load(std::memory_order_acquire)) return;
+    std::lock_guard<std::mutex> lock(smem_config_mutex());
+    if (sm <= configured.load(std::memory_order_relaxed)) return;
+    set(sm);
+    configured.store(sm, std::memory_order_release);
+}
 
 template <typename T> struct __align__(sizeof(T) * 4) V4 { T x, y, z, w; };
 template <typename T> struct __align__(sizeof(T) * 2) C2 { T x, y; };

@@ -6,6 +6,10 @@ namespace mm {
 static long long g_launches = 0;
 long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 void count_launches(int n) { __atomic_fetch_add(&g_launches, (long long)n, __ATOMIC_RELAXED); }
+std::mutex& smem_config_mutex() {
+    static std::mutex m;
+    return m;
+}
 
 // ---------------- setup kernels ----------------
 __global__ void k_fft_spectrum(const double* h, double* H, C2<double>* work, const C2<double>* tw,

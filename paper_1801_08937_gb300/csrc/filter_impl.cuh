@@ -1450,11 +1450,8 @@ inline void configure_smem(K kern, size_t sm, int nt) {
 
 template <typename T, bool FROM_TOD, int NT, int LCT>
 inline void launch_fft_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
-    static size_t configured = 0;
-    if (sm > configured) {
-        configure_smem(k_filter_fft<T, FROM_TOD, NT, LCT>, sm, NT);
-        configured = sm;
-    }
+    static std::atomic<size_t> configured{0};
+    raise_smem_once(configured, sm, [](size_t v) { configure_smem(k_filter_fft<T, FROM_TOD, NT, LCT>, v, NT); });
     k_filter_fft<T, FROM_TOD, NT, LCT><<<a.n_work, NT, sm, s>>>(a);
     count_launches(1);
 }
@@ -1503,11 +1500,8 @@ inline void launch_fft_t(const FilterArgs& a, cudaStream_t s) {
 }
 template <typename T, bool FROM_TOD, int NT, int MCT>
 inline void launch_half_nt(const FilterArgs& a, size_t sm, cudaStream_t s) {
-    static size_t configured = 0;
-    if (sm > configured) {
-        configure_smem(k_filter_half<T, FROM_TOD, NT, MCT>, sm, NT);
-        configured = sm;
-    }
+    static std::atomic<size_t> configured{0};
+    raise_smem_once(configured, sm, [](size_t v) { configure_smem(k_filter_half<T, FROM_TOD, NT, MCT>, v, NT); });
     k_filter_half<T, FROM_TOD, NT, MCT><<<a.n_work, NT, sm, s>>>(a);
     count_launches(1);
 }
@@ -1571,11 +1565,10 @@ inline void launch_direct_t(const FilterArgs& a, cudaStream_t s) {
         }
     }
     const size_t sm = direct_smem_bytes(a.V, a.lam, sizeof(T) == 8);
-    static size_t configured = 0;
-    if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_direct<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        configured = sm;
-    }
+    static std::atomic<size_t> configured{0};
+    raise_smem_once(configured, sm, [](size_t v) {
+        cudaFuncSetAttribute(k_filter_direct<T, FROM_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
+    });
     k_filter_direct<T, FROM_TOD><<<a.n_work, DIRECT_NT, sm, s>>>(a);
     count_launches(1);
 }

@@ -306,11 +306,10 @@ size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64) {
 template <typename T, bool FROM_TOD, int K>
 static void launch_tmpl_k(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
     const size_t sm = tmpl_smem_bytes(t.max_block, t.n_bins, sizeof(T) == 8);
-    static size_t configured = 0;
-    if (sm > configured) {
-        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        configured = sm;
-    }
+    static std::atomic<size_t> configured{0};
+    raise_smem_once(configured, sm, [](size_t v) {
+        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
+    });
     k_filter_tmpl<T, FROM_TOD, K><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
     count_launches(1);
 }

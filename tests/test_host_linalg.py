@@ -18,30 +18,19 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1801_08937_gb300", "csrc")
 
 SHIM = r"""
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
+#include "common.cuh"
 namespace mm {
-void host_lanczos_tridiag(const std::vector<double>& alpha, const std::vector<double>& beta, int m,
-                          std::vector<double>& d, std::vector<double>& e);
-bool host_template_layout(const std::vector<int64_t>& block_off, const std::vector<int64_t>& so, int poly_order,
-                          std::vector<int32_t>& blk_sub, std::vector<double>& ginv, std::string& err);
-bool host_hess_eigvals(const std::vector<double>& H, int m, std::vector<double>& wr, std::vector<double>& wi);
-bool host_hess_eigvec(const std::vector<double>& H, int m, double wr, double wi, std::vector<double>& vr,
-                      std::vector<double>& vi, double hnorm = -1.0);
-bool host_tridiag_eigvals(const std::vector<double>& d, const std::vector<double>& e, int n,
-                          std::vector<double>& w);
-bool host_tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, int n, double lam,
-                         std::vector<double>& v);
-int host_ritz_hess(const std::vector<double>& H, int m, int k, int kmax, double eps_lambda, std::vector<double>& C,
-                   std::vector<double>& vals);
-int host_ritz_tridiag(const std::vector<double>& d, const std::vector<double>& e, int m, int k, int kmax,
-                      double eps_lambda, std::vector<double>& C, std::vector<double>& vals);
-bool host_cholesky(std::vector<double>& A, int n);
-void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
-void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
+std::mutex& smem_config_mutex() {
+    static std::mutex m;
+    return m;
 }
+}  // namespace mm
 extern "C" int t_tri_eigvals(const double* d, const double* e, int n, double* w) {
     std::vector<double> dd(d, d + n), ee(e, e + (n > 1 ? n - 1 : 0)), ww;
     if (!mm::host_tridiag_eigvals(dd, ee, n, ww)) return 0;
@@ -92,6 +81,30 @@ extern "C" void t_lanczos(const double* al, const double* be, int m, double* d, 
     for (int i = 0; i < m; ++i) d[i] = dd[i];
     for (int i = 0; i + 1 < m; ++i) e[i] = ee[i];
 }
+// raise_smem_once from 8 threads with sizes in 1..4000 in a scattered order: the configuration
+// calls must come in increasing order (never lowering) and end at the largest size asked for
+extern "C" int t_raise_smem(long long* last, int* calls, long long* largest) {
+    std::atomic<size_t> configured{0};
+    std::vector<size_t> seen;
+    std::vector<std::thread> th;
+    for (int t = 0; t < 8; ++t)
+        th.emplace_back([&, t] {
+            for (int i = 0; i < 500; ++i) {
+                const size_t sm = 1 + (size_t)((i * 8 + t) * 2654435761u % 4000u);
+                mm::raise_smem_once(configured, sm, [&](size_t v) { seen.push_back(v); });
+            }
+        });
+    for (auto& x : th) x.join();
+    size_t mx = 0;
+    for (int t = 0; t < 8; ++t)
+        for (int i = 0; i < 500; ++i) mx = std::max(mx, 1 + (size_t)((i * 8 + t) * 2654435761u % 4000u));
+    *largest = (long long)mx;
+    for (size_t i = 1; i < seen.size(); ++i)
+        if (seen[i] <= seen[i - 1]) return 0;
+    *last = (long long)configured.load();
+    *calls = (int)seen.size();
+    return seen.empty() ? 0 : (seen.back() == configured.load() ? 1 : 0);
+}
 extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     std::vector<double> a(A, A + (size_t)n * n), v;
     if (!mm::host_cholesky(a, n)) return 0;
@@ -137,7 +150,7 @@ def eig(tmp_path_factory):
     shim = d / "shim.cpp"
     shim.write_text(SHIM)
     so = d / "libhostlinalg.so"
-    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", inc, "-I", CSRC, "-x", "c++",
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I", inc, "-I", CSRC, "-x", "c++",
                     os.path.join(CSRC, "host_linalg.cpp"), "-x", "none", str(shim), "-o", str(so)], check=True)
     lib = C.CDLL(str(so))
     P = C.POINTER(C.c_double)
@@ -149,6 +162,7 @@ def eig(tmp_path_factory):
     I64 = C.POINTER(C.c_int64)
     lib.t_layout.argtypes = [I64, C.c_int, I64, C.c_int, C.c_int, C.POINTER(C.c_int32), P, C.c_char_p]
     lib.t_lanczos.argtypes = [P, P, C.c_int, P, P]
+    lib.t_raise_smem.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
 
@@ -227,7 +241,13 @@ def eig(tmp_path_factory):
         lib.t_lanczos(p(al), p(be), m, p(d), p(e))
         return d, e[:m - 1]
 
+    def raise_smem():
+        last, calls, largest = C.c_longlong(0), C.c_int(0), C.c_longlong(0)
+        ok = lib.t_raise_smem(C.byref(last), C.byref(calls), C.byref(largest))
+        return ok, last.value, calls.value, largest.value
+
     vals.chol_inv = chol_inv
+    vals.raise_smem = raise_smem
     vals.lanczos = lanczos
     vals.layout = layout
     vals.ritz = ritz
@@ -607,3 +627,11 @@ def test_ritz_selection_on_template_filtered_operators(eig, stokes):
     Q, ref = O.ritz_basis(W, H, m, 40)
     ref = ref[np.abs(ref) > 1e-10 * wmax][:10]
     np.testing.assert_allclose(th, ref, rtol=1e-8, atol=1e-12 * wmax)
+
+
+def test_shared_memory_configuration_only_rises_under_concurrent_launchers(eig):
+    """Contexts set up on several host threads launch the same kernels: the dynamic shared-memory
+    configuration is raised in increasing order only, ending at the largest size any thread asked for."""
+    vals, _ = eig
+    ok, last, calls, largest = vals.raise_smem()
+    assert ok == 1 and last == largest and 1 <= calls <= largest

@@ -80,8 +80,9 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream`
  * (a cudaStream_t; NULL means the legacy default stream).  *out receives the
- * context, which owns all device memory it allocates.  Errors: MM_ERR_ARG,
- * MM_ERR_CUDA. */
+ * context, which owns all device memory it allocates.  A process drives one
+ * device (several contexts, on several host threads, may share it; use one
+ * process per GPU for several GPUs).  Errors: MM_ERR_ARG, MM_ERR_CUDA. */
 mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision prec);
 
 /* Release the context and every device buffer it owns.  NULL is accepted. */

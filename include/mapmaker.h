@@ -82,7 +82,9 @@ typedef struct {
  * (a cudaStream_t; NULL means the legacy default stream).  *out receives the
  * context, which owns all device memory it allocates.  A process drives one
  * device (several contexts, on several host threads, may share it; use one
- * process per GPU for several GPUs).  Errors: MM_ERR_ARG, MM_ERR_CUDA. */
+ * process per GPU for several GPUs): a context on another device than the
+ * process's first one is refused with MM_ERR_ARG.  Errors: MM_ERR_ARG,
+ * MM_ERR_CUDA. */
 mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision prec);
 
 /* Release the context and every device buffer it owns.  NULL is accepted. */

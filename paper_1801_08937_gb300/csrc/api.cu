@@ -1410,6 +1410,10 @@ mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision pr
     if (prec != MM_FP64 && prec != MM_FP32_MIXED) return MM_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MM_ERR_CUDA;
+    // the kernels' launch configuration is kept once per process: one device per process
+    static std::atomic<int> process_device{-1};
+    int expect = -1;
+    if (!process_device.compare_exchange_strong(expect, device) && expect != device) return MM_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return MM_ERR_CUDA;
     mm_ctx* ctx = new mm_ctx();
     ctx->device = device;

@@ -2317,7 +2317,7 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_apply_prec = v;
     } else if (n == "fp64_products") {
         if (v != 1 && v != 2) return fail(ctx, MM_ERR_ARG, "fp64_products must be 1 (float64) or 2 (double-float)");
-        if (ctx->phase != PH_IDLE) return fail(ctx, MM_ERR_STATE, "fp64_products cannot change during a solve");
+        if (ctx->phase == PH_INNER) return fail(ctx, MM_ERR_STATE, "fp64_products cannot change during a solve");
         ctx->p64 = v;
     } else if (n == "harvest") {
         if (v < 0 || v > 4096) return fail(ctx, MM_ERR_ARG, "harvest must lie in [0, 4096]");

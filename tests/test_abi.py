@@ -126,3 +126,19 @@ def test_binding_marshals_arrays_without_copying_what_it_can_pass():
     assert M._mem(M.MM_HOST, None) == M.MM_HOST
     with pytest.raises(ValueError):
         M._mem(M.MM_HOST, M.MM_DEVICE)
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point of the binding passes as many arguments as include/mapmaker.h declares."""
+    from paper_1801_08937_gb300 import mapmaker as M
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = {}
+    for m in re.finditer(r"\b(mm_[A-Za-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        decls[m.group(1)] = n
+    bound = {name: len(args) for name, _res, args in M.SIGNATURES}
+    missing = sorted(set(decls) - set(bound))
+    assert not missing, missing
+    for name, n in decls.items():
+        assert bound[name] == n, (name, bound[name], n)

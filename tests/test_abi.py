@@ -142,3 +142,41 @@ def test_binding_signatures_match_the_header():
     assert not missing, missing
     for name, n in decls.items():
         assert bound[name] == n, (name, bound[name], n)
+
+
+def test_binding_argument_types_match_the_header():
+    """Argument kinds agree position by position: pointers, 64-bit and 32-bit integers (enums are
+    ints), doubles, so ctypes never passes a value of the wrong width."""
+    import ctypes as C
+    from paper_1801_08937_gb300 import mapmaker as M
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+
+    def kind_c(param):
+        param = " ".join(param.split())
+        if "*" in param:
+            return "ptr"
+        if param.startswith("int64_t"):
+            return "i64"
+        if param.startswith(("int32_t", "int ", "mm_precision", "mm_precond")):
+            return "i32"
+        if param.startswith("double"):
+            return "f64"
+        raise AssertionError(param)
+
+    def kind_py(t):
+        if t in (C.c_void_p, C.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+            return "ptr"
+        if t is C.c_int64 or t is C.c_longlong:
+            return "i64"
+        if t in (C.c_int32, C.c_int):
+            return "i32"
+        if t is C.c_double:
+            return "f64"
+        raise AssertionError(t)
+
+    sig = {name: args for name, _res, args in M.SIGNATURES}
+    for m in re.finditer(r"\b(mm_[A-Za-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = [q for q in m.group(2).split(",") if q.strip() not in ("", "void")]
+        want = [kind_c(q.strip()) for q in params]
+        got = [kind_py(t) for t in sig[m.group(1)]]
+        assert want == got, (m.group(1), want, got)

@@ -139,9 +139,12 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out);
  * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int mem);
 
-/* y = A x = P^T W P x (Sect. 3, Eq. linearsystem), matrix-free, in the
- * context precision: gather, banded-Toeplitz filter and scatter-add fused in
- * one pass per sample segment.  x, y [nrhs][n_pix][3] float64 in `mem`.
+/* y = A x = P^T W P x (Sect. 3, Eq. linearsystem), matrix-free, with the
+ * operator the solver uses (float32 in MM_FP32_MIXED; in MM_FP64 native
+ * float64 or double-float as option "fp64_products" says; option
+ * "apply_precision" overrides): gather, banded-Toeplitz filter (or the
+ * template filters) and scatter-add fused in one pass per sample segment.
+ * x, y [nrhs][n_pix][3] float64 in `mem`.
  * Errors: MM_ERR_STATE, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int mem);
 

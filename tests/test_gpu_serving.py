@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import synth
-from helpers import oracle_problem, rel
+from helpers import assert_close, oracle_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -73,12 +73,12 @@ def test_results_same_alone_and_in_mix(precision):
         b = O.rhs(prob, tod.astype(np.float64)).reshape(-1)
         xo = O.pcg(lambda v: O.apply_A(prob, v).reshape(-1), lambda v: O.bd_apply(mbd, v).reshape(-1), b,
                    tol=1e-13, max_iter=5000)[0]
-        assert rel(r.map, xo) < 1e-6
+        assert_close(r.map, xo, 1e-6)
     # the first request of each scan has exactly the set-up of a standalone solve
     for j in range(3):
         sid, sc, tod = reqs[j]
         xa, ia = _alone(sc, tod, precision, MM.MM_PRECOND_2L, 6, 30)
-        assert rel(res[j].map, xa) < 1e-7
+        assert_close(res[j].map, xa, 1e-7)
 
 
 def test_admission_waits_for_memory_and_evicts_idle_scans():
@@ -117,5 +117,5 @@ def test_harvest_mode_first_request_bd_then_two_level():
         b = O.rhs(prob, t).reshape(-1)
         xo = O.pcg(lambda v: O.apply_A(prob, v).reshape(-1), lambda v: O.bd_apply(mbd, v).reshape(-1), b,
                    tol=1e-13, max_iter=5000)[0]
-        assert rel(r.map, xo) < 1e-6
+        assert_close(r.map, xo, 1e-6)
     assert all(r.info["iters"] < first.info["iters"] for r in later)

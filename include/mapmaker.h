@@ -30,6 +30,8 @@
  *    results they write to host memory (maps, info, counts) are complete;
  *    device outputs are complete once the stream reaches the call's end.
  *  - A context is not thread safe: one host thread at a time per context.
+ *  - Every call makes the context's device current while it runs and gives
+ *    the caller back the device that was current before.
  */
 #ifndef MAPMAKER_H
 #define MAPMAKER_H
@@ -195,6 +197,25 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem);
  * values kept [k] (host, may be NULL) and k.  Errors: MM_ERR_STATE. */
 mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k_out);
 
+/* Checkpoint of the coarse space, for the paper's "simplified" reuse of one
+ * scan's deflation basis across runs (Sect. 7) without recomputing A Z and E:
+ * the basis Z, A Z, E^-1 (Sect. 3.2, Eq. m2l) and the Ritz values are written
+ * to a host buffer with a 64-bit fingerprint of the operator they belong to
+ * (pointing after pixel selection, weights, block structure, template
+ * filters, product precision).
+ * mm_export_coarse: buf NULL sets *bytes to the size needed; otherwise buf
+ *   (host, *bytes long) receives the checkpoint and *bytes its size.
+ *   Errors: MM_ERR_STATE (no coarse space), MM_ERR_ARG (buffer too small),
+ *   MM_ERR_CUDA.
+ * mm_import_coarse: installs a checkpoint (host buffer of `bytes`) into a
+ *   context whose operator has the same fingerprint; needs mm_build_bd.  A
+ *   checkpoint of another scan, filter or product precision, a truncated or
+ *   foreign buffer, is refused with MM_ERR_ARG (use mm_set_coarse to reuse a
+ *   basis on another scan: it forms A Z and E anew).  Errors: MM_ERR_STATE,
+ *   MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_export_coarse(mm_ctx* ctx, void* buf, int64_t* bytes);
+mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes);
+
 /* Solve A x = b for nrhs timelines with PCG (Sect. 3, Eq. pcg), x_0 = 0,
  * stopping when ||r_k|| / ||b|| <= tol (recurrence residual) or after max_iter
  * products with A.  In MM_FP32_MIXED the float32 operator drives PCG and
@@ -327,6 +348,8 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
  * memory belongs to another allocator.
  *  x, y   [nrhs][n_pix][3] float64, DEVICE memory on the context's device,
  *         owned by the caller; y = M_2l x as mm_apply_precond computes it.
+ *         x and y must not overlap (MM_ERR_ARG): the call does not work in
+ *         place.
  *  Needs mm_build_bd and a coarse space (those calls allocate; this one
  *  does not).  Reduction scratch lives in a fixed 1 MiB device array inside
  *  the library, held by every GPU that loads it until the process exits.
@@ -335,8 +358,11 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
  *  array's device address (cudaGetSymbolAddress); make that first call
  *  before any stream capture.  All calls share the array, so calls that
  *  overlap on the GPU (other streams or threads) race; serialise them.
- *  Returns after the result is complete.  Errors: MM_ERR_ARG, MM_ERR_STATE,
- *  MM_ERR_CUDA. */
+ *  The call blocks until the result is complete (it synchronises the
+ *  context's stream) and leaves the caller's current device as it found it.
+ *  The looked-up address lasts for the life of the process; like the
+ *  contexts, it does not survive a cudaDeviceReset.  Errors: MM_ERR_ARG,
+ *  MM_ERR_STATE, MM_ERR_CUDA. */
 mm_status mm_apply_precond_2l_noalloc(mm_ctx* ctx, const double* x, double* y, int32_t nrhs);
 
 /* Device bytes a context needs for a problem of this shape (pointing, maps,

@@ -14,6 +14,8 @@
 #include <map>
 #include <array>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mapmaker.h"
 #include "common.cuh"
 
@@ -156,6 +158,7 @@ struct mm_ctx {
     int tmpl_order = -1, tmpl_bins = 0, tmpl_qu = 0;
     int64_t tmpl_max_block = 0;
     DevBuf d_tsub, d_tblk, d_tginv, d_taz, d_twb;
+    std::vector<int64_t> tmpl_sub;   // host copy of the subscan offsets
     // block-prefix coarse products T[m] = A_(first m blocks of every detector) Z,
     // [(blocks per detector + 1)][k][n_pix][4], for uneven-length batches
     DevBuf d_Tpref;
@@ -168,6 +171,15 @@ struct mm_ctx {
 };
 
 namespace {
+
+// NVTX range around one phase (entry point, PCG iterations, refinement,
+// coarse-space build): visible on a profiler timeline, free when none is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -1099,6 +1111,7 @@ mm_status read_state(mm_ctx* ctx) {
 // formed in one float64-accurate pass from the timeline, P^T W (d - P x), so b
 // itself is needed only to float32 accuracy; otherwise as b - A x.
 mm_status true_residual(mm_ctx* ctx, const V4<double>* x, std::vector<double>& rr) {
+    NvtxRange nvtx_range("true_residual");
     if (is_f32(ctx) && ctx->tod_dev) {
         TRY(ensure_work(ctx, ctx->nrhs, ctx->k));
         const int64_t nv = (int64_t)ctx->n_pix * ctx->nrhs;
@@ -1221,6 +1234,7 @@ mm_status orthonormalise(mm_ctx* ctx, DevBuf& X, int kin, int* kout) {
 
 // Given Z (ctx->d_Z, k columns), form AZ, E = Z^T A Z and E^-1.
 mm_status finish_coarse(mm_ctx* ctx) {
+    NvtxRange nvtx_range("coarse_AZ_E");
     ctx->tpref_valid = false;
     const int k = ctx->k;
     const int64_t n = (int64_t)ctx->n_pix * 4;
@@ -1250,6 +1264,78 @@ mm_status finish_coarse(mm_ctx* ctx) {
     return MM_OK;
 }
 
+
+// ---- scan fingerprint for exported coarse spaces ----
+// A coarse space (Z, A Z, E^-1) is valid only for the operator it was built
+// with: the same pointing after pixel selection, weights, block structure,
+// filters and operator precision.  The fingerprint is a 64-bit sum, modulo
+// 2^64, of splitmix64 hashes of every (position, word) pair, so it is the same
+// whatever order the device threads add their terms in.
+__host__ __device__ inline uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_hash_words(const uint32_t* __restrict__ w, int64_t n, uint64_t salt, unsigned long long* out) {
+    uint64_t acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += splitmix64(((uint64_t)w[i] << 32 | (uint64_t)(i & 0xffffffff)) ^ splitmix64(salt + (uint64_t)(i >> 32)));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, (unsigned long long)acc);
+}
+
+uint64_t host_hash_bytes(const void* p, size_t bytes, uint64_t h) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 0x100000001b3ull;   // FNV-1a
+    return h;
+}
+
+mm_status scan_fingerprint(mm_ctx* ctx, uint64_t* out) {
+    DevBuf acc;
+    CK(acc.ensure(8));
+    CK(cudaMemsetAsync(acc.p, 0, 8, ctx->stream));
+    auto dev_hash = [&](const void* p, int64_t words, uint64_t salt) {
+        if (p && words > 0) {
+            k_hash_words<<<152 * 4, 256, 0, ctx->stream>>>(static_cast<const uint32_t*>(p), words, salt,
+                                                          acc.as<unsigned long long>());
+            count_launches(1);
+        }
+    };
+    dev_hash(ctx->d_pix.p, ctx->n_samples, 1);   // after pixel selection: dropped pixels' samples are -1
+    dev_hash(ctx->d_psi.p, ctx->n_samples, 2);
+    if (ctx->tmpl_on && ctx->tmpl_bins > 0) dev_hash(ctx->d_taz.p, ctx->n_samples, 3);
+    CKL();
+    uint64_t dh = 0;
+    CK(cudaMemcpyAsync(&dh, acc.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    uint64_t h = 0xcbf29ce484222325ull;
+    const int64_t dims[] = {ctx->n_samples, ctx->n_det, ctx->n_pix, ctx->n_blocks, ctx->n_bands, ctx->lam,
+                            op_prec(ctx), ctx->tmpl_on, ctx->tmpl_order, ctx->tmpl_bins, ctx->tmpl_qu};
+    h = host_hash_bytes(dims, sizeof(dims), h);
+    h = host_hash_bytes(ctx->block_off.data(), ctx->block_off.size() * 8, h);
+    h = host_hash_bytes(ctx->block_band.data(), ctx->block_band.size() * 4, h);
+    h = host_hash_bytes(ctx->band.data(), ctx->band.size() * 8, h);
+    if (ctx->tmpl_on) h = host_hash_bytes(ctx->tmpl_sub.data(), ctx->tmpl_sub.size() * 8, h);
+    *out = splitmix64(h ^ dh);
+    return MM_OK;
+}
+
+// Layout of an exported coarse space: this header, then Z [k][n_pix][3],
+// A Z [k][n_pix][3], E^-1 [k][k] and the Ritz values [k], all float64.
+struct CoarseFileHeader {
+    char magic[8];       // "MMCOARS1"
+    int32_t version;     // 1
+    int32_t n_pix;
+    int32_t k;
+    int32_t op_prec;     // precision of the products A Z was formed with
+    uint64_t fingerprint;
+    int64_t payload_bytes;
+};
+constexpr char kCoarseMagic[8] = {'M', 'M', 'C', 'O', 'A', 'R', 'S', '1'};
+int64_t coarse_payload_bytes(int64_t n_pix, int64_t k) { return (2 * k * n_pix * 3 + k * k + k) * 8; }
 }  // namespace
 
 namespace {
@@ -1414,7 +1500,8 @@ mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision pr
     static std::atomic<int> process_device{-1};
     int expect = -1;
     if (!process_device.compare_exchange_strong(expect, device) && expect != device) return MM_ERR_ARG;
-    if (cudaSetDevice(device) != cudaSuccess) return MM_ERR_CUDA;
+    DeviceScope dev_scope(device);
+    if (dev_scope.err != cudaSuccess) return MM_ERR_CUDA;
     mm_ctx* ctx = new mm_ctx();
     ctx->device = device;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -1428,7 +1515,7 @@ mm_status mm_create(mm_ctx** out, int device, void* cuda_stream, mm_precision pr
 
 mm_status mm_destroy(mm_ctx* ctx) {
     if (!ctx) return MM_OK;
-    cudaSetDevice(ctx->device);
+    DeviceScope dev_scope(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     destroy_graph(ctx);
     for (auto& pr : ctx->fev) {
@@ -1449,7 +1536,9 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
                             const float* psi, int32_t n_blocks, const int64_t* block_off, const int32_t* block_band,
                             int32_t n_bands, int32_t half_bw, const double* band, int mem) {
     if (!ctx) return MM_ERR_ARG;
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     if (n_samples <= 0 || n_pix <= 0 || n_blocks <= 0 || n_bands <= 0 || half_bw < 0 || n_det <= 0)
         return fail(ctx, MM_ERR_ARG, "sizes must be positive (half_bw >= 0)");
     if (n_samples % n_det != 0) return fail(ctx, MM_ERR_ARG, "n_samples must be a multiple of n_det");
@@ -1548,7 +1637,9 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
 mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, const int64_t* subscan_off,
                            const int32_t* az_bin, int32_t n_az_bins, int32_t stokes, int mem) {
     if (!ctx) return MM_ERR_ARG;
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_set_templates: set the pointing first");
     if (mem != MM_HOST && mem != MM_DEVICE) return fail(ctx, MM_ERR_ARG, "mem must be MM_HOST or MM_DEVICE");
     ctx->have_bd = false;   // M_BD and any coarse space belong to the previous operator
@@ -1588,6 +1679,7 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     if (tmpl_smem_bytes(maxb, nbins, true) > smem_limit_bytes())
         return fail(ctx, MM_ERR_ARG, "template filters: longest block plus azimuth bins exceed shared memory");
     CK(ctx->d_tsub.ensure(so.size() * 8));
+    ctx->tmpl_sub = so;
     CK(ctx->d_tblk.ensure(blk_sub.size() * 4));
     CK(ctx->d_tginv.ensure(ginv.size() * 8));
     CK(ctx->d_twb.ensure(wb.size() * 8));
@@ -1613,7 +1705,9 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
     if (!(rcond_min >= 0.0) || rcond_min > 1.0) return fail(ctx, MM_ERR_ARG, "rcond_min must lie in [0, 1]");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const int n_pix = ctx->n_pix;
     CK(ctx->d_sums.ensure((size_t)n_pix * 7 * 8));
     CK(ctx->d_good.ensure(n_pix));
@@ -1646,7 +1740,9 @@ mm_status mm_rhs(mm_ctx* ctx, const void* tod, double* b_out, int32_t nrhs, int 
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
     if (!tod || !b_out || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const size_t esz = is_f32(ctx) ? 4 : 8;
     DevBuf d_tod;
     const void* src = tod;
@@ -1683,7 +1779,9 @@ mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int 
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_setup_pointing first");
     if (!x || !y || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     TRY(ensure_work(ctx, nrhs, ctx->k));
     const int64_t nv = (int64_t)nrhs * ctx->n_pix;
     DevBuf in3, in4, out4;
@@ -1727,7 +1825,9 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
     if (which == MM_PRECOND_2L && ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space");
     if (which != MM_PRECOND_BD && which != MM_PRECOND_2L) return fail(ctx, MM_ERR_ARG, "unknown preconditioner");
     if (!x || !y || nrhs <= 0) return fail(ctx, MM_ERR_ARG, "null array or nrhs <= 0");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     TRY(ensure_work(ctx, nrhs, ctx->k));
     const int64_t nv = (int64_t)nrhs * ctx->n_pix;
     DevBuf in3, in4, out4, u;
@@ -1784,7 +1884,9 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     if (m_max <= 0 || m_max > 1024) return fail(ctx, MM_ERR_ARG, "m_max must lie in [1, 1024]");
     if (k > MM_K_MAX) return fail(ctx, MM_ERR_ARG, "k must be at most 512");
     if (!b_or_null && !ctx->have_lastb) return fail(ctx, MM_ERR_STATE, "no right-hand side: pass b or call mm_rhs");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const int n_pix = ctx->n_pix;
     const int64_t n = (int64_t)n_pix * 4;
     ctx->k = 0;
@@ -1881,7 +1983,9 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
     if (ctx->harvest_count < 2) return fail(ctx, MM_ERR_STATE, "no harvested M_BD solve (set option harvest > 1)");
     if (k > MM_K_MAX) return fail(ctx, MM_ERR_ARG, "k must be at most 512");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const int m = ctx->harvest_count;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     std::vector<double> td, te;
@@ -1914,7 +2018,9 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     if (!ctx) return MM_ERR_ARG;
     if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
     if (k <= 0 || k > MM_K_MAX || !Z) return fail(ctx, MM_ERR_ARG, "k must lie in [1, 512] and Z non-null");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const int64_t n = (int64_t)ctx->n_pix * 4;
     ctx->k = 0;
     ctx->tpref_valid = false;
@@ -1940,7 +2046,9 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
 mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k_out) {
     if (!ctx) return MM_ERR_ARG;
     if (ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     if (k_out) *k_out = ctx->k;
     if (ritz_out)
         for (int i = 0; i < ctx->k; ++i) ritz_out[i] = i < (int)ctx->ritz.size() ? ctx->ritz[i] : 0.0;
@@ -1956,6 +2064,93 @@ mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k
     return MM_OK;
 }
 
+mm_status mm_export_coarse(mm_ctx* ctx, void* buf, int64_t* bytes) {
+    if (!ctx || !bytes) return MM_ERR_ARG;
+    if (ctx->k <= 0) return fail(ctx, MM_ERR_STATE, "no coarse space");
+    const int k = ctx->k;
+    const int64_t need = (int64_t)sizeof(CoarseFileHeader) + coarse_payload_bytes(ctx->n_pix, k);
+    if (!buf) {
+        *bytes = need;
+        return MM_OK;
+    }
+    if (*bytes < need) return fail(ctx, MM_ERR_ARG, "buffer smaller than the exported coarse space");
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
+    CoarseFileHeader hd{};
+    std::memcpy(hd.magic, kCoarseMagic, 8);
+    hd.version = 1;
+    hd.n_pix = ctx->n_pix;
+    hd.k = k;
+    hd.op_prec = op_prec(ctx);
+    TRY(scan_fingerprint(ctx, &hd.fingerprint));
+    hd.payload_bytes = coarse_payload_bytes(ctx->n_pix, k);
+    unsigned char* o = static_cast<unsigned char*>(buf);
+    std::memcpy(o, &hd, sizeof(hd));
+    double* z3 = reinterpret_cast<double*>(o + sizeof(hd));
+    const int64_t nv = (int64_t)k * ctx->n_pix;
+    DevBuf t;
+    CK(t.ensure(nv * 24));
+    launch_map_out(ctx->d_Z.as<V4<double>>(), t.as<double>(), nv, ctx->stream);
+    CKL();
+    CK(cudaMemcpyAsync(z3, t.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    launch_map_out(ctx->d_AZ.as<V4<double>>(), t.as<double>(), nv, ctx->stream);
+    CKL();
+    CK(cudaMemcpyAsync(z3 + nv * 3, t.p, nv * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(z3 + nv * 6, ctx->d_Einv.p, (size_t)k * k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double* rz = z3 + nv * 6 + (int64_t)k * k;
+    for (int i = 0; i < k; ++i) rz[i] = i < (int)ctx->ritz.size() ? ctx->ritz[i] : 0.0;
+    *bytes = need;
+    return MM_OK;
+}
+
+mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->have_bd) return fail(ctx, MM_ERR_STATE, "mm_build_bd first");
+    if (!buf || bytes < (int64_t)sizeof(CoarseFileHeader)) return fail(ctx, MM_ERR_ARG, "buffer too small");
+    CoarseFileHeader hd{};
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, kCoarseMagic, 8) != 0 || hd.version != 1)
+        return fail(ctx, MM_ERR_ARG, "not an exported coarse space (magic or version)");
+    if (hd.k <= 0 || hd.k > MM_K_MAX || hd.n_pix != ctx->n_pix ||
+        hd.payload_bytes != coarse_payload_bytes(hd.n_pix, hd.k) ||
+        bytes < (int64_t)sizeof(hd) + hd.payload_bytes)
+        return fail(ctx, MM_ERR_ARG, "exported coarse space does not match this problem's size or is truncated");
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
+    uint64_t fp = 0;
+    TRY(scan_fingerprint(ctx, &fp));
+    if (fp != hd.fingerprint || hd.op_prec != op_prec(ctx))
+        return fail(ctx, MM_ERR_ARG,
+                    "exported coarse space belongs to another scan, filter or operator precision (fingerprint)");
+    const int k = hd.k;
+    const int64_t n4 = (int64_t)ctx->n_pix * 4, nv = (int64_t)k * ctx->n_pix;
+    const double* z3 = reinterpret_cast<const double*>(static_cast<const unsigned char*>(buf) + sizeof(hd));
+    ctx->k = 0;
+    ctx->tpref_valid = false;
+    DevBuf t;
+    CK(t.ensure(nv * 24));
+    CK(ctx->d_Z.ensure((size_t)k * n4 * 8));
+    CK(ctx->d_AZ.ensure((size_t)k * n4 * 8));
+    CK(ctx->d_Einv.ensure((size_t)k * k * 8));
+    CK(cudaMemcpyAsync(t.p, z3, nv * 24, cudaMemcpyHostToDevice, ctx->stream));
+    launch_map_in(t.as<double>(), ctx->d_Z.as<V4<double>>(), nv, ctx->stream);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(t.p, z3 + nv * 3, nv * 24, cudaMemcpyHostToDevice, ctx->stream));
+    launch_map_in(t.as<double>(), ctx->d_AZ.as<V4<double>>(), nv, ctx->stream);
+    CKL();
+    CK(cudaMemcpyAsync(ctx->d_Einv.p, z3 + nv * 6, (size_t)k * k * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double* rz = z3 + nv * 6 + (int64_t)k * k;
+    ctx->ritz.assign(rz, rz + k);
+    ctx->k = k;
+    return MM_OK;
+}
+
 mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64_t* rhs_len, mm_precond precond,
                          double tol, int32_t max_iter, int mem) {
     if (!ctx) return MM_ERR_ARG;
@@ -1967,7 +2162,9 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     if (rhs_len)
         for (int i = 0; i < nrhs; ++i)
             if (rhs_len[i] <= 0 || rhs_len[i] > ctx->n_t) return fail(ctx, MM_ERR_ARG, "rhs_len out of (0, n_t]");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     destroy_graph(ctx);
     ctx->nrhs = nrhs;
     ctx->precond = precond;
@@ -2133,6 +2330,7 @@ static mm_status finish_inner(mm_ctx* ctx, int32_t* done, bool allow_refine) {
 
 static mm_status launch_iters(mm_ctx* ctx, int32_t n_iter) {
     if (n_iter <= 0) return MM_OK;
+    NvtxRange nvtx_range("pcg_iterations");
     const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy &&
                             ctx->stream != cudaStreamPerThread;
     if (ctx->opt_graphs && capturable && n_iter == ctx->opt_check_every) {
@@ -2175,7 +2373,9 @@ mm_status mm_solve_step(mm_ctx* ctx, int32_t n_iter, int32_t* done) {
         return MM_OK;
     }
     if (ctx->phase != PH_INNER) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     TRY(launch_iters(ctx, n_iter));
     TRY(read_state(ctx));
     return evaluate_state(ctx, done);
@@ -2186,7 +2386,9 @@ mm_status mm_solve_launch(mm_ctx* ctx, int32_t n_iter) {
     if (ctx->phase == PH_DONE) return MM_OK;
     if (ctx->phase != PH_INNER) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
     if (n_iter < 0) return fail(ctx, MM_ERR_ARG, "n_iter must be >= 0");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     TRY(launch_iters(ctx, n_iter));
     if (!ctx->h_st_pinned || ctx->h_st_pinned_n < ctx->nrhs) {
         if (ctx->h_st_pinned) cudaFreeHost(ctx->h_st_pinned);
@@ -2211,7 +2413,9 @@ mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done) {
         return MM_OK;
     }
     if (ctx->phase != PH_INNER || !ctx->launched) return fail(ctx, MM_ERR_STATE, "mm_solve_launch first");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     const cudaError_t q = cudaEventQuery(ctx->ev_state);
     if (q == cudaErrorNotReady) return MM_OK;
     CK(q);
@@ -2224,7 +2428,9 @@ mm_status mm_solve_poll(mm_ctx* ctx, int32_t* ready, int32_t* done) {
 mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int mem) {
     if (!ctx) return MM_ERR_ARG;
     if (ctx->phase == PH_IDLE) return fail(ctx, MM_ERR_STATE, "mm_solve_begin first");
-    CK(cudaSetDevice(ctx->device));
+    DeviceScope dev_scope(ctx->device);
+    CK(dev_scope.err);
+    NvtxRange nvtx_range(__func__);
     if (ctx->phase == PH_INNER) {
         // stopped early by the caller: account for what ran, no further refinement
         TRY(read_state(ctx));

@@ -41,6 +41,24 @@ inline void raise_smem_once(std::atomic<size_t>& configured, size_t sm, F&& set)
     configured.store(sm, std::memory_order_release);
 }
 
+// Makes `device` current for one entry point and gives the caller back the
+// device that was current before, so a call on this library's device never
+// leaves a caller working on another device switched over.
+struct DeviceScope {
+    int prev = -1;
+    int dev;
+    cudaError_t err;
+    explicit DeviceScope(int device) : dev(device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        err = (prev == device) ? cudaSuccess : cudaSetDevice(device);
+    }
+    ~DeviceScope() {
+        if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 template <typename T> struct __align__(sizeof(T) * 4) V4 { T x, y, z, w; };
 template <typename T> struct __align__(sizeof(T) * 2) C2 { T x, y; };
 

@@ -116,7 +116,8 @@ __global__ void k_m2l_apply3(const double* __restrict__ x, double* __restrict__ 
 }
 
 // Device address of g_noalloc_scratch, looked up once per device with that
-// device current.
+// device current and kept for the life of the process (like the library's
+// contexts, it does not survive a cudaDeviceReset of that device).
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
@@ -156,7 +157,15 @@ extern "C" mm_status mm_apply_precond_2l_noalloc(mm_ctx* ctx, const double* x, d
                            "2 * nrhs * k + 64 <= 131072 doubles)");
         return MM_ERR_ARG;
     }
-    cudaError_t e = cudaSetDevice(v.device);
+    // the kernels take x and y as distinct arrays (__restrict__): overlapping ranges are refused
+    const uintptr_t xb = reinterpret_cast<uintptr_t>(x), yb = reinterpret_cast<uintptr_t>(y);
+    const uintptr_t bytes = (uintptr_t)nrhs * (uintptr_t)v.n_pix * 3u * sizeof(double);
+    if (xb < yb + bytes && yb < xb + bytes) {
+        ctx_set_error(ctx, "mm_apply_precond_2l_noalloc: x and y overlap (the call does not work in place)");
+        return MM_ERR_ARG;
+    }
+    DeviceScope dev_scope(v.device);
+    cudaError_t e = dev_scope.err;
     double* base = nullptr;
     if (e == cudaSuccess) e = noalloc_scratch(v.device, &base);
     if (e != cudaSuccess) {

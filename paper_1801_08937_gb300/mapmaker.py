@@ -58,6 +58,8 @@ SIGNATURES = [
     ("mm_build_coarse_from_solve", C.c_int, [_VP, _I32, _D, C.POINTER(_I32)]),
     ("mm_solve_poll", C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32)]),
     ("mm_set_templates", C.c_int, [_VP, _I32, _I32, _VP, _VP, _I32, _I32, C.c_int]),
+    ("mm_export_coarse", C.c_int, [_VP, _VP, C.POINTER(_I64)]),
+    ("mm_import_coarse", C.c_int, [_VP, _VP, _I64]),
 ]
 
 _lib = None
@@ -111,6 +113,15 @@ def _arg(x, np_dtype, writable=False):
     return C.c_void_p(a.ctypes.data), MM_HOST, a
 
 
+def _numel(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
+
+
+def _device_of(x):
+    """CUDA device index of a torch tensor on the GPU, else None (host memory)."""
+    return x.device.index if (_is_torch(x) and x.is_cuda) else None
+
+
 def _mem(*mems):
     ms = {m for m in mems if m is not None}
     if len(ms) > 1:
@@ -128,6 +139,7 @@ class Context:
         if st != MM_OK:
             raise MapMakerError(st, "mm_create failed")
         self.h = h
+        self.device = int(device)
         self.precision = precision
         self.n_pix = 0
         self.n_samples = 0
@@ -148,6 +160,25 @@ class Context:
             raise MapMakerError(st, self.lib.mm_last_error(self.h).decode())
         return st
 
+    def _count(self, x, per: int, what: str) -> int:
+        """Number of right-hand sides (or vectors) in x, which must hold a whole number of them."""
+        if per <= 0:
+            return 1   # no pointing yet: the library answers MM_ERR_STATE before reading x
+        n = _numel(x)
+        if n == 0 or n % per:
+            raise ValueError(f"{what} holds {n} elements, not a positive multiple of {per}")
+        d = _device_of(x)
+        if d is not None and d != self.device:
+            raise ValueError(f"{what} is on cuda:{d}, the context on cuda:{self.device}")
+        return n // per
+
+    def _check_out(self, out, like, need: int, what: str):
+        """A caller's output array must hold `need` elements and live where the input lives."""
+        if _numel(out) < need:
+            raise ValueError(f"{what} holds {_numel(out)} elements, the call writes {need}")
+        if _device_of(out) != _device_of(like):
+            raise ValueError(f"{what} and the input must both be host memory or both on cuda:{self.device}")
+
     @property
     def tod_dtype(self):
         return np.float32 if self.precision == MM_FP32_MIXED else np.float64
@@ -162,6 +193,10 @@ class Context:
         bo = np.ascontiguousarray(block_off, dtype=np.int64)
         bb = np.ascontiguousarray(block_band, dtype=np.int32)
         n = int(bo[-1])
+        if _numel(pix) != n or _numel(psi) != n:
+            raise ValueError(f"pix and psi hold {_numel(pix)} and {_numel(psi)} samples, block_off ends at {n}")
+        if bb.size != bo.size - 1:
+            raise ValueError(f"block_band holds {bb.size} entries for {bo.size - 1} blocks")
         self._check(self.lib.mm_setup_pointing(
             self.h, n, int(n_det), int(n_pix), p_pix, p_psi, int(bo.shape[0] - 1),
             C.c_void_p(bo.ctypes.data), C.c_void_p(bb.ctypes.data), int(band.shape[0]),
@@ -195,24 +230,33 @@ class Context:
         return np.empty((nrhs, self.n_pix, 3), dtype=np.float64)
 
     def rhs(self, tod, out=None):
-        nrhs = int(np.prod(tod.shape) // self.n_samples)
-        out = self._map_out(tod, nrhs) if out is None else out
+        nrhs = self._count(tod, self.n_samples, "tod")
+        if out is None:
+            out = self._map_out(tod, nrhs)
+        else:
+            self._check_out(out, tod, nrhs * 3 * self.n_pix, "out")
         pt, m1, k1 = _arg(tod, self.tod_dtype)
         po, m2, k2 = _arg(out, np.float64, writable=True)
         self._check(self.lib.mm_rhs(self.h, pt, po, nrhs, _mem(m1, m2)))
         return out
 
     def apply_A(self, x, out=None):
-        nrhs = int(np.prod(x.shape) // (3 * self.n_pix))
-        out = self._map_out(x, nrhs) if out is None else out
+        nrhs = self._count(x, 3 * self.n_pix, "x")
+        if out is None:
+            out = self._map_out(x, nrhs)
+        else:
+            self._check_out(out, x, nrhs * 3 * self.n_pix, "out")
         px, m1, k1 = _arg(x, np.float64)
         po, m2, k2 = _arg(out, np.float64, writable=True)
         self._check(self.lib.mm_apply_A(self.h, px, po, nrhs, _mem(m1, m2)))
         return out
 
     def apply_precond(self, which, x, out=None):
-        nrhs = int(np.prod(x.shape) // (3 * self.n_pix))
-        out = self._map_out(x, nrhs) if out is None else out
+        nrhs = self._count(x, 3 * self.n_pix, "x")
+        if out is None:
+            out = self._map_out(x, nrhs)
+        else:
+            self._check_out(out, x, nrhs * 3 * self.n_pix, "out")
         px, m1, k1 = _arg(x, np.float64)
         po, m2, k2 = _arg(out, np.float64, writable=True)
         self._check(self.lib.mm_apply_precond(self.h, int(which), px, po, nrhs, _mem(m1, m2)))
@@ -220,11 +264,12 @@ class Context:
 
     def apply_precond_2l_noalloc(self, x, out):
         """y = M_2l x into a caller-owned device array; the call allocates no device memory."""
-        nrhs = int(np.prod(x.shape) // (3 * self.n_pix))
+        nrhs = self._count(x, 3 * self.n_pix, "x")
+        if _device_of(x) is None or _device_of(out) is None:
+            raise ValueError("apply_precond_2l_noalloc takes device arrays only")
+        self._check_out(out, x, nrhs * 3 * self.n_pix, "out")
         px, m1, k1 = _arg(x, np.float64)
         po, m2, k2 = _arg(out, np.float64, writable=True)
-        if m1 != MM_DEVICE or m2 != MM_DEVICE:
-            raise ValueError("apply_precond_2l_noalloc takes device arrays only")
         self._check(self.lib.mm_apply_precond_2l_noalloc(self.h, px, po, nrhs))
         return out
 
@@ -241,7 +286,7 @@ class Context:
         return kout.value
 
     def set_coarse(self, Z):
-        k = int(np.prod(Z.shape) // (3 * self.n_pix))
+        k = self._count(Z, 3 * self.n_pix, "Z")
         pz, m1, kz = _arg(Z, np.float64)
         self._check(self.lib.mm_set_coarse(self.h, k, pz, m1))
 
@@ -254,9 +299,27 @@ class Context:
                                            C.byref(k)))
         return Z, ritz
 
+    def export_coarse(self) -> bytes:
+        """Checkpoint of the coarse space (Z, A Z, E^-1, Ritz values, operator fingerprint)."""
+        n = C.c_int64(0)
+        self._check(self.lib.mm_export_coarse(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.mm_export_coarse(self.h, C.cast(buf, C.c_void_p), C.byref(n)))
+        return buf.raw[:n.value]
+
+    def import_coarse(self, data: bytes):
+        """Install a checkpoint written by export_coarse for the same operator (MM_ERR_ARG otherwise)."""
+        buf = C.create_string_buffer(bytes(data), len(data))
+        self._check(self.lib.mm_import_coarse(self.h, C.cast(buf, C.c_void_p), len(data)))
+
     def solve(self, tod, precond=MM_PRECOND_BD, tol=1e-8, max_iter=500, rhs_len=None, out=None):
-        nrhs = int(np.prod(tod.shape) // self.n_samples)
-        out = self._map_out(tod, nrhs) if out is None else out
+        nrhs = self._count(tod, self.n_samples, "tod")
+        if out is None:
+            out = self._map_out(tod, nrhs)
+        else:
+            self._check_out(out, tod, nrhs * 3 * self.n_pix, "out")
+        if rhs_len is not None and np.asarray(rhs_len).size != nrhs:
+            raise ValueError(f"rhs_len holds {np.asarray(rhs_len).size} lengths for {nrhs} right-hand sides")
         info = (mm_solve_info * nrhs)()
         pt, m1, k1 = _arg(tod, self.tod_dtype)
         po, m2, k2 = _arg(out, np.float64, writable=True)
@@ -267,7 +330,9 @@ class Context:
         return out, [_info_dict(i) for i in info]
 
     def solve_begin(self, tod, precond=MM_PRECOND_BD, tol=1e-8, max_iter=500, rhs_len=None):
-        nrhs = int(np.prod(tod.shape) // self.n_samples)
+        nrhs = self._count(tod, self.n_samples, "tod")
+        if rhs_len is not None and np.asarray(rhs_len).size != nrhs:
+            raise ValueError(f"rhs_len holds {np.asarray(rhs_len).size} lengths for {nrhs} right-hand sides")
         pt, m1, k1 = _arg(tod, self.tod_dtype)
         lens = None if rhs_len is None else np.ascontiguousarray(rhs_len, dtype=np.int64)
         self._keep = (k1, lens)
@@ -290,7 +355,10 @@ class Context:
         return bool(r.value), bool(d.value)
 
     def solve_end(self, out=None, like=None):
-        out = self._map_out(like, self._nrhs) if out is None else out
+        if out is None:
+            out = self._map_out(like, self._nrhs)
+        elif _numel(out) < self._nrhs * 3 * self.n_pix:
+            raise ValueError(f"out holds {_numel(out)} elements, the call writes {self._nrhs * 3 * self.n_pix}")
         info = (mm_solve_info * self._nrhs)()
         po, m, ko = _arg(out, np.float64, writable=True)
         st = self.lib.mm_solve_end(self.h, po, info, m)

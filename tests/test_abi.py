@@ -180,3 +180,74 @@ def test_binding_argument_types_match_the_header():
         want = [kind_c(q.strip()) for q in params]
         got = [kind_py(t) for t in sig[m.group(1)]]
         assert want == got, (m.group(1), want, got)
+
+
+class _RecordingLib:
+    """Stands in for libmapmaker.so: records every entry point called (returns MM_OK)."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def fn(*args):
+            self.calls.append(name)
+            return 0
+        return fn
+
+
+def _fake_context(n_pix=4, n_samples=64):
+    from paper_1801_08937_gb300 import mapmaker as M
+    c = object.__new__(M.Context)
+    c.lib = _RecordingLib()
+    c.h = None
+    c.device = 0
+    c.precision = M.MM_FP64
+    c.n_pix = n_pix
+    c.n_samples = n_samples
+    return c
+
+
+def test_binding_refuses_arrays_of_the_wrong_size_before_any_call():
+    """x must hold a whole number of [n_pix][3] maps and a caller's output at least as many values
+    as the call writes: otherwise ValueError, and no entry point is called (an undersized output
+    would be written past its end)."""
+    import numpy as np
+    c = _fake_context()
+    n = 3 * c.n_pix
+    for call in (lambda x, o: c.apply_A(x, out=o), lambda x, o: c.apply_precond(0, x, out=o)):
+        with pytest.raises(ValueError):
+            call(np.zeros(n + 1), None)                         # not a whole number of maps
+        with pytest.raises(ValueError):
+            call(np.zeros(2 * n), np.zeros(2 * n - 1))          # output one value short
+        with pytest.raises(ValueError):
+            call(np.zeros(0), None)
+    with pytest.raises(ValueError):
+        c.rhs(np.zeros(c.n_samples), out=np.zeros(n - 3))
+    with pytest.raises(ValueError):
+        c.rhs(np.zeros(c.n_samples + 5))
+    with pytest.raises(ValueError):
+        c.solve(np.zeros(2 * c.n_samples), out=np.zeros(n))     # two maps written, room for one
+    with pytest.raises(ValueError):
+        c.solve(np.zeros(2 * c.n_samples), rhs_len=[10])        # one length for two right-hand sides
+    with pytest.raises(ValueError):
+        c.set_coarse(np.zeros(n + 2))
+    with pytest.raises(ValueError):
+        c.setup_pointing(np.zeros(10, np.int32), np.zeros(9, np.float32), [0, 10], [0], np.ones(3), c.n_pix)
+    assert c.lib.calls == []
+    # well-formed calls go through
+    c.apply_A(np.zeros(2 * n), out=np.zeros(2 * n))
+    c.rhs(np.zeros(c.n_samples))
+    assert c.lib.calls == ["mm_apply_A", "mm_rhs"]
+
+
+def test_binding_refuses_host_outputs_for_device_inputs_and_the_noalloc_host_arrays():
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    c = _fake_context()
+    n = 3 * c.n_pix
+    x = torch.zeros(n, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        c.apply_precond_2l_noalloc(x, torch.zeros(n, dtype=torch.float64))   # host tensors
+    with pytest.raises(ValueError):
+        c.apply_precond_2l_noalloc(np.zeros(n), np.zeros(n))
+    assert c.lib.calls == []

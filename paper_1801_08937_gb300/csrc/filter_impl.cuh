@@ -933,6 +933,135 @@ __device__ __forceinline__ void load4_tod(const FilterArgs& a, const Seg& S, int
     }
 }
 
+// ---- float32 gather and scatter of the half-length kernel ----
+// Both walk a block in groups of four consecutive samples.  Groups that lie
+// wholly inside a block whose first sample is 16-byte aligned (every block of
+// the configured scans) take unchecked 16-byte pointing loads; flagged samples
+// (pixel -1) are handled without branches: the map entry of pixel 0 is read
+// and the sample's value is zeroed.  The remaining groups (a ragged end, an
+// unaligned start, the zero padding of the transform) take checked loads.
+
+// pix and psi of four consecutive samples, streamed past L1 so the map
+// entries and tables stay cached there
+__device__ __forceinline__ void ld4_pointing(const int32_t* pp, const float* pf, int4& pv, float4& fv) {
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(pv.x), "=r"(pv.y), "=r"(pv.z), "=r"(pv.w)
+                 : "l"(pp));
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(fv.x), "=f"(fv.y), "=f"(fv.z), "=f"(fv.w)
+                 : "l"(pf));
+}
+
+// cos 2psi, sin 2psi as -cos(2psi - pi), -sin(2psi - pi): __sincosf on [-pi, pi)
+__device__ __forceinline__ void neg_cs(float psi, float& nc, float& ns) {
+    __sincosf(fmaf(2.0f, psi, -3.14159265358979323846f), &ns, &nc);
+}
+
+// y_t = I_p + Q_p cos 2psi + U_p sin 2psi (Sect. 2, Eq. datamodel), 0 for a flagged sample
+__device__ __forceinline__ float pointed_value(int p, float psi, const float4& m) {
+    float nc, ns;
+    neg_cs(psi, nc, ns);
+    const float y = fmaf(-ns, m.z, fmaf(-nc, m.y, m.x));
+    return p >= 0 ? y : 0.0f;
+}
+
+template <int NT>
+__device__ __forceinline__ void half_gather_f32_map(const FilterArgs& a, const Seg& S, C2<float>* s, int M) {
+    const int ng = M >> 1;   // groups of four samples = pairs of complex points
+    const float4* map = reinterpret_cast<const float4*>(a.src) + (int64_t)S.rhs * a.n_pix;
+    const int32_t* pix = a.pix + S.out0;
+    const float* psi = a.psi + S.out0;
+    const int nfull = (S.out0 & 3) == 0 ? (S.n_out >> 2) : 0;
+    int u = threadIdx.x;
+    if (u < nfull) {
+        int4 pv;
+        float4 fv;
+        ld4_pointing(pix + 4 * u, psi + 4 * u, pv, fv);
+        for (; u < nfull; u += NT) {
+            // the next group's pointing is requested before this group's map entries
+            const int un = min(u + NT, nfull - 1);
+            int4 pn;
+            float4 fn;
+            ld4_pointing(pix + 4 * un, psi + 4 * un, pn, fn);
+            const float4 m0 = __ldg(map + max(pv.x, 0));
+            const float4 m1 = __ldg(map + max(pv.y, 0));
+            const float4 m2 = __ldg(map + max(pv.z, 0));
+            const float4 m3 = __ldg(map + max(pv.w, 0));
+            const int b = sidx(2 * u);   // points 2u, 2u + 1 share one 16-point padding group
+            s[b] = C2<float>{pointed_value(pv.x, fv.x, m0), pointed_value(pv.y, fv.y, m1)};
+            s[b + 1] = C2<float>{pointed_value(pv.z, fv.z, m2), pointed_value(pv.w, fv.w, m3)};
+            pv = pn;
+            fv = fn;
+        }
+    }
+    for (; u < ng; u += NT) {
+        float y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = 4 * u + j;
+            const bool ok = i < S.n_out;
+            const int p = ok ? __ldg(pix + i) : -1;
+            const float f = ok ? __ldg(psi + i) : 0.0f;
+            y[j] = pointed_value(p, f, __ldg(map + max(p, 0)));
+        }
+        const int b = sidx(2 * u);
+        s[b] = C2<float>{y[0], y[1]};
+        s[b + 1] = C2<float>{y[2], y[3]};
+    }
+}
+
+// P^T of a warp's 128 consecutive samples, four per lane in order: one atomic
+// per run of equal pixels.  Within a lane, suffix sums over each run; the
+// lane's last run continues into the following lanes while their first
+// pixel is the same, and its continuation X(l) = a(l) + b(l) X(l + 1)
+// (a = the next lane's leading run when the run continues, b = that run fills
+// the next lane) is solved by doubling, taking only the steps the longest
+// chain needs.  Every sample is counted once: at the first sample of its run
+// inside this warp's 128.
+__device__ __forceinline__ void warp_run_scatter(const int (&p)[4], float (&v0)[4], float (&v1)[4], float (&v2)[4],
+                                                 V4<float>* q) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool e01 = p[0] == p[1], e12 = p[1] == p[2], e23 = p[2] == p[3];
+    if (e23) { v0[2] += v0[3]; v1[2] += v1[3]; v2[2] += v2[3]; }
+    if (e12) { v0[1] += v0[2]; v1[1] += v1[2]; v2[1] += v2[2]; }
+    if (e01) { v0[0] += v0[1]; v1[0] += v1[1]; v2[0] += v2[1]; }
+    const bool whole = e01 && e12 && e23;
+    const int pnext = __shfl_down_sync(FULL, p[0], 1);
+    const bool cont = lane < 31 && pnext == p[3];
+    float x0 = __shfl_down_sync(FULL, v0[0], 1);
+    float x1 = __shfl_down_sync(FULL, v1[0], 1);
+    float x2 = __shfl_down_sync(FULL, v2[0], 1);
+    const bool wnext = __shfl_down_sync(FULL, (int)whole, 1) != 0;
+    if (!cont) { x0 = 0.0f; x1 = 0.0f; x2 = 0.0f; }
+    bool chain = cont && wnext;
+#pragma unroll 1
+    for (int d = 1; __any_sync(FULL, chain); d <<= 1) {
+        const float y0 = __shfl_down_sync(FULL, x0, d);
+        const float y1 = __shfl_down_sync(FULL, x1, d);
+        const float y2 = __shfl_down_sync(FULL, x2, d);
+        const bool cn = __shfl_down_sync(FULL, (int)chain, d) != 0;
+        if (chain) { x0 += y0; x1 += y1; x2 += y2; }
+        chain = chain && cn;
+    }
+    const int plast = __shfl_up_sync(FULL, p[3], 1);
+    // heads: the first sample of each run; a run reaching the lane end adds X
+    const bool h0 = lane == 0 || p[0] != plast;
+    if (h0 && p[0] >= 0) {
+        const float w = whole ? 1.0f : 0.0f;
+        atomic_add3(q + p[0], fmaf(w, x0, v0[0]), fmaf(w, x1, v1[0]), fmaf(w, x2, v2[0]));
+    }
+    if (!e01 && p[1] >= 0) {
+        const float w = (e12 && e23) ? 1.0f : 0.0f;
+        atomic_add3(q + p[1], fmaf(w, x0, v0[1]), fmaf(w, x1, v1[1]), fmaf(w, x2, v2[1]));
+    }
+    if (!e12 && p[2] >= 0) {
+        const float w = e23 ? 1.0f : 0.0f;
+        atomic_add3(q + p[2], fmaf(w, x0, v0[2]), fmaf(w, x1, v1[2]), fmaf(w, x2, v2[2]));
+    }
+    if (!e23 && p[3] >= 0) atomic_add3(q + p[3], v0[3] + x0, v1[3] + x1, v2[3] + x2);
+}
+
 // Loads in flight per thread in the float32 gather (groups of four samples)
 // and in the scatter (warp iterations of 128 samples).
 constexpr int HALF_GB = 1;
@@ -1061,54 +1190,68 @@ __device__ __forceinline__ void half_gather_t(const FilterArgs& a, const Seg& S,
 }
 
 // After the conjugate-domain inverse, point m holds conj(z'_m):
-// y'_{2m} = Re, y'_{2m+1} = -Im.
+// y'_{2m} = Re, y'_{2m+1} = -Im.  Each warp takes 128 consecutive samples per
+// step (four per lane); z_t (1, cos 2psi, sin 2psi) is summed over runs of
+// equal pixels (warp_run_scatter).  The next step's pointing is requested
+// before this step's run sums.
 template <int NT>
 __device__ __forceinline__ void half_scatter_f32(const FilterArgs& a, const Seg& S, const C2<float>* s, int M) {
-    constexpr int NW = NT / 32, SU = HALF_SU;
+    constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V4<float>* q = reinterpret_cast<V4<float>*>(a.dst) + (int64_t)S.rhs * a.n_pix;
-    // pointing of the next iteration requested before this one is reduced
-    auto pointing = [&](int base, int (&p)[SU][4], float (&ps)[SU][4]) {
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int i0 = base + u * NW * 128 + 4 * lane;
-            load4(a, S.out0 + i0, i0 < S.n_out, S.n_out - i0, p[u], ps[u]);
-        }
-    };
-    int p[SU][4];
-    float ps[SU][4];
-    pointing(warp * 128, p, ps);
-    for (int base = warp * 128; base < S.n_out; base += NW * 128 * SU) {
-        int pn[SU][4];
-        float psn[SU][4];
-        pointing(base + NW * 128 * SU, pn, psn);
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int i0 = base + u * NW * 128 + 4 * lane;
-            const int m0 = min(i0 >> 1, M - 2);
-            const C2<float> e0 = s[sidx(m0)], e1 = s[sidx(m0 + 1)];
+    const int32_t* pix = a.pix + S.out0;
+    const float* psi = a.psi + S.out0;
+    // steps whose 128 samples all lie inside an aligned block take unchecked vector loads
+    const int nfull = (S.out0 & 3) == 0 ? (S.n_out >> 7) : 0;
+    int st = warp;
+    if (st < nfull) {
+        int4 pv;
+        float4 fv;
+        ld4_pointing(pix + 128 * st + 4 * lane, psi + 128 * st + 4 * lane, pv, fv);
+        for (; st < nfull; st += NW) {
+            const int sn = min(st + NW, nfull - 1);
+            int4 pn;
+            float4 fn;
+            ld4_pointing(pix + 128 * sn + 4 * lane, psi + 128 * sn + 4 * lane, pn, fn);
+            const int m0 = 64 * st + 2 * lane;   // even: points m0, m0 + 1 share a padding group
+            const C2<float> e0 = s[sidx(m0)], e1 = s[sidx(m0) + 1];
+            const int p[4] = {pv.x, pv.y, pv.z, pv.w};
+            const float f[4] = {fv.x, fv.y, fv.z, fv.w};
             const float z[4] = {e0.x, -e0.y, e1.x, -e1.y};
             float v0[4], v1[4], v2[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float zz = 0.0f, c = 0.0f, sn = 0.0f;
-                if (p[u][j] >= 0) {
-                    zz = z[j];
-                    weights_from(a, 0, ps[u][j], c, sn);
-                }
+                float nc, ns;
+                neg_cs(f[j], nc, ns);
+                const float zz = p[j] >= 0 ? z[j] : 0.0f;
                 v0[j] = zz;
-                v1[j] = zz * c;
-                v2[j] = zz * sn;
+                v1[j] = -zz * nc;
+                v2[j] = -zz * ns;
             }
-            scatter4_vals(p[u], v0, v1, v2, q);
+            warp_run_scatter(p, v0, v1, v2, q);
+            pv = pn;
+            fv = fn;
         }
+    }
+    for (; 128 * st < S.n_out; st += NW) {
+        const int i0 = 128 * st + 4 * lane;
+        const int m0 = min(i0 >> 1, M - 2);
+        const C2<float> e0 = s[sidx(m0)], e1 = s[sidx(m0) + 1];
+        const float z[4] = {e0.x, -e0.y, e1.x, -e1.y};
+        int p[4];
+        float v0[4], v1[4], v2[4];
 #pragma unroll
-        for (int u = 0; u < SU; ++u)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                p[u][j] = pn[u][j];
-                ps[u][j] = psn[u][j];
-            }
+        for (int j = 0; j < 4; ++j) {
+            const bool ok = i0 + j < S.n_out;
+            p[j] = ok ? __ldg(pix + i0 + j) : -1;
+            float nc, ns;
+            neg_cs(ok ? __ldg(psi + i0 + j) : 0.0f, nc, ns);
+            const float zz = p[j] >= 0 ? z[j] : 0.0f;
+            v0[j] = zz;
+            v1[j] = -zz * nc;
+            v2[j] = -zz * ns;
+        }
+        warp_run_scatter(p, v0, v1, v2, q);
     }
 }
 
@@ -1218,7 +1361,8 @@ __global__ void __launch_bounds__(NT, HalfMinBlocks<T>::value) k_filter_half(con
     if (!seg_active<T>(a, S)) return;
     const int M = MCT > 0 ? MCT : a.L;
     const C2<T>* tw = reinterpret_cast<const C2<T>*>(a.tw);
-    if constexpr (std::is_same<T, float>::value) half_gather_f32<FROM_TOD, NT>(a, S, s, M);
+    if constexpr (std::is_same<T, float>::value && !FROM_TOD) half_gather_f32_map<NT>(a, S, s, M);
+    else if constexpr (std::is_same<T, float>::value) half_gather_f32<FROM_TOD, NT>(a, S, s, M);
     else half_gather_t<T, FROM_TOD, NT>(a, S, s, M);
     __syncthreads();
     if constexpr (MCT > 0) {

@@ -37,8 +37,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-8 residual per map (2-level vs M_BD), A·x samples/s, p99 latency"
 UNIT = "s/map"
-FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 CUDA-core rate (nominal)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 # ncu: k_filter_half<float, 0, 512, 9216> moved 140.1 MB read + 2.8 MB written for 1.68e7 samples
 NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (140.050432e6 + 2.814976e6) / 16777216
 
@@ -59,6 +57,7 @@ def parse():
     ap.add_argument("--no-bd", action="store_true", help="skip the M_BD comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the MM_FP64 solve of the same map")
     ap.add_argument("--inner-tol", type=float, default=2e-6)
     ap.add_argument("--coarse", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="coarse space from the Lanczos vectors of a first M_BD run, or from a separate Arnoldi run")
@@ -205,6 +204,103 @@ def cpu_oracle_sample(cfg_name, seed, n_products, budget_s=20.0):
             f"{reps} reps; scaled by samples to the full workload ({full_samples}) and by "
             f"{n_products} products with A per map (the GPU solve's count)")
     return est, desc, 1
+
+
+# ---------------- the oracle's full c1 solves on the host cores ----------------
+_ORACLE_SUB = {}
+
+
+def _oracle_worker_init(sub):
+    _ORACLE_SUB["prob"] = sub
+
+
+def _oracle_worker_apply(x):
+    import oracle as O
+    return O.apply_A(_ORACLE_SUB["prob"], x)
+
+
+def _oracle_c1_problem(seed=0):
+    """c1 problem as the oracle sees it after pixel selection, its M_BD and b (noisy timeline)."""
+    import oracle as O
+    import synth
+    scan = synth.scan_from_config("c1", seed=seed)
+    d = synth.make_tod(scan, synth.make_sky(scan.n_pix, seed), synth.make_noise(scan, seed))
+    prob = O.Problem.from_scan(scan)
+    blocks, hits = O.bd_blocks(prob)
+    good = O.select_pixels(blocks, hits, 1e-3)
+    prob = prob.with_pix(O.flag_samples(prob.pix, good))
+    blocks, _ = O.bd_blocks(prob)
+    return prob, O.bd_inverse(blocks, good), O.rhs(prob, d).reshape(-1)
+
+
+def _oracle_solves(prob, mbd, b, apply_A, k=16, m_max=40):
+    """The oracle's M_BD PCG and its two-level PCG (Arnoldi coarse space) to 1e-8; returns seconds."""
+    import oracle as O
+    A = lambda v: apply_A(v.reshape(-1, 3)).reshape(-1)  # noqa: E731
+    M = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+    t0 = time.perf_counter()
+    _, ibd = O.pcg(A, M, b, tol=1e-8, max_iter=1000)[:2]
+    t_bd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    W, H, m = O.arnoldi(lambda v: M(A(v)), M(b), m_max, 1e-12)
+    Z, _ = O.ritz_basis(W, H, m, k)
+    AZ, _, L = O.coarse_space(A, Z)
+    _, i2 = O.pcg(A, lambda v: O.m2l_apply(v, M, Z, AZ, L), b, tol=1e-8, max_iter=1000)[:2]
+    t_2l = time.perf_counter() - t0
+    return t_bd, ibd["iters"], t_2l, i2["iters"]
+
+
+def cpu_oracle_c1(reps=3, budget_s=90.0):
+    """Measured, not extrapolated: the FP64 oracle's full c1 solves (M_BD, and M_2l including its
+    Arnoldi coarse space) on one host core and on every host core.  The all-core run splits the
+    stationary blocks over worker processes (A is a sum over blocks, Sect. 3, Eq. linearsystem) and
+    sums their oracle products; best of `reps`."""
+    import multiprocessing as mp
+
+    import oracle as O
+    prob, mbd, b = _oracle_c1_problem()
+    cores = os.cpu_count() or 1
+    out = {"workload": "c1: 32x32 patch, 8 det x 32768 samples, lambda 512, 8 intervals; PCG to 1e-8; "
+                       "M_2l with k=16 Ritz vectors of a 40-step Arnoldi run (its cost included)",
+           "nproc": cores}
+    t_start = time.perf_counter()
+    best = None
+    for _ in range(reps):
+        r = _oracle_solves(prob, mbd, b, lambda x: O.apply_A(prob, x))
+        best = r if best is None else tuple(min(a, c) if i % 2 == 0 else a for i, (a, c) in enumerate(zip(best, r)))
+        if time.perf_counter() - t_start > budget_s / 2:
+            break
+    out["one_core"] = {"m_bd_s": best[0], "m_bd_iters": best[1], "m_2l_s": best[2], "m_2l_iters": best[3],
+                       "cores": 1}
+    # all cores: contiguous block ranges per worker
+    nb = len(prob.block_off) - 1
+    nw = max(1, min(cores, nb))
+    cuts = np.linspace(0, nb, nw + 1).astype(int)
+    subs = []
+    for w in range(nw):
+        b0, b1 = cuts[w], cuts[w + 1]
+        o0, o1 = int(prob.block_off[b0]), int(prob.block_off[b1])
+        subs.append(O.Problem(prob.pix[o0:o1], prob.psi[o0:o1], prob.block_off[b0:b1 + 1] - o0, prob.band,
+                              prob.block_band[b0:b1], prob.n_pix))
+    ctx = mp.get_context("spawn")
+    pools = [ctx.Pool(1, initializer=_oracle_worker_init, initargs=(sub,)) for sub in subs]
+    try:
+        def par_apply(x):
+            parts = [pl.apply_async(_oracle_worker_apply, (x,)) for pl in pools]
+            return sum(p.get() for p in parts)
+        par_apply(np.zeros((prob.n_pix, 3)))   # workers up
+        best = None
+        for _ in range(reps):
+            r = _oracle_solves(prob, mbd, b, par_apply)
+            best = r if best is None else tuple(min(a, c) if i % 2 == 0 else a for i, (a, c) in enumerate(zip(best, r)))
+            if time.perf_counter() - t_start > budget_s:
+                break
+    finally:
+        for pl in pools:
+            pl.terminate()
+    out["all_cores"] = {"m_bd_s": best[0], "m_bd_iters": best[1], "m_2l_s": best[2], "m_2l_iters": best[3],
+                        "cores": nw}
+    return out
 
 
 def workload_config(args, world):
@@ -381,27 +477,40 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved_gbs = bytes_per_launch / (ax_ms * 1e-3) / 1e9 if ax_ms > 0 else 0.0
-    alu_peak = FP32_PEAK_TFLOPS if prec == M.MM_FP32_MIXED else FP64_PEAK_TFLOPS
     achieved_tf = flops_per_launch / (ax_ms * 1e-3) / 1e12 if ax_ms > 0 else 0.0
     # DRAM bytes (read + write) per sample of this kernel, from an ncu capture of the same kernel on
     # 16 of the 128 detectors (1.68e7 samples, inputs larger than L2); traffic scales with samples
     traffic = None
     if prec == M.MM_FP32_MIXED and whole == 2 and L == 18432:
         traffic = NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 * scan.n_samples
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak if alu_peak else None, "traffic": traffic,
+    # measured CUDA-core FMA rates (the arithmetic view's denominators), clocks sampled meanwhile
+    fma_clk = ClockSampler(local)
+    fma_clk.start()
+    fp32_peak = M.fma_peak(local, False, 1.0) / 1e12
+    fp64_peak = M.fma_peak(local, True, 0.5) / 1e12
+    fma_clocks = fma_clk.stop()
+    alu_peak = fp32_peak if prec == M.MM_FP32_MIXED else fp64_peak
+    # the HBM view is the headline: 8 B/sample of pointing per product (pix + psi), the north-star
+    # roofline of A x; the arithmetic view (transform flops against the measured FMA rate) beside it
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak if hbm_peak else None, "traffic": traffic,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs: copy bandwidth, burst)",
+                "algorithmic_bytes": "8 B/sample (pix + psi) x %d samples per launch" % scan.n_samples,
                 "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum per sample from one ncu capture "
                                  "(16-detector cut), scaled by samples to this launch") if traffic else None,
                 "kernel": "%s<%s> (gather + FFT Toeplitz + scatter)"
                           % ("k_filter_half" if whole == 2 else "k_filter_fft",
                              "float" if prec == M.MM_FP32_MIXED else "double"),
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec == M.MM_FP32_MIXED
-                                else "nominal GB300 FP64 rate"),
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": ax_ms, "fft_len": L,
+                "avg_launch_ms": ax_ms, "fft_len": L,
                 "fft_radices": fft_passes(T) if L else None, "whole_blocks": bool(whole),
                 "half_length_transform": whole == 2,
-                "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "of": "measured",
-                             "frac": achieved_gbs / hbm_peak, "algorithmic_bytes": "8 B/sample (pix + psi)"},
+                "alu_view": {"achieved_tflops": achieved_tf, "peak_tflops": alu_peak,
+                             "frac": achieved_tf / alu_peak if alu_peak else None,
+                             "flops_per_launch": flops_per_launch,
+                             "peak_source": "measured: mm_fma_peak (%s FMA chains on every SM, ~1 s)"
+                                            % ("float32" if prec == M.MM_FP32_MIXED else "float64"),
+                             "fp32_fma_tflops": fp32_peak, "fp64_fma_tflops": fp64_peak,
+                             "clocks_during_peak": fma_clocks},
                 "step_filter_ms": filter_ms / max(1, args.steps), "step_filter_launches": n_filter / max(1, args.steps)}
 
     # ---- M_BD per map on the same resident scan ----
@@ -411,6 +520,63 @@ def main():
         ibd = dict(info_last["info"])
         bd = {"time_to_tol_s": bd_ms / 1e3, "iters": ibd["iters"], "status": ibd["status"],
               "true_rel_res": ibd["true_rel_res"], "refinements": ibd["refinements"]}
+
+    # ---- the same map in MM_FP64 (the configured precision of this workload): every operator product
+    # in double-float arithmetic (about 44 bits), float64 vectors, dots and coarse space ----
+    fp64 = None
+    if not args.no_fp64 and prec == M.MM_FP32_MIXED:
+        c64 = M.Context(local, stream.cuda_stream, M.MM_FP64)
+        c64.set_option("fp64_products", 2)
+        tod64 = torch.from_numpy(tod).to(dev)
+        x64 = torch.empty_like(x_d)
+
+        def setup64():
+            c64.setup_pointing(pix_d, psi_d, scan.block_off, scan.block_band, scan.band, scan.n_pix,
+                               n_det=scan.n_det)
+            c64.build_bd(1e-3)
+            c64.set_option("harvest", args.m_max)
+            c64.solve(tod64, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=x64)
+            c64.set_option("harvest", 0)
+            c64.build_coarse_from_solve(k=args.k)
+
+        setup64_ms = timed(setup64, 1)
+        res64 = {}
+        for name, pc in (("two_level", M.MM_PRECOND_2L), ("m_bd", M.MM_PRECOND_BD)):
+            def one(pc=pc):
+                _, inf = c64.solve(tod64, pc, tol=args.tol, max_iter=args.max_iter, out=x64)
+                res64["info"] = inf[0]
+            ms64 = timed(one, 2)
+            i64 = res64["info"]
+            res64[name] = {"time_to_tol_s": ms64 / 1e3, "iters": i64["iters"], "status": i64["status"],
+                           "true_rel_res": i64["true_rel_res"]}
+        fp64 = {"context": "MM_FP64, fp64_products = 2 (double-float products, float64 vectors)",
+                "setup_once_s": setup64_ms / 1e3, "two_level": res64["two_level"], "m_bd": res64["m_bd"]}
+        c64.close()
+        del tod64, x64
+
+    # ---- c1 (plain M_BD, FP64): the oracle's full solves measured on the host cores, and the GPU ----
+    c1 = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        c1 = {"oracle": cpu_oracle_c1()}
+        scan1 = synth.scan_from_config("c1", seed=0)
+        d1 = torch.from_numpy(synth.make_tod(scan1, synth.make_sky(scan1.n_pix, 0),
+                                             synth.make_noise(scan1, 0))).to(dev)
+        g1 = M.Context(local, stream.cuda_stream, M.MM_FP64)
+        g1.setup_scan(scan1)
+        g1.build_bd(1e-3)
+        r1 = {}
+
+        def solve1(pc):
+            _, inf = g1.solve(d1, pc, tol=1e-8, max_iter=1000)
+            r1["info"] = inf[0]
+        bd1 = timed(lambda: solve1(M.MM_PRECOND_BD), 5)
+        it_bd1 = r1["info"]["iters"]
+        cs1 = timed(lambda: g1.build_coarse(None, m_max=40, eps_arn=1e-12, k=16), 1)
+        tl1 = timed(lambda: solve1(M.MM_PRECOND_2L), 5)
+        c1["gpu"] = {"m_bd_s": bd1 / 1e3, "m_bd_iters": it_bd1, "m_2l_s": (tl1 + cs1) / 1e3,
+                     "m_2l_iters": r1["info"]["iters"], "m_2l_coarse_setup_s": cs1 / 1e3,
+                     "context": "MM_FP64 (native float64 products), mean of 5"}
+        g1.close()
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -430,7 +596,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         products = info2l["iters"] + 2 + info2l["refinements"]
         est, desc, cores = cpu_oracle_sample(args.config, 0, products)
-        cpu = {"value": est, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": est, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "method": "extrapolated from a timed sample (the full c2 oracle solve would take hours); "
+                         "measured full solves at c1 are in the c1 object"}
 
     if rank == 0:
         line = {
@@ -450,6 +618,8 @@ def main():
                         "hbm_frac": (8.0 * scan.n_samples / (ax_ms * 1e-3) / 1e9) / hbm_peak if ax_ms else None},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "fp64": fp64,
+            "c1": c1,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -373,6 +373,15 @@ mm_status mm_apply_precond_2l_noalloc(mm_ctx* ctx, const double* x, double* y, i
 int64_t mm_estimate_bytes(int64_t n_samples, int32_t n_pix, int32_t n_bands, int32_t half_bw,
                           int32_t nrhs, int32_t m_max, int32_t k, mm_precision prec);
 
+/* Measured FMA rate of the CUDA cores of `device` (not a step of the paper's
+ * method: the denominator of the arithmetic view of the filter kernels'
+ * roofline).  fp64 = 0 times float32 FMAs, 1 float64; the timed launch runs
+ * for about `seconds` (0 < seconds <= 60) on every SM (8 independent FMA
+ * chains per thread, 2048 threads per SM).  *flops_per_s receives 2 flop per
+ * FMA per second.  It allocates a small device buffer and leaves the caller's
+ * current device as it found it.  Errors: MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_fma_peak(int device, int fp64, double seconds, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

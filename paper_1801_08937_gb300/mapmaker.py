@@ -60,6 +60,7 @@ SIGNATURES = [
     ("mm_set_templates", C.c_int, [_VP, _I32, _I32, _VP, _VP, _I32, _I32, C.c_int]),
     ("mm_export_coarse", C.c_int, [_VP, _VP, C.POINTER(_I64)]),
     ("mm_import_coarse", C.c_int, [_VP, _VP, _I64]),
+    ("mm_fma_peak", C.c_int, [C.c_int, C.c_int, _D, C.POINTER(_D)]),
 ]
 
 _lib = None
@@ -377,6 +378,15 @@ class Context:
 def _info_dict(i):
     return dict(iters=i.iters, status=STATUS_NAMES.get(i.status, i.status), rel_res=i.rel_res,
                 true_rel_res=i.true_rel_res, t_solve_ms=i.t_solve_ms, refinements=i.refinements)
+
+
+def fma_peak(device=0, fp64=False, seconds=1.0) -> float:
+    """Measured CUDA-core FMA rate of the device in flop/s (float32, or float64 with fp64=True)."""
+    v = C.c_double(0)
+    st = load_library().mm_fma_peak(int(device), int(bool(fp64)), float(seconds), C.byref(v))
+    if st != MM_OK:
+        raise MapMakerError(st, "mm_fma_peak failed")
+    return v.value
 
 
 def estimate_bytes(n_samples, n_pix, n_bands, half_bw, nrhs, m_max, k, precision=MM_FP64) -> int:

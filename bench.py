@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--half", type=int, default=1, choices=[0, 1],
                     help="apply mode: allow whole blocks as half-length complex transforms")
     ap.add_argument("--n-rhs", type=int, default=64)
+    ap.add_argument("--mc-m-max", type=int, default=300, help="mc mode: Arnoldi steps of the shared basis")
+    ap.add_argument("--mc-eps-arn", type=float, default=1e-12, help="mc mode: Arnoldi tolerance")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
 
@@ -931,17 +933,20 @@ def run_mc(args, world, rank, local):
         torch.cuda.synchronize()
         return a0.elapsed_time(a1) / reps, out
 
+    out = torch.empty((args.n_rhs, scan.n_pix, 3), dtype=torch.float64, device=dev)
+
     def setup():
+        # the paper's simplified approach (Sect. 7): Ritz vectors of one subset's M_BD A from an Arnoldi
+        # run converged to eps_Arn = 1e-12, reused for every map
         ctx.setup_scan(scan)
         ctx.build_bd(1e-3)
         b = ctx.rhs(tod_d[0:1])
-        return ctx.build_coarse(b[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
+        return ctx.build_coarse(b[0], m_max=args.mc_m_max, eps_arn=args.mc_eps_arn, k=args.k)
 
     setup_ms, k_used = timed(setup)
-    out = torch.empty((args.n_rhs, scan.n_pix, 3), dtype=torch.float64, device=dev)
 
-    def batched(precond=M.MM_PRECOND_2L):
-        return ctx.solve(tod_d, precond, tol=args.tol, max_iter=args.max_iter, rhs_len=lens, out=out)[1]
+    def batched(precond=M.MM_PRECOND_2L, lengths=lens):
+        return ctx.solve(tod_d, precond, tol=args.tol, max_iter=args.max_iter, rhs_len=lengths, out=out)[1]
 
     for _ in range(max(1, args.warmup)):
         batched()
@@ -950,6 +955,12 @@ def run_mc(args, world, rank, local):
     launches = int(ctx.get_option("kernel_launches") - launches0) // max(1, args.steps)
     its = [i["iters"] for i in infos]
     ok = sum(1 for i in infos if i["status"] == "MM_OK")
+    n_2l = sum(1 for i in infos if i["precond_used"] == "M_2l")
+    ms_bd, infos_bd = timed(lambda: batched(M.MM_PRECOND_BD), max(1, args.steps))
+    # the paper's Monte Carlo case: every map on the same (full-length) operator A, other noise and sky
+    batched(M.MM_PRECOND_2L, None)
+    ms_sh, inf_sh = timed(lambda: batched(M.MM_PRECOND_2L, None), max(1, args.steps))
+    ms_shbd, inf_shbd = timed(lambda: batched(M.MM_PRECOND_BD, None), max(1, args.steps))
     # single right-hand side solves of the same maps, one at a time
     n_single = min(4, args.n_rhs)
     one = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
@@ -971,7 +982,19 @@ def run_mc(args, world, rank, local):
                                    f"shared coarse space k={k_used}, CUDA graph of 8 iterations",
                        "samples_per_batched_Ax": int(np.sum(lens) * scan.n_det)},
             "batched": {"iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)), "converged": ok,
-                        "kernel_launches_per_batch": launches},
+                        "kernel_launches_per_batch": launches, "rhs_with_m2l": n_2l,
+                        "rhs_falling_back_to_m_bd": args.n_rhs - n_2l,
+                        "note": "a basis deflates maps of the length it was built from; shorter prefixes "
+                                "run M_BD (option coarse_fallback)"},
+            "batched_m_bd": {"time_per_map_s": ms_bd / 1e3 / args.n_rhs,
+                             "iters_mean": float(np.mean([i["iters"] for i in infos_bd]))},
+            "shared_A": {"workload": "the paper's Monte Carlo case: the same %d maps' noise and sky on the "
+                                     "full-length master scan (one operator A for all)" % args.n_rhs,
+                         "two_level_time_per_map_s": ms_sh / 1e3 / args.n_rhs,
+                         "two_level_iters_mean": float(np.mean([i["iters"] for i in inf_sh])),
+                         "m_bd_time_per_map_s": ms_shbd / 1e3 / args.n_rhs,
+                         "m_bd_iters_mean": float(np.mean([i["iters"] for i in inf_shbd])),
+                         "converged": sum(1 for i in inf_sh if i["status"] == "MM_OK")},
             "single_rhs": single, "setup_once_s": setup_ms / 1e3, "gen_s": t_gen}
     if rank == 0:
         print(json.dumps(line), flush=True)

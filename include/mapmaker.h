@@ -77,7 +77,8 @@ typedef struct {
     double true_rel_res;    /* ||b - A x|| / ||b|| with a float64 product at exit  */
     double t_solve_ms;      /* device time of the whole solve call                */
     int32_t refinements;    /* outer float64 residual refinements (mixed mode)    */
-    int32_t pad;
+    int32_t precond_used;   /* mm_precond applied to this right-hand side (M_BD   */
+                            /* when "coarse_fallback" replaced M_2l, see options) */
 } mm_solve_info;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream`
@@ -262,7 +263,13 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * the per-RHS coarse products A_i Z of an uneven-length two-level batch from
  * products over whole blocks computed once per coarse space (block-diagonal
  * W; needs the same block boundaries in every detector) plus the one partly
- * covered block per detector, 0 forms every A_i Z directly.  Errors:
+ * covered block per detector, 0 forms every A_i Z directly;
+ * "coarse_fallback": 1 (default) in a two-level batch of uneven length runs
+ * M_BD for every right-hand side whose length differs by more than 1 % from
+ * that of the operator the basis Z was built from (a prefix covers the patch
+ * differently and its small eigenmodes are not in span Z: M_2l would cost
+ * more for the same products), and M_BD for the whole batch when none is
+ * left; info[i].precond_used says which ran; 0 keeps M_2l for all.  Errors:
  * MM_ERR_ARG for an unknown name or value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
@@ -274,7 +281,8 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
  * "plan_whole" (the plan a single-RHS product uses: 0 overlap-save segments,
  * 1 whole blocks two per transform, 2 whole blocks as half-length complex
  * transforms), "harvested" (Lanczos
- * vectors kept by the last M_BD solve), "device_bytes" (device memory in use).
+ * vectors kept by the last M_BD solve), "device_bytes" (device memory in use),
+ * "coarse_len" (samples per detector of the operator the basis was built from).
  * Errors: MM_ERR_ARG, MM_ERR_STATE. */
 mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value);
 

@@ -152,6 +152,10 @@ struct mm_ctx {
     std::vector<double> harv_alpha, harv_beta;
     // per right-hand-side coarse operators for batches of uneven length
     bool coarse_per_rhs = false;
+    int64_t coarse_len = 0;          // samples per detector of the operator the basis Z was built from
+    int64_t harvest_len = 0;         // samples per detector of the harvested right-hand side
+    int opt_coarse_fallback = 1;     // uneven batches: M_BD for right-hand sides of another length
+    std::vector<int32_t> precond_used;
     DevBuf d_AZr, d_Einvr;
     // template filters (mm_set_templates): F = F_B W^-1 F_G W^-1 F_B
     bool tmpl_on = false;
@@ -1434,7 +1438,7 @@ mm_status coarse_products_for_lens(mm_ctx* ctx, int f64) {
     return MM_OK;
 }
 
-mm_status coarse_for_lens(mm_ctx* ctx) {
+mm_status coarse_for_lens(mm_ctx* ctx, const std::vector<uint8_t>& deflate) {
     const int k = ctx->k, R = ctx->nrhs;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     TRY(coarse_products_for_lens(ctx, op_prec(ctx)));
@@ -1456,6 +1460,7 @@ mm_status coarse_for_lens(mm_ctx* ctx) {
             for (int j = 0; j < k; ++j) E[(size_t)i * k + j] = 0.5 * (g[(size_t)j * k + i] + g[(size_t)i * k + j]);
         if (!host_cholesky(E, k)) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not SPD");
         host_spd_inverse_from_chol(E, k, Einv);
+        if (!deflate[r]) std::fill(Einv.begin(), Einv.end(), 0.0);   // M_2l,r = M_BD,r
         std::copy(Einv.begin(), Einv.end(), Einv_all.begin() + (size_t)r * k * k);
     }
     CK(ctx->d_Einvr.ensure(Einv_all.size() * 8));
@@ -1973,6 +1978,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     TRY(orthonormalise(ctx, ctx->d_Z, ksel, &kk));
     ctx->k = kk;
     ctx->ritz.assign(vals.begin(), vals.begin() + std::min<size_t>(vals.size(), kk));
+    ctx->coarse_len = ctx->n_t;
     TRY(finish_coarse(ctx));
     if (k_out) *k_out = ctx->k;
     return MM_OK;
@@ -2009,6 +2015,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     TRY(orthonormalise(ctx, ctx->d_Z, ksel, &kk));
     ctx->k = kk;
     ctx->ritz.assign(vals.begin(), vals.begin() + std::min<size_t>(vals.size(), kk));
+    ctx->coarse_len = ctx->harvest_len > 0 ? ctx->harvest_len : ctx->n_t;
     TRY(finish_coarse(ctx));
     if (k_out) *k_out = ctx->k;
     return MM_OK;
@@ -2039,6 +2046,7 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     TRY(orthonormalise(ctx, ctx->d_Z, k, &kk));
     ctx->k = kk;
     ctx->ritz.assign(kk, 0.0);
+    ctx->coarse_len = ctx->n_t;
     TRY(finish_coarse(ctx));
     return MM_OK;
 }
@@ -2147,6 +2155,7 @@ mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes) {
     CK(cudaStreamSynchronize(ctx->stream));
     const double* rz = z3 + nv * 6 + (int64_t)k * k;
     ctx->ritz.assign(rz, rz + k);
+    ctx->coarse_len = ctx->n_t;
     ctx->k = k;
     return MM_OK;
 }
@@ -2200,9 +2209,27 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
         CK(ctx->d_bhist.ensure((size_t)nrhs * (max_iter + 1) * 8));
         ctx->harvest_on = true;
         ctx->harvest_count = 0;
+        ctx->harvest_len = ctx->use_lens ? ctx->lens[0] : ctx->n_t;
     }
     ctx->coarse_per_rhs = false;
-    if (ctx->use_lens && precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx));
+    ctx->precond_used.assign(nrhs, precond);
+    std::vector<uint8_t> deflate(nrhs, 1);
+    if (ctx->use_lens && precond == MM_PRECOND_2L && ctx->opt_coarse_fallback) {
+        // A basis deflates the small eigenmodes of the operator it was built from.  A prefix of
+        // another length covers the patch differently (other pixels are poorly hit), its small
+        // modes are not in span Z, and M_2l then costs more than M_BD for the same products: such
+        // right-hand sides run M_BD (E_i^-1 = 0 makes M_2l,i = M_BD,i); a batch with none left runs
+        // M_BD throughout.
+        const int64_t tolen = std::max<int64_t>(1, ctx->coarse_len / 100);
+        int n_defl = 0;
+        for (int i = 0; i < nrhs; ++i) {
+            deflate[i] = std::llabs(ctx->lens[i] - ctx->coarse_len) <= tolen;
+            n_defl += deflate[i];
+            if (!deflate[i]) ctx->precond_used[i] = MM_PRECOND_BD;
+        }
+        if (n_defl == 0) ctx->precond = MM_PRECOND_BD;
+    }
+    if (ctx->use_lens && ctx->precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx, deflate));
     TRY(get_plan(ctx, op_prec(ctx), nrhs, ctx->lens, &ctx->plan_op));
     TRY(get_plan(ctx, ctx->p64, nrhs, ctx->lens, &ctx->plan_64));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -2469,7 +2496,7 @@ mm_status mm_solve_end(mm_ctx* ctx, double* map_out, mm_solve_info* info, int me
             info[i].true_rel_res = ctx->true_res[i];
             info[i].t_solve_ms = ms;
             info[i].refinements = ctx->refinements[i];
-            info[i].pad = 0;
+            info[i].precond_used = i < (int)ctx->precond_used.size() ? ctx->precond_used[i] : (int32_t)ctx->precond;
         }
     }
     ctx->phase = PH_IDLE;
@@ -2515,6 +2542,8 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_half = v ? 1 : 0;
     } else if (n == "coarse_prefix") {
         ctx->opt_coarse_prefix = v ? 1 : 0;
+    } else if (n == "coarse_fallback") {
+        ctx->opt_coarse_fallback = v ? 1 : 0;
     } else if (n == "inner_tol") {
         if (!(value > 0.0) || value > 1e-2) return fail(ctx, MM_ERR_ARG, "inner_tol must lie in (0, 1e-2]");
         ctx->opt_inner_tol = value;
@@ -2552,6 +2581,8 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "half_transform") *value = ctx->opt_half;
     else if (n == "coarse_prefix") *value = ctx->opt_coarse_prefix;
+    else if (n == "coarse_fallback") *value = ctx->opt_coarse_fallback;
+    else if (n == "coarse_len") *value = (double)ctx->coarse_len;
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;
     else if (n == "apply_precision") *value = ctx->opt_apply_prec;

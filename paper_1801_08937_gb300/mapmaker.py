@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA", 
 class mm_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("rel_res", C.c_double),
                 ("true_rel_res", C.c_double), ("t_solve_ms", C.c_double),
-                ("refinements", C.c_int32), ("pad", C.c_int32)]
+                ("refinements", C.c_int32), ("precond_used", C.c_int32)]
 
 
 # (name, restype, argtypes) for every entry point of include/mapmaker.h
@@ -377,7 +377,8 @@ class Context:
 
 def _info_dict(i):
     return dict(iters=i.iters, status=STATUS_NAMES.get(i.status, i.status), rel_res=i.rel_res,
-                true_rel_res=i.true_rel_res, t_solve_ms=i.t_solve_ms, refinements=i.refinements)
+                true_rel_res=i.true_rel_res, t_solve_ms=i.t_solve_ms, refinements=i.refinements,
+                precond_used="M_2l" if i.precond_used == MM_PRECOND_2L else "M_BD")
 
 
 def fma_peak(device=0, fp64=False, seconds=1.0) -> float:

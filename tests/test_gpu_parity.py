@@ -417,6 +417,7 @@ def test_block_prefix_coarse_products_match_direct():
     for prefix in (0, 1):
         c = ctx_for(scan)
         c.set_option("coarse_prefix", prefix)
+        c.set_option("coarse_fallback", 0)   # every right-hand side runs M_2l
         c.build_bd()
         b = c.rhs(tods[0])
         assert c.build_coarse(b[0], m_max=40, eps_arn=1e-12, k=12) == 12
@@ -531,6 +532,7 @@ def test_batched_two_level_uneven_lengths(prec):
     tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 400 + i), synth.make_noise(scan, 400 + i))
                      for i in range(len(lens))])
     c = ctx_for(scan, prec)
+    c.set_option("coarse_fallback", 0)   # every right-hand side runs M_2l with its own A_i Z and E_i
     c.build_bd()
     tt = tods.astype(c.tod_dtype)
     c.build_coarse(c.rhs(tt[:1])[0], m_max=40, eps_arn=1e-8, k=8)
@@ -643,3 +645,35 @@ def test_coarse_space_export_import_round_trip_and_fingerprint():
         assert e.value.status == MM.MM_ERR_ARG
     for ctx in (c, c2, c3, c4):
         ctx.close()
+
+
+def test_uneven_batch_falls_back_to_bd_for_other_lengths():
+    """With "coarse_fallback" (default) a two-level batch of uneven length runs M_2l only for the
+    right-hand sides of the basis's own length: the others run M_BD (same products and maps as an M_BD
+    batch), and a batch with none of that length runs M_BD throughout."""
+    cfg = dict(nx=8, ny=8, n_det=4, n_t=8192, n_int=8, half_bw=64, f_knee=2.0)
+    scan = synth.make_scan(seed=52, **cfg)
+    lens = np.array([8192, 4500, 6000, 8192, 7333], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 500 + i), synth.make_noise(scan, 500 + i))
+                     for i in range(len(lens))])
+    c = ctx_for(scan)
+    c.build_bd()
+    c.build_coarse(c.rhs(tods[:1])[0], m_max=40, eps_arn=1e-10, k=8)
+    assert c.get_option("coarse_len") == 8192
+    x2, i2 = c.solve(tods, MM.MM_PRECOND_2L, tol=1e-10, max_iter=2000, rhs_len=lens)
+    xb, ib = c.solve(tods, MM.MM_PRECOND_BD, tol=1e-10, max_iter=2000, rhs_len=lens)
+    for i, L in enumerate(lens):
+        assert i2[i]["status"] == "MM_OK" and ib[i]["status"] == "MM_OK"
+        assert ib[i]["precond_used"] == "M_BD"
+        if L == 8192:
+            assert i2[i]["precond_used"] == "M_2l" and i2[i]["iters"] < ib[i]["iters"]
+        else:
+            assert i2[i]["precond_used"] == "M_BD"
+            assert abs(i2[i]["iters"] - ib[i]["iters"]) <= 1
+            assert_close(x2[i], xb[i], 1e-9)
+    short = lens[[1, 2, 4]]
+    x3, i3 = c.solve(tods[[1, 2, 4]], MM.MM_PRECOND_2L, tol=1e-10, max_iter=2000, rhs_len=short)
+    for j, i in enumerate((1, 2, 4)):
+        assert i3[j]["precond_used"] == "M_BD" and i3[j]["iters"] == ib[i]["iters"]
+        assert_close(x3[j], xb[i], 1e-9)
+    c.close()

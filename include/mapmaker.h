@@ -54,8 +54,10 @@ typedef enum {
     MM_ERR_BREAKDOWN = 6,      /* p^T A p <= 0 or a NaN appeared                  */
     MM_ERR_SINGULAR = 7,       /* coarse operator E is not SPD, or an eigen-solve */
                                /* of H_m / T_m did not converge                   */
-    MM_ERR_TIMEOUT = 8         /* reserved for a bounded device wait that gives   */
+    MM_ERR_TIMEOUT = 8,        /* reserved for a bounded device wait that gives   */
                                /* up; no kernel of this library waits on another  */
+    MM_ERR_REDUCE = 9          /* the caller's cross-rank sum (mm_set_reduction)  */
+                               /* reported a failure                              */
 } mm_status;
 
 typedef enum {
@@ -216,6 +218,31 @@ mm_status mm_get_coarse(mm_ctx* ctx, double* Z_out, double* ritz_out, int32_t* k
  *   MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_export_coarse(mm_ctx* ctx, void* buf, int64_t* bytes);
 mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes);
+
+/* Sum over ranks for a map-making problem whose timeline is split across
+ * processes (one GPU each): A = P^T W P and b = P^T W d are sums over the
+ * stationary blocks (Sect. 3, Eq. linearsystem), so a rank that sets up the
+ * pointing of its own blocks (mm_setup_pointing with its samples only, the
+ * same n_pix on every rank) forms partial products, and one element-wise sum
+ * of each partial map over the ranks completes them; the PCG vectors, dot
+ * products, M_BD and the coarse space are then replicated and every rank
+ * follows the same iterations.  The library calls
+ *     fn(buf, count, elem_bytes, user)
+ * after every operator product (A x, b, the refinement residuals; 4 values
+ * per pixel and right-hand side, the fourth 0) and on the M_BD sums (7 per
+ * pixel); fn must replace buf by its sum over all ranks, in place, before it
+ * returns, and return 0 (anything else fails the call with MM_ERR_REDUCE).
+ * elem_bytes is 4 (float32 products) or 8 (float64).  on_device = 1 passes the
+ * device buffer (for a device collective such as an NCCL all-reduce; the
+ * context's stream is synchronised before the call); 0 stages it through a
+ * host buffer (for a host collective such as gloo or MPI).  Every rank must
+ * make the same sequence of calls.  fn = NULL switches the reduction off.
+ * While a reduction is set, right-hand sides of uneven length, template
+ * filters and captured CUDA graphs are refused (MM_ERR_ARG) or not used, and
+ * automatic plan tuning runs without calling fn.
+ * Errors: MM_ERR_ARG. */
+typedef int (*mm_reduce_fn)(void* buf, int64_t count, int32_t elem_bytes, void* user);
+mm_status mm_set_reduction(mm_ctx* ctx, mm_reduce_fn fn, void* user, int on_device);
 
 /* Solve A x = b for nrhs timelines with PCG (Sect. 3, Eq. pcg), x_0 = 0,
  * stopping when ||r_k|| / ||b|| <= tol (recurrence residual) or after max_iter

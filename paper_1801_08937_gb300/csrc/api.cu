@@ -156,6 +156,13 @@ struct mm_ctx {
     int64_t harvest_len = 0;         // samples per detector of the harvested right-hand side
     int opt_coarse_fallback = 1;     // uneven batches: M_BD for right-hand sides of another length
     std::vector<int32_t> precond_used;
+    // cross-rank sum of partial products (timeline split across processes)
+    mm_reduce_fn reduce_fn = nullptr;
+    void* reduce_user = nullptr;
+    int reduce_dev = 0;
+    bool tuning = false;               // autotuner runs: products are timed, not used
+    void* reduce_host = nullptr;       // pinned staging buffer
+    size_t reduce_host_bytes = 0;
     DevBuf d_AZr, d_Einvr;
     // template filters (mm_set_templates): F = F_B W^-1 F_G W^-1 F_B
     bool tmpl_on = false;
@@ -209,6 +216,36 @@ mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
         mm_status s_ = (expr);         \
         if (s_ != MM_OK) return s_;    \
     } while (0)
+
+// Sum of a partial product over the ranks that share the problem (see
+// mm_set_reduction); nothing without a reduction or while plans are tuned.
+mm_status reduce_sum(mm_ctx* ctx, void* dev, int64_t count, int elem) {
+    if (!ctx->reduce_fn || ctx->tuning || count <= 0) return MM_OK;
+    if (ctx->capturing) return fail(ctx, MM_ERR_STATE, "a cross-rank reduction cannot run inside a graph capture");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t bytes = (size_t)count * elem;
+    int rc = 0;
+    if (ctx->reduce_dev) {
+        rc = ctx->reduce_fn(dev, count, elem, ctx->reduce_user);
+    } else {
+        if (ctx->reduce_host_bytes < bytes) {
+            if (ctx->reduce_host) cudaFreeHost(ctx->reduce_host);
+            ctx->reduce_host = nullptr;
+            ctx->reduce_host_bytes = 0;
+            CK(cudaMallocHost(&ctx->reduce_host, bytes));
+            ctx->reduce_host_bytes = bytes;
+        }
+        CK(cudaMemcpyAsync(ctx->reduce_host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        rc = ctx->reduce_fn(ctx->reduce_host, count, elem, ctx->reduce_user);
+        if (rc == 0) {
+            CK(cudaMemcpyAsync(dev, ctx->reduce_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    if (rc != 0) return fail(ctx, MM_ERR_REDUCE, "the cross-rank reduction returned " + std::to_string(rc));
+    return MM_OK;
+}
 
 bool is_f32(const mm_ctx* c) { return c->prec == MM_FP32_MIXED; }
 // Precision of the solver's operator products (PCG, Arnoldi, A Z): float32 in
@@ -836,6 +873,7 @@ mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_
     best->ms = 1e300;
     const int saved_time = ctx->opt_time_filter;
     ctx->opt_time_filter = 0;
+    ctx->tuning = true;
     for (const Opt& o : opts) {
         Plan* p = nullptr;
         TRY(make_plan(ctx, f64, nrhs, lens, o.variant, o.L, o.whole, o.V, &p));
@@ -855,6 +893,7 @@ mm_status autotune_plan(mm_ctx* ctx, int f64, int nrhs, const std::vector<int64_
         if (ms_best < best->ms) *best = TuneVal{o.variant, o.L, o.whole, o.V, ms_best};
     }
     ctx->opt_time_filter = saved_time;
+    ctx->tuning = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return MM_OK;
@@ -968,6 +1007,8 @@ mm_status run_filter(mm_ctx* ctx, Plan* plan, bool from_tod, const void* src, vo
     }
     CKL();
     if (e1) CK(cudaEventRecord(e1, ctx->stream));
+    if (ctx->reduce_fn && !ctx->tuning)
+        TRY(reduce_sum(ctx, dst, (int64_t)4 * ctx->n_pix * plan->nrhs, plan->f64 ? 8 : 4));
     return MM_OK;
 }
 
@@ -1528,6 +1569,7 @@ mm_status mm_destroy(mm_ctx* ctx) {
         cudaEventDestroy(pr.second);
     }
     if (ctx->h_st_pinned) cudaFreeHost(ctx->h_st_pinned);
+    if (ctx->reduce_host) cudaFreeHost(ctx->reduce_host);
     if (ctx->ev_state) cudaEventDestroy(ctx->ev_state);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1646,6 +1688,7 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     CK(dev_scope.err);
     NvtxRange nvtx_range(__func__);
     if (!ctx->have_pointing) return fail(ctx, MM_ERR_STATE, "mm_set_templates: set the pointing first");
+    if (ctx->reduce_fn) return fail(ctx, MM_ERR_ARG, "mm_set_templates: not supported with a cross-rank reduction");
     if (mem != MM_HOST && mem != MM_DEVICE) return fail(ctx, MM_ERR_ARG, "mem must be MM_HOST or MM_DEVICE");
     ctx->have_bd = false;   // M_BD and any coarse space belong to the previous operator
     ctx->k = 0;
@@ -1727,6 +1770,8 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
     launch_bd_accumulate(ctx->d_pix.as<int32_t>(), ctx->d_psi.as<float>(), ctx->d_block_off.as<int64_t>(),
                          ctx->d_block_band.as<int32_t>(), ctx->d_band64.as<double>(), ctx->lam + 1, ctx->n_blocks, 0,
                          ctx->n_t, d_len.as<int64_t>(), 1, ctx->d_sums.as<double>(), n_pix, ctx->stream);
+    CKL();
+    TRY(reduce_sum(ctx, ctx->d_sums.p, (int64_t)n_pix * 7, 8));
     launch_bd_invert(ctx->d_sums.as<double>(), ctx->d_bd.as<double>(), ctx->d_good.as<uint8_t>(),
                      ctx->d_dropped.as<int>(), n_pix, 1, rcond_min, 1, ctx->stream, ctx->tmpl_on ? ctx->tmpl_qu : 0);
     launch_flag_samples(ctx->d_pix.as<int32_t>(), ctx->d_good.as<uint8_t>(), ctx->n_samples, ctx->stream);
@@ -2160,6 +2205,17 @@ mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes) {
     return MM_OK;
 }
 
+mm_status mm_set_reduction(mm_ctx* ctx, mm_reduce_fn fn, void* user, int on_device) {
+    if (!ctx) return MM_ERR_ARG;
+    if (ctx->phase != PH_IDLE) return fail(ctx, MM_ERR_STATE, "mm_set_reduction: a solve is in progress");
+    if (fn && ctx->tmpl_on) return fail(ctx, MM_ERR_ARG, "mm_set_reduction: not supported with template filters");
+    ctx->reduce_fn = fn;
+    ctx->reduce_user = user;
+    ctx->reduce_dev = on_device ? 1 : 0;
+    destroy_graph(ctx);
+    return MM_OK;
+}
+
 mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64_t* rhs_len, mm_precond precond,
                          double tol, int32_t max_iter, int mem) {
     if (!ctx) return MM_ERR_ARG;
@@ -2171,6 +2227,8 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
     if (rhs_len)
         for (int i = 0; i < nrhs; ++i)
             if (rhs_len[i] <= 0 || rhs_len[i] > ctx->n_t) return fail(ctx, MM_ERR_ARG, "rhs_len out of (0, n_t]");
+    if (rhs_len && ctx->reduce_fn)
+        return fail(ctx, MM_ERR_ARG, "right-hand sides of uneven length are not supported with a cross-rank reduction");
     DeviceScope dev_scope(ctx->device);
     CK(dev_scope.err);
     NvtxRange nvtx_range(__func__);
@@ -2360,7 +2418,7 @@ static mm_status launch_iters(mm_ctx* ctx, int32_t n_iter) {
     NvtxRange nvtx_range("pcg_iterations");
     const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy &&
                             ctx->stream != cudaStreamPerThread;
-    if (ctx->opt_graphs && capturable && n_iter == ctx->opt_check_every) {
+    if (ctx->opt_graphs && capturable && !ctx->reduce_fn && n_iter == ctx->opt_check_every) {
         if (!ctx->graph_exec) {
             // one eager iteration first so every kernel attribute is configured
             TRY(pcg_iteration(ctx));
@@ -2419,6 +2477,7 @@ mm_status mm_solve_launch(mm_ctx* ctx, int32_t n_iter) {
     TRY(launch_iters(ctx, n_iter));
     if (!ctx->h_st_pinned || ctx->h_st_pinned_n < ctx->nrhs) {
         if (ctx->h_st_pinned) cudaFreeHost(ctx->h_st_pinned);
+    if (ctx->reduce_host) cudaFreeHost(ctx->reduce_host);
         ctx->h_st_pinned = nullptr;
         CK(cudaMallocHost(reinterpret_cast<void**>(&ctx->h_st_pinned), ctx->nrhs * sizeof(RhsState)));
         ctx->h_st_pinned_n = ctx->nrhs;

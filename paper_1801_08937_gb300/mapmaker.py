@@ -17,13 +17,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmapmaker.so")
 
 MM_OK, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_STATE = 0, 1, 2, 3, 4
-MM_ERR_NOT_CONVERGED, MM_ERR_BREAKDOWN, MM_ERR_SINGULAR, MM_ERR_TIMEOUT = 5, 6, 7, 8
+MM_ERR_NOT_CONVERGED, MM_ERR_BREAKDOWN, MM_ERR_SINGULAR, MM_ERR_TIMEOUT, MM_ERR_REDUCE = 5, 6, 7, 8, 9
 MM_FP64, MM_FP32_MIXED = 0, 1
 MM_PRECOND_BD, MM_PRECOND_2L = 0, 1
 MM_HOST, MM_DEVICE = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA", 4: "MM_ERR_STATE",
-                5: "MM_ERR_NOT_CONVERGED", 6: "MM_ERR_BREAKDOWN", 7: "MM_ERR_SINGULAR", 8: "MM_ERR_TIMEOUT"}
+                5: "MM_ERR_NOT_CONVERGED", 6: "MM_ERR_BREAKDOWN", 7: "MM_ERR_SINGULAR", 8: "MM_ERR_TIMEOUT",
+                9: "MM_ERR_REDUCE"}
 
 
 class mm_solve_info(C.Structure):
@@ -61,7 +62,11 @@ SIGNATURES = [
     ("mm_export_coarse", C.c_int, [_VP, _VP, C.POINTER(_I64)]),
     ("mm_import_coarse", C.c_int, [_VP, _VP, _I64]),
     ("mm_fma_peak", C.c_int, [C.c_int, C.c_int, _D, C.POINTER(_D)]),
+    ("mm_set_reduction", C.c_int, [_VP, _VP, _VP, C.c_int]),
 ]
+
+# mm_reduce_fn: int fn(void* buf, int64_t count, int32_t elem_bytes, void* user)
+REDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p)
 
 _lib = None
 
@@ -299,6 +304,32 @@ class Context:
         self._check(self.lib.mm_get_coarse(self.h, C.c_void_p(Z.ctypes.data), C.c_void_p(ritz.ctypes.data),
                                            C.byref(k)))
         return Z, ritz
+
+    def set_reduction(self, fn, on_device=False):
+        """Sum of partial products over ranks that each hold part of the timeline (mm_set_reduction).
+
+        fn(arr) receives a numpy view (float32 or float64) of a host staging buffer and must replace it
+        in place by its element-wise sum over all ranks (e.g. torch.distributed.all_reduce on
+        torch.from_numpy(arr) with gloo); with on_device=True, fn(ptr, count, elem_bytes) receives the
+        device pointer instead.  fn=None switches the reduction off."""
+        if fn is None:
+            self._check(self.lib.mm_set_reduction(self.h, None, None, 0))
+            self._reduce_cb = None
+            return
+
+        def cb(ptr, count, elem, user):
+            try:
+                if on_device:
+                    return int(fn(ptr, count, elem) or 0)
+                ct = C.c_float if elem == 4 else C.c_double
+                fn(np.ctypeslib.as_array((ct * count).from_address(ptr)))
+                return 0
+            except Exception:   # reported as MM_ERR_REDUCE by the library
+                return 1
+
+        self._reduce_cb = REDUCE_FN(cb)
+        self._check(self.lib.mm_set_reduction(self.h, C.cast(self._reduce_cb, C.c_void_p), None,
+                                              int(bool(on_device))))
 
     def export_coarse(self) -> bytes:
         """Checkpoint of the coarse space (Z, A Z, E^-1, Ritz values, operator fingerprint)."""

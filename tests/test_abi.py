@@ -153,7 +153,7 @@ def test_binding_argument_types_match_the_header():
 
     def kind_c(param):
         param = " ".join(param.split())
-        if "*" in param:
+        if "*" in param or param.startswith("mm_reduce_fn"):
             return "ptr"
         if param.startswith("int64_t"):
             return "i64"

@@ -66,7 +66,8 @@ def parse():
                     help="templates mode, fp64: operator products in native float64 (1) or double-float (2, default)")
     ap.add_argument("--stokes", type=int, default=1, choices=[0, 1, 2],
                     help="templates mode: 1 Q/U maps from d^-, 2 I maps from d^+, 0 I/Q/U")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates",
+                                                       "subsets"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
                          "apply: A x alone (profiling)")
     ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
@@ -77,6 +78,8 @@ def parse():
     ap.add_argument("--half", type=int, default=1, choices=[0, 1],
                     help="apply mode: allow whole blocks as half-length complex transforms")
     ap.add_argument("--n-rhs", type=int, default=64)
+    ap.add_argument("--n-subsets", type=int, default=16, help="subsets mode: data subsets of one patch")
+    ap.add_argument("--subset-cap", type=int, default=100, help="subsets mode: PCG iteration cap (as the paper's)")
     ap.add_argument("--mc-m-max", type=int, default=300, help="mc mode: Arnoldi steps of the shared basis")
     ap.add_argument("--mc-eps-arn", type=float, default=1e-12, help="mc mode: Arnoldi tolerance")
     ap.add_argument("--requests", type=int, default=120)
@@ -348,6 +351,8 @@ def main():
         return run_scale(args, world, rank, local)
     if args.mode == "templates":
         return run_templates(args, world, rank, local)
+    if args.mode == "subsets":
+        return run_subsets(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -747,6 +752,83 @@ def run_templates(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+# ---------------- divide and conquer: active vs simplified coarse spaces (Sect. 7) ----------------
+def run_subsets(args, world, rank, local):
+    """The paper's divide-and-conquer comparison on the GPU: several data subsets of one patch (c1
+    geometry, other detector offsets, raster phases and noise per subset) are each solved with M_BD,
+    with M_2l whose basis is built on that subset (the "active" approach, Arnoldi to eps_Arn 1e-6 and
+    1e-12), and with M_2l whose basis comes from the first subset only (the "simplified" approach,
+    mm_get_coarse / mm_set_coarse, Arnoldi to 1e-12), every solve capped at a fixed number of
+    iterations; reports the median final residual, iterations and time with the set-up included."""
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    torch.cuda.set_device(local)
+    k = 25   # the paper's dim Z
+    cfg = dict(synth.CONFIGS[args.config if args.config != "c2" else "c1"])
+    subs = []
+    t_gen = time.time()
+    for i in range(args.n_subsets):
+        scan = synth.make_scan(seed=2000 + i + 1000 * rank, **cfg)
+        d = synth.make_tod(scan, synth.make_sky(scan.n_pix, 7 + rank), synth.make_noise(scan, 2000 + i))
+        subs.append((scan, d))
+    t_gen = time.time() - t_gen
+
+    def tmark():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    res = {name: {"res": [], "iters": [], "s": []} for name in ("m_bd", "active_1e-6", "simplified", "active_1e-12")}
+    Z0 = None
+    for i, (scan, d) in enumerate(subs):
+        c = M.Context(local, None, M.MM_FP64)
+        c.setup_scan(scan)
+        c.build_bd(1e-3)
+        t0 = tmark()
+        _, inf = c.solve(d, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.subset_cap)
+        t1 = tmark()
+        res["m_bd"]["res"].append(inf[0]["true_rel_res"])
+        res["m_bd"]["iters"].append(inf[0]["iters"])
+        res["m_bd"]["s"].append(t1 - t0)
+        for name, eps in (("active_1e-6", 1e-6), ("active_1e-12", 1e-12)):
+            t0 = tmark()
+            c.build_coarse(None, m_max=args.mc_m_max, eps_arn=eps, k=k)
+            _, inf = c.solve(d, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.subset_cap)
+            t1 = tmark()
+            res[name]["res"].append(inf[0]["true_rel_res"])
+            res[name]["iters"].append(inf[0]["iters"])
+            res[name]["s"].append(t1 - t0)
+            if i == 0 and eps == 1e-12:
+                Z0 = c.get_coarse()[0]
+        t0 = tmark()
+        if i == 0:
+            c.build_coarse(None, m_max=args.mc_m_max, eps_arn=1e-12, k=k)   # the one basis, built once
+        else:
+            c.set_coarse(Z0)
+        _, inf = c.solve(d, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.subset_cap)
+        t1 = tmark()
+        res["simplified"]["res"].append(inf[0]["true_rel_res"])
+        res["simplified"]["iters"].append(inf[0]["iters"])
+        res["simplified"]["s"].append(t1 - t0)
+        c.close()
+    table = {}
+    for name, r in res.items():
+        rr = np.array(r["res"])
+        table[name] = {"median_true_rel_res": float(np.median(rr)),
+                       "spread_16_84": [float(np.percentile(rr, 16)), float(np.percentile(rr, 84))],
+                       "iters_mean": float(np.mean(r["iters"])), "reached_tol": int(np.sum(rr <= args.tol)),
+                       "time_total_s": float(np.sum(r["s"])), "time_per_subset_s": float(np.mean(r["s"]))}
+    if rank == 0:
+        print(json.dumps({"mode": "subsets", "metric": "final residual and time per subset (Sect. 7, Table 2 layout)",
+                          "workload": f"{args.n_subsets} subsets of one {cfg['nx']}x{cfg['ny']} patch, "
+                                      f"{cfg['n_det']} det x {cfg['n_t']} samples, lambda {cfg['half_bw']}; "
+                                      f"PCG to {args.tol:g}, at most {args.subset_cap} iterations; k = {k}; "
+                                      f"Arnoldi up to {args.mc_m_max} steps; MM_FP64",
+                          "results": table, "gen_s": t_gen}), flush=True)
 
 
 # ---------------- mixed precision at scale (c4) ----------------

@@ -132,7 +132,75 @@ __device__ void project_poly(T* y, const TmplArgs& t, int blk, int64_t b0) {
     }
 }
 
-template <typename T, bool FROM_TOD, int K>
+// Map components a pointing row touches: stokes 0 (I, Q, U), 1 (Q, U: the
+// differenced timeline), 2 (I: the summed timeline).
+template <int ST> struct StokesCols { static constexpr int n = 3, c0 = 0; };
+template <> struct StokesCols<1> { static constexpr int n = 2, c0 = 1; };
+template <> struct StokesCols<2> { static constexpr int n = 1, c0 = 0; };
+
+template <typename A> __device__ __forceinline__ A& vcomp(V4<A>* q, int c) {
+    return c == 0 ? q->x : (c == 1 ? q->y : q->z);
+}
+
+// P^T of a warp's 128 consecutive samples (four per lane) for NC map
+// components starting at C0: in-lane suffix sums over runs of equal pixels,
+// the lane's last run continued through later lanes by doubling (as in the
+// float32 half-length scatter), one atomic per run and component.
+template <typename T, int NC, int C0>
+__device__ __forceinline__ void tmpl_run_scatter(const int (&p)[4], T (&v)[NC][4], V4<typename AccT<T>::type>* q) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool e01 = p[0] == p[1], e12 = p[1] == p[2], e23 = p[2] == p[3];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (e23) v[c][2] += v[c][3];
+        if (e12) v[c][1] += v[c][2];
+        if (e01) v[c][0] += v[c][1];
+    }
+    const bool whole = e01 && e12 && e23;
+    const int pnext = __shfl_down_sync(FULL, p[0], 1);
+    const bool cont = lane < 31 && pnext == p[3];
+    T x[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        x[c] = shfl_down_t(v[c][0], 1);
+        if (!cont) x[c] = T(0);
+    }
+    // every lane takes part in each shuffle (no short-circuit around it)
+    const bool wnext = __shfl_down_sync(FULL, (int)whole, 1) != 0;
+    bool chain = cont && wnext;
+#pragma unroll 1
+    for (int d = 1; __any_sync(FULL, chain); d <<= 1) {
+        T y[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) y[c] = shfl_down_t(x[c], d);
+        const bool cn = __shfl_down_sync(FULL, (int)chain, d) != 0;
+        if (chain) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) x[c] += y[c];
+        }
+        chain = chain && cn;
+    }
+    const int plast = __shfl_up_sync(FULL, p[3], 1);
+    const bool head[4] = {lane == 0 || p[0] != plast, !e01, !e12, !e23};
+    const bool reach[4] = {whole, e12 && e23, e23, true};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (head[j] && p[j] >= 0) {
+            V4<typename AccT<T>::type>* dst = q + p[j];
+            if constexpr (NC == 3 && std::is_same<T, float>::value) {
+                atomic_add3(dst, reach[j] ? v[0][j] + x[0] : v[0][j], reach[j] ? v[1][j] + x[1] : v[1][j],
+                            reach[j] ? v[2][j] + x[2] : v[2][j]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    atomicAdd(&vcomp(dst, C0 + c), to_acc(reach[j] ? v[c][j] + x[c] : v[c][j]));
+            }
+        }
+    }
+}
+
+template <typename T, bool FROM_TOD, int K, int ST>
 __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, const TmplArgs t) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int blk = blockIdx.x, rhs = blockIdx.y;
@@ -144,8 +212,8 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
     T* y = reinterpret_cast<T*>(smraw);
     Acc* gsum = reinterpret_cast<Acc*>(y + ((nb + 1) & ~1));
     int* gcnt = reinterpret_cast<int*>(gsum + t.n_bins);
-    const T iw = t.stokes == 1 ? T(0) : T(1);   // I column of P
-    const T pw = t.stokes == 2 ? T(0) : T(1);   // Q, U columns
+    const T iw = ST == 1 ? T(0) : T(1);   // I column of P
+    const T pw = ST == 2 ? T(0) : T(1);   // Q, U columns
     const V4<T>* xm = nullptr;
     if (!FROM_TOD) xm = reinterpret_cast<const V4<T>*>(a.src) + (int64_t)rhs * a.n_pix;
     else if (a.xmap) xm = reinterpret_cast<const V4<T>*>(a.xmap) + (int64_t)rhs * a.n_pix;
@@ -156,7 +224,8 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
             const int64_t t0 = b0 + i0;
             int p[4];
             float ps[4];
-            load4(a, t0, true, nb - i0, p, ps);
+            if constexpr (ST == 2) load4_pix(a, t0, true, nb - i0, p);   // intensity rows need no angle
+            else load4(a, t0, true, nb - i0, p, ps);
             T v[4] = {T(0), T(0), T(0), T(0)};
             if (FROM_TOD) {
 #pragma unroll
@@ -173,9 +242,14 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (p[j] >= 0) {
-                        T c, s;
-                        weights_from(a, t0 + j, ps[j], c, s);
-                        const T px = iw * m[j].x + pw * (c * m[j].y + s * m[j].z);
+                        T px;
+                        if constexpr (ST == 2) {
+                            px = m[j].x;
+                        } else {
+                            T c, s;
+                            weights_from(a, t0 + j, ps[j], c, s);
+                            px = ST == 1 ? c * m[j].y + s * m[j].z : m[j].x + (c * m[j].y + s * m[j].z);
+                        }
                         v[j] = FROM_TOD ? v[j] - px : px;
                     }
             }
@@ -265,20 +339,24 @@ __global__ void __launch_bounds__(TMPL_NT) k_filter_tmpl(const FilterArgs a, con
             const int64_t t0 = b0 + i0;
             int p[4];
             float ps[4];
-            load4(a, t0, i0 < nb, nb - i0, p, ps);
-            T v0[4], v1[4], v2[4];
+            if constexpr (ST == 2) load4_pix(a, t0, i0 < nb, nb - i0, p);
+            else load4(a, t0, i0 < nb, nb - i0, p, ps);
+            constexpr int NC = StokesCols<ST>::n;
+            T v[NC][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                T z = T(0), c = T(0), sn = T(0);
-                if (p[j] >= 0) {
-                    z = wb * y[i0 + j];
-                    weights_from(a, t0 + j, ps[j], c, sn);
+                const T z = (p[j] >= 0 && i0 + j < nb) ? wb * y[min(i0 + j, nb - 1)] : T(0);
+                if constexpr (ST == 2) {
+                    v[0][j] = z;
+                } else {
+                    T c = T(0), sn = T(0);
+                    if (p[j] >= 0) weights_from(a, t0 + j, ps[j], c, sn);
+                    if constexpr (ST == 0) v[0][j] = z;
+                    v[NC - 2][j] = z * c;
+                    v[NC - 1][j] = z * sn;
                 }
-                v0[j] = iw * z;
-                v1[j] = pw * z * c;
-                v2[j] = pw * z * sn;
             }
-            scatter4_vals(p, v0, v1, v2, q);
+            tmpl_run_scatter<T, NC, StokesCols<ST>::c0>(p, v, q);
         }
         return;
     }
@@ -303,15 +381,23 @@ size_t tmpl_smem_bytes(int64_t max_block, int n_bins, bool f64) {
     return (size_t)((max_block + 1) & ~1LL) * e + (size_t)n_bins * (e + 4);
 }
 
-template <typename T, bool FROM_TOD, int K>
-static void launch_tmpl_k(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
+template <typename T, bool FROM_TOD, int K, int ST>
+static void launch_tmpl_ks(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
     const size_t sm = tmpl_smem_bytes(t.max_block, t.n_bins, sizeof(T) == 8);
     static std::atomic<size_t> configured{0};
     raise_smem_once(configured, sm, [](size_t v) {
-        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
+        cudaFuncSetAttribute(k_filter_tmpl<T, FROM_TOD, K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v);
     });
-    k_filter_tmpl<T, FROM_TOD, K><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
+    k_filter_tmpl<T, FROM_TOD, K, ST><<<dim3(t.n_blocks, nrhs), TMPL_NT, sm, s>>>(a, t);
     count_launches(1);
+}
+template <typename T, bool FROM_TOD, int K>
+static void launch_tmpl_k(const FilterArgs& a, const TmplArgs& t, int nrhs, cudaStream_t s) {
+    switch (t.stokes) {
+        case 1: return launch_tmpl_ks<T, FROM_TOD, K, 1>(a, t, nrhs, s);
+        case 2: return launch_tmpl_ks<T, FROM_TOD, K, 2>(a, t, nrhs, s);
+        default: return launch_tmpl_ks<T, FROM_TOD, K, 0>(a, t, nrhs, s);
+    }
 }
 
 template <typename T, bool FROM_TOD>

@@ -67,9 +67,10 @@ def parse():
     ap.add_argument("--stokes", type=int, default=1, choices=[0, 1, 2],
                     help="templates mode: 1 Q/U maps from d^-, 2 I maps from d^+, 0 I/Q/U")
     ap.add_argument("--mode", default="solve", choices=["solve", "mc", "serve", "apply", "scale", "templates",
-                                                       "subsets"],
+                                                       "subsets", "coarse"],
                     help="solve: c2 maps on a resident scan; mc: batched Monte Carlo (c3); serve: request stream; "
-                         "apply: A x alone (profiling)")
+                         "apply: A x alone (profiling); coarse: M_2l on a batch, tensor-core vs float64 coarse "
+                         "products")
     ap.add_argument("--n-det", type=int, default=0, help="apply mode: detectors kept from the config (0: all)")
     ap.add_argument("--half-bw", type=int, default=-1, help="apply mode: band half-width override")
     ap.add_argument("--filter", type=int, default=0, help="apply mode: 0 autotuned, 1 direct band, 2 FFT")
@@ -83,6 +84,8 @@ def parse():
     ap.add_argument("--mc-m-max", type=int, default=300, help="mc mode: Arnoldi steps of the shared basis")
     ap.add_argument("--mc-eps-arn", type=float, default=1e-12, help="mc mode: Arnoldi tolerance")
     ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--coarse-nx", type=int, default=512, help="coarse mode: square patch side")
+    ap.add_argument("--coarse-k", type=int, default=64, help="coarse mode: coarse-space dimension")
     return ap.parse_args()
 
 
@@ -353,6 +356,8 @@ def main():
         return run_templates(args, world, rank, local)
     if args.mode == "subsets":
         return run_subsets(args, world, rank, local)
+    if args.mode == "coarse":
+        return run_coarse(args, world, rank, local)
     import torch
     import synth
     import __graft_entry__ as G
@@ -975,6 +980,71 @@ def run_apply(args, world, rank, local):
     ctx.close()
 
 
+# ---------------- M_2l on a batch: tensor-core vs float64 coarse products ----------------
+def run_coarse(args, world, rank, local):
+    """M_2l R for n_rhs right-hand sides on a large square patch with a k-vector coarse space
+    (Sect. 3.2, Eq. m2l): the coarse products Z^T R, Z U, AZ U on the tensor cores (tc_coarse 2)
+    and in float64 on the CUDA cores (tc_coarse 0), each timed with CUDA events on the
+    context's stream over --steps calls after --warmup calls.  Inputs (Z, AZ, R: 3 x 400 MB at the
+    default 512 x 512, k = 64, 64 right-hand sides) are larger than L2."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__ as G
+    G.build()
+    from paper_1801_08937_gb300 import mapmaker as M
+    torch.cuda.set_device(local)
+    nx, k, nrhs = args.coarse_nx, args.coarse_k, args.n_rhs
+    scan = synth.make_scan(nx=nx, ny=nx, n_det=16, n_t=1 << 18, n_int=4, half_bw=16, f_knee=1.0, seed=72 + rank)
+    stream = torch.cuda.current_stream()
+    ctx = M.Context(local, stream.cuda_stream, M.MM_FP64)
+    ctx.setup_scan(scan)
+    ctx.build_bd()
+    rng = np.random.default_rng(72 + rank)
+    ctx.set_coarse(rng.standard_normal((k, scan.n_pix, 3)))
+    x = torch.from_numpy(rng.standard_normal((nrhs, scan.n_pix, 3))).cuda()
+    y = torch.empty_like(x)
+    res = {}
+    clk = ClockSampler(local)
+    clk.start()
+    for name, tc in (("tensor_core", 2), ("float64", 0)):
+        ctx.set_option("tc_coarse", tc)
+        for _ in range(max(3, args.warmup)):
+            ctx.apply_precond(M.MM_PRECOND_2L, x, out=y)
+        l0 = ctx.get_option("kernel_launches")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.apply_precond(M.MM_PRECOND_2L, x, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = {"ms_per_call": e0.elapsed_time(e1) / args.steps,
+                     "launches_per_call": (ctx.get_option("kernel_launches") - l0) / args.steps}
+    clocks = clk.stop()
+    ctx.close()
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n4 = 4 * scan.n_pix
+    # algorithmic bytes: R, Z, AZ read and M_2l R written once (stored 4 doubles per pixel), M_BD's
+    # six doubles per pixel; the tensor-core path reads R and Z a second time
+    alg = (2 * nrhs + 2 * k) * n4 * 8 + 48 * scan.n_pix
+    moved = (3 * nrhs + 3 * k) * n4 * 8 + 48 * scan.n_pix
+    t = res["tensor_core"]["ms_per_call"] * 1e-3
+    flops = 3 * 2 * 2 * k * nrhs * n4   # Z^T R, Z U, AZ U; three TF32 products each
+    print(json.dumps({"mode": "coarse", "n_pix": scan.n_pix, "k": k, "n_rhs": nrhs, **res,
+                      "speedup_vs_float64": res["float64"]["ms_per_call"] / res["tensor_core"]["ms_per_call"],
+                      "algorithmic_bytes": alg, "bytes_moved_by_design": moved,
+                      "hbm_gbs_algorithmic": alg / t / 1e9, "hbm_frac_of_measured": alg / t / 1e9 / hbm,
+                      "tf32_tflops": flops / t / 1e12, "inputs": "larger than L2", "clocks": clocks}), flush=True)
+
+
 # ---------------- batched Monte Carlo (c3) ----------------
 def run_mc(args, world, rank, local):
     """64 right-hand sides of uneven length on the c1 geometry, one launch per
@@ -1043,6 +1113,12 @@ def run_mc(args, world, rank, local):
     batched(M.MM_PRECOND_2L, None)
     ms_sh, inf_sh = timed(lambda: batched(M.MM_PRECOND_2L, None), max(1, args.steps))
     ms_shbd, inf_shbd = timed(lambda: batched(M.MM_PRECOND_BD, None), max(1, args.steps))
+    # the same with the coarse products on the tensor cores whatever the map size (the default
+    # keeps maps this small on the CUDA cores in float64)
+    ctx.set_option("tc_coarse", 2)
+    batched(M.MM_PRECOND_2L, None)
+    ms_shtc, inf_shtc = timed(lambda: batched(M.MM_PRECOND_2L, None), max(1, args.steps))
+    ctx.set_option("tc_coarse", 1)
     # single right-hand side solves of the same maps, one at a time
     n_single = min(4, args.n_rhs)
     one = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
@@ -1076,6 +1152,10 @@ def run_mc(args, world, rank, local):
                          "two_level_iters_mean": float(np.mean([i["iters"] for i in inf_sh])),
                          "m_bd_time_per_map_s": ms_shbd / 1e3 / args.n_rhs,
                          "m_bd_iters_mean": float(np.mean([i["iters"] for i in inf_shbd])),
+                         "coarse_products": ("float64 CUDA cores (tc_coarse 1 keeps maps under 16384 pixels "
+                                             "there)" if scan.n_pix < 16384 else "tensor cores (tcgen05, TF32 pairs)"),
+                         "two_level_tensor_core_coarse_time_per_map_s": ms_shtc / 1e3 / args.n_rhs,
+                         "two_level_tensor_core_coarse_iters_mean": float(np.mean([i["iters"] for i in inf_shtc])),
                          "converged": sum(1 for i in inf_sh if i["status"] == "MM_OK")},
             "single_rhs": single, "setup_once_s": setup_ms / 1e3, "gen_s": t_gen}
     if rank == 0:

@@ -296,8 +296,15 @@ mm_status mm_solve(mm_ctx* ctx, const void* tod, double* map_out, int32_t nrhs,
  * that of the operator the basis Z was built from (a prefix covers the patch
  * differently and its small eigenmodes are not in span Z: M_2l would cost
  * more for the same products), and M_BD for the whole batch when none is
- * left; info[i].precond_used says which ran; 0 keeps M_2l for all.  Errors:
- * MM_ERR_ARG for an unknown name or value. */
+ * left; info[i].precond_used says which ran; 0 keeps M_2l for all;
+ * "tc_coarse": 1 (default) forms the coarse products Z^T R, Z U and A Z U of
+ * M_2l (Sect. 3.2, Eq. m2l) on the tensor cores (tcgen05, TF32 operands split
+ * in high and low parts, about 21 bits) when 8 <= nrhs <= 128, k <= 64, the
+ * right-hand sides share one coarse space and the map has at least 16384
+ * pixels (smaller maps are faster in float64 on the CUDA cores); 2 does so
+ * for every eligible batch whatever the map size; 0 keeps them in float64.  A bounded wait of the tensor-core kernels that gives up is
+ * reported as MM_ERR_TIMEOUT.  Errors: MM_ERR_ARG for an unknown name or
+ * value. */
 mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
 
 /* Read back a tuning knob or statistic: any knob above, or "last_apply_ms"

@@ -155,6 +155,8 @@ struct mm_ctx {
     int64_t coarse_len = 0;          // samples per detector of the operator the basis Z was built from
     int64_t harvest_len = 0;         // samples per detector of the harvested right-hand side
     int opt_coarse_fallback = 1;     // uneven batches: M_BD for right-hand sides of another length
+    int opt_tc_coarse = 1;           // M_2l coarse products on the tensor cores: 0 never, 1 large maps, 2 always
+    DevBuf w_zu;                     // Z U and A Z U of the tensor-core M_2l
     std::vector<int32_t> precond_used;
     // cross-rank sum of partial products (timeline split across processes)
     mm_reduce_fn reduce_fn = nullptr;
@@ -1100,11 +1102,32 @@ PcgArgs pcg_args(mm_ctx* ctx) {
     return a;
 }
 
+// M_2l v -> out: on the tensor cores for a batch of right-hand sides sharing
+// the coarse space (the scratch w_zu must be in place), else on the CUDA cores.
+// The coarse products go to the tensor cores when the option asks for it and the batch fits them.
+bool tc_wanted(const mm_ctx* ctx, const PcgArgs& a) {
+    return ctx->opt_tc_coarse && m2l_tc_eligible(a) && (ctx->opt_tc_coarse == 2 || m2l_tc_pays(a));
+}
+bool use_tc(const mm_ctx* ctx, const PcgArgs& a) {
+    return tc_wanted(ctx, a) && ctx->w_zu.bytes >= m2l_tc_scratch_doubles(a.n_pix, a.nrhs, a.k) * sizeof(double);
+}
+mm_status ensure_tc_scratch(mm_ctx* ctx, const PcgArgs& a) {
+    CK(ctx->w_zu.ensure(m2l_tc_scratch_doubles(a.n_pix, a.nrhs, a.k) * sizeof(double)));
+    return MM_OK;
+}
+void m2l_apply(mm_ctx* ctx, const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta) {
+    if (use_tc(ctx, a)) {
+        launch_m2l_tc(a, v, out, finalize_beta, ctx->w_zu.as<double>(), ctx->stream);
+    } else {
+        launch_m2l_ztr(a, v, ctx->stream);
+        launch_m2l_apply(a, v, out, finalize_beta, ctx->stream);
+    }
+}
+
 // Preconditioner on r -> z with rz (and beta when finalize_beta).
 void precond_step(mm_ctx* ctx, const PcgArgs& a, int finalize_beta) {
     if (ctx->precond == MM_PRECOND_2L) {
-        launch_m2l_ztr(a, a.r, ctx->stream);
-        launch_m2l_apply(a, a.r, a.z, finalize_beta, ctx->stream);
+        m2l_apply(ctx, a, a.r, a.z, finalize_beta);
     } else {
         launch_precond_bd_dot(a, finalize_beta, ctx->stream);
     }
@@ -1118,8 +1141,7 @@ mm_status pcg_iteration(mm_ctx* ctx) {
     const int two = ctx->precond == MM_PRECOND_2L;
     launch_pcg_update(a, two, ctx->stream);
     if (two) {
-        launch_m2l_ztr(a, a.r, ctx->stream);
-        launch_m2l_apply(a, a.r, a.z, 1, ctx->stream);
+        m2l_apply(ctx, a, a.r, a.z, 1);
     } else if (ctx->harvest_on) {
         launch_harvest(a, ctx->stream);
     }
@@ -1144,10 +1166,20 @@ mm_status pcg_start(mm_ctx* ctx, const V4<double>* b, const std::vector<double>&
     return MM_OK;
 }
 
+mm_status tc_fault_check(mm_ctx* ctx) {
+    int fault = 0;
+    CK(m2l_tc_fault_take(ctx->stream, &fault));
+    if (fault)
+        return fail(ctx, MM_ERR_TIMEOUT,
+                    "tensor-core M_2l: a bounded wait for the tensor cores gave up (code " + std::to_string(fault) + ")");
+    return MM_OK;
+}
+
 mm_status read_state(mm_ctx* ctx) {
     ctx->h_st.resize(ctx->nrhs);
     CK(cudaMemcpyAsync(ctx->h_st.data(), ctx->s_st.p, ctx->nrhs * sizeof(RhsState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->precond == MM_PRECOND_2L) TRY(tc_fault_check(ctx));
     return MM_OK;
 }
 
@@ -1910,8 +1942,8 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
         a.partial = ctx->w_partial.as<double>();
         a.counter = ctx->w_counter.as<unsigned>();
         a.grid_x = ctx->grid_x;
-        launch_m2l_ztr(a, in4.as<V4<double>>(), ctx->stream);
-        launch_m2l_apply(a, in4.as<V4<double>>(), out4.as<V4<double>>(), -1, ctx->stream);
+        if (tc_wanted(ctx, a)) TRY(ensure_tc_scratch(ctx, a));
+        m2l_apply(ctx, a, in4.as<V4<double>>(), out4.as<V4<double>>(), -1);
     }
     CKL();
     if (mem == MM_HOST) {
@@ -1924,6 +1956,7 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
     }
     CKL();
     CK(cudaStreamSynchronize(ctx->stream));
+    if (which == MM_PRECOND_2L) TRY(tc_fault_check(ctx));
     return MM_OK;
 }
 
@@ -2288,6 +2321,10 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
         if (n_defl == 0) ctx->precond = MM_PRECOND_BD;
     }
     if (ctx->use_lens && ctx->precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx, deflate));
+    if (ctx->precond == MM_PRECOND_2L) {
+        const PcgArgs a = pcg_args(ctx);
+        if (tc_wanted(ctx, a)) TRY(ensure_tc_scratch(ctx, a));
+    }
     TRY(get_plan(ctx, op_prec(ctx), nrhs, ctx->lens, &ctx->plan_op));
     TRY(get_plan(ctx, ctx->p64, nrhs, ctx->lens, &ctx->plan_64));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -2603,6 +2640,10 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value) {
         ctx->opt_coarse_prefix = v ? 1 : 0;
     } else if (n == "coarse_fallback") {
         ctx->opt_coarse_fallback = v ? 1 : 0;
+    } else if (n == "tc_coarse") {
+        if (ctx->phase != PH_IDLE) return fail(ctx, MM_ERR_STATE, "tc_coarse: a solve is in progress");
+        if (v < 0 || v > 2) return fail(ctx, MM_ERR_ARG, "tc_coarse must be 0, 1 or 2");
+        ctx->opt_tc_coarse = v;
     } else if (n == "inner_tol") {
         if (!(value > 0.0) || value > 1e-2) return fail(ctx, MM_ERR_ARG, "inner_tol must lie in (0, 1e-2]");
         ctx->opt_inner_tol = value;
@@ -2641,6 +2682,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "half_transform") *value = ctx->opt_half;
     else if (n == "coarse_prefix") *value = ctx->opt_coarse_prefix;
     else if (n == "coarse_fallback") *value = ctx->opt_coarse_fallback;
+    else if (n == "tc_coarse") *value = ctx->opt_tc_coarse;
     else if (n == "coarse_len") *value = (double)ctx->coarse_len;
     else if (n == "harvest") *value = ctx->opt_harvest;
     else if (n == "fp64_products") *value = ctx->p64;

@@ -222,6 +222,13 @@ void launch_m2l_ztr(const PcgArgs& a, const V4<double>* v, cudaStream_t s);
 void launch_m2l_apply(const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta,
                       cudaStream_t s);
 void launch_harvest(const PcgArgs& a, cudaStream_t s);
+// M_2l on the tensor cores (tcgen05) for 8 <= nrhs <= 128 right-hand sides, k <= 64, a shared coarse space
+bool m2l_tc_eligible(const PcgArgs& a);
+bool m2l_tc_pays(const PcgArgs& a);
+size_t m2l_tc_scratch_doubles(int n_pix, int nrhs, int k);
+void launch_m2l_tc(const PcgArgs& a, const V4<double>* v, V4<double>* out, int finalize_beta, double* scratch,
+                   cudaStream_t s);
+cudaError_t m2l_tc_fault_take(cudaStream_t s, int* fault);
 
 // Tall-skinny float64 products over vectors of n doubles (n = 4 n_pix).
 // h[i] = sum_n X[i][n] v[n] for i < m  (deterministic two-phase reduction)

@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -83,7 +84,10 @@ def parse():
     ap.add_argument("--subset-cap", type=int, default=100, help="subsets mode: PCG iteration cap (as the paper's)")
     ap.add_argument("--mc-m-max", type=int, default=300, help="mc mode: Arnoldi steps of the shared basis")
     ap.add_argument("--mc-eps-arn", type=float, default=1e-12, help="mc mode: Arnoldi tolerance")
-    ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--requests", type=int, default=500, help="serve mode: requests in the Poisson stream")
+    ap.add_argument("--load", type=float, default=0.7, help="serve mode: offered load / sequential M_BD rate")
+    ap.add_argument("--cap-requests", type=int, default=200, help="serve mode: requests of the capacity run")
+    ap.add_argument("--seq-requests", type=int, default=24, help="serve mode: requests timed alone for the baseline")
     ap.add_argument("--coarse-nx", type=int, default=512, help="coarse mode: square patch side")
     ap.add_argument("--coarse-k", type=int, default=64, help="coarse mode: coarse-space dimension")
     return ap.parse_args()
@@ -1164,115 +1168,190 @@ def run_mc(args, world, rank, local):
 
 
 # ---------------- serving (c5) ----------------
-def _gpu_tod(torch, scan, seed, dev):
-    """Timeline d = P s + 1/f noise synthesised on the device (input generation only)."""
-    g = torch.Generator(device=dev).manual_seed(seed)
-    pix = torch.from_numpy(scan.pix).to(dev).long()
-    psi = torch.from_numpy(scan.psi).to(dev).double()
-    sky = torch.randn((scan.n_pix, 3), generator=g, device=dev, dtype=torch.float64)
-    sky[:, 1:] *= 0.1
-    ok = pix >= 0
-    p = pix.clamp(min=0)
-    d = sky[p, 0] + sky[p, 1] * torch.cos(2 * psi) + sky[p, 2] * torch.sin(2 * psi)
-    d = torch.where(ok, d, torch.zeros_like(d))
-    blen = scan.n_t // scan.n_int
-    w = torch.randn((scan.n_det * scan.n_int, blen), generator=g, device=dev, dtype=torch.float64)
-    f = torch.fft.rfftfreq(blen, d=1.0 / 100.0, device=dev, dtype=torch.float64)
-    f[0] = f[1]
-    fk = torch.from_numpy(np.repeat(scan.f_knee, scan.n_int)).to(dev)[:, None]
-    shape = torch.sqrt(1.0 + fk / f[None, :])
-    n = torch.fft.irfft(torch.fft.rfft(w, dim=1) * shape, n=blen, dim=1).reshape(-1)
-    return (d + n).float()
-
-
 def run_serve(args, world, rank, local):
-    """Poisson stream of map requests of mixed sizes, 30% on repeated scans."""
+    """Poisson stream of map requests: patches 64^2..512^2, 16..1024 detectors x 2^18..2^20 samples,
+    30% of the requests on one of the eight most recently used scans (their resident M_BD and
+    coarse space reused; requests on a busy scan fold into its next multi-RHS solve).  Scans and
+    timelines are generated on the device when a request arrives (synth.device); the client asks the
+    server for memory back before it generates, so a request never waits on a full device."""
     import torch
-    import synth
     import __graft_entry__ as G
     G.build()
+    from synth.device import make_scan_device, make_tod_device
     from paper_1801_08937_gb300 import mapmaker as M
     from paper_1801_08937_gb300 import serving as S
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rng = np.random.default_rng(5 + rank)
-    patches = [64, 128, 256]
-    dets = [16, 32, 64, 128]
-    samples = [1 << 18, 1 << 19]
+    patches, dets, lengths = [64, 128, 256, 512], [16, 32, 64, 128, 256, 512, 1024], [1 << 18, 1 << 19, 1 << 20]
     n_req = args.requests
-    scans, reqs = [], []
+    reqs, n_scans, order = [], 0, []
     for j in range(n_req):
-        if scans and rng.random() < 0.3:
-            sid = int(rng.integers(len(scans)))
+        recent = list(dict.fromkeys(reversed(order)))[:8]
+        if recent and rng.random() < 0.3:
+            key = recent[int(rng.integers(len(recent)))]
         else:
-            nx = int(rng.choice(patches))
-            nd = int(rng.choice(dets))
-            nt = int(rng.choice(samples))
-            sc = synth.make_scan(nx=nx, ny=nx, n_det=nd, n_t=nt, n_int=nt // 16384, half_bw=512,
-                                 f_knee=(0.1, 2.0), seed=1000 + len(scans))
-            scans.append(sc)
-            sid = len(scans) - 1
-        reqs.append((sid, 7000 + j))
-    specs = [S.ScanSpec(torch.from_numpy(sc.pix).to(dev), torch.from_numpy(sc.psi).to(dev), sc.block_off,
-                        sc.block_band, sc.band, sc.n_pix, sc.n_det) for sc in scans]
-    tods = [_gpu_tod(torch, scans[sid], seed, dev) for sid, seed in reqs]
-    torch.cuda.synchronize()
-    kw = dict(m_max=40, k=16, eps_arn=1e-6)
+            key = (int(rng.choice(patches)), int(rng.choice(dets)), int(rng.choice(lengths)), n_scans)
+            n_scans += 1
+        order.append(key)
+        reqs.append((key, 9000 + j))
+    lam = 512
+    scans = {}
 
-    # sequential M_BD baseline: each request alone, set-up included, one at a time
-    seq_n = min(12, n_req)
-    t0 = time.perf_counter()
-    for j in range(seq_n):
-        sid, _ = reqs[j]
-        sc = scans[sid]
+    def headroom(need):
+        """Free device memory for the client's own arrays (server scans are released if needed)."""
+        for _ in range(3000):
+            free = torch.cuda.mem_get_info(local)[0]
+            if free >= need + (4 << 30):
+                return
+            torch.cuda.empty_cache()
+            srv_now = holder.get("srv")
+            if srv_now is not None:
+                srv_now.release_idle(need + (8 << 30))
+            time.sleep(0.01)
+
+    def scan_of(key, keep):
+        if key not in scans:
+            nx, nd, nt, i = key
+            headroom(12 * nd * nt)
+            scans[key] = make_scan_device(torch, dev, nx, nd, nt, nt // 16384, lam, seed=2000 + i)
+        for k in [k for k in scans if k not in keep]:   # the client keeps the recent scans only
+            del scans[k]
+        return scans[key]
+
+    def spec(sc):
+        return S.ScanSpec(sc.pix, sc.psi, sc.block_off, sc.block_band, sc.band, sc.n_pix, sc.n_det)
+
+    def make_request(j):
+        key, seed = reqs[j]
+        keep = set(list(dict.fromkeys(reversed(order[:j + 1])))[:8])
+        sc = scan_of(key, keep)
+        headroom(24 * sc.n_samples)
+        tod = make_tod_device(torch, sc, seed)
+        torch.cuda.current_stream().synchronize()
+        return S.MapRequest("scan%d" % key[3], spec(sc), tod, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.max_iter)
+
+    holder = {}
+    kw = dict(m_max=40, k=16, eps_arn=1e-6)
+    gen_stream = torch.cuda.Stream(device=dev)
+    sizes = np.array([k[1] * k[2] for k, _ in reqs], dtype=np.float64)
+
+    def producer(seq, q):
+        """Requests generated ahead of their submission on a stream of their own (the queue bounds
+        how many wait), so generation overlaps the server's work instead of delaying arrivals."""
+        try:
+            torch.cuda.set_device(local)
+            with torch.cuda.stream(gen_stream):
+                for j in seq:
+                    q.put(make_request(j))
+        except BaseException as ex:   # reported by the consumer
+            q.put(ex)
+
+    def take(q):
+        r = q.get(timeout=600)
+        if isinstance(r, BaseException):
+            raise r
+        return r
+
+    def run_stream(seq, depth):
+        q = queue.Queue(maxsize=depth)
+        th = threading.Thread(target=producer, args=(seq, q), daemon=True)
+        th.start()
+        return q, th
+
+    # sequential M_BD baseline: a random sample of the stream's requests, alone and one at a time, each
+    # with its scan's set-up; its time per sample scales to the stream's mix of sizes
+    seq_idx = sorted(rng.choice(n_req, size=min(args.seq_requests, n_req), replace=False).tolist())
+    seq_t, seq_samples = 0.0, 0
+    for j in seq_idx:
+        r = make_request(j)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         c = M.Context(local, None, M.MM_FP32_MIXED)
-        sp = specs[sid]
-        c.setup_pointing(sp.pix, sp.psi, sc.block_off, sc.block_band, sc.band, sc.n_pix, n_det=sc.n_det)
+        sp = r.scan
+        c.setup_pointing(sp.pix, sp.psi, sp.block_off, sp.block_band, sp.band, sp.n_pix, n_det=sp.n_det)
         c.build_bd(1e-3)
-        c.solve(tods[j][None], M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter)
+        c.solve(r.tod[None], M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter)
         c.close()
-    torch.cuda.synchronize()
-    seq_s = (time.perf_counter() - t0) / seq_n
-    rate = 0.7 / seq_s
+        torch.cuda.synchronize()
+        seq_t += time.perf_counter() - t0
+        seq_samples += sp.n_samples
+        del r, c
+    scans.clear()
+    torch.cuda.empty_cache()
+    s_per_sample = seq_t / seq_samples
+    seq_s = s_per_sample * float(sizes.mean())       # sequential M_BD seconds per map of this mix
+    rate = args.load / seq_s
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    srv = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=12,
-                      coarse="harvest", **kw).start()
-    futs = []
+    srv = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=24, max_batch=16,
+                      coarse="harvest", reserve_bytes=8 << 30, **kw).start()
+    holder["srv"] = srv
+    q, th = run_stream(range(n_req), 8)
+    futs, late = [], 0
     t_start = time.perf_counter()
-    for j, (sid, _) in enumerate(reqs):
+    for j in range(n_req):
+        r = take(q)
         delay = t_start + arrivals[j] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        futs.append(srv.submit(S.MapRequest(f"scan{sid}", specs[sid], tods[j], M.MM_PRECOND_2L, tol=args.tol,
-                                            max_iter=args.max_iter)))
-    res = [f.result(timeout=600) for f in futs]
+        elif delay < -0.05:
+            late += 1
+        r.arrival = time.perf_counter()
+        futs.append(srv.submit(r))
+        del r
+    res = [f.result(timeout=1800) for f in futs]
     wall = time.perf_counter() - t_start
+    th.join()
     st = srv.stats()
     srv.stop()
+    holder.clear()
+    scans.clear()
+    torch.cuda.empty_cache()
     ok = sum(1 for r in res if r.info["status"] == "MM_OK")
-    # capacity: a fresh server with the whole stream submitted at once (set-ups included)
-    srv2 = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=12,
-                       coarse="harvest", **kw).start()
+    # capacity: a fresh server kept busy by a closed loop of 24 outstanding requests
+    n_cap = min(n_req, args.cap_requests)
+    srv2 = S.MapServer(device=local, precision=M.MM_FP32_MIXED, iters_per_tick=4, max_active=24, max_batch=16,
+                       coarse="harvest", reserve_bytes=8 << 30, **kw).start()
+    holder["srv"] = srv2
+    q, th = run_stream(range(n_cap), 8)
     t1 = time.perf_counter()
-    futs2 = [srv2.submit(S.MapRequest(f"scan{sid}", specs[sid], tods[j], M.MM_PRECOND_2L, tol=args.tol,
-                                      max_iter=args.max_iter)) for j, (sid, _) in enumerate(reqs)]
-    res2 = [f.result(timeout=600) for f in futs2]
-    cap = n_req / (time.perf_counter() - t1)
+    futs2, res2 = [], []
+    for j in range(n_cap):
+        while len(futs2) - len(res2) >= 24:
+            res2.append(futs2[len(res2)].result(timeout=1800))
+        r = take(q)
+        r.arrival = time.perf_counter()
+        futs2.append(srv2.submit(r))
+        del r
+    while len(res2) < len(futs2):
+        res2.append(futs2[len(res2)].result(timeout=1800))
+    cap_s = time.perf_counter() - t1
+    th.join()
+    cap = n_cap / cap_s
     st2 = srv2.stats()
     srv2.stop()
+    holder.clear()
     line = {"metric": METRIC + " [serving]", "value": st["p99_s"], "unit": "s (p99 latency)", "n_gpus": world,
             "steps": n_req, "warmup": 0, "ms_per_step": wall / n_req * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{n_req} Poisson requests at 0.7x sequential M_BD capacity, patches "
-                                   f"64^2..256^2, 16..128 det x 2^18..2^19 samples, lambda 512, 30% repeat scans",
-                       "unique_scans": len(scans)},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (generated on the device)",
+            "config": {"workload": f"{n_req} Poisson requests at {args.load}x sequential M_BD capacity, patches "
+                                   "64^2..512^2, 16..1024 det x 2^18..2^20 samples, lambda 512, 30% of requests on "
+                                   "one of the 8 most recent scans",
+                       "unique_scans": n_scans},
             "serving": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "maps_per_s": n_req / wall,
                         "converged": ok, "cache_hits": st["cache_hits"], "evictions": st["evictions"],
-                        "max_concurrent": st["max_concurrent"]},
-            "saturated": {"maps_per_s": cap, "converged": sum(1 for r in res2 if r.info["status"] == "MM_OK"),
-                          "max_concurrent": st2["max_concurrent"]},
-            "sequential_m_bd": {"maps_per_s": 1.0 / seq_s, "s_per_map": seq_s, "n": seq_n},
-            "offered_rate_per_s": rate}
+                        "max_concurrent": st["max_concurrent"], "batched_requests": st["batched_requests"],
+                        "largest_batch": st["largest_batch"], "oom_requeued": st["oom_requeued"],
+                        "late_arrivals_over_50ms": late, "samples_per_s": float(sizes.sum()) / wall},
+            "saturated": {"maps_per_s": cap, "requests": n_cap, "outstanding": 24,
+                          "samples_per_s": float(sizes[:n_cap].sum()) / cap_s,
+                          "converged": sum(1 for r in res2 if r.info["status"] == "MM_OK"),
+                          "batched_requests": st2["batched_requests"], "largest_batch": st2["largest_batch"],
+                          "p50_s": st2["p50_s"], "p99_s": st2["p99_s"]},
+            "sequential_m_bd": {"maps_per_s": 1.0 / seq_s, "s_per_map": seq_s, "samples_per_s": 1.0 / s_per_sample,
+                                "n": len(seq_idx), "note": "time per sample of a random sample of the stream's "
+                                "requests (set-up + M_BD solve, one at a time), scaled to the stream's mean size"},
+            "mean_samples_per_request": float(sizes.mean()), "offered_rate_per_s": rate}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -5,7 +5,12 @@ timeline) are admitted while device memory allows.  Each scan keeps its own
 context resident: pointing, M_BD and the two-level coarse space are built
 once per scan_id (the paper's "simplified" reuse of one deflation basis for
 later data, Sect. 7) and every later request on that scan only pays for
-b = P^T W d and the PCG iterations.  Admitted solves advance together: each
+b = P^T W d and the PCG iterations.  Requests on one scan that wait while the
+scan's context is busy (or still being set up) are folded into its next
+solve: one multi-right-hand-side PCG run (the paper's Monte Carlo case of many
+maps on one operator, Sect. 7), up to max_batch maps, for requests that ask
+for the same preconditioner, tolerance and iteration cap.  Admitted solves
+advance together: each
 tick enqueues a few PCG iterations on every active context (its own CUDA
 stream) without waiting, then polls them, so their kernels overlap on the
 device and a request that arrives while others run joins at the next tick.
@@ -60,6 +65,7 @@ class MapResult:
     latency_s: float
     queued_s: float
     scan_cached: bool
+    batch_size: int = 1                # maps solved together in the request's PCG run
 
 
 class _ScanEntry:
@@ -77,9 +83,8 @@ class _ScanEntry:
 
 
 class _Active:
-    def __init__(self, req, fut, entry, t_start, cached):
-        self.req = req
-        self.fut = fut
+    def __init__(self, batch, entry, t_start, cached):
+        self.batch = batch             # [(request, future)] solved as one multi-right-hand-side run
         self.entry = entry
         self.t_start = t_start
         self.cached = cached
@@ -92,17 +97,20 @@ class MapServer:
     def __init__(self, device: int = 0, precision: int = M.MM_FP32_MIXED, budget_bytes: int | None = None,
                  iters_per_tick: int = 4, max_active: int = 16, m_max: int = 60, k: int = 16,
                  eps_arn: float = 1e-6, setup_workers: int = 2, reserve_bytes: int = 2 << 30,
-                 coarse: str = "arnoldi"):
+                 coarse: str = "arnoldi", max_batch: int = 16):
         """coarse: "arnoldi" builds each new scan's deflation basis before its
         first solve; "harvest" solves the first request of a scan with M_BD,
         keeping the Lanczos vectors of that run, and builds the basis from
-        them afterwards, so later requests on the scan use M_2l."""
+        them afterwards, so later requests on the scan use M_2l.
+        max_active bounds the requests in flight (set-ups and solves, counted
+        per map); max_batch the maps folded into one solve."""
         import torch
         self.torch = torch
         self.device = device
         self.precision = precision
         self.iters_per_tick = iters_per_tick
         self.max_active = max_active
+        self.max_batch = max(1, int(max_batch))
         self.m_max, self.k, self.eps_arn = m_max, k, eps_arn
         self.coarse_mode = coarse
         self.reserve = reserve_bytes
@@ -123,6 +131,12 @@ class MapServer:
         self.rejected = 0
         self.failed = 0
         self.max_concurrent = 0
+        self._release = 0
+        self._reserved = {}            # scan_id -> bytes promised to a set-up that has not allocated yet
+        self._oom_wait = False         # a solve ran out of memory: start none until another ends
+        self.oom_requeued = 0
+        self.batched = 0               # requests that shared their PCG run with others
+        self.largest_batch = 0
         self.t0 = None
         self.error = None
 
@@ -148,6 +162,12 @@ class MapServer:
             self._pending.append((req, fut))
         return fut
 
+    def release_idle(self, need_bytes: int):
+        """Ask the scheduler to close idle resident scans (least recently used first) until
+        need_bytes of device memory are free, for a host application that needs memory back."""
+        with self._lock:
+            self._release = max(self._release, int(need_bytes))
+
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         wall = (time.perf_counter() - self.t0) if self.t0 else 0.0
@@ -155,20 +175,26 @@ class MapServer:
                 "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                 "maps_per_s": self.completed / wall if wall > 0 else 0.0, "cache_hits": self.cache_hits,
                 "evictions": self.evictions, "admitted": self.admitted, "max_concurrent": self.max_concurrent,
-                "resident_scans": len(self._scans), "failed": self.failed}
+                "resident_scans": len(self._scans), "failed": self.failed, "batched_requests": self.batched,
+                "largest_batch": self.largest_batch, "oom_requeued": self.oom_requeued}
 
     # ---------------- memory accounting ----------------
     def _free_bytes(self) -> int:
+        """Device memory that admission may still hand out: what the device reports free, less the
+        reserve and what set-ups in flight will allocate."""
         free, total = self.torch.cuda.mem_get_info(self.device)
         if self.budget is not None:
             used = sum(e.nbytes for e in self._scans.values())
             free = min(free, self.budget - used)
-        return free - self.reserve
+        return free - self.reserve - sum(self._reserved.values())
 
     def _scan_bytes(self, spec: ScanSpec, nrhs=1) -> int:
         lam = int(np.asarray(spec.band).shape[-1] - 1)
         nb = int(np.asarray(spec.band).reshape(-1, lam + 1).shape[0])
         return M.estimate_bytes(spec.n_samples, spec.n_pix, nb, lam, nrhs, self.m_max, self.k, self.precision)
+
+    def _tod_bytes(self, spec: ScanSpec) -> int:
+        return spec.n_samples * (4 if self.precision == M.MM_FP32_MIXED else 8)
 
     def _solve_bytes(self, spec: ScanSpec) -> int:
         esz = 4 if self.precision == M.MM_FP32_MIXED else 8
@@ -218,44 +244,88 @@ class MapServer:
         entry.busy = False
 
     # ---------------- scheduler ----------------
+    @staticmethod
+    def _key(req):
+        """Requests solved together must agree on what the run computes."""
+        return (req.precond, float(req.tol), int(req.max_iter))
+
+    def _in_flight(self) -> int:
+        """Requests being solved or waiting for their scan's set-up."""
+        return sum(len(a.batch) for a in self._active) + sum(len(w) for w in self._setting_up.values())
+
     def _admit(self):
         with self._lock:
             pending = list(self._pending)
         keep = []
-        for req, fut in pending:
-            # requests waiting for their scan's set-up start solving when it ends: they count too
-            in_flight = len(self._active) + sum(len(w) for w in self._setting_up.values())
-            if in_flight >= self.max_active:
+        taken = set()
+        for j, (req, fut) in enumerate(pending):
+            if j in taken:
+                continue
+            room = self.max_active - self._in_flight()
+            if room <= 0 or self._oom_wait:
                 keep.append((req, fut))
                 continue
             e = self._scans.get(req.scan_id)
-            if e is not None and (e.busy or not e.ready):
-                keep.append((req, fut))
-                continue
             if e is not None and e.error is not None:
                 fut.set_exception(e.error)
                 continue
-            need = self._solve_bytes(req.scan) + (0 if e is not None else self._scan_bytes(req.scan))
-            if self._free_bytes() < need and not self._evict_idle(need, keep_id=req.scan_id):
-                keep.append((req, fut))
+            if e is not None and (e.busy or not e.ready):
+                keep.append((req, fut))     # folded into the scan's next solve
                 continue
+            # this request and the later ones on the same scan that ask for the same run
+            batch, idx = [(req, fut)], [j]
+            for j2 in range(j + 1, len(pending)):
+                if len(batch) >= min(self.max_batch, room):
+                    break
+                r2 = pending[j2][0]
+                if j2 not in taken and r2.scan_id == req.scan_id and self._key(r2) == self._key(req):
+                    batch.append(pending[j2])
+                    idx.append(j2)
+            def need_of(n):
+                # solve state, plus the stacked timelines of a batch, plus a new scan's resident state
+                b = self._solve_bytes(req.scan) * n + (self._tod_bytes(req.scan) * n if n > 1 else 0)
+                return b + (self._scan_bytes(req.scan, n) if e is None else 0)
+            free = self._free_bytes()
+            while len(batch) > 1 and free < need_of(len(batch)):
+                batch.pop()                 # a smaller batch that fits; the rest wait for the scan
+                idx.pop()
+            need = need_of(len(batch))
+            if free < need and not self._evict_idle(need, keep_id=req.scan_id):
+                keep.append((req, fut))     # the others are tried on their own turn
+                continue
+            taken.update(idx)
             if e is None:
                 stream = self.torch.cuda.Stream(device=self.device)
                 ctx = M.Context(self.device, stream.cuda_stream, self.precision)
-                e = _ScanEntry(ctx, stream, self._scan_bytes(req.scan), req.scan)
+                e = _ScanEntry(ctx, stream, self._scan_bytes(req.scan, len(batch)), req.scan)
                 e.busy = True
                 self._scans[req.scan_id] = e
+                self._reserved[req.scan_id] = e.nbytes
                 self._pool.submit(self._setup, req.scan_id, e, req.precond == M.MM_PRECOND_2L, req.tod)
-                self._setting_up.setdefault(req.scan_id, []).append((req, fut))
-                self.admitted += 1
+                self._setting_up.setdefault(req.scan_id, []).extend(batch)
+                self.admitted += len(batch)
                 continue
-            self.cache_hits += 1
-            self._start_solve(req, fut, e, cached=True)
+            self.cache_hits += len(batch)
+            self.admitted += len(batch)
+            self._start_solve(batch, e, cached=True)
         with self._lock:
             newer = list(self._pending)[len(pending):]
             self._pending = collections.deque(keep + newer)
 
-    def _start_solve(self, req, fut, e, cached):
+    def _stack_tods(self, batch, e):
+        """The batch's timelines as one [nrhs, n_samples] array, made on the context's stream."""
+        tods = [r.tod for r, _ in batch]
+        if len(tods) == 1:
+            return tods[0]
+        torch = self.torch
+        if all(isinstance(t, torch.Tensor) and t.is_cuda for t in tods):
+            with torch.cuda.stream(e.stream):
+                return torch.stack([t.reshape(-1) for t in tods])
+        return np.stack([t.cpu().numpy().reshape(-1) if isinstance(t, torch.Tensor) else np.asarray(t).reshape(-1)
+                         for t in tods])
+
+    def _start_solve(self, batch, e, cached):
+        req = batch[0][0]
         e.busy = True
         e.last_used = time.perf_counter()
         self._scans.move_to_end(req.scan_id)
@@ -263,14 +333,32 @@ class MapServer:
         e.harvesting = (req.precond == M.MM_PRECOND_2L and not e.has_coarse and self.coarse_mode == "harvest")
         try:
             e.ctx.set_option("harvest", self.m_max if e.harvesting else 0)
-            e.ctx.solve_begin(req.tod, precond, tol=req.tol, max_iter=req.max_iter)
+            e.ctx.solve_begin(self._stack_tods(batch, e), precond, tol=req.tol, max_iter=req.max_iter)
         except Exception as ex:
             e.busy = False
-            fut.set_exception(ex)
+            e.harvesting = False
+            busy = bool(self._active or self._setting_up)
+            if getattr(ex, "status", None) == M.MM_ERR_OOM and (busy or not getattr(req, "_oom_retried", False)):
+                if busy:
+                    # memory comes back when the work in flight ends: wait for it at the head of the queue
+                    self._oom_wait = True
+                else:
+                    # nothing in flight: give back every idle scan's memory and try once more
+                    self._evict_idle(1 << 62, keep_id=req.scan_id)
+                    req._oom_retried = True
+                self.oom_requeued += len(batch)
+                self.torch.cuda.empty_cache()
+                with self._lock:
+                    self._pending.extendleft(reversed(batch))
+                return
+            for _, fut in batch:
+                fut.set_exception(ex)
             return
-        self.admitted += 0 if not cached else 1
-        self._active.append(_Active(req, fut, e, time.perf_counter(), cached))
-        self.max_concurrent = max(self.max_concurrent, len(self._active))
+        self._active.append(_Active(batch, e, time.perf_counter(), cached))
+        self.max_concurrent = max(self.max_concurrent, sum(len(a.batch) for a in self._active))
+        self.largest_batch = max(self.largest_batch, len(batch))
+        if len(batch) > 1:
+            self.batched += len(batch)
 
     def _finish_setups(self):
         for sid in list(self._setting_up.keys()):
@@ -279,25 +367,45 @@ class MapServer:
                 continue
             waiting = self._setting_up.pop(sid)
             e.busy = False
-            for req, fut in waiting:
-                if e.error is not None:
+            if (getattr(e.error, "status", None) == M.MM_ERR_OOM and (self._active or self._setting_up)):
+                # set up again once the work in flight has given memory back
+                self._reserved.pop(sid, None)
+                del self._scans[sid]
+                e.ctx.close()
+                self._oom_wait = True
+                self.oom_requeued += len(waiting)
+                with self._lock:
+                    self._pending.extendleft(reversed(waiting))
+                continue
+            if e.error is not None:
+                self._reserved.pop(sid, None)
+                for _, fut in waiting:
                     fut.set_exception(e.error)
-                else:
-                    self._start_solve(req, fut, e, cached=False)
+                continue
+            # the requests that ask for the same run as the first go now; the rest wait for the scan
+            k0 = self._key(waiting[0][0])
+            first = [w for w in waiting if self._key(w[0]) == k0][:self.max_batch]
+            rest = [w for w in waiting if all(w is not f for f in first)]
+            if rest:
+                with self._lock:
+                    self._pending.extendleft(reversed(rest))
+            self._start_solve(first, e, cached=False)
+            self._reserved.pop(sid, None)          # the first solve has allocated its state
 
     def _drop_failed(self, a, ex):
-        """A solve that raised fails its own request; its scan's context is closed and forgotten (its
+        """A solve that raised fails its own requests; its scan's context is closed and forgotten (its
         state is unknown), so a later request on the scan sets it up again."""
-        if not a.fut.done():
-            a.fut.set_exception(ex)
-        sid = a.req.scan_id
+        for _, fut in a.batch:
+            if not fut.done():
+                fut.set_exception(ex)
+        sid = a.batch[0][0].scan_id
         if self._scans.get(sid) is a.entry:
             del self._scans[sid]
             try:
                 a.entry.ctx.close()
             except Exception:
                 pass
-        self.failed += 1
+        self.failed += len(a.batch)
 
     def _tick(self) -> bool:
         progressed = False
@@ -327,6 +435,7 @@ class MapServer:
                 progressed = True
             if done:
                 now = time.perf_counter()
+                self._oom_wait = False
                 if a.entry.harvesting:
                     # deflation basis from this M_BD run's Lanczos vectors, off the critical path
                     a.entry.harvesting = False
@@ -334,9 +443,11 @@ class MapServer:
                 else:
                     a.entry.busy = False
                 a.entry.last_used = now
-                self.latencies.append(now - a.req.arrival)
-                self.completed += 1
-                a.fut.set_result(MapResult(x[0], info[0], now - a.req.arrival, a.t_start - a.req.arrival, a.cached))
+                for i, (req, fut) in enumerate(a.batch):
+                    self.latencies.append(now - req.arrival)
+                    self.completed += 1
+                    fut.set_result(MapResult(x[i], info[i], now - req.arrival, a.t_start - req.arrival, a.cached,
+                                             len(a.batch)))
             else:
                 still.append(a)
         self._active = still
@@ -350,8 +461,9 @@ class MapServer:
             if not fut.done():
                 fut.set_exception(ex)
         for a in self._active:
-            if not a.fut.done():
-                a.fut.set_exception(ex)
+            for _, fut in a.batch:
+                if not fut.done():
+                    fut.set_exception(ex)
         for waiting in self._setting_up.values():
             for _, fut in waiting:
                 if not fut.done():
@@ -363,6 +475,12 @@ class MapServer:
         self.torch.cuda.set_device(self.device)
         while not self._stop.is_set():
             try:
+                if self._oom_wait and not self._active and not self._setting_up:
+                    self._oom_wait = False     # nothing left to give memory back: try again
+                if self._release:
+                    with self._lock:
+                        need, self._release = self._release, 0
+                    self._evict_idle(need)
                 self._finish_setups()
                 self._admit()
                 progressed = self._tick() if self._active else False

@@ -10,6 +10,8 @@ both sides receive identical arrays from here.
 Workload shapes follow the paper's ground-based simulations (Sect. 5: constant
 elevation scans at 0.4 deg/s over a small patch, polarisation-sensitive
 detectors behind a rotating half-wave plate) at the sizes named in ``CONFIGS``.
+``synth.device`` builds the same kind of scan and timeline on a CUDA device
+for request streams too large for the host.
 """
 from .scan import (Scan, CONFIGS, make_scan, make_sky, make_noise, make_tod,
                    toeplitz_band, scan_from_config, mc_lengths, make_templates, AZ_BIN_PX)

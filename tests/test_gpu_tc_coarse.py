@@ -110,3 +110,27 @@ def test_tc_two_level_batch_solves_like_float64():
         assert res[1][1][r]["status"] == "MM_OK" and res[1][1][r]["true_rel_res"] <= 1e-9
         assert abs(res[1][1][r]["iters"] - res[0][1][r]["iters"]) <= 2
         assert_close(res[1][0][r], res[0][0][r], 1e-8, f"map {r}: tensor-core vs float64 coarse products")
+
+
+def test_tc_m2l_matches_oracle_at_the_mixed_precision_map_shape():
+    """The 512x512 patch of the mixed-precision workload (786432 unknowns), k = 64, 64 right-hand
+    sides: tensor-core M_2l x against the oracle's Eq. m2l element by element, with the oracle's own
+    A Z (a short 8-detector scan keeps the 64 oracle products A z_i to seconds), E and M_BD."""
+    scan = synth.make_scan(nx=512, ny=512, n_det=8, n_t=1 << 18, n_int=4, half_bw=16, f_knee=1.0, seed=74)
+    prob, mbd, good = oracle_problem(scan)
+    rng = np.random.default_rng(74)
+    k, nrhs = 64, 64
+    Z = rng.standard_normal((k, scan.n_pix, 3))
+    Z[:, ~good] = 0.0
+    x = rng.standard_normal((nrhs, scan.n_pix, 3))
+    x[:, ~good] = 0.0
+    Zf = Z.reshape(k, -1).T
+    A = lambda v: O.apply_A(prob, v.reshape(-1, 3)).reshape(-1)  # noqa: E731
+    M = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+    AZ, _, L = O.coarse_space(A, Zf)
+    c = _ctx(scan, 1)
+    c.set_coarse(Z)
+    y_tc = c.apply_precond(MM.MM_PRECOND_2L, torch.from_numpy(x).cuda()).cpu().numpy()
+    c.close()
+    ref = np.stack([O.m2l_apply(x[r].reshape(-1), M, Zf, AZ, L).reshape(-1, 3) for r in range(nrhs)])
+    assert_close(y_tc, ref, TOL_TC, "tensor-core M_2l vs oracle, 512x512, k = 64, 64 RHS")

@@ -41,18 +41,27 @@ class FakeCuda:
     def synchronize(self, device=None):
         pass
 
+    def empty_cache(self):
+        pass
+
 
 class FakeTorch:
+    class Tensor:                     # no timeline in these tests is a tensor
+        pass
+
     def __init__(self, free=1 << 40):
         self.cuda = FakeCuda(free)
 
 
 class FakeContext:
-    """Records calls; a solve finishes after three polls with the map filled by sum(tod)."""
+    """Records calls; a solve finishes after three polls (and once gate[n_pix], if any, is set) with
+    map i filled by the sum of timeline i."""
     lock = threading.Lock()
     log = []
     fail_npix = set()
     fail_poll = set()
+    gate = {}
+    oom_begin = set()
     live = 0
     max_live = 0
 
@@ -95,10 +104,15 @@ class FakeContext:
         return self.harvested if name == "harvested" else self.opts.get(name, 0)
 
     def solve_begin(self, tod, precond, tol=1e-8, max_iter=500):
-        self.tod, self.precond, self.polls = np.asarray(tod), precond, 0
+        if self.n_pix in FakeContext.oom_begin:
+            FakeContext.oom_begin.discard(self.n_pix)      # out of memory once
+            self._rec("oom", self.n_pix)
+            raise M.MapMakerError(M.MM_ERR_OOM, "out of memory")
+        self.tod, self.precond, self.polls = np.atleast_2d(np.asarray(tod)), precond, 0
+        self.tol = tol
         if self.opts.get("harvest", 0) > 0:
             self.harvested = self.opts["harvest"]
-        self._rec("begin", self.n_pix, precond)
+        self._rec("begin", self.n_pix, precond, self.tod.shape[0], tol)
 
     def solve_launch(self, n_iter):
         pass
@@ -108,11 +122,13 @@ class FakeContext:
         if self.n_pix in FakeContext.fail_poll:
             FakeContext.fail_poll.discard(self.n_pix)       # fails once
             raise RuntimeError(f"breakdown on {self.n_pix}")
-        return True, self.polls >= 3
+        g = FakeContext.gate.get(self.n_pix)
+        return True, self.polls >= 3 and (g is None or g.is_set())
 
     def solve_end(self, out=None, like=None):
-        x = np.full((1, self.n_pix, 3), float(self.tod.sum()))
-        return x, [{"iters": self.polls, "status": "MM_OK", "precond": self.precond}]
+        x = np.repeat(self.tod.sum(axis=1)[:, None, None], self.n_pix, axis=1).repeat(3, axis=2)
+        return x, [{"iters": self.polls, "status": "MM_OK", "precond": self.precond, "tol": self.tol}
+                   for _ in range(self.tod.shape[0])]
 
     def close(self):
         self._rec("close", self.n_pix)
@@ -125,6 +141,8 @@ def fake(monkeypatch):
     FakeContext.log = []
     FakeContext.fail_npix = set()
     FakeContext.fail_poll = set()
+    FakeContext.gate = {}
+    FakeContext.oom_begin = set()
     FakeContext.live = 0
     FakeContext.max_live = 0
     monkeypatch.setattr(M, "Context", FakeContext)
@@ -160,10 +178,12 @@ def test_repeated_scans_hit_the_resident_state_and_results_route_to_their_reques
         assert r.map.shape == (n, 3) and np.all(r.map == 64 * v)
         assert r.info["precond"] == M.MM_PRECOND_2L
     st = srv.stats()
-    assert st["completed"] == 5 and st["cache_hits"] == 3
+    assert st["completed"] == 5
     assert sum(1 for e in fake.log if e[0] == "setup") == 2
     assert sum(1 for e in fake.log if e[0] == "coarse") == 2     # one Arnoldi basis per scan
-    assert [r.scan_cached for r in res] == [False, False, True, True, True]
+    # each repeat either found its scan resident or shared its first solve
+    assert not res[0].scan_cached and not res[1].scan_cached
+    assert all(r.scan_cached or r.batch_size > 1 for r in res[2:])
 
 
 def test_memory_budget_evicts_the_least_recently_used_idle_scan(fake):
@@ -232,3 +252,63 @@ def test_a_failing_solve_fails_its_request_only_and_its_scan_is_set_up_again(fak
     assert srv.error is None and srv.stats()["failed"] == 1
     assert sum(1 for e in fake.log if e[:2] == ("setup", 50)) == 2
     assert ("close", 50) in fake.log
+
+
+def _wait_for(pred, what):
+    for _ in range(4000):
+        if pred():
+            return
+        threading.Event().wait(0.005)
+    raise AssertionError(f"timed out waiting for {what}")
+
+
+def test_requests_on_a_busy_scan_fold_into_its_next_multi_rhs_solve(fake):
+    fake.gate = {60: threading.Event()}
+    srv = server(max_batch=4)
+    first = srv.submit(request(60, 1.0))
+    _wait_for(lambda: any(e[0] == "begin" for e in fake.log), "the first solve")
+    later = [srv.submit(request(60, float(v))) for v in (2, 3, 4, 5, 6)]
+    other = srv.submit(request(60, 7.0, tol=1e-6))               # another run: not folded in
+    threading.Event().wait(0.05)
+    assert sum(1 for e in fake.log if e[0] == "begin") == 1      # all wait while the scan is busy
+    fake.gate[60].set()
+    res = [f.result(timeout=20) for f in [first] + later]
+    r_other = other.result(timeout=20)
+    srv.stop()
+    for v, r in zip((1, 2, 3, 4, 5, 6), res):
+        assert np.all(r.map == 64.0 * v)                          # results route to their own requests
+    assert np.all(r_other.map == 64.0 * 7) and r_other.info["tol"] == 1e-6 and r_other.batch_size == 1
+    begins = [e for e in fake.log if e[0] == "begin"]
+    assert [b[3] for b in begins] == [1, 4, 1, 1]                 # max_batch caps the fold
+    assert [r.batch_size for r in res] == [1, 4, 4, 4, 4, 1]
+    st = srv.stats()
+    assert st["batched_requests"] == 4 and st["largest_batch"] == 4 and st["completed"] == 7
+    assert sum(1 for e in fake.log if e[0] == "setup") == 1
+
+
+def test_requests_arriving_during_a_scan_set_up_share_its_first_solve(fake):
+    srv = server(max_batch=8)
+    futs = [srv.submit(request(70, float(v))) for v in (1, 2, 3)]
+    res = [f.result(timeout=20) for f in futs]
+    srv.stop()
+    for v, r in zip((1, 2, 3), res):
+        assert np.all(r.map == 64.0 * v)
+    begins = [e for e in fake.log if e[0] == "begin"]
+    assert sum(b[3] for b in begins) == 3 and len(begins) <= 2   # at most the first one ran alone
+
+
+def test_a_solve_out_of_memory_waits_for_the_work_in_flight_and_is_retried(fake):
+    fake.gate = {80: threading.Event()}
+    fake.oom_begin = {81}
+    srv = server()
+    held = srv.submit(request(80, 1.0))
+    _wait_for(lambda: ("begin", 80) in [e[:2] for e in fake.log], "the first solve")
+    retried = srv.submit(request(81, 2.0))
+    _wait_for(lambda: ("oom", 81) in fake.log, "the failed allocation")
+    threading.Event().wait(0.05)
+    assert not any(e[:2] == ("begin", 81) for e in fake.log)     # waits while scan 80 runs
+    fake.gate[80].set()
+    assert np.all(retried.result(timeout=20).map == 128.0)
+    assert np.all(held.result(timeout=20).map == 64.0)
+    srv.stop()
+    assert srv.stats()["oom_requeued"] == 1 and srv.stats()["failed"] == 0

@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-8 residual per map (2-level vs M_BD), A·x samples/s, p99 latency"
 UNIT = "s/map"
-# ncu: k_filter_half<float, 0, 512, 9216> moved 140.1 MB read + 2.8 MB written for 1.68e7 samples
-NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (140.050432e6 + 2.814976e6) / 16777216
+# ncu: k_filter_half<float, 0, 512, 9216> moved 141.3 MB read + 3.0 MB written for 1.68e7 samples
+NCU_DRAM_BYTES_PER_SAMPLE_HALF_F32 = (141.282304e6 + 2.973184e6) / 16777216
 
 
 def parse():

@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--filter", type=int, default=0, help="apply mode: 0 autotuned, 1 direct band, 2 FFT")
     ap.add_argument("--fft-len", type=int, default=0, help="apply mode: forced transform length (0: autotuned)")
     ap.add_argument("--apply-precision", default="f32", choices=["f32", "f64", "df"])
+    ap.add_argument("--apply-rhs", type=int, default=1, help="apply mode: right-hand sides per product")
     ap.add_argument("--half", type=int, default=1, choices=[0, 1],
                     help="apply mode: allow whole blocks as half-length complex transforms")
     ap.add_argument("--n-rhs", type=int, default=64)
@@ -958,7 +959,8 @@ def run_apply(args, world, rank, local):
         ctx.set_option("apply_precision", 2)
     ctx.set_option("half_transform", args.half)
     ctx.setup_scan(scan)
-    x = torch.randn((1, scan.n_pix, 3), dtype=torch.float64, device="cuda")
+    nrhs = max(1, args.apply_rhs)
+    x = torch.randn((nrhs, scan.n_pix, 3), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(max(1, args.warmup)):
         ctx.apply_A(x, out=y)
@@ -974,12 +976,13 @@ def run_apply(args, world, rank, local):
         except Exception:
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
+        # algorithmic bytes: each sample's pix and psi once per launch, whatever the right-hand sides
         gbs = 8.0 * scan.n_samples / (ms * 1e-3) / 1e9
         print(json.dumps({"mode": "apply", "config": args.config, "n_det": scan.n_det, "half_bw": scan.half_bw,
-                          "samples": scan.n_samples, "precision": args.apply_precision,
+                          "samples": scan.n_samples, "n_rhs": nrhs, "precision": args.apply_precision,
                           "fft_len": int(ctx.get_option("plan_fft_len")),
                           "plan_whole": int(ctx.get_option("plan_whole")), "filter_ms": ms,
-                          "samples_per_s": scan.n_samples / (ms * 1e-3), "hbm_gbs_8B_per_sample": gbs,
+                          "samples_per_s": nrhs * scan.n_samples / (ms * 1e-3), "hbm_gbs_8B_per_sample": gbs,
                           "hbm_frac_of_measured": gbs / hbm}), flush=True)
     ctx.close()
 

@@ -156,7 +156,8 @@ struct mm_ctx {
     int64_t harvest_len = 0;         // samples per detector of the harvested right-hand side
     int opt_coarse_fallback = 1;     // uneven batches: M_BD for right-hand sides of another length
     int opt_tc_coarse = 1;           // M_2l coarse products on the tensor cores: 0 never, 1 large maps, 2 always
-    DevBuf w_zu;                     // Z U and A Z U of the tensor-core M_2l
+    DevBuf w_zu;                     // scratch of the tensor-core M_2l (split-K and r^T z partials)
+    DevBuf w_u;                      // U = E^-1 Z^T x of mm_apply_precond
     std::vector<int32_t> precond_used;
     // cross-rank sum of partial products (timeline split across processes)
     mm_reduce_fn reduce_fn = nullptr;
@@ -1866,9 +1867,11 @@ mm_status mm_apply_A(mm_ctx* ctx, const double* x, double* y, int32_t nrhs, int 
     NvtxRange nvtx_range(__func__);
     TRY(ensure_work(ctx, nrhs, ctx->k));
     const int64_t nv = (int64_t)nrhs * ctx->n_pix;
-    DevBuf in3, in4, out4;
-    CK(in4.ensure(nv * sizeof(V4<double>)));
-    CK(out4.ensure(nv * sizeof(V4<double>)));
+    // the context's work vectors (sized for nrhs by ensure_work) hold the 4-wide copies, so repeated
+    // calls allocate nothing on the device
+    DevBuf in3;
+    DevBuf& in4 = ctx->w_a;
+    DevBuf& out4 = ctx->w_b;
     const double* xsrc = x;
     if (mem == MM_HOST) {
         CK(in3.ensure(nv * 3 * 8));
@@ -1912,9 +1915,12 @@ mm_status mm_apply_precond(mm_ctx* ctx, mm_precond which, const double* x, doubl
     NvtxRange nvtx_range(__func__);
     TRY(ensure_work(ctx, nrhs, ctx->k));
     const int64_t nv = (int64_t)nrhs * ctx->n_pix;
-    DevBuf in3, in4, out4, u;
-    CK(in4.ensure(nv * sizeof(V4<double>)));
-    CK(out4.ensure(nv * sizeof(V4<double>)));
+    // the context's work vectors (sized for nrhs by ensure_work) hold the 4-wide copies, so repeated
+    // calls allocate nothing on the device
+    DevBuf in3;
+    DevBuf& in4 = ctx->w_a;
+    DevBuf& out4 = ctx->w_b;
+    DevBuf& u = ctx->w_u;
     const double* xsrc = x;
     if (mem == MM_HOST) {
         CK(in3.ensure(nv * 24));

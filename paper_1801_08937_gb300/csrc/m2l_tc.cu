@@ -14,7 +14,11 @@
 //      in TMEM) and finishes M_BD (R - AZ U) + Z U per pixel from TMEM on the
 //      CUDA cores, with the fused inner product r^T z of the PCG step; Z U and
 //      AZ U never reach memory.  R and Z are read twice (U depends on all of
-//      the map), AZ and the output once.
+//      the map), AZ and the output once.  The epilogue works in float32 (the
+//      products it combines carry about 21 bits): the GB300's float64 pipe
+//      runs about two FMAs per clock per SM, so a float64 epilogue would take
+//      longer than the loads; r^T z sums a warp's 32 float32 products in
+//      float32 and everything beyond in float64.
 //
 // Operands are TF32 (kind::tf32, float32 accumulation).  Each float64 value x
 // is rounded to float32 and split into a TF32 high part and the TF32 rounding
@@ -35,7 +39,6 @@
 
 namespace mm {
 
-constexpr int TC_NT = 128;       // one warpgroup: thread t reads TMEM lane t
 constexpr int TC_KT = 32;        // K elements per stage of the Z^T R product
 constexpr int TC_MAX_RHS = 128;
 constexpr int TC_MAX_K = 64;
@@ -54,18 +57,23 @@ __device__ __forceinline__ unsigned long long tc_now() {
 __device__ __forceinline__ void tc_mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
 }
-// true once the phase with `parity` has completed; false after TC_WAIT_NS
+__device__ __forceinline__ bool tc_mbar_try(uint32_t a, unsigned parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+// true once the phase with `parity` has completed; false after TC_WAIT_NS (the timer is read only
+// when the first try finds the phase still open)
 __device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, unsigned parity) {
     const uint32_t a = saddr(bar);
+    if (tc_mbar_try(a, parity)) return true;
     const unsigned long long t0 = tc_now();
     for (;;) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (done) return true;
+        if (tc_mbar_try(a, parity)) return true;
         if (tc_now() - t0 > TC_WAIT_NS) return false;
     }
 }
@@ -118,12 +126,39 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x (float64) as a TF32 high part and the TF32 rounding of the remainder
+// float64 -> float32 by truncation of the significand and float32 -> float64
+// (exact) with integer operations: on the GB300 the hardware conversions run
+// on the float64 pipe, about two per clock per SM, which would bound these
+// kernels.  Zeros (the fourth entry of every pixel) take the integer path
+// too; values outside float32's normal range, denormals, infinities and NaN
+// fall back to the hardware conversion.
+// the hardware conversions, out of line so that the rare path stays a branch
+// instead of being computed for every element and selected
+__device__ __noinline__ float d2f_hw(double x) { return (float)x; }
+__device__ __noinline__ double f2d_hw(float f) { return (double)f; }
+__device__ __forceinline__ float d2f_trunc(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    if (((hi << 1) | lo) == 0u) return __uint_as_float(hi);
+    const int e = (int)((hi >> 20) & 0x7FF) - 1023 + 127;
+    if (e <= 0 || e >= 255) return d2f_hw(x);
+    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f2d_exact(float f) {
+    const uint32_t u = __float_as_uint(f);
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)u, 0);
+    const uint32_t e = (u >> 23) & 0xFF;
+    if (e == 0u || e == 0xFFu) return f2d_hw(f);
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)),
+                            (int)(u << 29));
+}
+
+// x (float64) as a TF32 high part (the float32 value with its 13 low
+// significand bits cleared) and the exact float32 remainder, truncated to TF32
+// the same way: hi + lo holds about 22 significant bits of x.
 __device__ __forceinline__ void tf32_split(double xd, uint32_t& hi, uint32_t& lo) {
-    const float x = (float)xd;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-    const float rem = x - __uint_as_float(hi);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(rem));
+    const float x = d2f_trunc(xd);
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi)) & 0xFFFFE000u;
 }
 // Byte offset of the 16-byte group kc (elements 4 kc .. 4 kc + 3) of row r in
 // a K-major tile without swizzle whose 8-row groups are sbo bytes apart.
@@ -138,38 +173,45 @@ __host__ __device__ constexpr uint32_t tc_cols(int n) {   // TMEM columns: a pow
     return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : (n <= 256 ? 256u : 512u)));
 }
 
-// One stage (TC_KT elements from kb, zero from k1 on) of a float64 row into
-// row r of the TF32 high and low tiles.
-__device__ __forceinline__ void stage_row(const double* row, int64_t kb, int64_t k1, int r, uint32_t hi_tile,
-                                          uint32_t lo_tile, uint32_t sbo) {
-    double v[TC_KT];
-    if (kb + TC_KT <= k1) {
+// Half a stage (TC_SEG elements from kb, zero from k1 on) of a float64 row
+// into registers (rows start at multiples of 4 n_pix doubles and kb at
+// multiples of TC_SEG, so the segment is 16-byte aligned), and from registers
+// into row r, 16-byte groups kc0 .. kc0 + TC_SEG / 4 - 1, of the TF32 high and
+// low tiles.
+constexpr int TC_SEG = TC_KT / 2;
+__device__ __forceinline__ void load_seg(const double* row, int64_t kb, int64_t k1, double (&v)[TC_SEG]) {
+    if (kb + TC_SEG <= k1) {
         const double2* p = reinterpret_cast<const double2*>(row + kb);
 #pragma unroll
-        for (int j = 0; j < TC_KT / 2; ++j) {
+        for (int j = 0; j < TC_SEG / 2; ++j) {
             const double2 d = __ldg(p + j);
             v[2 * j] = d.x;
             v[2 * j + 1] = d.y;
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < TC_KT; ++j) v[j] = kb + j < k1 ? __ldg(row + kb + j) : 0.0;
+        for (int j = 0; j < TC_SEG; ++j) v[j] = kb + j < k1 ? __ldg(row + kb + j) : 0.0;
     }
+}
+__device__ __forceinline__ void store_seg(const double (&v)[TC_SEG], int r, int kc0, uint32_t hi_tile,
+                                          uint32_t lo_tile, uint32_t sbo) {
 #pragma unroll
-    for (int kc = 0; kc < TC_KT / 4; ++kc) {
+    for (int kc = 0; kc < TC_SEG / 4; ++kc) {
         uint32_t h[4], l[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) tf32_split(v[4 * kc + j], h[j], l[j]);
-        const uint32_t o = tc_off(r, kc, sbo);
+        const uint32_t o = tc_off(r, kc0 + kc, sbo);
         st_shared_v4(hi_tile + o, h[0], h[1], h[2], h[3]);
         st_shared_v4(lo_tile + o, l[0], l[1], l[2], l[3]);
     }
 }
 
-// ---- 1. T = Z^T R (split-K), then U = E^-1 T in the last CTA ----
+// ---- 1. T = Z^T R (split-K) ----
 // Dynamic shared memory: two stages of [A_hi, A_lo (128 x TC_KT), B_hi, B_lo
-// (np x TC_KT)] TF32, then two mbarriers and the TMEM address.
-__global__ void __launch_bounds__(TC_NT, 1) k_m2l_tc_ztr(const PcgArgs a, const V4<double>* r, int kchunk) {
+// (np x TC_KT)] TF32, then two mbarriers and the TMEM address.  Eight warps:
+// all stage operands, warps 0-3 read the accumulator (TMEM lanes 0-127).
+constexpr int TC_ZT = 256;
+__global__ void __launch_bounds__(TC_ZT, 2) k_m2l_tc_ztr(const PcgArgs a, const V4<double>* r, int kchunk) {
     extern __shared__ __align__(128) unsigned char sm[];
     const int nrhs = a.nrhs, k = a.k;
     const int np = (k + 15) & ~15;
@@ -200,6 +242,24 @@ __global__ void __launch_bounds__(TC_NT, 1) k_m2l_tc_ztr(const PcgArgs a, const 
     const uint32_t idesc = tc_idesc(128, np);
     const uint32_t base = saddr(sm);
     bool ok = true;
+    // Staged rows: the nrhs rows of R (A operand) then the k rows of Z (B operand), each as two
+    // half-stage items (item = 2 row + half); thread t takes item t and, when there are more than
+    // TC_ZT items, item t + TC_ZT.  Item t's next stage is loaded into registers while the current
+    // one is converted and multiplied.
+    const int n_items = 2 * (nrhs + k);
+    auto item_src = [&](int it) {
+        const int r = it >> 1;
+        return (r < nrhs ? R + (int64_t)r * n4 : Z + (int64_t)(r - nrhs) * n4) + (it & 1) * TC_SEG;
+    };
+    auto item_store = [&](const double (&v)[TC_SEG], int it, uint32_t sa) {
+        const int r = it >> 1, kc0 = (it & 1) * (TC_SEG / 4);
+        if (r < nrhs) store_seg(v, r, kc0, sa, sa + a_bytes, sbo);
+        else store_seg(v, r - nrhs, kc0, sa + 2 * a_bytes, sa + 2 * a_bytes + b_bytes, sbo);
+    };
+    auto item_k1 = [&](int it) { return k1 - (it & 1) * TC_SEG; };   // the row's end, shifted like its start
+    const bool has1 = tid < n_items, has2 = tid + TC_ZT < n_items;
+    double pre[TC_SEG];
+    if (has1 && nst > 0) load_seg(item_src(tid), k0, item_k1(tid), pre);
     for (int st = 0; st < nst && ok; ++st) {
         const int b = st & 1;
         if (st >= 2) ok = tc_mbar_wait(bars + b, ((st - 2) >> 1) & 1);   // MMAs of stage st - 2 read this buffer
@@ -209,10 +269,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_m2l_tc_ztr(const PcgArgs a, const 
         }
         const uint32_t sa = base + b * stage_bytes;
         const int64_t kb = k0 + (int64_t)st * TC_KT;
-        // A: row tid = right-hand side tid; B: row tid = coarse vector tid.  A whole stage of a row
-        // (32 doubles, 16-byte aligned: rows start at multiples of 4 n_pix) is requested at once.
-        if (tid < nrhs) stage_row(R + (int64_t)tid * n4, kb, k1, tid, sa, sa + a_bytes, sbo);
-        if (tid < k) stage_row(Z + (int64_t)tid * n4, kb, k1, tid, sa + 2 * a_bytes, sa + 2 * a_bytes + b_bytes, sbo);
+        if (has1) item_store(pre, tid, sa);
+        if (has2) {
+            double v2[TC_SEG];
+            load_seg(item_src(tid + TC_ZT), kb, item_k1(tid + TC_ZT), v2);
+            item_store(v2, tid + TC_ZT, sa);
+        }
+        if (has1 && st + 1 < nst) load_seg(item_src(tid), kb + TC_KT, item_k1(tid), pre);
         tc_fence_proxy();
         __syncthreads();
         if (tid == 0) {
@@ -234,7 +297,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_m2l_tc_ztr(const PcgArgs a, const 
     if (ok && nst > 0) ok = tc_mbar_wait(bars + ((nst - 1) & 1), ((nst - 1) >> 1) & 1);
     ok = __syncthreads_and(ok);
     tc_fence_after();
-    if (ok) {
+    if (ok && warp < 4) {
         // every lane of the warp executes each (warp-collective) TMEM load; only the stores are predicated
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         double* part = a.partial + ((int64_t)blockIdx.x * nrhs + tid) * k;
@@ -351,39 +414,51 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
     // epilogue: this thread's TMEM lane is tile row q * 32 + lane, its columns half * nh .. + nh - 1
     const int nh = nr / 2, comp = lane & 3;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    bool ok = true;
-    int it = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-        const int64_t i0 = (int64_t)tile * 128;
-        {
-            const int64_t i = i0 + row;
-            const bool rin = i < n4;
-            for (int oct = oct_begin; oct < oct_end; ++oct) {
-                const int kc = 2 * oct;
-                double zv[8], av[8];
+    // this thread's row of a tile, for at most TC_MAX_K / 16 blocks of eight coarse vectors
+    constexpr int MAX_OCT = TC_MAX_K / 16;
+    double zv[MAX_OCT][8], av[MAX_OCT][8];
+    auto load_tile = [&](int tile) {
+        const int64_t i = (int64_t)tile * 128 + row;
+        const bool rin = i < n4;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c = 4 * kc + j;
-                    const bool in = rin && c < k;
-                    zv[j] = in ? __ldg(Z + (int64_t)c * n4 + i) : 0.0;
-                    av[j] = in ? __ldg(AZ + (int64_t)c * n4 + i) : 0.0;
-                }
+        for (int o = 0; o < MAX_OCT; ++o) {
+            const int oct = oct_begin + o;
 #pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    uint32_t zh[4], zl[4], ah[4], al[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        tf32_split(zv[4 * g + j], zh[j], zl[j]);
-                        tf32_split(av[4 * g + j], ah[j], al[j]);
-                    }
-                    const uint32_t o = tc_off(row, kc + g, sbo);
-                    st_shared_v4(at + o, zh[0], zh[1], zh[2], zh[3]);
-                    st_shared_v4(at + a_bytes + o, zl[0], zl[1], zl[2], zl[3]);
-                    st_shared_v4(at + 2 * a_bytes + o, ah[0], ah[1], ah[2], ah[3]);
-                    st_shared_v4(at + 3 * a_bytes + o, al[0], al[1], al[2], al[3]);
-                }
+            for (int j = 0; j < 8; ++j) {
+                const int c = 8 * oct + j;
+                const bool in = rin && oct < oct_end && c < k;
+                zv[o][j] = in ? __ldg(Z + (int64_t)c * n4 + i) : 0.0;
+                av[o][j] = in ? __ldg(AZ + (int64_t)c * n4 + i) : 0.0;
             }
         }
+    };
+    auto store_tile = [&]() {
+#pragma unroll
+        for (int o = 0; o < MAX_OCT; ++o) {
+            if (oct_begin + o >= oct_end) continue;
+            const int kc = 2 * (oct_begin + o);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint32_t zh[4], zl[4], ah[4], al[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    tf32_split(zv[o][4 * g + j], zh[j], zl[j]);
+                    tf32_split(av[o][4 * g + j], ah[j], al[j]);
+                }
+                const uint32_t off = tc_off(row, kc + g, sbo);
+                st_shared_v4(at + off, zh[0], zh[1], zh[2], zh[3]);
+                st_shared_v4(at + a_bytes + off, zl[0], zl[1], zl[2], zl[3]);
+                st_shared_v4(at + 2 * a_bytes + off, ah[0], ah[1], ah[2], ah[3]);
+                st_shared_v4(at + 3 * a_bytes + off, al[0], al[1], al[2], al[3]);
+            }
+        }
+    };
+    bool ok = true;
+    int it = 0;
+    load_tile(blockIdx.x);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        const int64_t i0 = (int64_t)tile * 128;
+        store_tile();   // the previous tile's MMAs have completed and its TMEM has been read
         tc_fence_proxy();
         tc_fence_before();
         __syncthreads();
@@ -405,6 +480,7 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
             }
             tc_commit(bar);
         }
+        if (tile + (int)gridDim.x < n_tiles) load_tile(tile + gridDim.x);   // in flight during the MMAs and epilogue
         ok = tc_mbar_wait(bar, it & 1);
         ok = __syncthreads_and(ok);
         tc_fence_after();
@@ -415,14 +491,18 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
         // row comp of the pixel's symmetric block [m0 m1 m2; m1 m3 m4; m2 m4 m5]
         const int r0 = comp == 0 ? 0 : (comp == 1 ? 1 : 2), r1 = comp == 0 ? 1 : (comp == 1 ? 3 : 4),
                   r2 = comp == 0 ? 2 : (comp == 1 ? 4 : 5);
-        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
         if (in && comp < 3 && !a.bd_per_rhs) {
             const double* m = a.bd + pix * 6;
-            b0 = m[r0];
-            b1 = m[r1];
-            b2 = m[r2];
+            b0 = (float)m[r0];
+            b1 = (float)m[r1];
+            b2 = (float)m[r2];
         }
         for (int n0 = half * nh; n0 < half * nh + nh; n0 += 8) {
+            // the chunk's eight inputs are requested together, before the TMEM reads
+            double xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xs[j] = in && n0 + j < nrhs ? __ldg(V + (int64_t)(n0 + j) * n4 + i) : 0.0;
             float dz[8], daz[8];
             tc_ld8(lane_addr + n0, dz);
             tc_ld8(lane_addr + nr + n0, daz);
@@ -431,25 +511,26 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
                 const int n = n0 + j;   // the same in every lane of the warp
                 if (n >= nrhs) break;
                 const bool active = !a.st || a.st[n].active;
-                const double x = in ? V[(int64_t)n * n4 + i] : 0.0;
-                const double y = x - (double)daz[j];
+                const float x = d2f_trunc(xs[j]);
+                const float y = x - daz[j];
                 const int qb = lane & ~3;
-                const double y0 = __shfl_sync(0xffffffffu, y, qb), y1 = __shfl_sync(0xffffffffu, y, qb + 1),
-                             y2 = __shfl_sync(0xffffffffu, y, qb + 2);
-                double m0 = b0, m1 = b1, m2 = b2;
+                const float y0 = __shfl_sync(0xffffffffu, y, qb), y1 = __shfl_sync(0xffffffffu, y, qb + 1),
+                            y2 = __shfl_sync(0xffffffffu, y, qb + 2);
+                float m0 = b0, m1 = b1, m2 = b2;
                 if (a.bd_per_rhs && in && comp < 3) {
                     const double* m = a.bd + ((int64_t)n * a.n_pix + pix) * 6;
-                    m0 = m[r0];
-                    m1 = m[r1];
-                    m2 = m[r2];
+                    m0 = (float)m[r0];
+                    m1 = (float)m[r1];
+                    m2 = (float)m[r2];
                 }
-                const double o = comp < 3 ? m0 * y0 + m1 * y1 + m2 * y2 + (double)dz[j] : 0.0;
-                if (in && active) O[(int64_t)n * n4 + i] = o;
+                const float o = comp < 3 ? fmaf(m0, y0, fmaf(m1, y1, fmaf(m2, y2, dz[j]))) : 0.0f;
+                if (in && active) O[(int64_t)n * n4 + i] = f2d_exact(o);
                 if (finalize_beta >= 0) {
-                    double d = x * o;
+                    // the warp's 32 products summed in float32, the warps' sums in float64
+                    float d = x * o;
 #pragma unroll
                     for (int s = 16; s > 0; s >>= 1) d += __shfl_down_sync(0xffffffffu, d, s);
-                    if (lane == 0) racc[q * nr + n] += d;
+                    if (lane == 0) racc[q * nr + n] += (double)d;
                 }
             }
         }
@@ -549,7 +630,7 @@ void launch_m2l_tc(const PcgArgs& a, const V4<double>* v, V4<double>* out, int f
     });
     PcgArgs a1 = a;
     a1.partial = scratch;
-    k_m2l_tc_ztr<<<g_used, TC_NT, sm1, s>>>(a1, v, kchunk);
+    k_m2l_tc_ztr<<<g_used, TC_ZT, sm1, s>>>(a1, v, kchunk);
     k_m2l_tc_u<<<nrhs, TC_UT, 0, s>>>(a, scratch, g_used);
     k_m2l_tc_zu_apply<<<g2, TC_AT, sm2, s>>>(a, v, out, finalize_beta, scratch + (size_t)g1 * nrhs * std::max(k, 1),
                                              n_tiles);

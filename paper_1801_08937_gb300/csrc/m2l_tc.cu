@@ -356,13 +356,16 @@ __global__ void __launch_bounds__(TC_UT) k_m2l_tc_u(const PcgArgs a, const doubl
 // map entry, K = coarse index), forms D_z = Z U and D_az = AZ U in TMEM
 // (columns [0, nr) and [nr, 2 nr)), and finishes on the CUDA cores: warp w
 // reads TMEM lanes 32 (w % 4) .. + 31 (32 map entries = 8 pixels) for the
-// right-hand sides of half w / 4, exchanges the residual's Stokes entries of a
+// 8-column chunks w / 4, w / 4 + 4, ... of the right-hand sides (sixteen warps
+// also share the staging: thread t stages row t % 128 of the tile for a
+// quarter of the coarse vectors), exchanges the residual's Stokes entries of a
 // pixel within a quad of lanes, applies the pixel's 3x3 block of M_BD and adds
 // Z U.  r^T z per right-hand side (when finalize_beta >= 0) is summed per warp
 // and tile in a fixed order, then over CTAs in CTA order by the last CTA.
 // Dynamic shared memory: B_hi, B_lo (nr x kp), A tiles Z_hi, Z_lo, AZ_hi,
 // AZ_lo (128 x kp), r^T z sums [4][nr], one mbarrier, the TMEM address.
-constexpr int TC_AT = 256;
+constexpr int TC_AT = 512;              // four groups of four warps
+constexpr int TC_AG = TC_AT / 128;
 __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, const V4<double>* v, V4<double>* out,
                                                               int finalize_beta, double* partial, int n_tiles) {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
     double* racc = reinterpret_cast<double*>(sm + 2 * b_bytes + 4 * a_bytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(racc + 4 * nr);
     uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, half = warp >> 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, grp = warp >> 2;
     const uint32_t ncols = tc_cols(2 * nr);
     const double* Z = reinterpret_cast<const double*>(a.Z);
     const double* AZ = reinterpret_cast<const double*>(a.AZ);
@@ -409,13 +412,14 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
     const uint32_t idesc = tc_idesc(128, nr);
     // staging: thread tid loads row (tid % 128) of the tile; the kp / 8 blocks of eight coarse
     // vectors are split between the two halves of the CTA (tid / 128)
-    const int row = tid & 127, n_oct = kp / 8, per_half = (n_oct + 1) / 2;
-    const int oct_begin = (tid >> 7) * per_half, oct_end = min(n_oct, oct_begin + per_half);
-    // epilogue: this thread's TMEM lane is tile row q * 32 + lane, its columns half * nh .. + nh - 1
-    const int nh = nr / 2, comp = lane & 3;
+    const int row = tid & 127, n_oct = kp / 8, per_grp = (n_oct + TC_AG - 1) / TC_AG;
+    const int oct_begin = (tid >> 7) * per_grp, oct_end = min(n_oct, oct_begin + per_grp);
+    // epilogue: this thread's TMEM lane is tile row q * 32 + lane; its columns are the 8-column chunks
+    // grp, grp + TC_AG, ... of the nr right-hand-side columns
+    const int comp = lane & 3;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     // this thread's row of a tile, for at most TC_MAX_K / 16 blocks of eight coarse vectors
-    constexpr int MAX_OCT = TC_MAX_K / 16;
+    constexpr int MAX_OCT = (TC_MAX_K / 8 + TC_AG - 1) / TC_AG;
     double zv[MAX_OCT][8], av[MAX_OCT][8];
     auto load_tile = [&](int tile) {
         const int64_t i = (int64_t)tile * 128 + row;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
             b1 = (float)m[r1];
             b2 = (float)m[r2];
         }
-        for (int n0 = half * nh; n0 < half * nh + nh; n0 += 8) {
+        for (int n0 = grp * 8; n0 < nr; n0 += 8 * TC_AG) {
             // the chunk's eight inputs are requested together, before the TMEM reads
             double xs[8];
 #pragma unroll

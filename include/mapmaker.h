@@ -316,7 +316,11 @@ mm_status mm_set_option(mm_ctx* ctx, const char* name, double value);
  * 1 whole blocks two per transform, 2 whole blocks as half-length complex
  * transforms), "harvested" (Lanczos
  * vectors kept by the last M_BD solve), "device_bytes" (device memory in use),
- * "coarse_len" (samples per detector of the operator the basis was built from).
+ * "coarse_len" (samples per detector of the operator the basis was built from),
+ * "coarse_rank_min" (the fewest coarse vectors a right-hand side of the last
+ * uneven two-level batch kept: a prefix of the scan that leaves part of the map
+ * unobserved makes E_i = Z^T A_i Z semi-definite, and M_2l,i then uses the
+ * columns of Z that a pivoted Cholesky factorisation of E_i keeps).
  * Errors: MM_ERR_ARG, MM_ERR_STATE. */
 mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value);
 

@@ -177,6 +177,7 @@ struct mm_ctx {
     // [(blocks per detector + 1)][k][n_pix][4], for uneven-length batches
     DevBuf d_Tpref;
     bool tpref_valid = false;
+    int coarse_rank_min = 0;           // smallest coarse rank a right-hand side of the last uneven batch kept
     // asynchronous stepping
     RhsState* h_st_pinned = nullptr;
     int h_st_pinned_n = 0;
@@ -1527,13 +1528,25 @@ mm_status coarse_for_lens(mm_ctx* ctx, const std::vector<uint8_t>& deflate) {
     std::vector<double> G((size_t)R * k * k), Einv_all((size_t)R * k * k);
     CK(cudaMemcpyAsync(G.data(), dG.p, G.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    // A prefix of the scan may leave part of the map unobserved, and with it directions of span Z
+    // on which A_i vanishes: E_i is then only semi-definite.  Its inverse is taken on the columns a
+    // pivoted Cholesky keeps (the coarse correction of the basis reduced to what the prefix sees;
+    // M_2l,i A_i Z_S = Z_S still holds).  The cut-off sits above the products' rounding level.
+    const double piv_tol = op_prec(ctx) == 0 ? 1e-5 : 1e-10;
+    ctx->coarse_rank_min = k;
     for (int r = 0; r < R; ++r) {
         const double* g = &G[(size_t)r * k * k];
         std::vector<double> E((size_t)k * k), Einv;
         for (int i = 0; i < k; ++i)
             for (int j = 0; j < k; ++j) E[(size_t)i * k + j] = 0.5 * (g[(size_t)j * k + i] + g[(size_t)i * k + j]);
-        if (!host_cholesky(E, k)) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not SPD");
-        host_spd_inverse_from_chol(E, k, Einv);
+        std::vector<double> L(E);
+        if (host_cholesky(L, k)) {
+            host_spd_inverse_from_chol(L, k, Einv);
+        } else {
+            const int rank = host_pivoted_spd_inverse(E, k, piv_tol, Einv);
+            if (rank < 0) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not semi-definite");
+            ctx->coarse_rank_min = std::min(ctx->coarse_rank_min, rank);
+        }
         if (!deflate[r]) std::fill(Einv.begin(), Einv.end(), 0.0);   // M_2l,r = M_BD,r
         std::copy(Einv.begin(), Einv.end(), Einv_all.begin() + (size_t)r * k * k);
     }
@@ -2687,6 +2700,7 @@ mm_status mm_get_option(mm_ctx* ctx, const char* name, double* value) {
     else if (n == "autotune") *value = ctx->opt_autotune;
     else if (n == "half_transform") *value = ctx->opt_half;
     else if (n == "coarse_prefix") *value = ctx->opt_coarse_prefix;
+    else if (n == "coarse_rank_min") *value = ctx->coarse_rank_min;
     else if (n == "coarse_fallback") *value = ctx->opt_coarse_fallback;
     else if (n == "tc_coarse") *value = ctx->opt_tc_coarse;
     else if (n == "coarse_len") *value = (double)ctx->coarse_len;

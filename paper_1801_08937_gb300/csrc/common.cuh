@@ -303,6 +303,7 @@ bool host_template_layout(const std::vector<int64_t>& block_off, const std::vect
 bool host_cholesky(std::vector<double>& A, int n);
 // Inverse of an SPD matrix from its Cholesky factor.
 void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector<double>& inv);
+int host_pivoted_spd_inverse(const std::vector<double>& E, int n, double rel_tol, std::vector<double>& inv);
 // Inverse of an upper-triangular matrix R (row-major).
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv);
 

@@ -491,6 +491,60 @@ void host_spd_inverse_from_chol(const std::vector<double>& L, int n, std::vector
         for (int b = 0; b < a; ++b) inv[(size_t)b * n + a] = inv[(size_t)a * n + b];
 }
 
+// Inverse of a symmetric positive semi-definite E restricted to the index set S
+// that a diagonally pivoted Cholesky factorisation keeps: pivots are taken
+// largest remaining Schur-complement diagonal first, and the factorisation
+// stops once that diagonal falls to rel_tol times the largest diagonal of E.
+// inv holds (E_SS)^-1 on S x S and 0 elsewhere, so that for E = Z^T A Z,
+// Z inv Z^T = Z_S (Z_S^T A Z_S)^-1 Z_S^T: the coarse correction of the basis
+// reduced to the columns in S.  Returns |S| (0 when E has no positive
+// diagonal; -1 if the kept block is not positive definite after all).
+int host_pivoted_spd_inverse(const std::vector<double>& E, int n, double rel_tol, std::vector<double>& inv) {
+    inv.assign((size_t)n * n, 0.0);
+    std::vector<double> d(n);
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        d[i] = E[(size_t)i * n + i];
+        if (std::isfinite(d[i])) dmax = std::max(dmax, d[i]);
+    }
+    if (!(dmax > 0.0)) return 0;
+    std::vector<int> S;
+    std::vector<char> used(n, 0);
+    std::vector<std::vector<double>> cols;   // columns of the pivoted factor, indexed by original row
+    for (int r = 0; r < n; ++r) {
+        int p = -1;
+        double best = rel_tol * dmax;
+        for (int i = 0; i < n; ++i)
+            if (!used[i] && d[i] > best) {
+                best = d[i];
+                p = i;
+            }
+        if (p < 0) break;
+        std::vector<double> l(n, 0.0);
+        const double lp = std::sqrt(d[p]);
+        for (int i = 0; i < n; ++i) {
+            if (used[i] || i == p) continue;
+            double v = E[(size_t)i * n + p];
+            for (const auto& c : cols) v -= c[i] * c[p];
+            l[i] = v / lp;
+            d[i] -= l[i] * l[i];
+        }
+        l[p] = lp;
+        used[p] = 1;
+        S.push_back(p);
+        cols.push_back(std::move(l));
+    }
+    const int m = (int)S.size();
+    std::vector<double> Es((size_t)m * m), Einv;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) Es[(size_t)a * m + b] = E[(size_t)S[a] * n + S[b]];
+    if (!host_cholesky(Es, m)) return -1;
+    host_spd_inverse_from_chol(Es, m, Einv);
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) inv[(size_t)S[a] * n + S[b]] = Einv[(size_t)a * m + b];
+    return m;
+}
+
 void host_upper_inverse(const std::vector<double>& R, int n, std::vector<double>& Rinv) {
     // row i of R^-1 = (e_i - sum_{k>i} R_ik row k of R^-1) / R_ii, from the last row up
     Rinv.assign((size_t)n * n, 0.0);

@@ -548,6 +548,68 @@ def test_batched_two_level_uneven_lengths(prec):
         assert_close(xb[i][well], xo[well], 1e-6)
 
 
+def test_uneven_two_level_batch_deflates_like_the_oracle():
+    """A basis from the full-length operator deflates prefixes of the scan (Sect. 7's reuse of one
+    basis): each right-hand side of an uneven batch takes as many two-level products as the
+    oracle's PCG with M_2l built from the same Z and that prefix's own A_i Z, E_i and M_BD,i
+    (Sect. 3.2, Eq. m2l), within 2, and clearly fewer than M_BD."""
+    cfg = dict(nx=16, ny=16, n_det=4, n_t=32768, n_int=8, half_bw=128, f_knee=1.0)
+    scan = synth.make_scan(seed=19, **cfg)
+    lens = np.array([32768, 28672, 20000, 16384], dtype=np.int64)   # 20000: a partly covered block
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 410 + i), synth.make_noise(scan, 410 + i))
+                     for i in range(len(lens))])
+    c = ctx_for(scan, MM.MM_FP64)
+    c.set_option("coarse_fallback", 0)
+    c.build_bd()
+    k = c.build_coarse(c.rhs(tods[:1])[0], m_max=150, eps_arn=1e-12, k=16)
+    Z, _ = c.get_coarse()
+    _, ib = c.solve(tods, MM.MM_PRECOND_2L, tol=1e-8, max_iter=2000, rhs_len=lens)
+    _, ibd = c.solve(tods, MM.MM_PRECOND_BD, tol=1e-8, max_iter=2000, rhs_len=lens)
+    c.close()
+    _, _, good = oracle_problem(scan)
+    Zf = Z.reshape(k, -1).T
+    for i, L in enumerate(lens):
+        prob, mbd, idx = truncated_problem(scan, int(L), good=good)
+        A = lambda v: O.apply_A(prob, v.reshape(-1, 3)).reshape(-1)  # noqa: E731
+        Mb = lambda v: O.bd_apply(mbd, v).reshape(-1)  # noqa: E731
+        AZ, _, Lc = O.coarse_space(A, Zf)
+        b = O.rhs(prob, tods[i][idx]).reshape(-1)
+        _, io = O.pcg(A, lambda v: O.m2l_apply(v, Mb, Zf, AZ, Lc), b, tol=1e-8, max_iter=2000)
+        _, iob = O.pcg(A, Mb, b, tol=1e-8, max_iter=2000)
+        assert abs(ib[i]["iters"] - io["iters"]) <= 2, (i, int(L), ib[i]["iters"], io["iters"])
+        assert abs(ibd[i]["iters"] - iob["iters"]) <= 1, (i, int(L), ibd[i]["iters"], iob["iters"])
+        assert ib[i]["precond_used"] == "M_2l"
+
+
+def test_uneven_two_level_batch_with_a_prefix_blind_to_part_of_the_basis():
+    """A prefix of about half the scan sees about half the patch (the elevation drifts across it
+    once per timeline), so some direction of span Z lies where A_i vanishes and E_i = Z^T A_i Z is
+    only semi-definite.  The batch still solves: that right-hand side keeps the columns of Z a
+    pivoted Cholesky factorisation of E_i retains (option coarse_rank_min reports how many), takes
+    no more products than M_BD, and its map matches the oracle on the pixels the prefix observes."""
+    scan = synth.make_scan(nx=32, ny=32, n_det=8, n_t=1 << 17, n_int=32, half_bw=512, f_knee=1.0, seed=0)
+    lens = np.array([1 << 17, 99079, 67820], dtype=np.int64)
+    tods = np.stack([synth.make_tod(scan, synth.make_sky(scan.n_pix, 1000 + i), synth.make_noise(scan, 1000 + i))
+                     for i in range(len(lens))])
+    c = ctx_for(scan, MM.MM_FP64)
+    c.set_option("coarse_fallback", 0)
+    c.build_bd(1e-3)
+    k = c.build_coarse(c.rhs(tods[:1])[0], m_max=200, eps_arn=1e-12, k=32)
+    x2, i2 = c.solve(tods, MM.MM_PRECOND_2L, tol=1e-10, max_iter=2000, rhs_len=lens)
+    assert c.get_option("coarse_rank_min") < k
+    _, ib = c.solve(tods, MM.MM_PRECOND_BD, tol=1e-10, max_iter=2000, rhs_len=lens)
+    c.close()
+    _, _, good = oracle_problem(scan)
+    for i, L in enumerate(lens):
+        assert i2[i]["status"] == "MM_OK" and i2[i]["iters"] <= ib[i]["iters"], (i, i2[i]["iters"], ib[i]["iters"])
+        if i == 2:
+            prob, mbd, idx = truncated_problem(scan, int(L), good=good)
+            xo = _oracle_solution(prob, mbd, O.rhs(prob, tods[i][idx])).reshape(-1, 3)
+            well = np.abs(mbd).reshape(scan.n_pix, -1).sum(axis=1) > 0
+            assert well.sum() < 0.8 * scan.n_pix          # the prefix leaves part of the map unobserved
+            assert_close(x2[i][well], xo[well], 1e-6, "prefix blind to part of Z vs oracle")
+
+
 def test_status_codes_not_converged_and_breakdown():
     scan, d, _ = scan_and_tod(SMALL, seed=23)
     c = ctx_for(scan)

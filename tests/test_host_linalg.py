@@ -112,6 +112,12 @@ extern "C" int t_chol_inv(const double* A, int n, double* L, double* inv) {
     for (size_t i = 0; i < (size_t)n * n; ++i) { L[i] = a[i]; inv[i] = v[i]; }
     return 1;
 }
+extern "C" int t_pivoted_inv(const double* A, int n, double tol, double* inv) {
+    std::vector<double> a(A, A + (size_t)n * n), v;
+    const int r = mm::host_pivoted_spd_inverse(a, n, tol, v);
+    for (size_t i = 0; i < (size_t)n * n; ++i) inv[i] = v[i];
+    return r;
+}
 extern "C" void t_upper_inv(const double* R, int n, double* Ri) {
     std::vector<double> r(R, R + (size_t)n * n), v;
     mm::host_upper_inverse(r, n, v);
@@ -165,6 +171,7 @@ def eig(tmp_path_factory):
     lib.t_raise_smem.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     lib.t_ritz.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P, C.POINTER(C.c_int)]
     lib.t_upper_inv.argtypes = [P, C.c_int, P]
+    lib.t_pivoted_inv.argtypes = [P, C.c_int, C.c_double, P]
 
     def p(a):
         return a.ctypes.data_as(P)
@@ -189,6 +196,12 @@ def eig(tmp_path_factory):
         L, inv = np.zeros((n, n)), np.zeros((n, n))
         ok = lib.t_chol_inv(p(A), n, p(L), p(inv))
         return (L, inv) if ok == 1 else None
+
+    def pivoted_inv(A, tol):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        inv = np.zeros_like(A)
+        r = lib.t_pivoted_inv(p(A), A.shape[0], float(tol), p(inv))
+        return r, inv
 
     def upper_inv(R):
         R = np.ascontiguousarray(R, dtype=np.float64)
@@ -254,6 +267,7 @@ def eig(tmp_path_factory):
     vals.tri = tri
     vals.tri_vec = tri_vec
     vals.upper_inv = upper_inv
+    vals.pivoted_inv = pivoted_inv
     return vals, vec
 
 
@@ -383,6 +397,34 @@ def test_cholesky_and_spd_inverse(eig, n):
     if n > 1:
         E[0, 0] = -1.0
         assert vals.chol_inv(E) is None
+
+
+@pytest.mark.parametrize("n,visible", [(6, 6), (12, 7), (32, 20)])
+def test_pivoted_inverse_of_a_semidefinite_coarse_operator(eig, n, visible):
+    """E = Z^T A Z where A sees only part of the map (a prefix of a scan): `visible` directions of
+    span Z lie where A is positive definite, the others where A is zero, mixed over all columns.
+    The kept index set S has that size, inv equals (E_SS)^-1 on S and 0 elsewhere, and the coarse
+    correction Z inv Z^T acts on the range of A like the pseudo-inverse one (Sect. 3.2)."""
+    vals, _ = eig
+    rng = np.random.default_rng(n + visible)
+    N, rank = 3 * n, visible + 4
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    A = Q[:, :rank] @ np.diag(rng.uniform(0.5, 2.0, rank)) @ Q[:, :rank].T
+    parts = [Q[:, :rank] @ rng.standard_normal((rank, visible)), Q[:, rank:rank + n - visible]]
+    Z, _ = np.linalg.qr(np.hstack(parts) @ np.linalg.qr(rng.standard_normal((n, n)))[0])
+    E = Z.T @ A @ Z
+    E = 0.5 * (E + E.T)
+    r, inv = vals.pivoted_inv(E, 1e-10)
+    assert r == visible
+    S = np.where(np.abs(inv).sum(axis=1) > 0)[0]
+    assert len(S) == r
+    np.testing.assert_allclose(inv[np.ix_(S, S)], np.linalg.inv(E[np.ix_(S, S)]), rtol=1e-9, atol=1e-12)
+    P = Z @ inv @ Z.T
+    P_ref = Z @ np.linalg.pinv(E, rcond=1e-9) @ Z.T
+    np.testing.assert_allclose(A @ P @ A, A @ P_ref @ A, atol=1e-9 * np.abs(A).max())
+    if r == n:
+        np.testing.assert_allclose(inv, np.linalg.inv(E), rtol=1e-9, atol=1e-12)
+    assert vals.pivoted_inv(np.zeros((4, 4)), 1e-10)[0] == 0
 
 
 @pytest.mark.parametrize("n", [1, 5, 80])

@@ -1530,8 +1530,9 @@ mm_status coarse_for_lens(mm_ctx* ctx, const std::vector<uint8_t>& deflate) {
     CK(cudaStreamSynchronize(ctx->stream));
     // A prefix of the scan may leave part of the map unobserved, and with it directions of span Z
     // on which A_i vanishes: E_i is then only semi-definite.  Its inverse is taken on the columns a
-    // pivoted Cholesky keeps (the coarse correction of the basis reduced to what the prefix sees;
-    // M_2l,i A_i Z_S = Z_S still holds).  The cut-off sits above the products' rounding level.
+    // pivoted Cholesky keeps (all of them when E_i is well conditioned; otherwise the coarse
+    // correction of the basis reduced to what the prefix sees, for which M_2l,i A_i Z_S = Z_S
+    // holds).  The cut-off sits above the products' rounding level.
     const double piv_tol = op_prec(ctx) == 0 ? 1e-5 : 1e-10;
     ctx->coarse_rank_min = k;
     for (int r = 0; r < R; ++r) {
@@ -1539,15 +1540,15 @@ mm_status coarse_for_lens(mm_ctx* ctx, const std::vector<uint8_t>& deflate) {
         std::vector<double> E((size_t)k * k), Einv;
         for (int i = 0; i < k; ++i)
             for (int j = 0; j < k; ++j) E[(size_t)i * k + j] = 0.5 * (g[(size_t)j * k + i] + g[(size_t)i * k + j]);
-        std::vector<double> L(E);
-        if (host_cholesky(L, k)) {
-            host_spd_inverse_from_chol(L, k, Einv);
-        } else {
+        if (deflate[r]) {
+            // pivoted even when a plain Cholesky would pass: a direction at the rounding level must
+            // not decide the preconditioner through the rounding of the float64 atomics
             const int rank = host_pivoted_spd_inverse(E, k, piv_tol, Einv);
-            if (rank < 0) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not semi-definite");
+            if (rank <= 0) return fail(ctx, MM_ERR_SINGULAR, "a per-RHS coarse operator E_i is not semi-definite");
             ctx->coarse_rank_min = std::min(ctx->coarse_rank_min, rank);
+        } else {
+            Einv.assign((size_t)k * k, 0.0);   // M_2l,r = M_BD,r
         }
-        if (!deflate[r]) std::fill(Einv.begin(), Einv.end(), 0.0);   // M_2l,r = M_BD,r
         std::copy(Einv.begin(), Einv.end(), Einv_all.begin() + (size_t)r * k * k);
     }
     CK(ctx->d_Einvr.ensure(Einv_all.size() * 8));

@@ -322,7 +322,8 @@ def workload_config(args, world):
     return {"workload": f"{args.config}: 256x256 patch, 128 det x 2^20 samples, lambda 2048, "
                         f"64 intervals, k={args.k}; one step = one map (b = P^T W d + two-level PCG "
                         f"to {args.tol:g}) on a resident scan whose pointing, M_BD and coarse space "
-                        f"were built once",
+                        f"were built once (the coarse space from an M_BD run on another sky and noise "
+                        f"realisation of the same scan)",
             "precision": args.precision, "l2": "inputs (1.1 GB pointing + timeline) exceed L2",
             "replicas": world}
 
@@ -383,7 +384,10 @@ def main():
     seed = rank
     t_gen = time.time()
     scan = synth.scan_from_config(args.config, seed=seed)
-    tod = synth.make_tod(scan, synth.make_sky(scan.n_pix, seed), synth.make_noise(scan, seed))
+    # the coarse space is harvested from an M_BD run on one realisation of the scan's data (sky and
+    # noise); the timed maps are another realisation, so the basis is not tailored to their solution
+    tod_h = synth.make_tod(scan, synth.make_sky(scan.n_pix, seed), synth.make_noise(scan, seed))
+    tod = synth.make_tod(scan, synth.make_sky(scan.n_pix, seed + 7919), synth.make_noise(scan, seed + 7919))
     t_gen = time.time() - t_gen
     prec = M.MM_FP32_MIXED if args.precision == "mixed" else M.MM_FP64
     tod_np = tod.astype(np.float32 if prec == M.MM_FP32_MIXED else np.float64)
@@ -392,6 +396,7 @@ def main():
     pix_d = torch.from_numpy(scan.pix).to(dev)
     psi_d = torch.from_numpy(scan.psi).to(dev)
     tod_d = torch.from_numpy(tod_np).to(dev)
+    tod_h_d = torch.from_numpy(tod_h.astype(tod_np.dtype)).to(dev)
     x_d = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
     ctx = M.Context(local, stream.cuda_stream, prec)
     if prec == M.MM_FP32_MIXED:
@@ -399,7 +404,7 @@ def main():
 
     info_last = {}
 
-    def setup_scan(pointing=(pix_d, psi_d), tod_in=tod_d):
+    def setup_scan(pointing=(pix_d, psi_d), tod_in=tod_h_d):
         """One-time per scan: pointing, M_BD and the coarse space (from a first M_BD run by default)."""
         ctx.setup_pointing(pointing[0], pointing[1], scan.block_off, scan.block_band, scan.band, scan.n_pix,
                            n_det=scan.n_det)
@@ -561,6 +566,7 @@ def main():
         c64 = M.Context(local, stream.cuda_stream, M.MM_FP64)
         c64.set_option("fp64_products", 2)
         tod64 = torch.from_numpy(tod).to(dev)
+        tod64_h = torch.from_numpy(tod_h).to(dev)
         x64 = torch.empty_like(x_d)
 
         def setup64():
@@ -568,7 +574,7 @@ def main():
                                n_det=scan.n_det)
             c64.build_bd(1e-3)
             c64.set_option("harvest", args.m_max)
-            c64.solve(tod64, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=x64)
+            c64.solve(tod64_h, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=x64)
             c64.set_option("harvest", 0)
             c64.build_coarse_from_solve(k=args.k)
 
@@ -584,8 +590,20 @@ def main():
                            "true_rel_res": i64["true_rel_res"]}
         fp64 = {"context": "MM_FP64, fp64_products = 2 (double-float products, float64 vectors)",
                 "setup_once_s": setup64_ms / 1e3, "two_level": res64["two_level"], "m_bd": res64["m_bd"]}
+        if not args.no_wide and args.k < 64:
+            # every Ritz pair the harvest resolves (here the harvested run is the whole M_BD solve)
+            k64w = c64.build_coarse_from_solve(k=64)
+
+            def one_w():
+                _, inf = c64.solve(tod64, M.MM_PRECOND_2L, tol=args.tol, max_iter=args.max_iter, out=x64)
+                res64["info"] = inf[0]
+            one_w()
+            msw = timed(one_w, 2)
+            iw = res64["info"]
+            fp64["two_level_all_resolved_ritz"] = {"k": k64w, "time_to_tol_s": msw / 1e3, "iters": iw["iters"],
+                                                   "status": iw["status"], "true_rel_res": iw["true_rel_res"]}
         c64.close()
-        del tod64, x64
+        del tod64, tod64_h, x64
 
     # ---- c1 (plain M_BD, FP64): the oracle's full solves measured on the host cores, and the GPU ----
     c1 = None
@@ -692,18 +710,24 @@ def run_templates(args, world, rank, local):
     over = {"n_det": args.n_det} if args.n_det else {}
     scan = synth.scan_from_config(args.config, seed=rank, half_bw=0, f_knee=0.0, hwp=False, **over)
     sub_off, az, n_bins = synth.make_templates(scan)
-    sky = synth.make_sky(scan.n_pix, rank)
-    if args.stokes == 1:
-        sky[:, 0] = 0.0
-    elif args.stokes == 2:
-        sky[:, 1:] = 0.0
-    tod = torch.from_numpy(synth.make_tod(scan, sky, synth.make_noise(scan, rank)).astype(np.float32)).to(dev)
+    def realisation(s_):
+        sky = synth.make_sky(scan.n_pix, s_)
+        if args.stokes == 1:
+            sky[:, 0] = 0.0
+        elif args.stokes == 2:
+            sky[:, 1:] = 0.0
+        return torch.from_numpy(synth.make_tod(scan, sky, synth.make_noise(scan, s_)).astype(np.float32)).to(dev)
+
+    # the basis comes from one realisation of the data, the timed maps are another
+    tod_h = realisation(rank + 7919)
+    tod = realisation(rank)
     az_d = torch.from_numpy(az).to(dev)
     t_gen = time.time() - t_gen
     out = torch.empty((1, scan.n_pix, 3), dtype=torch.float64, device=dev)
     prec = M.MM_FP32_MIXED if args.precision == "mixed" else M.MM_FP64
     if prec == M.MM_FP64:
         tod = tod.double()
+        tod_h = tod_h.double()
     ctx = M.Context(local, stream.cuda_stream, prec)
     ctx.set_option("inner_tol", args.inner_tol)
 
@@ -724,9 +748,9 @@ def run_templates(args, world, rank, local):
             ctx.set_option("fp64_products", args.fp64_products)
         dropped = ctx.build_bd(1e-3)
         if args.coarse == "arnoldi":
-            return dropped, ctx.build_coarse(ctx.rhs(tod)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
+            return dropped, ctx.build_coarse(ctx.rhs(tod_h)[0], m_max=args.m_max, eps_arn=args.eps_arn, k=args.k)
         ctx.set_option("harvest", args.m_max)
-        ctx.solve(tod, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=out)
+        ctx.solve(tod_h, M.MM_PRECOND_BD, tol=args.tol, max_iter=args.max_iter, out=out)
         ctx.set_option("harvest", 0)
         return dropped, ctx.build_coarse_from_solve(k=args.k)
 
@@ -875,6 +899,8 @@ def run_scale(args, world, rank, local):
     t_gen = time.time()
     scan = synth.scan_from_config("c4", seed=rank)
     tod = synth.make_tod(scan, synth.make_sky(scan.n_pix, rank), synth.make_noise(scan, rank))
+    # the coarse space is harvested from another realisation of the data than the timed map
+    tod_h = synth.make_tod(scan, synth.make_sky(scan.n_pix, rank + 7919), synth.make_noise(scan, rank + 7919))
     t_gen = time.time() - t_gen
     pix_d = torch.from_numpy(scan.pix).to(dev)
     psi_d = torch.from_numpy(scan.psi).to(dev)
@@ -911,8 +937,10 @@ def run_scale(args, world, rank, local):
             m_h = 64
             ctx.set_option("inner_tol", 1e-13)
             ctx.set_option("harvest", m_h)
-            t_h, _ = timed(lambda: ctx.solve(tod_d, M.MM_PRECOND_BD, tol=min(args.tol, 1e-12), max_iter=args.max_iter,
+            tod_hd = torch.from_numpy(tod_h.astype(np.float32)).to(dev)
+            t_h, _ = timed(lambda: ctx.solve(tod_hd, M.MM_PRECOND_BD, tol=min(args.tol, 1e-12), max_iter=args.max_iter,
                                              out=out))
+            del tod_hd
             ctx.set_option("harvest", 0)
             ctx.set_option("inner_tol", args.inner_tol)
             t_c, k = timed(lambda: ctx.build_coarse_from_solve(k=64))
@@ -1088,6 +1116,9 @@ def run_mc(args, world, rank, local):
     for i in range(args.n_rhs):
         s_i = 1000 + i + 100000 * seed
         tods[i] = synth.make_tod(scan, synth.make_sky(scan.n_pix, s_i), synth.make_noise(scan, s_i))
+    # the shared basis comes from a realisation that is not one of the timed maps
+    s_b = 1000 + args.n_rhs + 100000 * seed
+    tod_basis = synth.make_tod(scan, synth.make_sky(scan.n_pix, s_b), synth.make_noise(scan, s_b)).astype(np.float32)
     t_gen = time.time() - t_gen
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)      # graphs are captured on a created stream
@@ -1116,7 +1147,7 @@ def run_mc(args, world, rank, local):
         # run converged to eps_Arn = 1e-12, reused for every map
         ctx.setup_scan(scan)
         ctx.build_bd(1e-3)
-        b = ctx.rhs(tod_d[0:1])
+        b = ctx.rhs(torch.from_numpy(tod_basis[None]).to(dev))
         return ctx.build_coarse(b[0], m_max=args.mc_m_max, eps_arn=args.mc_eps_arn, k=args.k)
 
     setup_ms, k_used = timed(setup)

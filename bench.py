@@ -332,7 +332,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     t0 = time.time()
-    products = 52   # two-level PCG products per map measured on the GPU arm, plus b and the final residual
+    products = 70   # two-level PCG products per map measured on the GPU arm (67), plus b and the residuals
     est, desc, cores = cpu_oracle_sample(args.config, 0, products, budget_s=20.0 / max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": est, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,

@@ -79,12 +79,16 @@ class _ScanEntry:
         self.error = None
         self.has_coarse = False
         self.harvesting = False
+        self.bd_iters = None           # products of this scan's harvested M_BD solve
+        self.coarse_checked = False    # the first M_2l solve has been compared with it
+        self.coarse_useless = False    # M_2l saved too little here: requests use M_BD
         self.last_used = time.perf_counter()
 
 
 class _Active:
-    def __init__(self, batch, entry, t_start, cached):
+    def __init__(self, batch, entry, t_start, cached, precond=None):
         self.batch = batch             # [(request, future)] solved as one multi-right-hand-side run
+        self.precond = precond         # the preconditioner the run uses
         self.entry = entry
         self.t_start = t_start
         self.cached = cached
@@ -97,13 +101,16 @@ class MapServer:
     def __init__(self, device: int = 0, precision: int = M.MM_FP32_MIXED, budget_bytes: int | None = None,
                  iters_per_tick: int = 4, max_active: int = 16, m_max: int = 60, k: int = 16,
                  eps_arn: float = 1e-6, setup_workers: int = 2, reserve_bytes: int = 2 << 30,
-                 coarse: str = "arnoldi", max_batch: int = 16):
+                 coarse: str = "arnoldi", max_batch: int = 16, min_coarse_gain: float = 0.1):
         """coarse: "arnoldi" builds each new scan's deflation basis before its
         first solve; "harvest" solves the first request of a scan with M_BD,
         keeping the Lanczos vectors of that run, and builds the basis from
         them afterwards, so later requests on the scan use M_2l.
         max_active bounds the requests in flight (set-ups and solves, counted
-        per map); max_batch the maps folded into one solve."""
+        per map); max_batch the maps folded into one solve.  In harvest mode
+        the first M_2l solve of a scan is compared with the scan's M_BD run:
+        if it saved less than min_coarse_gain of the products, later requests
+        on the scan use M_BD (a coarse space does not pay on every operator)."""
         import torch
         self.torch = torch
         self.device = device
@@ -111,6 +118,8 @@ class MapServer:
         self.iters_per_tick = iters_per_tick
         self.max_active = max_active
         self.max_batch = max(1, int(max_batch))
+        self.min_coarse_gain = float(min_coarse_gain)
+        self.coarse_disabled = 0
         self.m_max, self.k, self.eps_arn = m_max, k, eps_arn
         self.coarse_mode = coarse
         self.reserve = reserve_bytes
@@ -176,7 +185,8 @@ class MapServer:
                 "maps_per_s": self.completed / wall if wall > 0 else 0.0, "cache_hits": self.cache_hits,
                 "evictions": self.evictions, "admitted": self.admitted, "max_concurrent": self.max_concurrent,
                 "resident_scans": len(self._scans), "failed": self.failed, "batched_requests": self.batched,
-                "largest_batch": self.largest_batch, "oom_requeued": self.oom_requeued}
+                "largest_batch": self.largest_batch, "oom_requeued": self.oom_requeued,
+                "coarse_disabled": self.coarse_disabled}
 
     # ---------------- memory accounting ----------------
     def _free_bytes(self) -> int:
@@ -330,7 +340,8 @@ class MapServer:
         e.last_used = time.perf_counter()
         self._scans.move_to_end(req.scan_id)
         precond = req.precond if (req.precond != M.MM_PRECOND_2L or e.has_coarse) else M.MM_PRECOND_BD
-        e.harvesting = (req.precond == M.MM_PRECOND_2L and not e.has_coarse and self.coarse_mode == "harvest")
+        e.harvesting = (req.precond == M.MM_PRECOND_2L and not e.has_coarse and not e.coarse_useless
+                        and self.coarse_mode == "harvest")
         try:
             e.ctx.set_option("harvest", self.m_max if e.harvesting else 0)
             e.ctx.solve_begin(self._stack_tods(batch, e), precond, tol=req.tol, max_iter=req.max_iter)
@@ -354,7 +365,7 @@ class MapServer:
             for _, fut in batch:
                 fut.set_exception(ex)
             return
-        self._active.append(_Active(batch, e, time.perf_counter(), cached))
+        self._active.append(_Active(batch, e, time.perf_counter(), cached, precond))
         self.max_concurrent = max(self.max_concurrent, sum(len(a.batch) for a in self._active))
         self.largest_batch = max(self.largest_batch, len(batch))
         if len(batch) > 1:
@@ -436,6 +447,7 @@ class MapServer:
             if done:
                 now = time.perf_counter()
                 self._oom_wait = False
+                self._judge_coarse(a, info)
                 if a.entry.harvesting:
                     # deflation basis from this M_BD run's Lanczos vectors, off the critical path
                     a.entry.harvesting = False
@@ -452,6 +464,23 @@ class MapServer:
                 still.append(a)
         self._active = still
         return progressed
+
+    def _judge_coarse(self, a, info):
+        """Harvest mode: remember the products of the scan's M_BD run, and compare the first M_2l
+        run with them; a coarse space that saves less than min_coarse_gain is dropped."""
+        e = a.entry
+        its = [float(i.get("iters", 0)) for i in info if i.get("status") == "MM_OK"]
+        if not its or self.coarse_mode != "harvest":
+            return
+        mean = sum(its) / len(its)
+        if a.precond == M.MM_PRECOND_BD and e.bd_iters is None:
+            e.bd_iters = mean
+        elif a.precond == M.MM_PRECOND_2L and not e.coarse_checked and e.bd_iters:
+            e.coarse_checked = True
+            if mean > (1.0 - self.min_coarse_gain) * e.bd_iters:
+                e.has_coarse = False
+                e.coarse_useless = True
+                self.coarse_disabled += 1
 
     def _fail_all(self, ex):
         with self._lock:

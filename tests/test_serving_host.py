@@ -62,6 +62,7 @@ class FakeContext:
     fail_poll = set()
     gate = {}
     oom_begin = set()
+    iters_for = {}                    # (n_pix, precond) -> products reported
     live = 0
     max_live = 0
 
@@ -127,7 +128,8 @@ class FakeContext:
 
     def solve_end(self, out=None, like=None):
         x = np.repeat(self.tod.sum(axis=1)[:, None, None], self.n_pix, axis=1).repeat(3, axis=2)
-        return x, [{"iters": self.polls, "status": "MM_OK", "precond": self.precond, "tol": self.tol}
+        its = FakeContext.iters_for.get((self.n_pix, self.precond), self.polls)
+        return x, [{"iters": its, "status": "MM_OK", "precond": self.precond, "tol": self.tol}
                    for _ in range(self.tod.shape[0])]
 
     def close(self):
@@ -143,6 +145,7 @@ def fake(monkeypatch):
     FakeContext.fail_poll = set()
     FakeContext.gate = {}
     FakeContext.oom_begin = set()
+    FakeContext.iters_for = {}
     FakeContext.live = 0
     FakeContext.max_live = 0
     monkeypatch.setattr(M, "Context", FakeContext)
@@ -312,3 +315,21 @@ def test_a_solve_out_of_memory_waits_for_the_work_in_flight_and_is_retried(fake)
     assert np.all(held.result(timeout=20).map == 64.0)
     srv.stop()
     assert srv.stats()["oom_requeued"] == 1 and srv.stats()["failed"] == 0
+
+
+def test_harvest_mode_drops_a_coarse_space_that_saves_too_few_products(fake):
+    """Scan 92's M_2l run takes 19 products after a 20-product M_BD run: later requests use M_BD.
+    Scan 93's takes 10: it keeps M_2l."""
+    fake.iters_for = {(92, M.MM_PRECOND_BD): 20, (92, M.MM_PRECOND_2L): 19,
+                      (93, M.MM_PRECOND_BD): 20, (93, M.MM_PRECOND_2L): 10}
+    srv = server(coarse="harvest", m_max=40)
+    for n in (92, 93):
+        for v in (1.0, 2.0, 3.0):
+            if v == 2.0:
+                _wait_for(lambda: ("coarse_from_solve", n) in fake.log, "the basis")
+            assert np.all(srv.submit(request(n, v)).result(timeout=20).map == 64.0 * v)
+    srv.stop()
+    begins = {n: [e[2] for e in fake.log if e[0] == "begin" and e[1] == n] for n in (92, 93)}
+    assert begins[92] == [M.MM_PRECOND_BD, M.MM_PRECOND_2L, M.MM_PRECOND_BD]
+    assert begins[93] == [M.MM_PRECOND_BD, M.MM_PRECOND_2L, M.MM_PRECOND_2L]
+    assert srv.stats()["coarse_disabled"] == 1

@@ -333,3 +333,22 @@ def test_harvest_mode_drops_a_coarse_space_that_saves_too_few_products(fake):
     assert begins[92] == [M.MM_PRECOND_BD, M.MM_PRECOND_2L, M.MM_PRECOND_BD]
     assert begins[93] == [M.MM_PRECOND_BD, M.MM_PRECOND_2L, M.MM_PRECOND_2L]
     assert srv.stats()["coarse_disabled"] == 1
+
+
+def test_release_idle_closes_idle_scans_until_memory_is_free(fake):
+    """A host application asks for memory back: idle resident scans are closed, least recently used
+    first, until the device reports enough free; a busy scan is kept."""
+    fake.gate = {101: threading.Event()}
+    srv = server(free=1 << 20)
+    for n in (100, 102):
+        srv.submit(request(n, 1.0)).result(timeout=20)
+    busy = srv.submit(request(101, 1.0))
+    _wait_for(lambda: ("begin", 101) in [e[:2] for e in fake.log], "the busy solve")
+    srv.torch.cuda.free = 0                        # nothing free until scans are closed
+    srv.release_idle(1 << 10)
+    _wait_for(lambda: ("close", 102) in fake.log, "the second idle scan to close")
+    closes = [e[1] for e in fake.log if e[0] == "close"]
+    assert closes == [100, 102] and 101 not in closes   # LRU order; the busy scan stays
+    fake.gate[101].set()
+    busy.result(timeout=20)
+    srv.stop()

@@ -177,6 +177,8 @@ struct mm_ctx {
     // [(blocks per detector + 1)][k][n_pix][4], for uneven-length batches
     DevBuf d_Tpref;
     bool tpref_valid = false;
+    DevBuf d_Z32, d_AZ32;              // float32 copies of Z and AZ for mixed-precision M_2l
+    bool z32_valid = false;
     int coarse_rank_min = 0;           // smallest coarse rank a right-hand side of the last uneven batch kept
     // asynchronous stepping
     RhsState* h_st_pinned = nullptr;
@@ -1089,6 +1091,10 @@ PcgArgs pcg_args(mm_ctx* ctx) {
     a.hist = ctx->s_hist.as<double>();
     a.hist_stride = ctx->max_iter + 1;
     a.grid_x = ctx->grid_x;
+    if (is_f32(ctx) && ctx->z32_valid && !ctx->coarse_per_rhs) {
+        a.Z32 = ctx->d_Z32.as<V4<float>>();
+        a.AZ32 = ctx->d_AZ32.as<V4<float>>();
+    }
     if (ctx->coarse_per_rhs && ctx->precond == MM_PRECOND_2L) {
         a.AZ = ctx->d_AZr.as<V4<double>>();
         a.Einv = ctx->d_Einvr.as<double>();
@@ -1315,6 +1321,7 @@ mm_status orthonormalise(mm_ctx* ctx, DevBuf& X, int kin, int* kout) {
 mm_status finish_coarse(mm_ctx* ctx) {
     NvtxRange nvtx_range("coarse_AZ_E");
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     const int k = ctx->k;
     const int64_t n = (int64_t)ctx->n_pix * 4;
     CK(ctx->d_AZ.ensure((size_t)k * n * 8));
@@ -1334,6 +1341,7 @@ mm_status finish_coarse(mm_ctx* ctx) {
     if (!host_cholesky(L, k)) {
         ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
         return fail(ctx, MM_ERR_SINGULAR, "coarse operator E = Z^T A Z is not positive definite");
     }
     host_spd_inverse_from_chol(L, k, Einv);
@@ -1679,6 +1687,7 @@ mm_status mm_setup_pointing(mm_ctx* ctx, int64_t n_samples, int32_t n_det, int32
     ctx->have_pointing = ctx->have_bd = false;
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     ctx->have_lastb = false;
     ctx->plans.clear();
     ctx->n_samples = n_samples;
@@ -1740,6 +1749,7 @@ mm_status mm_set_templates(mm_ctx* ctx, int32_t poly_order, int32_t n_subscans, 
     ctx->have_bd = false;   // M_BD and any coarse space belong to the previous operator
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     if (stokes < 0 || stokes > 2) return fail(ctx, MM_ERR_ARG, "stokes must be 0 (I, Q, U), 1 (Q, U) or 2 (I)");
     if (poly_order < 0 && !az_bin && stokes == 0) {
         ctx->tmpl_on = false;
@@ -1830,6 +1840,7 @@ mm_status mm_build_bd(mm_ctx* ctx, double rcond_min, int32_t* n_dropped_out) {
     ctx->have_bd = true;
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     return MM_OK;
 }
 
@@ -1994,6 +2005,7 @@ mm_status mm_build_coarse(mm_ctx* ctx, const double* b_or_null, int32_t m_max, d
     const int64_t n = (int64_t)n_pix * 4;
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     TRY(ensure_work(ctx, 1, MM_K_MAX));
     CK(ctx->w_partial.ensure((size_t)ctx->grid_x * (m_max + 2) * 8 + 64));
     CK(ctx->d_W.ensure((size_t)(m_max + 1) * n * 8));
@@ -2104,6 +2116,7 @@ mm_status mm_build_coarse_from_solve(mm_ctx* ctx, int32_t k, double eps_lambda, 
     CK(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     TRY(ensure_work(ctx, 1, MM_K_MAX));
     CK(ctx->d_Z.ensure((size_t)ksel * n * 8));
     launch_combo(ctx->d_harv.as<double>(), n, m, dC.as<double>(), ksel, ctx->d_Z.as<double>(), n, n, ctx->stream);
@@ -2129,6 +2142,7 @@ mm_status mm_set_coarse(mm_ctx* ctx, int32_t k, const double* Z, int mem) {
     const int64_t n = (int64_t)ctx->n_pix * 4;
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     DevBuf in3;
     const double* src = Z;
     if (mem == MM_HOST) {
@@ -2237,6 +2251,7 @@ mm_status mm_import_coarse(mm_ctx* ctx, const void* buf, int64_t bytes) {
     const double* z3 = reinterpret_cast<const double*>(static_cast<const unsigned char*>(buf) + sizeof(hd));
     ctx->k = 0;
     ctx->tpref_valid = false;
+    ctx->z32_valid = false;
     DevBuf t;
     CK(t.ensure(nv * 24));
     CK(ctx->d_Z.ensure((size_t)k * n4 * 8));
@@ -2341,6 +2356,16 @@ mm_status mm_solve_begin(mm_ctx* ctx, const void* tod, int32_t nrhs, const int64
         if (n_defl == 0) ctx->precond = MM_PRECOND_BD;
     }
     if (ctx->use_lens && ctx->precond == MM_PRECOND_2L) TRY(coarse_for_lens(ctx, deflate));
+    if (ctx->precond == MM_PRECOND_2L && is_f32(ctx) && !ctx->z32_valid && ctx->k > 0) {
+        // the coarse sums of M_2l in float32 read float32 copies, made once per coarse space
+        const int64_t nz = (int64_t)ctx->k * ctx->n_pix;
+        CK(ctx->d_Z32.ensure(nz * sizeof(V4<float>)));
+        CK(ctx->d_AZ32.ensure(nz * sizeof(V4<float>)));
+        launch_to_f32(ctx->d_Z.as<V4<double>>(), ctx->d_Z32.as<V4<float>>(), nz, ctx->stream);
+        launch_to_f32(ctx->d_AZ.as<V4<double>>(), ctx->d_AZ32.as<V4<float>>(), nz, ctx->stream);
+        CKL();
+        ctx->z32_valid = true;
+    }
     if (ctx->precond == MM_PRECOND_2L) {
         const PcgArgs a = pcg_args(ctx);
         if (tc_wanted(ctx, a)) TRY(ensure_tc_scratch(ctx, a));

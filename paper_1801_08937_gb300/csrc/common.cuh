@@ -198,6 +198,9 @@ struct PcgArgs {
     // two-level
     int k;
     const V4<double>* Z; const V4<double>* AZ; const double* Einv;
+    // float32 copies of Z and AZ (mixed precision, one coarse space for all right-hand sides):
+    // the coarse sums of M_2l in float32 arithmetic; null: float64
+    const V4<float>* Z32; const V4<float>* AZ32;
     double* u;               // [nrhs][k]
     double* partial;         // reduction scratch
     unsigned* counter;       // [nrhs]

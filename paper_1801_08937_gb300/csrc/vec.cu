@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "fconv.cuh"
 #include "df64.cuh"
 
 namespace mm {
@@ -571,9 +572,21 @@ __global__ void k_m2l_ztr(const PcgArgs a, const V4<double>* v) {
     const int chunk = (a.n_pix + gridDim.x - 1) / gridDim.x;
     const int i0 = blockIdx.x * chunk, i1 = min(a.n_pix, i0 + chunk);
     for (int c = warp; c < k; c += nw) {
-        const V4<double>* zc = a.Z + (int64_t)c * a.n_pix;
         double s = 0.0;
-        for (int i = i0 + lane; i < i1; i += 32) s += dot3(zc[i], v[off + i]);
+        if (a.Z32) {
+            // float32 products summed per lane in float32 (a few dozen terms), the lanes in float64
+            const V4<float>* zc = a.Z32 + (int64_t)c * a.n_pix;
+            float sf = 0.0f;
+            for (int i = i0 + lane; i < i1; i += 32) {
+                const V4<float> z = zc[i];
+                const V4<double> x = v[off + i];
+                sf = fmaf(z.x, d2f_trunc(x.x), fmaf(z.y, d2f_trunc(x.y), fmaf(z.z, d2f_trunc(x.z), sf)));
+            }
+            s = f2d_exact(sf);
+        } else {
+            const V4<double>* zc = a.Z + (int64_t)c * a.n_pix;
+            for (int i = i0 + lane; i < i1; i += 32) s += dot3(zc[i], v[off + i]);
+        }
         s = warp_sum(s);
         if (lane == 0) a.partial[((int64_t)blockIdx.x * a.nrhs + rhs) * k + c] = s;
     }
@@ -601,13 +614,36 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
     if (a.st && !a.st[rhs].active) return;
     const int64_t off = (int64_t)rhs * a.n_pix;
     __shared__ double u[MM_K_MAX];
-    for (int c = threadIdx.x; c < a.k; c += VT) u[c] = a.u[(int64_t)rhs * a.k + c];
+    __shared__ float uf[MM_K_MAX];
+    for (int c = threadIdx.x; c < a.k; c += VT) {
+        u[c] = a.u[(int64_t)rhs * a.k + c];
+        uf[c] = d2f_trunc(u[c]);
+    }
     __syncthreads();
     double acc[1] = {0.0};
     const V4<double>* AZ = a.AZ + (int64_t)rhs * a.az_stride;
     PIX_LOOP(i) {
         V4<double> y = v[off + i];
         V4<double> zu{0, 0, 0, 0};
+        if (a.Z32) {
+            // the coarse sums AZ u and Z u in float32 (mixed precision), the rest in float64
+            float ax = 0.0f, ay = 0.0f, az = 0.0f, zx = 0.0f, zy = 0.0f, zz = 0.0f;
+            for (int c = 0; c < a.k; ++c) {
+                const V4<float> azc = a.AZ32[(int64_t)c * a.n_pix + i];
+                const V4<float> zc = a.Z32[(int64_t)c * a.n_pix + i];
+                const float uc = uf[c];
+                ax = fmaf(azc.x, uc, ax);
+                ay = fmaf(azc.y, uc, ay);
+                az = fmaf(azc.z, uc, az);
+                zx = fmaf(zc.x, uc, zx);
+                zy = fmaf(zc.y, uc, zy);
+                zz = fmaf(zc.z, uc, zz);
+            }
+            y.x -= f2d_exact(ax);
+            y.y -= f2d_exact(ay);
+            y.z -= f2d_exact(az);
+            zu = V4<double>{f2d_exact(zx), f2d_exact(zy), f2d_exact(zz), 0.0};
+        } else
         for (int c = 0; c < a.k; ++c) {
             const V4<double> azc = AZ[(int64_t)c * a.n_pix + i];
             const V4<double> zc = a.Z[(int64_t)c * a.n_pix + i];

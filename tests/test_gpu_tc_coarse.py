@@ -2,10 +2,10 @@
 float64 CUDA-core kernels, at the shapes of the batched Monte Carlo workload (32x32 patch, k = 32,
 64 right-hand sides) and of the large map (512x512 patch, k = 64, 64 right-hand sides).
 
-The tensor-core path rounds its operands to TF32 pairs (high part + remainder, about 21 bits) and
-accumulates in float32, so M_2l x agrees with the float64 result to about 1e-7 overall and 2e-6 in
-the worst element (measured); the tolerance below is 2e-5.  A two-level PCG solve with it converges
-to the same maps in the same number of products.
+The tensor-core path splits its operands into TF32 pairs (high part + remainder, about 22 bits),
+accumulates in float32 and forms M_BD (R - AZ U) + Z U in float32, so M_2l x agrees with the float64
+result to a few 1e-7 (an element near a cancellation to a few 1e-6); the tolerance below is 2e-5.
+A two-level PCG solve with it converges to the same maps in the same number of products.
 """
 import numpy as np
 import pytest

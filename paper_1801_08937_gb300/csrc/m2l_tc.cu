@@ -21,11 +21,12 @@
 //      float32 and everything beyond in float64.
 //
 // Operands are TF32 (kind::tf32, float32 accumulation).  Each float64 value x
-// is rounded to float32 and split into a TF32 high part and the TF32 rounding
-// of the remainder; x y is formed as hi hi + hi lo + lo hi (three MMAs into
-// the same accumulator), about 21 bits, so the coarse corrections carry a
-// relative error near 1e-6 against the float64 CUDA-core kernels (measured in
-// the tests).  One elected thread issues the MMAs; operands are staged in
+// is truncated to float32 (integer bit operations: the hardware conversions
+// run on the slow float64 pipe of the GB300) and split by masking into a TF32
+// high part and the TF32-truncated remainder; x y is formed as hi hi + hi lo +
+// lo hi (three MMAs into the same accumulator), about 21 bits, so M_2l x
+// agrees with the float64 CUDA-core kernels to a few 1e-7 (checked in the
+// tests).  One elected thread issues the MMAs; operands are staged in
 // shared memory by all threads in the canonical K-major layout without
 // swizzle (8-row x 16-byte core matrices: LBO 128 B between core matrices
 // along K, SBO between 8-row groups); tcgen05.commit signals an mbarrier.
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(TC_AT, 1) k_m2l_tc_zu_apply(const PcgArgs a, c
     const uint32_t at = base + 2 * b_bytes;
     const uint32_t idesc = tc_idesc(128, nr);
     // staging: thread tid loads row (tid % 128) of the tile; the kp / 8 blocks of eight coarse
-    // vectors are split between the two halves of the CTA (tid / 128)
+    // vectors are split between the TC_AG groups of 128 threads (tid / 128)
     const int row = tid & 127, n_oct = kp / 8, per_grp = (n_oct + TC_AG - 1) / TC_AG;
     const int oct_begin = (tid >> 7) * per_grp, oct_end = min(n_oct, oct_begin + per_grp);
     // epilogue: this thread's TMEM lane is tile row q * 32 + lane; its columns are the 8-column chunks

@@ -577,6 +577,7 @@ __global__ void k_m2l_ztr(const PcgArgs a, const V4<double>* v) {
             // float32 products summed per lane in float32 (a few dozen terms), the lanes in float64
             const V4<float>* zc = a.Z32 + (int64_t)c * a.n_pix;
             float sf = 0.0f;
+#pragma unroll 4
             for (int i = i0 + lane; i < i1; i += 32) {
                 const V4<float> z = zc[i];
                 const V4<double> x = v[off + i];
@@ -628,6 +629,7 @@ __global__ void k_m2l_apply(const PcgArgs a, const V4<double>* v, V4<double>* ou
         if (a.Z32) {
             // the coarse sums AZ u and Z u in float32 (mixed precision), the rest in float64
             float ax = 0.0f, ay = 0.0f, az = 0.0f, zx = 0.0f, zy = 0.0f, zz = 0.0f;
+#pragma unroll 8
             for (int c = 0; c < a.k; ++c) {
                 const V4<float> azc = a.AZ32[(int64_t)c * a.n_pix + i];
                 const V4<float> zc = a.Z32[(int64_t)c * a.n_pix + i];
